@@ -1,0 +1,281 @@
+"""Benchmark: noisy density-matrix TFIM evolution (n = 13, 20 Trotter steps, FP64).
+
+One step = one pass of the whole hot path over one synthetic input:
+  reset rho to |0..0><0..0|  ->  run the lowered noisy circuit (980 gates, each
+  followed by depolarising + thermal-relaxation noise; 60 shared-memory sweeps)
+  ->  <Z_i> and <H>  ->  outcome distribution with 2% readout error.
+Metric: gate-updates/s = (gates x 4^n density-matrix elements updated) / s.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own replica (independent problems, weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 13
+TROTTER_STEPS = 20
+METRIC = "gate-updates/s"
+UNIT = "gate-updates/s"
+WORKLOAD = f"dm_noisy_tfim_n{N}_{TROTTER_STEPS}steps"
+KERNEL_SRC = os.path.join(ROOT, "paper_2401_06861_gb300", "csrc", "sweep_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_sweep_f64_n13_traffic.json")
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flop x max clock
+
+
+def workload():
+    from paper_2401_06861_gb300 import inputs
+    gates, noise = inputs.dm_noisy_tfim(N, TROTTER_STEPS)
+    return gates, noise, inputs.z_terms(N), inputs.tfim_terms(N)
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("NWQ_BENCH_BACKEND") != "gloo" else "gloo")
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (200 ms period)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.p = None
+        self.device = device
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_per_launch():
+    """DRAM bytes per sweep launch from the committed ncu summary, or None if the
+    kernel source changed since the counters were taken."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+        h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        return rec["traffic_bytes_per_launch"] if rec.get("kernel_sha") == h else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_sample(gates, noise, ngates):
+    """Time the CPU oracle on the first ``ngates`` noisy gates of the workload."""
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    oracle.dm_run(N, gates[:ngates], noise)
+    dt = time.perf_counter() - t0
+    return ngates * 4.0 ** N / dt, dt
+
+
+def cpu_cores():
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except AttributeError:
+        aff = os.cpu_count()
+    return int(os.environ.get("OMP_NUM_THREADS", aff))
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    gates, noise, _, _ = workload()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, _ = oracle_sample(gates, noise, 1)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    sample = f"first noisy gate (CX(0,1) + 2q depolarising + relaxation) of the n={N} circuit, per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 4.0 ** N / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build
+    from paper_2401_06861_gb300.sim import Plan, State, launch_count
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    gates, noise, zt, ht = workload()
+    plan = Plan(L.DM, N, gates, L.F64, noise)
+    info = plan.info()
+    st = State(L.DM, N, L.F64, stream=stream.cuda_stream)
+    ro = noise["readout_e"]
+    gate_updates = len(gates) * 4.0 ** N
+
+    def step(ev=None):
+        st.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        st.run(plan)
+        if ev is not None:
+            ev[1].record(stream)
+        z = st.expect(zt)
+        e = st.expect(ht, sum=True)
+        p = st.probs(ro)
+        return z, e, p
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    barrier()
+    clocks = Clocks(dev)
+    n0 = launch_count()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweep_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start.record(stream)
+    for k in range(args.steps):
+        z, e, p = step(sweep_ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = launch_count() - n0
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = gate_updates * ws / (ms / 1e3)
+
+    # end to end through the public ABI with host buffers: host circuit in,
+    # plan built and uploaded, run, results copied back, every step
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.reset()
+        st.apply(gates, noise)
+        z2 = st.expect(zt)
+        e2 = st.expect(ht, sum=True)
+        p2 = st.probs(ro)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    assert abs(e2 - e) <= 1e-12 and np.max(np.abs(p2 - p)) <= 1e-15, "e2e result differs from device-timed run"
+    h2d = info["table_bytes"] + 24 * (len(zt) + len(ht))
+    d2h = 8 * (len(zt) + 1 + (1 << N))
+
+    # roofline of the dominant kernel (the FP64 DM sweep), from the live events
+    nlaunch = info["sweeps"]
+    flops_per_launch = 2.0 * info["fma_per_elem"] * 4.0 ** N / nlaunch
+    launch_s = sweep_ms / 1e3 / nlaunch
+    achieved = flops_per_launch / launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(),
+                "kernel": "sweep_kernel<double,real> (FP64 Pauli-basis DM sweep)",
+                "launches_per_step": nlaunch, "ms_per_launch": launch_s * 1e3,
+                "algorithmic_bytes_per_launch": info["bytes"] / nlaunch,
+                "hbm_gbs": info["bytes"] / nlaunch / launch_s / 1e9}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, dt = oracle_sample(gates, noise, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"first noisy gate (CX(0,1) + depolarising + relaxation) of the n={N} circuit "
+                         f"from |0><0|, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": N, "gates": len(gates), "trotter_steps": TROTTER_STEPS,
+                           "state_bytes": 8 << (2 * N), "l2": "inputs larger than L2 (512 MiB state)",
+                           "plan": {"sweeps": info["sweeps"], "operators": info["ops"]},
+                           "parallelism": f"replicas x{ws}"},
+                "e2e": {"value": gate_updates * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "results": {"energy": e, "z0": float(z[0]), "prob_sum": float(p.sum())}}
+        print(json.dumps(line), flush=True)
+    st.close()
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        rc = run_reference(args, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * nwqgb.h -- C ABI of the GB300 state-vector / density-matrix simulator.
+ *
+ * The library simulates quantum circuits the way the NWQ-Sim paper frames
+ * the problem (Sec. II: a circuit run on a state-vector back end, SV-Sim, or
+ * on a noise-aware density-matrix back end, DM-Sim; Sec. III: a device noise
+ * model made of depolarising, thermal-relaxation and measurement noise).
+ *
+ * Conventions used by every call:
+ *   - qubit q is bit q of a basis index (little-endian);
+ *   - a two-qubit gate acts in the local basis j = b(q[0]) + 2 b(q[1]); for
+ *     CX, q[0] is the control and q[1] the target;
+ *   - Pauli string (x_mask, z_mask) means i^{|x & z|} X^x Z^z (Hermitian);
+ *   - all device work is issued on the state's CUDA stream; calls that return
+ *     host results synchronise that stream;
+ *   - every call returns NWQ_OK or a negative status and never throws;
+ *     nwq_last_error() gives a message for the calling thread.
+ * One state must be used by one host thread at a time; different states may
+ * be used concurrently on different streams.
+ */
+#ifndef NWQGB_H
+#define NWQGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nwq_state nwq_state; /* opaque: one SV or DM state on one device */
+typedef struct nwq_plan nwq_plan;   /* opaque: a circuit lowered to device sweeps */
+
+enum nwq_status {
+  NWQ_OK = 0,
+  NWQ_EINVAL = -1,       /* bad argument (qubit out of range, size mismatch, NULL) */
+  NWQ_ENOMEM = -2,       /* device or host allocation failed */
+  NWQ_ECUDA = -3,        /* a CUDA call failed (message has the CUDA error string) */
+  NWQ_EBUDGET = -4,      /* a memory budget would be exceeded */
+  NWQ_ETIMEOUT = -5,     /* a bounded device wait ran out */
+  NWQ_EUNSUPPORTED = -6  /* valid request this build does not support */
+};
+
+/* Precision of the stored state.  SV: complex64 / complex128 amplitudes.
+ * DM: float / double Pauli-basis coefficients (see nwq_dm_create). */
+enum nwq_dtype { NWQ_F32 = 1, NWQ_F64 = 2, NWQ_C64 = 1, NWQ_C128 = 2 };
+
+enum nwq_kind { NWQ_SV = 1, NWQ_DM = 2 };
+
+/* Gate kinds.  Matrices (radians):
+ *   RX/RY/RZ(t) = exp(-i t P / 2);  P(l) = diag(1, e^{il});  S = P(pi/2);
+ *   T = P(pi/4);  SX = sqrt(X) = ((1+i) I + (1-i) X) / 2;
+ *   U3(t, p, l) = [[cos t/2, -e^{il} sin t/2], [e^{ip} sin t/2, e^{i(p+l)} cos t/2]];
+ *   RZZ(t) = exp(-i t Z(x)Z / 2);  CX flips q[1] when q[0] = 1;
+ *   MAT1 / MAT2: caller matrix (2x2 / 4x4, row-major, re/im interleaved). */
+enum nwq_gate_kind {
+  NWQ_GATE_ID = 1, NWQ_GATE_X, NWQ_GATE_Y, NWQ_GATE_Z, NWQ_GATE_H, NWQ_GATE_S, NWQ_GATE_SDG,
+  NWQ_GATE_T, NWQ_GATE_TDG, NWQ_GATE_SX, NWQ_GATE_RX, NWQ_GATE_RY, NWQ_GATE_RZ, NWQ_GATE_P,
+  NWQ_GATE_U3, NWQ_GATE_MAT1,
+  NWQ_GATE_CX = 64, NWQ_GATE_CZ, NWQ_GATE_SWAP, NWQ_GATE_RZZ, NWQ_GATE_MAT2
+};
+
+typedef struct {
+  uint16_t kind;      /* nwq_gate_kind */
+  uint16_t reserved;  /* must be 0 */
+  int32_t q[2];       /* qubits; q[1] ignored for one-qubit gates */
+  double theta[3];    /* angles; U3 uses all three, rotations theta[0] */
+  int32_t param_idx;  /* batched calls: theta[0] := params[set * nparams + param_idx]; -1 = fixed */
+  int32_t reserved2;
+  const double* mat;  /* MAT1/MAT2 only; host memory, read during the call */
+} nwq_gate;
+
+typedef struct {
+  uint64_t x_mask;
+  uint64_t z_mask;
+  double coeff;
+} nwq_pauli_term;
+
+/* Device noise model (paper Sec. III).  After every gate the library applies
+ * depolarising noise on the gate's qubits (p1 for one-qubit gates, p2 for
+ * two-qubit gates) in the form E(rho) = (1-p) rho + p Tr_S(rho) (x) I/2^|S|,
+ * then thermal relaxation on each of the gate's qubits for the gate duration
+ * (t1q_ns / t2q_ns) with gamma = 1 - exp(-t/T1) and coherence factor
+ * eta = exp(-t/T2).  readout_e records the device's symmetric readout error
+ * for callers; nwq_probs takes the readout error as an argument. */
+enum nwq_noise_flags {
+  NWQ_NOISE_RZ_VIRTUAL = 1u,      /* RZ is error-free and instantaneous */
+  NWQ_NOISE_DEPOL_PAULI_FORM = 2u /* p is the total Pauli-error probability (p/3 each) */
+};
+typedef struct {
+  int32_t n;            /* entries in T1_us / T2_us (>= number of qubits) */
+  uint32_t flags;       /* nwq_noise_flags */
+  const double* T1_us;  /* per-qubit T1, microseconds (host) */
+  const double* T2_us;  /* per-qubit T2, microseconds (host) */
+  double t1q_ns;        /* one-qubit gate duration */
+  double t2q_ns;        /* two-qubit gate duration */
+  double p1;            /* one-qubit depolarising parameter */
+  double p2;            /* two-qubit depolarising parameter */
+  double readout_e;     /* symmetric readout error */
+} nwq_noise_model;
+
+/* Plan / apply flags. */
+enum nwq_plan_flags {
+  NWQ_PLAN_FUSED = 0u,      /* default: gates fused into shared-memory sweeps */
+  NWQ_PLAN_PLAIN = 1u,      /* one gate (plus its noise) per pass over the state */
+  NWQ_PLAN_NO_MERGE = 2u,   /* fused sweeps, but no algebraic merging of operators */
+  NWQ_PLAN_NO_RESCALE = 4u  /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
+};
+
+/* Expectation flags.  NWQ_EXPECT_NORMALIZE divides every value by the FP64
+ * norm <psi|psi> (SV) or trace (DM) measured in the same call: the physical
+ * expectation of an unnormalised state.  The raw norm is the value of the
+ * identity string (x_mask = z_mask = 0) without this flag. */
+enum nwq_expect_flags { NWQ_EXPECT_TERMS = 0u, NWQ_EXPECT_SUM = 1u, NWQ_EXPECT_NORMALIZE = 2u };
+
+/* ---------------------------------------------------------------- states */
+
+/* Bytes a state occupies on the device.  SV: 2^n amplitudes of 8 (F32) or
+ * 16 (F64) bytes.  DM: 4^n real Pauli coefficients of 4 or 8 bytes. */
+size_t nwq_state_bytes(int kind, int n, int dtype);
+
+/* Create an n-qubit state vector |0..0> (paper Sec. II, SV-Sim).
+ * dev_buf: NULL = the library allocates (and nwq_destroy frees) the state;
+ *   otherwise a caller-owned device buffer of >= nwq_state_bytes() bytes,
+ *   16-byte aligned, which the library never frees.
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ * n in [1, 34].  Errors: NWQ_EINVAL, NWQ_ENOMEM, NWQ_ECUDA. */
+int nwq_sv_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, nwq_state** out);
+
+/* Create an n-qubit density matrix rho = |0..0><0..0| (paper Sec. II, DM-Sim).
+ * The device copy holds the Pauli-basis coefficients r[x + 2^n z] = Tr(rho P(x,z)),
+ * which are real for a Hermitian rho; nwq_state_copy returns the standard
+ * column-stacked vec(rho).  n in [1, 16].  Arguments as nwq_sv_create. */
+int nwq_dm_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, nwq_state** out);
+
+/* Reset to |0..0> (SV) or |0..0><0..0| (DM).  Asynchronous. */
+int nwq_state_reset(nwq_state* st);
+
+/* Load a state.  SV: 2^n complex amplitudes in the state's precision.
+ * DM: the column-stacked vec(rho), 4^n complex entries in the state's
+ * precision (element r + 2^n c = <r|rho|c>); rho must be Hermitian.
+ * src_on_device selects the memory space of src.  Synchronises the stream. */
+int nwq_state_load(nwq_state* st, const void* src, size_t bytes, int src_on_device);
+
+/* Copy the state out.  SV: the amplitudes.  DM: vec(rho) as 4^n complex entries
+ * in the state's precision.  dst_on_device selects the memory space of dst.
+ * Synchronises the stream. */
+int nwq_state_copy(nwq_state* st, void* dst, size_t bytes, int dst_on_device);
+
+/* DM only: copy the raw Pauli-basis coefficients (4^n reals). */
+int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst_on_device);
+
+/* Free library-owned memory and the handle. */
+int nwq_destroy(nwq_state* st);
+
+/* ---------------------------------------------------------------- circuits */
+
+/* Apply a circuit to a state vector: psi <- U_ng ... U_1 psi (paper Sec. II).
+ * Gates are validated, lowered to sweeps (nwq_plan_create) and launched on
+ * the state's stream; the call returns without waiting for the device.
+ * gates: host array, read during the call only. */
+int nwq_sv_apply_circuit(nwq_state* st, const nwq_gate* gates, size_t ng, uint32_t flags);
+
+/* Apply a circuit with the device noise model to a density matrix
+ * (paper Sec. II DM-Sim, Sec. III noise model): per gate
+ * rho <- R_q ... D_S(U rho U^dag), with D and R as in nwq_noise_model.
+ * nm NULL = noiseless.  Asynchronous like nwq_sv_apply_circuit. */
+int nwq_dm_apply_circuit_noisy(nwq_state* st, const nwq_gate* gates, size_t ng,
+                               const nwq_noise_model* nm, uint32_t flags);
+
+/* Lower a circuit once for repeated runs (same n, kind and dtype).  Lowering
+ * (paper Sec. III, "we optimize the quantum circuit"): each gate, with its
+ * noise channels for DM, becomes one operator; adjacent operators sharing
+ * qubits are multiplied together when that does not add arithmetic; DM
+ * operators defer per-qubit diagonal scale factors to the next operator on
+ * the same qubit (flushed on its last one); operators are grouped into sweeps
+ * that each read and write the state once.  The plan's operator tables are
+ * uploaded to the device on its first run (stream is unused; kept for ABI
+ * stability).  Host-only: needs no device. */
+int nwq_plan_create(int kind, int n, int dtype, const nwq_gate* gates, size_t ng,
+                    const nwq_noise_model* nm, uint32_t flags, void* stream, nwq_plan** out);
+
+/* Run a plan on a state of matching kind, n and dtype.  Asynchronous. */
+int nwq_plan_run(nwq_state* st, const nwq_plan* plan);
+
+/* Plan statistics: number of sweeps, number of device operators, the
+ * algorithmic bytes one run moves (one read and one write of the state per
+ * sweep), the floating-point instructions (multiply, add or fused
+ * multiply-add, each counted once) one run issues per state element, and the
+ * bytes of operator tables uploaded to the device.  Any pointer may be NULL. */
+int nwq_plan_info(const nwq_plan* plan, int* sweeps, int* ops, double* bytes, double* fma_per_elem,
+                  size_t* table_bytes);
+
+/* Debug / test hook: copy the plan's sweep structure to host arrays.
+ * sweep_nops[s]: operators in sweep s; op_gate[k]: index of the first input
+ * gate folded into operator k (operators listed sweep by sweep).  Sizes from
+ * nwq_plan_info.  Host-only; needs no device. */
+int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op_ngates);
+
+int nwq_plan_destroy(nwq_plan* plan);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Expectation values of Pauli strings (SV: <psi|P|psi>; DM: Tr(rho P)),
+ * accumulated in FP64.  flags NWQ_EXPECT_TERMS: out_host[t] = <P_t> (the
+ * coefficients are ignored); NWQ_EXPECT_SUM: out_host[0] = sum_t coeff_t <P_t>.
+ * Synchronises the stream. */
+int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, size_t nt, double* out_host,
+                         uint32_t flags);
+
+/* Outcome distribution of a computational-basis measurement with symmetric
+ * readout error e on every bit (paper Sec. III, measurement noise):
+ * out_host[b] = sum_b' prod_i C(b_i | b'_i) p(b'), C = [[1-e, e], [e, 1-e]].
+ * 2^n doubles.  n <= 30.  Synchronises the stream. */
+int nwq_probs(nwq_state* st, double readout_e, double* out_host);
+
+/* ---------------------------------------------------------------- batched VQE */
+
+/* Evaluate one parametrised circuit on nsets parameter sets in one launch
+ * (the VQE inner loop of paper Sec. III).  Each set starts from |0..0>, runs
+ * the gates (gate k takes theta[0] = params[s * nparams + param_idx] when
+ * param_idx >= 0), and produces ne energies
+ *   out[s * ne + e] = sum_t coeffs[e * nt + t] <psi_s| P_t |psi_s>.
+ * params: device, nsets * nparams doubles.  out: device, nsets * ne doubles.
+ * terms: host (coeff field ignored).  coeffs: host, ne * nt doubles.
+ * n <= 13 (F64) or 14 (F32).  Asynchronous on stream. */
+int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t ng, const double* params,
+                     int nsets, int nparams, const nwq_pauli_term* terms, size_t nt,
+                     const double* coeffs, int ne, double* out, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Message of the last failed call on the calling thread. */
+const char* nwq_last_error(void);
+
+/* Wait for the state's stream. */
+int nwq_device_sync(nwq_state* st);
+
+/* Number of device kernels this library has launched in this process
+ * (monotonic; for accounting in benchmarks). */
+uint64_t nwq_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NWQGB_H */

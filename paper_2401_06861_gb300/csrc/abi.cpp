@@ -1,0 +1,545 @@
+// C ABI of the simulator: state handles, plans, measurement.  Every device
+// step runs in the kernels of sweep_kernels.cu / batch_kernels.cu; this file
+// validates arguments, lowers circuits (planner.cpp), uploads operator tables
+// and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nwqgb.h"
+#include "kernels.hpp"
+#include "planner.hpp"
+
+using namespace nwq;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+static int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return NWQ_ECUDA;
+}
+#define CK(call, what)                          \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+struct nwq_plan {
+  Plan p;
+};
+
+struct nwq_state {
+  int kind = 0, n = 0, dtype = 0, B = 0;
+  void* buf = nullptr;
+  size_t bytes = 0;
+  bool owned = false;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 1;
+  std::unique_ptr<nwq_plan> p2r, r2p;               // DM conversions
+  std::map<double, std::unique_ptr<nwq_plan>> probs; // readout / transform plans keyed by e
+};
+
+// ------------------------------------------------------------------ helpers
+static bool f64_of(int dtype) { return dtype == NWQ_F64; }
+
+extern "C" size_t nwq_state_bytes(int kind, int n, int dtype) {
+  if ((kind != NWQ_SV && kind != NWQ_DM) || (dtype != NWQ_F32 && dtype != NWQ_F64) || n < 1) return 0;
+  size_t real = dtype == NWQ_F64 ? 8 : 4;
+  if (kind == NWQ_SV) return n > 34 ? 0 : (2 * real) << n;
+  return n > 16 ? 0 : real << (2 * n);
+}
+
+static void plan_options(int kind, int dtype, uint32_t flags, PlanOptions& o) {
+  bool cplx = kind == NWQ_SV;
+  size_t esz = (cplx ? 2 : 1) * (dtype == NWQ_F64 ? 8 : 4);
+  // 64 KiB tiles (three resident CTAs per SM), >= 128 contiguous bytes
+  o.tile_bits = esz == 16 ? 12 : esz == 8 ? 13 : 14;
+  o.min_low = esz == 16 ? 3 : esz == 8 ? 4 : 5;
+  if (const char* tb = std::getenv("NWQ_TILE_BITS")) {
+    int v = std::atoi(tb);
+    if (v >= 4 && v <= kMaxTileBits && (esz << v) <= (size_t)kMaxDynSmem) o.tile_bits = v;
+  }
+  o.plain = (flags & NWQ_PLAN_PLAIN) != 0;
+  o.merge = !(flags & (NWQ_PLAN_PLAIN | NWQ_PLAN_NO_MERGE));
+}
+
+static void init_plan_meta(Plan& p, int kind, int n, int dtype, int B) {
+  p.kind = kind;
+  p.n = n;
+  p.dtype = dtype;
+  p.B = B;
+  p.is_complex = kind == NWQ_SV;
+  size_t real = dtype == NWQ_F64 ? 8 : 4;
+  p.elem_bytes = (p.is_complex ? 2 : 1) * real;
+  p.ent_bytes = p.is_complex ? (dtype == NWQ_F64 ? sizeof(EntC<double>) : sizeof(EntC<float>))
+                             : (dtype == NWQ_F64 ? sizeof(EntR<double>) : sizeof(EntR<float>));
+}
+
+// Upload a plan's tables once (stream-ordered); later runs reuse them.
+static int plan_upload(Plan& p, cudaStream_t s) {
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (p.dev) return NWQ_OK;
+  size_t ob = p.ops.size() * sizeof(DevOp);
+  size_t total = ob + p.ents.size() + 16;
+  void* d = nullptr;
+  CK(cudaMalloc(&d, total), "plan table allocation");
+  if (ob) CK(cudaMemcpyAsync(d, p.ops.data(), ob, cudaMemcpyHostToDevice, s), "plan upload");
+  if (!p.ents.empty())
+    CK(cudaMemcpyAsync((char*)d + ob, p.ents.data(), p.ents.size(), cudaMemcpyHostToDevice, s), "plan upload");
+  CK(cudaStreamSynchronize(s), "plan upload");
+  p.dev = d;
+  p.dev_bytes = total;
+  return NWQ_OK;
+}
+
+static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
+  int rc = plan_upload(p, s);
+  if (rc) return rc;
+  const DevOp* ops = (const DevOp*)p.dev;
+  const void* ents = (const char*)p.dev + p.ops.size() * sizeof(DevOp);
+  for (const SweepDesc& sd : p.sweeps) {
+    if (sd.nops == 0) continue;
+    cudaError_t e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents, sm_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+  }
+  return NWQ_OK;
+}
+
+Plan::~Plan() {
+  if (dev) cudaFree(dev);
+}
+
+// ------------------------------------------------------------------ states
+static int create_state(int kind, int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, nwq_state** out) {
+  if (!out) return fail(NWQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  size_t need = nwq_state_bytes(kind, n, dtype);
+  if (!need) return fail(NWQ_EINVAL, "unsupported qubit count or dtype");
+  if (dev_buf && buf_bytes < need) return fail(NWQ_EINVAL, "device buffer too small");
+  if (dev_buf && ((uintptr_t)dev_buf & 15)) return fail(NWQ_EINVAL, "device buffer not 16-byte aligned");
+  auto st = std::make_unique<nwq_state>();
+  st->kind = kind;
+  st->n = n;
+  st->dtype = dtype;
+  st->B = kind == NWQ_SV ? n : 2 * n;
+  st->bytes = need;
+  st->stream = (cudaStream_t)stream;
+  CK(cudaGetDevice(&st->device), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&st->sm_count, cudaDevAttrMultiProcessorCount, st->device), "device query");
+  if (dev_buf) {
+    st->buf = dev_buf;
+  } else {
+    cudaError_t e = cudaMalloc(&st->buf, need);
+    if (e != cudaSuccess) return fail(NWQ_ENOMEM, std::string("state allocation: ") + cudaGetErrorString(e));
+    st->owned = true;
+  }
+  cudaError_t e = launch_init(kind == NWQ_SV, f64_of(dtype), st->buf, n, st->sm_count, st->stream);
+  if (e != cudaSuccess) {
+    if (st->owned) cudaFree(st->buf);
+    return cuda_fail(e, "state init");
+  }
+  *out = st.release();
+  return NWQ_OK;
+}
+
+extern "C" int nwq_sv_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, nwq_state** out) {
+  return create_state(NWQ_SV, n, dtype, dev_buf, buf_bytes, stream, out);
+}
+extern "C" int nwq_dm_create(int n, int dtype, void* dev_buf, size_t buf_bytes, void* stream, nwq_state** out) {
+  return create_state(NWQ_DM, n, dtype, dev_buf, buf_bytes, stream, out);
+}
+
+extern "C" int nwq_state_reset(nwq_state* st) {
+  if (!st) return fail(NWQ_EINVAL, "state is NULL");
+  cudaError_t e = launch_init(st->kind == NWQ_SV, f64_of(st->dtype), st->buf, st->n, st->sm_count, st->stream);
+  return e == cudaSuccess ? NWQ_OK : cuda_fail(e, "state reset");
+}
+
+extern "C" int nwq_destroy(nwq_state* st) {
+  if (!st) return NWQ_OK;
+  if (st->stream) cudaStreamSynchronize(st->stream);
+  else cudaDeviceSynchronize();
+  if (st->owned && st->buf) cudaFree(st->buf);
+  delete st;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_device_sync(nwq_state* st) {
+  if (!st) return fail(NWQ_EINVAL, "state is NULL");
+  CK(cudaStreamSynchronize(st->stream), "stream synchronize");
+  return NWQ_OK;
+}
+
+// Per-qubit basis change between Pauli coefficients and vec(rho) (complex, 2n bits).
+static nwq_plan* dm_conv_plan(nwq_state* st, bool to_rho) {
+  std::unique_ptr<nwq_plan>& slot = to_rho ? st->p2r : st->r2p;
+  if (slot) return slot.get();
+  auto pl = std::make_unique<nwq_plan>();
+  init_plan_meta(pl->p, NWQ_SV, st->n, st->dtype, 2 * st->n);  // complex elements over 2n bits
+  cd M[16];
+  if (to_rho) pauli_to_rho_matrix(M);
+  else rho_to_pauli_matrix(M);
+  std::vector<BitOp> ops(st->n);
+  for (int q = 0; q < st->n; q++) {
+    ops[q].k = 2;
+    ops[q].bits[0] = q;
+    ops[q].bits[1] = q + st->n;
+    ops[q].m.assign(M, M + 16);
+    ops[q].gate0 = q;
+  }
+  PlanOptions o;
+  plan_options(NWQ_SV, st->dtype, NWQ_PLAN_NO_MERGE, o);
+  build_plan(ops, o, pl->p);
+  slot = std::move(pl);
+  return slot.get();
+}
+
+static int dm_to_rho(nwq_state* st, void* dst_dev) {
+  bool f64 = f64_of(st->dtype);
+  uint64_t count = 1ull << (2 * st->n);
+  cudaError_t e = launch_real_to_cplx(f64, st->buf, dst_dev, count, st->sm_count, st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dm convert");
+  return plan_launch(dm_conv_plan(st, true)->p, dst_dev, st->stream, st->sm_count);
+}
+
+extern "C" int nwq_state_copy(nwq_state* st, void* dst, size_t bytes, int dst_on_device) {
+  if (!st || !dst) return fail(NWQ_EINVAL, "NULL argument");
+  if (st->kind == NWQ_SV) {
+    if (bytes < st->bytes) return fail(NWQ_EINVAL, "destination too small");
+    CK(cudaMemcpyAsync(dst, st->buf, st->bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st->stream),
+       "state copy");
+    CK(cudaStreamSynchronize(st->stream), "state copy");
+    return NWQ_OK;
+  }
+  size_t need = 2 * st->bytes;  // complex vec(rho)
+  if (bytes < need) return fail(NWQ_EINVAL, "destination too small");
+  void* tmp = dst;
+  if (!dst_on_device) CK(cudaMallocAsync(&tmp, need, st->stream), "scratch allocation");
+  int rc = dm_to_rho(st, tmp);
+  if (!rc && !dst_on_device) {
+    cudaError_t e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, st->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "state copy");
+  }
+  if (!dst_on_device) cudaFreeAsync(tmp, st->stream);
+  cudaError_t e = cudaStreamSynchronize(st->stream);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "state copy");
+  return rc;
+}
+
+extern "C" int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst_on_device) {
+  if (!st || !dst) return fail(NWQ_EINVAL, "NULL argument");
+  if (st->kind != NWQ_DM) return fail(NWQ_EINVAL, "not a density matrix");
+  if (bytes < st->bytes) return fail(NWQ_EINVAL, "destination too small");
+  CK(cudaMemcpyAsync(dst, st->buf, st->bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     st->stream),
+     "copy");
+  CK(cudaStreamSynchronize(st->stream), "copy");
+  return NWQ_OK;
+}
+
+extern "C" int nwq_state_load(nwq_state* st, const void* src, size_t bytes, int src_on_device) {
+  if (!st || !src) return fail(NWQ_EINVAL, "NULL argument");
+  cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (st->kind == NWQ_SV) {
+    if (bytes != st->bytes) return fail(NWQ_EINVAL, "size mismatch");
+    CK(cudaMemcpyAsync(st->buf, src, bytes, kind, st->stream), "state load");
+    CK(cudaStreamSynchronize(st->stream), "state load");
+    return NWQ_OK;
+  }
+  size_t need = 2 * st->bytes;
+  if (bytes != need) return fail(NWQ_EINVAL, "size mismatch");
+  void* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, need, st->stream), "scratch allocation");
+  int rc = NWQ_OK;
+  cudaError_t e = cudaMemcpyAsync(tmp, src, need, kind, st->stream);
+  if (e != cudaSuccess) rc = cuda_fail(e, "state load");
+  if (!rc) rc = plan_launch(dm_conv_plan(st, false)->p, tmp, st->stream, st->sm_count);
+  if (!rc) {
+    e = launch_cplx_to_real(f64_of(st->dtype), tmp, st->buf, 1ull << (2 * st->n), st->sm_count, st->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "state load");
+  }
+  cudaFreeAsync(tmp, st->stream);
+  e = cudaStreamSynchronize(st->stream);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "state load");
+  return rc;
+}
+
+// ------------------------------------------------------------------ plans
+extern "C" int nwq_plan_create(int kind, int n, int dtype, const nwq_gate* gates, size_t ng,
+                               const nwq_noise_model* nm, uint32_t flags, void* stream, nwq_plan** out) {
+  (void)stream;
+  if (!out) return fail(NWQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!nwq_state_bytes(kind, n, dtype)) return fail(NWQ_EINVAL, "unsupported qubit count or dtype");
+  if (ng && !gates) return fail(NWQ_EINVAL, "gates is NULL");
+  if (kind == NWQ_SV && nm) return fail(NWQ_EINVAL, "noise model needs a density matrix");
+  for (size_t i = 0; i < ng; i++)
+    if (gates[i].reserved || gates[i].reserved2) return fail(NWQ_EINVAL, "reserved gate field not 0");
+  auto pl = std::make_unique<nwq_plan>();
+  init_plan_meta(pl->p, kind, n, dtype, kind == NWQ_SV ? n : 2 * n);
+  std::vector<BitOp> ops;
+  std::string err;
+  bool ok = kind == NWQ_SV ? lower_sv(gates, ng, n, ops, err) : lower_dm(gates, ng, n, nm, ops, err);
+  if (!ok) return fail(NWQ_EINVAL, err);
+  PlanOptions o;
+  plan_options(kind, dtype, flags, o);
+  if (kind == NWQ_DM && !(flags & NWQ_PLAN_NO_RESCALE)) o.rescale_qubits = n;
+  build_plan(ops, o, pl->p);
+  *out = pl.release();
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_run(nwq_state* st, const nwq_plan* plan) {
+  if (!st || !plan) return fail(NWQ_EINVAL, "NULL argument");
+  const Plan& p = plan->p;
+  if (p.kind != st->kind || p.n != st->n || p.dtype != st->dtype) return fail(NWQ_EINVAL, "plan does not match state");
+  return plan_launch(const_cast<Plan&>(p), st->buf, st->stream, st->sm_count);
+}
+
+extern "C" int nwq_plan_info(const nwq_plan* plan, int* sweeps, int* ops, double* bytes, double* fma_per_elem,
+                             size_t* table_bytes) {
+  if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
+  int ns = 0;
+  for (auto& s : plan->p.sweeps) ns += s.nops > 0;
+  if (sweeps) *sweeps = ns;
+  if (ops) *ops = (int)plan->p.ops.size();
+  if (bytes) *bytes = plan->p.bytes;
+  if (fma_per_elem) *fma_per_elem = plan->p.fma_per_elem;
+  if (table_bytes) *table_bytes = plan->p.ops.size() * sizeof(DevOp) + plan->p.ents.size();
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op_ngates) {
+  if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
+  int s = 0;
+  for (auto& sd : plan->p.sweeps)
+    if (sd.nops > 0 && sweep_nops) sweep_nops[s++] = sd.nops;
+  for (size_t k = 0; k < plan->p.ops.size(); k++) {
+    if (op_gate) op_gate[k] = plan->p.op_gate0[k];
+    if (op_ngates) op_ngates[k] = plan->p.op_ngates[k];
+  }
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_destroy(nwq_plan* plan) {
+  delete plan;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_sv_apply_circuit(nwq_state* st, const nwq_gate* gates, size_t ng, uint32_t flags) {
+  if (!st) return fail(NWQ_EINVAL, "state is NULL");
+  if (st->kind != NWQ_SV) return fail(NWQ_EINVAL, "not a state vector");
+  nwq_plan* pl = nullptr;
+  int rc = nwq_plan_create(NWQ_SV, st->n, st->dtype, gates, ng, nullptr, flags, st->stream, &pl);
+  if (rc) return rc;
+  rc = nwq_plan_run(st, pl);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(st->stream);  // tables are freed below
+    if (e != cudaSuccess) rc = cuda_fail(e, "apply circuit");
+  }
+  nwq_plan_destroy(pl);
+  return rc;
+}
+
+extern "C" int nwq_dm_apply_circuit_noisy(nwq_state* st, const nwq_gate* gates, size_t ng,
+                                          const nwq_noise_model* nm, uint32_t flags) {
+  if (!st) return fail(NWQ_EINVAL, "state is NULL");
+  if (st->kind != NWQ_DM) return fail(NWQ_EINVAL, "not a density matrix");
+  nwq_plan* pl = nullptr;
+  int rc = nwq_plan_create(NWQ_DM, st->n, st->dtype, gates, ng, nm, flags, st->stream, &pl);
+  if (rc) return rc;
+  rc = nwq_plan_run(st, pl);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "apply circuit");
+  }
+  nwq_plan_destroy(pl);
+  return rc;
+}
+
+// ------------------------------------------------------------------ measurement
+extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, size_t nt, double* out_host,
+                                    uint32_t flags) {
+  if (!st || !out_host || (nt && !terms)) return fail(NWQ_EINVAL, "NULL argument");
+  if (nt == 0) {
+    if (flags & NWQ_EXPECT_SUM) out_host[0] = 0.0;
+    return NWQ_OK;
+  }
+  const uint64_t qmask = st->n >= 64 ? ~0ull : ((1ull << st->n) - 1);
+  for (size_t t = 0; t < nt; t++)
+    if ((terms[t].x_mask & ~qmask) || (terms[t].z_mask & ~qmask)) return fail(NWQ_EINVAL, "Pauli mask out of range");
+  const bool sum = (flags & NWQ_EXPECT_SUM) != 0;
+  const bool norm = (flags & NWQ_EXPECT_NORMALIZE) != 0;
+  const bool f64 = f64_of(st->dtype);
+  cudaStream_t s = st->stream;
+
+  if (st->kind == NWQ_DM) {
+    std::vector<uint64_t> h(3 * nt);
+    for (size_t t = 0; t < nt; t++) {
+      h[t] = terms[t].x_mask;
+      h[nt + t] = terms[t].z_mask;
+      std::memcpy(&h[2 * nt + t], &terms[t].coeff, 8);
+    }
+    void* d = nullptr;
+    size_t outn = sum ? 1 : nt;
+    CK(cudaMallocAsync(&d, h.size() * 8 + outn * 8, s), "scratch allocation");
+    uint64_t* dx = (uint64_t*)d;
+    double* dout = (double*)(dx + 3 * nt);
+    int rc = NWQ_OK;
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_dm_expect(f64, st->buf, st->n, dx, dx + nt, (const double*)(dx + 2 * nt), (int)nt, dout, sum, norm, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dout, outn * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "expectation");
+    cudaFreeAsync(d, s);
+    e = cudaStreamSynchronize(s);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "expectation");
+    return rc;
+  }
+
+  // SV: group terms by x mask, chunks of kExpectChunk terms per launch.
+  std::map<uint64_t, std::vector<int>> groups;
+  for (size_t t = 0; t < nt; t++) groups[terms[t].x_mask].push_back((int)t);
+  struct Chunk {
+    uint64_t x;
+    std::vector<int> idx;
+  };
+  std::vector<Chunk> chunks;
+  for (auto& g : groups)
+    for (size_t i = 0; i < g.second.size(); i += kExpectChunk)
+      chunks.push_back({g.first, std::vector<int>(g.second.begin() + i,
+                                                  g.second.begin() + std::min(g.second.size(), i + kExpectChunk))});
+  if (norm) chunks.push_back({0ull, std::vector<int>{-1}});  // identity string: <psi|psi>
+  uint64_t N = 1ull << st->n;
+  int nblocks = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)st->sm_count * 4);
+  // host staging: per chunk z masks (16 u64) + y (16 int) ; coefficients in group order
+  size_t nchunk = chunks.size();
+  std::vector<uint64_t> hz(nchunk * kExpectChunk, 0);
+  std::vector<int> hy(nchunk * kExpectChunk, 0);
+  std::vector<double> hcoef;
+  std::vector<int> order;
+  const nwq_pauli_term ident{0ull, 0ull, 0.0};
+  for (size_t c = 0; c < nchunk; c++)
+    for (size_t j = 0; j < chunks[c].idx.size(); j++) {
+      int ti = chunks[c].idx[j];
+      const nwq_pauli_term& tm = ti < 0 ? ident : terms[ti];
+      hz[c * kExpectChunk + j] = tm.z_mask;
+      hy[c * kExpectChunk + j] = __builtin_popcountll(tm.x_mask & tm.z_mask) & 3;
+      if (ti < 0) continue;
+      hcoef.push_back(tm.coeff);
+      order.push_back(ti);
+    }
+  size_t bz = hz.size() * 8, by = hy.size() * 4, bc = nt * 8, bv = nt * 8 + 16;
+  size_t bp = (size_t)nblocks * kExpectChunk * 8;
+  void* d = nullptr;
+  CK(cudaMallocAsync(&d, bz + by + bc + bv + bp + 64, s), "scratch allocation");
+  char* base = (char*)d;
+  uint64_t* dz = (uint64_t*)base;
+  int* dy = (int*)(base + bz);
+  double* dc = (double*)(base + ((bz + by + 7) & ~(size_t)7));
+  double* dv = dc + nt;       // values in chunk order; dv[nt] = norm, dv[nt+1] = sum
+  double* dpart = dv + nt + 2;
+  int rc = NWQ_OK;
+  cudaError_t e = cudaMemcpyAsync(dz, hz.data(), bz, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy.data(), by, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, hcoef.data(), bc, cudaMemcpyHostToDevice, s);
+  size_t done = 0;
+  for (size_t c = 0; c < nchunk && e == cudaSuccess; c++) {
+    int cnt = (int)chunks[c].idx.size();
+    e = launch_sv_expect_group(f64, st->buf, st->n, chunks[c].x, dz + c * kExpectChunk, dy + c * kExpectChunk, cnt,
+                               dpart, nblocks, dv + done, s);
+    done += cnt;
+  }
+  std::vector<double> vals(nt);
+  if (e == cudaSuccess && norm) e = launch_scale(dv, (int)nt, dv + nt, s);
+  if (e == cudaSuccess && sum) {
+    e = launch_weighted_sum(dv, dc, (int)nt, dv + nt + 1, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dv + nt + 1, 8, cudaMemcpyDeviceToHost, s);
+  } else if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(vals.data(), dv, nt * 8, cudaMemcpyDeviceToHost, s);
+  }
+  if (e != cudaSuccess) rc = cuda_fail(e, "expectation");
+  cudaFreeAsync(d, s);
+  e = cudaStreamSynchronize(s);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "expectation");
+  if (!rc && !sum)
+    for (size_t k = 0; k < nt; k++) out_host[order[k]] = vals[k];
+  return rc;
+}
+
+// Real f64 plan over n bits: readout confusion per bit (SV) or the
+// Walsh-Hadamard butterfly (DM diagonal from Z-string coefficients).
+static nwq_plan* probs_plan(nwq_state* st, double e, bool wht) {
+  double key = wht ? -1.0 - e : e;
+  auto it = st->probs.find(key);
+  if (it != st->probs.end()) return it->second.get();
+  auto pl = std::make_unique<nwq_plan>();
+  init_plan_meta(pl->p, NWQ_DM, st->n, NWQ_F64, st->n);  // real f64 elements over n bits
+  std::vector<BitOp> ops(st->n);
+  for (int q = 0; q < st->n; q++) {
+    ops[q].k = 1;
+    ops[q].bits[0] = q;
+    if (wht) ops[q].m = {1.0, 1.0, 1.0, -1.0};
+    else ops[q].m = {1.0 - e, e, e, 1.0 - e};
+    ops[q].gate0 = q;
+  }
+  PlanOptions o;
+  plan_options(NWQ_DM, NWQ_F64, NWQ_PLAN_NO_MERGE, o);
+  build_plan(ops, o, pl->p);
+  nwq_plan* raw = pl.get();
+  st->probs[key] = std::move(pl);
+  return raw;
+}
+
+extern "C" int nwq_probs(nwq_state* st, double readout_e, double* out_host) {
+  if (!st || !out_host) return fail(NWQ_EINVAL, "NULL argument");
+  if (st->n > 30) return fail(NWQ_EUNSUPPORTED, "probabilities limited to n <= 30");
+  if (!(readout_e >= 0.0 && readout_e <= 0.5)) return fail(NWQ_EINVAL, "readout error outside [0, 0.5]");
+  cudaStream_t s = st->stream;
+  uint64_t N = 1ull << st->n;
+  double* p = nullptr;
+  CK(cudaMallocAsync((void**)&p, N * 8, s), "scratch allocation");
+  int rc = NWQ_OK;
+  cudaError_t e;
+  if (st->kind == NWQ_SV) {
+    e = launch_sv_abs2(f64_of(st->dtype), st->buf, p, N, st->sm_count, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "probabilities");
+    if (!rc && readout_e > 0) rc = plan_launch(probs_plan(st, readout_e, false)->p, p, s, st->sm_count);
+  } else {
+    e = launch_dm_diag(f64_of(st->dtype), st->buf, p, st->n, readout_e, st->sm_count, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "probabilities");
+    if (!rc) rc = plan_launch(probs_plan(st, 0.0, true)->p, p, s, st->sm_count);
+  }
+  if (!rc) {
+    e = cudaMemcpyAsync(out_host, p, N * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "probabilities");
+  }
+  cudaFreeAsync(p, s);
+  e = cudaStreamSynchronize(s);
+  if (!rc && e != cudaSuccess) rc = cuda_fail(e, "probabilities");
+  return rc;
+}
+
+extern "C" const char* nwq_last_error(void) { return g_err.c_str(); }
+
+extern "C" uint64_t nwq_launch_count(void) { return (uint64_t)g_launches.load(); }
+
+extern "C" int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t ng, const double* params, int nsets,
+                                int nparams, const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne,
+                                double* out, void* stream) {
+  (void)n; (void)dtype; (void)gates; (void)ng; (void)params; (void)nsets; (void)nparams;
+  (void)terms; (void)nt; (void)coeffs; (void)ne; (void)out; (void)stream;
+  return fail(NWQ_EUNSUPPORTED, "batched energy kernel not built");
+}

@@ -1,0 +1,79 @@
+// Internal layout shared by the host planner and the device kernels.
+//
+// A circuit is lowered to a list of *operators*: a 2^k x 2^k matrix acting on
+// k <= 4 bits of the state index (SV: complex matrix on the gate's qubits;
+// DM: real Pauli-transfer matrix on bits q and q+n of every touched qubit).
+// Operators are grouped into *sweeps*: one sweep stages tiles of 2^T
+// elements (T tile bits = the low contiguous bits 0..m-1 plus h strided high
+// bits) in shared memory, applies its operators in order, and writes the tile
+// back, so the state is read and written once per sweep.
+#pragma once
+#include <cstdint>
+
+namespace nwq {
+
+constexpr int kMaxK = 4;          // bits per operator
+constexpr int kMaxTileBits = 15;  // shared-memory tile <= 2^15 elements
+constexpr int kMaxHigh = 15;
+
+// Row kinds: how output row i of an operator is produced.
+enum : uint8_t {
+  ROW_ID = 0,    // unchanged (no arithmetic, no store)
+  ROW_MOVE = 1,  // copy (or negated copy) of one input: no arithmetic
+  ROW_GEN = 2    // optional +-input (the row's unit entry) plus coefficient * input terms
+};
+
+// Complex entry kinds (coefficient structure, selects the cheapest arithmetic).
+enum : uint8_t { CE_RE = 0, CE_IM = 1, CE_GEN = 2 };
+
+// Output row i of an operator:
+//   ROW_MOVE: out = sgn * in[boff]
+//   ROW_GEN : out = [sgn * in[boff] if has_base] + sum_e c_e in[off_e]
+// Real operators keep all terms in one entry list (cnt[0] entries); complex
+// operators keep three kind-homogeneous lists: cnt[0] real-coefficient,
+// cnt[1] imaginary-coefficient and cnt[2] general entries, in that order.
+struct RowMeta {
+  uint16_t out;    // tile-local offset of output i
+  uint16_t boff;   // tile-local offset of the unit entry's input
+  uint16_t beg;    // first entry of the row (relative to DevOp::ent)
+  uint8_t kind;    // ROW_*
+  uint8_t base;    // 0: no unit entry, 1: +input, 2: -input
+  uint8_t cnt[3];  // entry counts (see above)
+  uint8_t pad;
+};
+
+struct alignas(16) DevOp {
+  uint8_t k;              // number of operator bits
+  uint8_t lb[4];          // tile-local bit position of operator bit j
+  uint8_t slb[4];         // the same positions sorted ascending (k used)
+  uint8_t pad[3];
+  uint32_t ent;           // first entry (index into the plan's entry array)
+  RowMeta row[16];
+};
+
+template <class R>
+struct EntR {  // real entry: out += c * in[off]
+  R c;
+  uint32_t off;
+};
+
+template <class R>
+struct EntC {  // complex entry: out += (re + i im) * in[off]
+  R re, im;
+  uint32_t off;
+  uint32_t kind;  // CE_*
+};
+
+struct SweepDesc {
+  uint64_t hmask;  // global mask of the high tile bits
+  uint64_t fmask;  // global mask of the bits that index tiles (not in the tile)
+  int32_t T;       // tile bits
+  int32_t m;       // low contiguous tile bits (global bits 0..m-1)
+  int32_t h;       // high tile bits
+  int32_t nops;    // operators in this sweep
+  uint32_t op0;    // index of the first operator
+  uint8_t hpos[kMaxHigh];  // global position of high tile bit i (ascending, >= m)
+  uint8_t pad;
+};
+
+}  // namespace nwq

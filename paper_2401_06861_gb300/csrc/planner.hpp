@@ -1,0 +1,70 @@
+// Host planner: lowers a gate list (plus noise model) to device sweeps.
+#pragma once
+#include <complex>
+#include <cstddef>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/nwqgb.h"
+#include "nwq_internal.h"
+
+namespace nwq {
+
+using cd = std::complex<double>;
+
+// One operator on k bits of the state index, before it is placed in a sweep.
+struct BitOp {
+  int k = 0;
+  int bits[4] = {0, 0, 0, 0};  // global bit of local operator bit j
+  std::vector<cd> m;           // 2^k x 2^k, row-major (imaginary parts 0 for DM)
+  int gate0 = 0, ngates = 1;   // provenance
+};
+
+struct PlanOptions {
+  int tile_bits = 12;     // T
+  int min_low = 3;        // coalescing: low contiguous bits always in the tile
+  bool merge = true;      // algebraic merging of adjacent operators
+  bool plain = false;     // one operator per sweep
+  int max_merge_bits = 4;
+  int lookahead = 4096;   // operators scanned when filling a sweep
+  int rescale_qubits = 0; // DM: deferred per-qubit scaling over this many qubits (0 = off)
+};
+
+struct Plan {
+  int kind = 0, n = 0, dtype = 0, B = 0;
+  bool is_complex = true;
+  size_t elem_bytes = 0, ent_bytes = 0;
+  std::vector<SweepDesc> sweeps;
+  std::vector<DevOp> ops;
+  std::vector<unsigned char> ents;  // EntR<R> or EntC<R> records
+  std::vector<int> op_gate0, op_ngates;
+  double fma_per_elem = 0.0;  // summed over operators, per state element
+  double bytes = 0.0;         // algorithmic bytes per run
+  // device copy (lazy upload on first run)
+  std::mutex mu;
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  ~Plan();
+};
+
+// Gate matrix in the local basis j = b(q0) + 2 b(q1).  Returns the number of
+// qubits (1 or 2), 0 for an unknown kind.
+int gate_matrix(const nwq_gate& g, double theta0, cd* U);
+
+// Lowering.  On error returns false and sets err.
+bool lower_sv(const nwq_gate* g, size_t ng, int n, std::vector<BitOp>& out, std::string& err);
+bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, std::vector<BitOp>& out,
+              std::string& err);
+
+// Merge + sweep grouping + device table layout.
+void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan);
+
+// Cost model: floating-point operations (multiply or add) per state element.
+double op_cost(const BitOp& op, bool is_complex);
+
+// Matrices used by the measurement helpers.
+void pauli_to_rho_matrix(cd M[16]);   // per-qubit Pauli -> standard vec(rho) map
+void rho_to_pauli_matrix(cd M[16]);   // its inverse
+
+}  // namespace nwq

@@ -1,0 +1,480 @@
+// Device kernels of the simulator (sm_103a).
+//
+// sweep_kernel: the hot path.  One sweep = stage a tile of 2^T state elements
+// (2^m contiguous elements x 2^h strided chunks) in shared memory with 16-byte
+// vector loads, apply the sweep's operators in order (each operator acts on
+// k <= 4 tile-local bits; __syncthreads between operators), write the tile
+// back.  The grid is persistent over tiles (grid = SMs x resident CTAs).
+//
+// Paper Sec. II: SV-Sim applies gates to the 2^n-amplitude state vector;
+// DM-Sim applies gates and noise channels to the density matrix.  Here the
+// density matrix is held as its 4^n real Pauli coefficients and every gate
+// plus its noise is one real Pauli-transfer matrix on bits (q, q+n), so the
+// same engine serves both (complex elements for SV, real for DM).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "nwq_internal.h"
+#include "kernels.hpp"
+
+namespace nwq {
+
+std::atomic<unsigned long long> g_launches{0};
+
+template <class R>
+struct Cplx;
+template <>
+struct Cplx<double> {
+  using T = double2;
+};
+template <>
+struct Cplx<float> {
+  using T = float2;
+};
+
+// Insert a zero bit at each position of `pos` (ascending) into g.
+template <int K>
+__device__ __forceinline__ uint32_t insert_zeros(uint32_t g, const uint8_t* sorted_pos) {
+#pragma unroll
+  for (int t = 0; t < K; t++) {
+    uint32_t p = sorted_pos[t];
+    uint32_t lowm = (1u << p) - 1u;
+    g = ((g & ~lowm) << 1) | (g & lowm);
+  }
+  return g;
+}
+
+// Signed copy of x (base = 1: +x, 2: -x) or +0 (base = 0), with integer
+// operations only: the FP64 pipe is the scarce unit on this GPU, so no
+// floating-point instruction is spent on unit coefficients.
+__device__ __forceinline__ double signed_base(double x, int base) {
+  long long b = __double_as_longlong(x) ^ (base == 2 ? (long long)0x8000000000000000ull : 0ll);
+  return __longlong_as_double(base ? b : 0ll);
+}
+__device__ __forceinline__ float signed_base(float x, int base) {
+  int b = __float_as_int(x) ^ (base == 2 ? (int)0x80000000u : 0);
+  return __int_as_float(base ? b : 0);
+}
+__device__ __forceinline__ double2 signed_base(double2 v, int base) {
+  return make_double2(signed_base(v.x, base), signed_base(v.y, base));
+}
+__device__ __forceinline__ float2 signed_base(float2 v, int base) {
+  return make_float2(signed_base(v.x, base), signed_base(v.y, base));
+}
+
+// ------------------------------------------------------------------ real operators
+// Output row i = [+-x[boff]] + sum_e c_e x[off_e].  Loops over entries are
+// kept rolled (warp-uniform trip counts) so that no predicated-off FP64
+// instruction occupies the pipe; all table reads are warp-uniform.
+template <int K, class R>
+__device__ __forceinline__ void apply_real(R* __restrict__ tile, int T, const DevOp& op,
+                                           const EntR<R>* __restrict__ ents) {
+  constexpr int D = 1 << K;
+  const uint32_t ngroups = 1u << (T - K);
+  const EntR<R>* e0 = ents + op.ent;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += kSweepThreads) {
+    const uint32_t base = insert_zeros<K>(g, op.slb);
+    R out[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const RowMeta& rm = op.row[i];
+      if (rm.kind == ROW_ID) continue;
+      R acc = signed_base(tile[base + rm.boff], rm.base);
+      if (rm.kind == ROW_GEN) {
+        const EntR<R>* e = e0 + rm.beg;
+        const int cnt = rm.cnt[0];
+#pragma unroll 1
+        for (int c = 0; c < cnt; c++) acc = fma(e[c].c, tile[base + e[c].off], acc);
+      }
+      out[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < D; i++)
+      if (op.row[i].kind != ROW_ID) tile[base + op.row[i].out] = out[i];
+  }
+}
+
+// ------------------------------------------------------------------ complex operators
+// Same row form with three kind-homogeneous entry lists: real coefficients
+// (2 FMA), imaginary coefficients (2 FMA) and general ones (4 FMA).
+template <int K, class R>
+__device__ __forceinline__ void apply_cplx(typename Cplx<R>::T* __restrict__ tile, int T, const DevOp& op,
+                                           const EntC<R>* __restrict__ ents) {
+  using C = typename Cplx<R>::T;
+  constexpr int D = 1 << K;
+  const uint32_t ngroups = 1u << (T - K);
+  const EntC<R>* e0 = ents + op.ent;
+  for (uint32_t g = threadIdx.x; g < ngroups; g += kSweepThreads) {
+    const uint32_t base = insert_zeros<K>(g, op.slb);
+    C out[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const RowMeta& rm = op.row[i];
+      if (rm.kind == ROW_ID) continue;
+      C acc = signed_base(tile[base + rm.boff], rm.base);
+      if (rm.kind == ROW_GEN) {
+        const EntC<R>* e = e0 + rm.beg;
+        const int c0 = rm.cnt[0], c1 = c0 + rm.cnt[1], c2 = c1 + rm.cnt[2];
+        int c = 0;
+#pragma unroll 1
+        for (; c < c0; c++) {
+          const C x = tile[base + e[c].off];
+          const R re = e[c].re;
+          acc.x = fma(re, x.x, acc.x);
+          acc.y = fma(re, x.y, acc.y);
+        }
+#pragma unroll 1
+        for (; c < c1; c++) {
+          const C x = tile[base + e[c].off];
+          const R im = e[c].im;
+          acc.x = fma(-im, x.y, acc.x);
+          acc.y = fma(im, x.x, acc.y);
+        }
+#pragma unroll 1
+        for (; c < c2; c++) {
+          const C x = tile[base + e[c].off];
+          const R re = e[c].re, im = e[c].im;
+          acc.x = fma(re, x.x, fma(-im, x.y, acc.x));
+          acc.y = fma(re, x.y, fma(im, x.x, acc.y));
+        }
+      }
+      out[i] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < D; i++)
+      if (op.row[i].kind != ROW_ID) tile[base + op.row[i].out] = out[i];
+  }
+}
+
+// ------------------------------------------------------------------ sweep kernel
+// Scatter the low bits of v onto the set bits of mask (ascending).
+__device__ __forceinline__ uint64_t deposit(uint64_t v, uint64_t mask) {
+  uint64_t out = 0;
+  while (v && mask) {
+    uint64_t lowbit = mask & (~mask + 1ull);
+    if (v & 1ull) out |= lowbit;
+    v >>= 1;
+    mask ^= lowbit;
+  }
+  return out;
+}
+
+// Resident CTAs per SM the register budget is tuned for (no spills at these bounds).
+template <class R, bool CPLX>
+struct SweepOcc {
+  static constexpr int value = (sizeof(R) == 4 && !CPLX) ? 3 : ((sizeof(R) == 8 && CPLX) ? 1 : 2);
+};
+
+template <class R, bool CPLX>
+__global__ void __launch_bounds__(kSweepThreads, SweepOcc<R, CPLX>::value) sweep_kernel(void* __restrict__ state_v, uint64_t ntiles,
+                                                                SweepDesc sd, const DevOp* __restrict__ ops,
+                                                                const void* __restrict__ ents_v) {
+  using E = typename std::conditional<CPLX, typename Cplx<R>::T, R>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E* tile = reinterpret_cast<E*>(smem_raw);
+  E* state = reinterpret_cast<E*>(state_v);
+  constexpr int VPE = 16 / sizeof(E);  // elements per 16-byte vector
+  const int T = sd.T;
+  const uint32_t nvec = (1u << T) / VPE;
+  const int lvpc = sd.m - __ffs(VPE) + 1;  // log2(vectors per contiguous chunk)
+  const uint32_t vpc_mask = (1u << lvpc) - 1u;
+
+  for (uint64_t tileid = blockIdx.x; tileid < ntiles; tileid += gridDim.x) {
+    // base = tile id scattered onto the non-tile bits
+    const uint64_t base = deposit(tileid, sd.fmask);
+    for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
+      uint32_t j = v >> lvpc;
+      uint64_t off = base + deposit(j, sd.hmask) + (uint64_t)(v & vpc_mask) * VPE;
+      reinterpret_cast<uint4*>(tile)[v] = __ldg(reinterpret_cast<const uint4*>(state + off));
+    }
+    __syncthreads();
+    for (int o = 0; o < sd.nops; o++) {
+      const DevOp& op = ops[sd.op0 + o];
+      if constexpr (CPLX) {
+        const EntC<R>* ents = reinterpret_cast<const EntC<R>*>(ents_v);
+        switch (op.k) {
+          case 1: apply_cplx<1, R>(tile, T, op, ents); break;
+          case 2: apply_cplx<2, R>(tile, T, op, ents); break;
+          case 3: apply_cplx<3, R>(tile, T, op, ents); break;
+          default: apply_cplx<4, R>(tile, T, op, ents); break;
+        }
+      } else {
+        const EntR<R>* ents = reinterpret_cast<const EntR<R>*>(ents_v);
+        switch (op.k) {
+          case 1: apply_real<1, R>(tile, T, op, ents); break;
+          case 2: apply_real<2, R>(tile, T, op, ents); break;
+          case 3: apply_real<3, R>(tile, T, op, ents); break;
+          default: apply_real<4, R>(tile, T, op, ents); break;
+        }
+      }
+      __syncthreads();
+    }
+    for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
+      uint32_t j = v >> lvpc;
+      uint64_t off = base + deposit(j, sd.hmask) + (uint64_t)(v & vpc_mask) * VPE;
+      reinterpret_cast<uint4*>(state + off)[0] = reinterpret_cast<const uint4*>(tile)[v];
+    }
+    __syncthreads();
+  }
+}
+
+template <class R, bool CPLX>
+static cudaError_t launch_sweep_t(void* state, int B, const SweepDesc& sd, const DevOp* ops, const void* ents,
+                                  int sm_count, cudaStream_t s) {
+  using E = typename std::conditional<CPLX, typename Cplx<R>::T, R>::type;
+  size_t smem = sizeof(E) << sd.T;
+  static bool attr_set = false;  // per instantiation
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  uint64_t ntiles = 1ull << (B - sd.T);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, CPLX>, kSweepThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)sm_count * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  sweep_kernel<R, CPLX><<<(unsigned)grid, kSweepThreads, smem, s>>>(state, ntiles, sd, ops, ents);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
+                         const void* ents, int sm_count, cudaStream_t s) {
+  if (cplx) {
+    if (f64) return launch_sweep_t<double, true>(state, B, sd, ops, ents, sm_count, s);
+    return launch_sweep_t<float, true>(state, B, sd, ops, ents, sm_count, s);
+  }
+  if (f64) return launch_sweep_t<double, false>(state, B, sd, ops, ents, sm_count, s);
+  return launch_sweep_t<float, false>(state, B, sd, ops, ents, sm_count, s);
+}
+
+// ------------------------------------------------------------------ init
+// SV: psi = |0..0>.  DM (Pauli basis): r[x + 2^n z] = Tr(|0><0| P(x,z)) = [x == 0].
+template <class R>
+__global__ void init_kernel(R* __restrict__ s, uint64_t count, uint64_t xmask, int cplx) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    R v = 0;
+    if (cplx) {
+      v = (i == 0) ? R(1) : R(0);
+    } else {
+      v = ((i & xmask) == 0) ? R(1) : R(0);
+    }
+    s[i] = v;
+  }
+}
+
+cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s) {
+  // SV: 2^n complex = 2^(n+1) reals, only real[0] = 1.  DM: 4^n reals.
+  uint64_t count = cplx ? (2ull << n) : (1ull << (2 * n));
+  uint64_t xmask = (1ull << n) - 1;
+  unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+  if (f64) init_kernel<double><<<grid, 256, 0, s>>>((double*)state, count, xmask, cplx);
+  else init_kernel<float><<<grid, 256, 0, s>>>((float*)state, count, xmask, cplx);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ conversions
+// Pauli reals -> complex (imag 0) and complex -> real parts.
+template <class R>
+__global__ void real_to_cplx(const R* __restrict__ in, typename Cplx<R>::T* __restrict__ out, uint64_t count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = typename Cplx<R>::T{in[i], R(0)};
+}
+template <class R>
+__global__ void cplx_to_real(const typename Cplx<R>::T* __restrict__ in, R* __restrict__ out, uint64_t count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = in[i].x;
+}
+
+cudaError_t launch_real_to_cplx(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s) {
+  unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+  if (f64) real_to_cplx<double><<<grid, 256, 0, s>>>((const double*)in, (double2*)out, count);
+  else real_to_cplx<float><<<grid, 256, 0, s>>>((const float*)in, (float2*)out, count);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+cudaError_t launch_cplx_to_real(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s) {
+  unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+  if (f64) cplx_to_real<double><<<grid, 256, 0, s>>>((const double2*)in, (double*)out, count);
+  else cplx_to_real<float><<<grid, 256, 0, s>>>((const float2*)in, (float*)out, count);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ probabilities
+// SV: p[b] = |psi_b|^2 in FP64.
+template <class R>
+__global__ void sv_abs2(const typename Cplx<R>::T* __restrict__ psi, double* __restrict__ p, uint64_t count) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    double re = psi[i].x, im = psi[i].y;
+    p[i] = fma(re, re, im * im);
+  }
+}
+// DM: g[z] = r[z << n] (1 - 2e)^{|z|} / 2^n ; a Walsh-Hadamard transform of g
+// over n bits then gives the outcome distribution with readout error e.
+template <class R>
+__global__ void dm_diag_gather(const R* __restrict__ r, double* __restrict__ g, int n, double one_m_2e) {
+  uint64_t N = 1ull << n;
+  double scale = ldexp(1.0, -n);
+  for (uint64_t z = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; z < N; z += (uint64_t)gridDim.x * blockDim.x) {
+    int w = __popcll(z);
+    double f = scale;
+    double b = one_m_2e;
+    // (1-2e)^w by binary powering in FP64 (w <= 16)
+    while (w) {
+      if (w & 1) f *= b;
+      b *= b;
+      w >>= 1;
+    }
+    g[z] = (double)r[z << n] * f;
+  }
+}
+
+cudaError_t launch_sv_abs2(bool f64, const void* psi, double* p, uint64_t count, int sm_count, cudaStream_t s) {
+  unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+  if (f64) sv_abs2<double><<<grid, 256, 0, s>>>((const double2*)psi, p, count);
+  else sv_abs2<float><<<grid, 256, 0, s>>>((const float2*)psi, p, count);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, int sm_count, cudaStream_t s) {
+  uint64_t count = 1ull << n;
+  unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
+  if (f64) dm_diag_gather<double><<<grid, 256, 0, s>>>((const double*)r, g, n, 1.0 - 2.0 * e);
+  else dm_diag_gather<float><<<grid, 256, 0, s>>>((const float*)r, g, n, 1.0 - 2.0 * e);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ expectations
+// SV, one group of terms sharing x: sum_b Re( conj(psi[b^x]) i^{y_t} (-1)^{|b & z_t|} psi[b] ),
+// FP64 accumulation; per-block partial sums written to part[block * nt + t];
+// a second kernel adds the partials in block order (deterministic).
+template <class R>
+__global__ void __launch_bounds__(256) sv_expect_group(const typename Cplx<R>::T* __restrict__ psi, uint64_t N,
+                                                       uint64_t x, const uint64_t* __restrict__ zm,
+                                                       const int* __restrict__ ym, int nt,
+                                                       double* __restrict__ part) {
+  double acc[kExpectChunk];
+#pragma unroll
+  for (int t = 0; t < kExpectChunk; t++) acc[t] = 0.0;
+  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < N; b += (uint64_t)gridDim.x * blockDim.x) {
+    double pr = psi[b].x, pi = psi[b].y;
+    double qr = pr, qi = pi;
+    if (x) {
+      qr = psi[b ^ x].x;
+      qi = psi[b ^ x].y;
+    }
+    // w = conj(q) * p
+    double wr = fma(qr, pr, qi * pi);
+    double wi = fma(qr, pi, -qi * pr);
+#pragma unroll
+    for (int t = 0; t < kExpectChunk; t++) {
+      if (t < nt) {
+        // Re(i^y w): y=0 wr, y=1 -wi, y=2 -wr, y=3 wi
+        int y = ym[t];
+        double v = (y & 1) ? wi : wr;
+        int neg = ((y == 1) || (y == 2)) ^ (__popcll(b & zm[t]) & 1);
+        acc[t] += neg ? -v : v;
+      }
+    }
+  }
+  __shared__ double red[kExpectChunk][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kExpectChunk; t++) {
+    if (t >= nt) break;
+    double v = acc[t];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[t][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nt) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
+    part[(size_t)blockIdx.x * nt + threadIdx.x] = v;
+  }
+}
+
+__global__ void reduce_partials(const double* __restrict__ part, int nblocks, int nt, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double v = 0;
+  for (int b = 0; b < nblocks; b++) v += part[(size_t)b * nt + t];
+  out[t] = v;
+}
+
+cudaError_t launch_sv_expect_group(bool f64, const void* psi, int n, uint64_t x, const uint64_t* zm, const int* ym,
+                                   int nt, double* part, int nblocks, double* out, cudaStream_t s) {
+  uint64_t N = 1ull << n;
+  if (f64) sv_expect_group<double><<<nblocks, 256, 0, s>>>((const double2*)psi, N, x, zm, ym, nt, part);
+  else sv_expect_group<float><<<nblocks, 256, 0, s>>>((const float2*)psi, N, x, zm, ym, nt, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_partials<<<(nt + 63) / 64, 64, 0, s>>>(part, nblocks, nt, out);
+  g_launches += 2;
+  return cudaGetLastError();
+}
+
+// DM: <P(x,z)> = r[x + 2^n z]; optional weighted sum in term order.
+template <class R>
+__global__ void dm_expect_gather(const R* __restrict__ r, int n, const uint64_t* __restrict__ xm,
+                                 const uint64_t* __restrict__ zm, const double* __restrict__ coef, int nt,
+                                 double* __restrict__ out, int sum, int normalize) {
+  const double tr = normalize ? (double)r[0] : 1.0;  // Tr(rho) = coefficient of the identity string
+  if (sum) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double acc = 0;
+      for (int t = 0; t < nt; t++) acc = fma(coef[t], (double)r[xm[t] | (zm[t] << n)], acc);
+      out[0] = acc / tr;
+    }
+    return;
+  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x)
+    out[t] = (double)r[xm[t] | (zm[t] << n)] / tr;
+}
+
+__global__ void weighted_sum(const double* __restrict__ v, const double* __restrict__ coef, int nt,
+                             double* __restrict__ out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double acc = 0;
+    for (int t = 0; t < nt; t++) acc = fma(coef[t], v[t], acc);
+    out[0] = acc;
+  }
+}
+
+cudaError_t launch_dm_expect(bool f64, const void* r, int n, const uint64_t* xm, const uint64_t* zm,
+                             const double* coef, int nt, double* out, int sum, int normalize, cudaStream_t s) {
+  int grid = sum ? 1 : (nt + 255) / 256;
+  if (f64) dm_expect_gather<double><<<grid, 256, 0, s>>>((const double*)r, n, xm, zm, coef, nt, out, sum, normalize);
+  else dm_expect_gather<float><<<grid, 256, 0, s>>>((const float*)r, n, xm, zm, coef, nt, out, sum, normalize);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+__global__ void scale_values(double* __restrict__ v, int nt, const double* __restrict__ denom) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nt) v[t] = v[t] / denom[0];
+}
+
+cudaError_t launch_scale(double* v, int nt, const double* denom, cudaStream_t s) {
+  scale_values<<<(nt + 127) / 128, 128, 0, s>>>(v, nt, denom);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_sum(const double* v, const double* coef, int nt, double* out, cudaStream_t s) {
+  weighted_sum<<<1, 32, 0, s>>>(v, coef, nt, out);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace nwq

@@ -1,0 +1,166 @@
+"""Thin Python layer over the C ABI (same names, numpy in and out).
+
+    st = State(SV, n, F64)            # nwq_sv_create
+    st.apply(gates)                   # nwq_sv_apply_circuit
+    st.expect(terms)                  # nwq_expect_pauli_sum
+    st.probs(readout_e)               # nwq_probs
+    st.copy()                         # nwq_state_copy
+
+Device memory may be library-owned (default) or a caller buffer such as a
+torch tensor (``buf=tensor.data_ptr(), buf_bytes=...``).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import DM, F32, F64, SV, check, encode_gates, encode_noise, encode_terms  # noqa: F401
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def state_bytes(kind, n, dtype):
+    return L.lib().nwq_state_bytes(kind, n, dtype)
+
+
+def launch_count():
+    """Kernels launched so far by the CUDA library in this process."""
+    return int(L.lib().nwq_launch_count())
+
+
+class State:
+    def __init__(self, kind, n, dtype=F64, buf=None, buf_bytes=0, stream=None):
+        self.kind, self.n, self.dtype = kind, n, dtype
+        self.h = ctypes.c_void_p()
+        create = L.lib().nwq_sv_create if kind == SV else L.lib().nwq_dm_create
+        check(create(n, dtype, ctypes.c_void_p(buf) if buf else None, buf_bytes,
+                     ctypes.c_void_p(stream) if stream else None, ctypes.byref(self.h)))
+
+    # -- lifetime
+    def close(self):
+        if self.h:
+            L.lib().nwq_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- circuits
+    def apply(self, gates, noise=None, flags=0):
+        arr, keep = encode_gates(gates)
+        if self.kind == SV:
+            check(L.lib().nwq_sv_apply_circuit(self.h, arr, len(gates), flags))
+        else:
+            nm, keep2 = encode_noise(noise, self.n)
+            check(L.lib().nwq_dm_apply_circuit_noisy(self.h, arr, len(gates),
+                                                      ctypes.byref(nm) if nm is not None else None, flags))
+        return self
+
+    def run(self, plan):
+        check(L.lib().nwq_plan_run(self.h, plan.h))
+        return self
+
+    def reset(self):
+        check(L.lib().nwq_state_reset(self.h))
+
+    def sync(self):
+        check(L.lib().nwq_device_sync(self.h))
+
+    # -- measurement
+    def expect(self, terms, sum=False, normalize=False):
+        """Per-term <P> (or sum_t coeff_t <P_t> with sum=True); normalize=True
+        divides by the FP64 norm (SV) / trace (DM) of the state."""
+        arr = encode_terms(terms)
+        out = np.zeros(1 if sum else max(len(terms), 1))
+        flags = (L.EXPECT_SUM if sum else L.EXPECT_TERMS) | (L.EXPECT_NORMALIZE if normalize else 0)
+        check(L.lib().nwq_expect_pauli_sum(self.h, arr, len(terms), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           flags))
+        return float(out[0]) if sum else out[:len(terms)]
+
+    def norm(self):
+        """<psi|psi> (SV) or Tr(rho) (DM), accumulated in FP64."""
+        return float(self.expect([(0, 0, 1.0)])[0])
+
+    def probs(self, readout_e=0.0):
+        out = np.zeros(1 << self.n)
+        check(L.lib().nwq_probs(self.h, float(readout_e), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    # -- state transfer
+    def _cdtype(self):
+        return np.complex128 if self.dtype == F64 else np.complex64
+
+    def copy(self):
+        """SV: amplitudes.  DM: rho as a row-major (2^n, 2^n) matrix."""
+        N = 1 << self.n
+        if self.kind == SV:
+            out = np.zeros(N, self._cdtype())
+        else:
+            out = np.zeros(N * N, self._cdtype())
+        check(L.lib().nwq_state_copy(self.h, _ptr(out), out.nbytes, 0))
+        if self.kind == DM:
+            return out.reshape(N, N).T.copy()
+        return out
+
+    def pauli(self):
+        out = np.zeros(1 << (2 * self.n), np.float64 if self.dtype == F64 else np.float32)
+        check(L.lib().nwq_dm_copy_pauli(self.h, _ptr(out), out.nbytes, 0))
+        return out
+
+    def load(self, data):
+        """SV: amplitude vector.  DM: row-major rho matrix."""
+        if self.kind == SV:
+            a = np.ascontiguousarray(data, self._cdtype())
+        else:
+            a = np.ascontiguousarray(np.asarray(data).T, self._cdtype()).reshape(-1)
+        check(L.lib().nwq_state_load(self.h, _ptr(a), a.nbytes, 0))
+
+
+class Plan:
+    def __init__(self, kind, n, gates, dtype=F64, noise=None, flags=0):
+        arr, keep = encode_gates(gates)
+        nm, keep2 = encode_noise(noise, n)
+        self.h = ctypes.c_void_p()
+        check(L.lib().nwq_plan_create(kind, n, dtype, arr, len(gates), ctypes.byref(nm) if nm is not None else None,
+                                      flags, None, ctypes.byref(self.h)))
+        self.ngates = len(gates)
+
+    def info(self):
+        s, o = ctypes.c_int(), ctypes.c_int()
+        b, f = ctypes.c_double(), ctypes.c_double()
+        tb = ctypes.c_size_t()
+        check(L.lib().nwq_plan_info(self.h, ctypes.byref(s), ctypes.byref(o), ctypes.byref(b), ctypes.byref(f),
+                                    ctypes.byref(tb)))
+        return dict(sweeps=s.value, ops=o.value, bytes=b.value, fma_per_elem=f.value, table_bytes=tb.value)
+
+    def layout(self):
+        info = self.info()
+        sw = (ctypes.c_int * max(info["sweeps"], 1))()
+        og = (ctypes.c_int * max(info["ops"], 1))()
+        on = (ctypes.c_int * max(info["ops"], 1))()
+        check(L.lib().nwq_plan_layout(self.h, sw, og, on))
+        return list(sw)[:info["sweeps"]], list(og)[:info["ops"]], list(on)[:info["ops"]]
+
+    def close(self):
+        if self.h:
+            L.lib().nwq_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

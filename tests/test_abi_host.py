@@ -1,0 +1,113 @@
+"""Host-side checks of the CUDA library (no GPU needed): it loads, exports
+every symbol the header declares, validates arguments, and its planner
+produces a valid schedule."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2401_06861_gb300 import _lib as L
+from paper_2401_06861_gb300 import inputs, sim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2401_06861_gb300 import build
+    build.build()
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "nwqgb.h")).read()
+    return sorted(set(re.findall(r"\b(nwq_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    syms = header_symbols()
+    assert len(syms) >= 20
+    lib = ctypes.CDLL(L.LIB_PATH)
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    lib = L.lib()
+    for s in header_symbols():
+        assert getattr(lib, s).argtypes is not None or s == "nwq_last_error", s
+
+
+def test_state_bytes():
+    assert sim.state_bytes(L.SV, 10, L.F64) == 16 << 10
+    assert sim.state_bytes(L.SV, 34, L.F32) == 8 << 34
+    assert sim.state_bytes(L.DM, 13, L.F64) == 8 << 26
+    assert sim.state_bytes(L.DM, 13, L.F32) == 4 << 26
+    assert sim.state_bytes(L.SV, 35, L.F64) == 0
+    assert sim.state_bytes(L.DM, 17, L.F64) == 0
+    assert sim.state_bytes(L.SV, 0, L.F64) == 0
+
+
+def test_invalid_arguments_fail_without_device():
+    h = ctypes.c_void_p()
+    assert L.lib().nwq_sv_create(0, L.F64, None, 0, None, ctypes.byref(h)) == L.EINVAL
+    assert L.lib().nwq_dm_create(20, L.F64, None, 0, None, ctypes.byref(h)) == L.EINVAL
+    assert L.lib().nwq_sv_create(4, 7, None, 0, None, ctypes.byref(h)) == L.EINVAL
+    assert b"unsupported" in L.lib().nwq_last_error()
+    with pytest.raises(L.NwqError):
+        sim.Plan(L.SV, 3, [inputs.gate("CX", (0, 3))])
+    with pytest.raises(L.NwqError):
+        sim.Plan(L.SV, 3, [inputs.gate("CX", (1, 1))])
+    with pytest.raises(L.NwqError):  # noise needs a density matrix
+        sim.Plan(L.SV, 3, [inputs.gate("X", (0,))], noise=inputs.noise_params(3))
+    with pytest.raises(L.NwqError):  # noise arrays shorter than the register
+        sim.Plan(L.DM, 4, [inputs.gate("X", (0,))], noise=inputs.noise_params(3))
+
+
+def _check_schedule(n, gates, kind, dtype, flags=0, noise=None):
+    p = sim.Plan(kind, n, gates, dtype, noise, flags)
+    sweeps, g0, ng = p.layout()
+    info = p.info()
+    assert sum(sweeps) == info["ops"] == len(g0)
+    # every gate folded into exactly one operator, in contiguous runs
+    covered = sorted((a, a + b) for a, b in zip(g0, ng))
+    pos = 0
+    for a, b in covered:
+        assert a == pos
+        pos = b
+    assert pos == len(gates)
+    # operators that share a qubit keep the gate order
+    qs = [set(gates[a][1]).union(*[set(gates[k][1]) for k in range(a, a + b)]) for a, b in zip(g0, ng)]
+    for i in range(len(g0)):
+        for j in range(i + 1, len(g0)):
+            if qs[i] & qs[j]:
+                assert g0[i] < g0[j]
+    return info
+
+
+@pytest.mark.parametrize("kind,dtype", [(L.SV, L.F64), (L.SV, L.F32), (L.DM, L.F64), (L.DM, L.F32)])
+@pytest.mark.parametrize("flags", [0, L.PLAN_PLAIN, L.PLAN_NO_MERGE])
+def test_planner_schedule_is_a_valid_reordering(kind, dtype, flags):
+    n = 9 if kind == L.SV else 6
+    gates = inputs.random_circuit(n, 300, 17)
+    noise = inputs.noise_params(n) if kind == L.DM else None
+    info = _check_schedule(n, gates, kind, dtype, flags, noise)
+    if flags == L.PLAN_PLAIN:
+        assert info["sweeps"] == len(gates)
+
+
+def test_planner_tfim_sweep_counts():
+    # n=13 noisy DM TFIM: 20 steps x (12 merged bond blocks + 13 RX) operators
+    g, noise = inputs.dm_noisy_tfim(13, 20)
+    info = _check_schedule(13, g, L.DM, L.F64, 0, noise)
+    assert info["ops"] == 20 * 25
+    assert info["sweeps"] <= 80
+    # the whole 10-qubit SV circuit fits one tile: one sweep
+    info = _check_schedule(10, inputs.tfim_trotter(10), L.SV, L.F64)
+    assert info["sweeps"] == 1
+    # large SV: fused plan moves far fewer bytes than the gate-by-gate plan
+    g, _ = inputs.large_sv_tfim(33)
+    fused = sim.Plan(L.SV, 33, g, L.F32).info()
+    plain = sim.Plan(L.SV, 33, g, L.F32, flags=L.PLAN_PLAIN).info()
+    assert fused["bytes"] < plain["bytes"] / 20
