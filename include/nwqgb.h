@@ -214,6 +214,25 @@ int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, size_t nt, 
  * 2^n doubles.  n <= 30.  Synchronises the stream. */
 int nwq_probs(nwq_state* st, double readout_e, double* out_host);
 
+/* Same result as nwq_expect_pauli_sum, computed without allocating any memory.
+ * The paper has no counterpart: this variant is for callers that cannot
+ * allocate device memory, because another allocator owns all of it (a
+ * framework's caching pool, a serving loop admitting work against a fixed
+ * memory budget) or because a latency-critical loop must neither wait for
+ * nor fail on an allocation.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine; its device scratch is one library-owned array of at
+ * most 192 KiB that every GPU which loads the library keeps until the
+ * process exits.
+ *   - nt <= NWQ_NOALLOC_MAX_TERMS, else NWQ_EINVAL (nothing is computed);
+ *   - the first call on a device looks up the scratch array's device address
+ *     on that device; make that first call before any stream capture;
+ *   - all calls share the scratch array (it keeps the last call's contents),
+ *     so calls that overlap on the GPU race: serialise them;
+ *   - arguments, flags, results and synchronisation as nwq_expect_pauli_sum. */
+#define NWQ_NOALLOC_MAX_TERMS 256
+int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term* terms, size_t nt, double* out_host,
+                                 uint32_t flags);
+
 /* ---------------------------------------------------------------- batched VQE */
 
 /* Evaluate one parametrised circuit on nsets parameter sets in one launch

@@ -21,6 +21,7 @@ SV, DM = 1, 2
 PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE = 0, 1, 2, 4
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
+NOALLOC_MAX_TERMS = 256
 
 GATE_KIND = {"ID": 1, "X": 2, "Y": 3, "Z": 4, "H": 5, "S": 6, "SDG": 7, "T": 8, "TDG": 9, "SX": 10,
              "RX": 11, "RY": 12, "RZ": 13, "P": 14, "U3": 15, "MAT1": 16,
@@ -81,6 +82,7 @@ def lib():
         "nwq_plan_layout": (i32, [vp, P(i32), P(i32), P(i32)]),
         "nwq_plan_destroy": (i32, [vp]),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
+        "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_probs": (i32, [vp, dbl, P(dbl)]),
         "nwq_batch_energy": (i32, [i32, i32, P(Gate), sz, vp, i32, i32, P(PauliTerm), sz, P(dbl), i32, vp, vp]),
         "nwq_last_error": (ctypes.c_char_p, []),

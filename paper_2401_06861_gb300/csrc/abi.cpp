@@ -16,6 +16,7 @@
 #include "../../include/nwqgb.h"
 #include "kernels.hpp"
 #include "planner.hpp"
+#include "state.hpp"
 
 using namespace nwq;
 
@@ -35,20 +36,11 @@ static int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-struct nwq_plan {
-  Plan p;
-};
-
-struct nwq_state {
-  int kind = 0, n = 0, dtype = 0, B = 0;
-  void* buf = nullptr;
-  size_t bytes = 0;
-  bool owned = false;
-  cudaStream_t stream = nullptr;
-  int device = 0, sm_count = 1;
-  std::unique_ptr<nwq_plan> p2r, r2p;               // DM conversions
-  std::map<double, std::unique_ptr<nwq_plan>> probs; // readout / transform plans keyed by e
-};
+// Error reporting shared with the other translation units of the library.
+int nwq::set_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
 
 // ------------------------------------------------------------------ helpers
 static bool f64_of(int dtype) { return dtype == NWQ_F64; }
