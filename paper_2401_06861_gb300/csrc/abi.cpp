@@ -55,12 +55,12 @@ extern "C" size_t nwq_state_bytes(int kind, int n, int dtype) {
 static void plan_options(int kind, int dtype, uint32_t flags, PlanOptions& o) {
   bool cplx = kind == NWQ_SV;
   size_t esz = (cplx ? 2 : 1) * (dtype == NWQ_F64 ? 8 : 4);
-  // 64 KiB tiles (three resident CTAs per SM), >= 128 contiguous bytes
-  o.tile_bits = esz == 16 ? 12 : esz == 8 ? 13 : 14;
+  // two 32 KiB ping-pong tiles per CTA (several resident CTAs per SM), >= 128 contiguous bytes
+  o.tile_bits = esz == 16 ? 11 : esz == 8 ? 12 : 13;
   o.min_low = esz == 16 ? 3 : esz == 8 ? 4 : 5;
   if (const char* tb = std::getenv("NWQ_TILE_BITS")) {
     int v = std::atoi(tb);
-    if (v >= 4 && v <= kMaxTileBits && (esz << v) <= (size_t)kMaxDynSmem) o.tile_bits = v;
+    if (v >= 4 && v <= kMaxTileBits && (2 * esz << v) <= (size_t)kMaxDynSmem) o.tile_bits = v;
   }
   o.plain = (flags & NWQ_PLAN_PLAIN) != 0;
   o.merge = !(flags & (NWQ_PLAN_PLAIN | NWQ_PLAN_NO_MERGE));

@@ -14,7 +14,8 @@ extern std::atomic<unsigned long long> g_launches;
 
 constexpr int kSweepThreads = 256;
 constexpr int kExpectChunk = 16;         // terms per expectation launch
-constexpr int kMaxDynSmem = 160 * 1024;  // dynamic shared memory cap of the sweep kernel
+constexpr int kMaxDynSmem = 200 * 1024;      // dynamic shared memory cap of the sweep kernel
+constexpr int kTableSmemLimit = 112 * 1024;  // stage a sweep's tables in shared memory up to this total
 
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
                          const void* ents, int sm_count, cudaStream_t s);

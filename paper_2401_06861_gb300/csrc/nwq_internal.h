@@ -72,6 +72,8 @@ struct SweepDesc {
   int32_t h;       // high tile bits
   int32_t nops;    // operators in this sweep
   uint32_t op0;    // index of the first operator
+  uint32_t ent0;   // index of the first entry of the sweep's operators
+  uint32_t nent;   // number of entries of the sweep's operators
   uint8_t hpos[kMaxHigh];  // global position of high tile bit i (ascending, >= m)
   uint8_t pad;
 };

@@ -570,11 +570,12 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
   const size_t esz = plan.ent_bytes;
   const bool f64 = plan.dtype == NWQ_F64;
   size_t nent = 0;
-  for (const SweepDesc& sd : plan.sweeps) {
+  for (SweepDesc& sd : plan.sweeps) {
     int local[64];
     for (int b = 0; b < 64; b++) local[b] = -1;
     for (int b = 0; b < sd.m; b++) local[b] = b;
     for (int i = 0; i < sd.h; i++) local[sd.hpos[i]] = sd.m + i;
+    const size_t sweep_ent0 = nent;
     for (int s = 0; s < sd.nops; s++) {
       const BitOp& op = ops[order[sd.op0 + s]];
       plan.fma_per_elem += op_cost(op, cplx);
@@ -654,6 +655,8 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
       }
       plan.ops.push_back(d);
     }
+    sd.ent0 = (uint32_t)sweep_ent0;
+    sd.nent = (uint32_t)(nent - sweep_ent0);
   }
   double state_bytes = (double)plan.elem_bytes * (double)(1ull << B);
   plan.bytes = 2.0 * state_bytes * (double)plan.sweeps.size();

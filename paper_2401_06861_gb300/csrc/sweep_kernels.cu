@@ -65,87 +65,133 @@ __device__ __forceinline__ float2 signed_base(float2 v, int base) {
   return make_float2(signed_base(v.x, base), signed_base(v.y, base));
 }
 
-// ------------------------------------------------------------------ real operators
-// Output row i = [+-x[boff]] + sum_e c_e x[off_e].  Loops over entries are
-// kept rolled (warp-uniform trip counts) so that no predicated-off FP64
-// instruction occupies the pipe; all table reads are warp-uniform.
+// ------------------------------------------------------------------ operator application
+// Each operator is applied out of place, src tile -> dst tile (ping-pong in
+// shared memory), one output row at a time: a warp takes one row i of the
+// operator and 32*G of its 2^(T-k) groups (lane l handles groups
+// c0 + u*32 + l, u < G, so the lanes of a warp touch consecutive shared
+// memory words).  The row's entries are warp-uniform; each entry feeds G
+// independent FMA chains.  Rows are either copies (identity / +-unit entry,
+// integer operations only) or a unit-entry start plus one FMA per remaining
+// entry; entry loops stay rolled so no predicated-off FP64 instruction
+// occupies the FP64 pipe, the unit this GPU has least of.
+constexpr int kILP = 4;
+
+template <int K>
+__device__ __forceinline__ void group_bases(uint32_t c0, uint32_t ngroups, const uint8_t* slb, uint32_t (&b)[kILP],
+                                            bool (&valid)[kILP]) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int u = 0; u < kILP; u++) {
+    uint32_t g = c0 + (uint32_t)u * 32u + lane;
+    valid[u] = g < ngroups;
+    b[u] = insert_zeros<K>(valid[u] ? g : 0u, slb);
+  }
+}
+
 template <int K, class R>
-__device__ __forceinline__ void apply_real(R* __restrict__ tile, int T, const DevOp& op,
-                                           const EntR<R>* __restrict__ ents) {
+__device__ __forceinline__ void apply_real(const R* __restrict__ src, R* __restrict__ dst, int T, const DevOp& op,
+                                           const EntR<R>* __restrict__ e0) {
   constexpr int D = 1 << K;
   const uint32_t ngroups = 1u << (T - K);
-  const EntR<R>* e0 = ents + op.ent;
-  for (uint32_t g = threadIdx.x; g < ngroups; g += kSweepThreads) {
-    const uint32_t base = insert_zeros<K>(g, op.slb);
-    R out[D];
+  const uint32_t per = 32u * kILP;
+  const uint32_t nchunk = (ngroups + per - 1) / per;
+  const uint32_t nitems = (uint32_t)D * nchunk;
+  for (uint32_t item = threadIdx.x >> 5; item < nitems; item += kSweepThreads / 32) {
+    const uint32_t i = item / nchunk, c0 = (item % nchunk) * per;
+    const RowMeta rm = op.row[i];
+    uint32_t b[kILP];
+    bool valid[kILP];
+    group_bases<K>(c0, ngroups, op.slb, b, valid);
+    R acc[kILP];
+    if (rm.kind == ROW_ID) {
 #pragma unroll
-    for (int i = 0; i < D; i++) {
-      const RowMeta& rm = op.row[i];
-      if (rm.kind == ROW_ID) continue;
-      R acc = signed_base(tile[base + rm.boff], rm.base);
+      for (int u = 0; u < kILP; u++) acc[u] = src[b[u] + rm.out];
+    } else {
+#pragma unroll
+      for (int u = 0; u < kILP; u++) acc[u] = signed_base(src[b[u] + rm.boff], rm.base);
       if (rm.kind == ROW_GEN) {
         const EntR<R>* e = e0 + rm.beg;
         const int cnt = rm.cnt[0];
 #pragma unroll 1
-        for (int c = 0; c < cnt; c++) acc = fma(e[c].c, tile[base + e[c].off], acc);
+        for (int c = 0; c < cnt; c++) {
+          const R cf = e[c].c;
+          const uint32_t off = e[c].off;
+#pragma unroll
+          for (int u = 0; u < kILP; u++) acc[u] = fma(cf, src[b[u] + off], acc[u]);
+        }
       }
-      out[i] = acc;
     }
 #pragma unroll
-    for (int i = 0; i < D; i++)
-      if (op.row[i].kind != ROW_ID) tile[base + op.row[i].out] = out[i];
+    for (int u = 0; u < kILP; u++)
+      if (valid[u]) dst[b[u] + rm.out] = acc[u];
   }
 }
 
-// ------------------------------------------------------------------ complex operators
-// Same row form with three kind-homogeneous entry lists: real coefficients
-// (2 FMA), imaginary coefficients (2 FMA) and general ones (4 FMA).
 template <int K, class R>
-__device__ __forceinline__ void apply_cplx(typename Cplx<R>::T* __restrict__ tile, int T, const DevOp& op,
-                                           const EntC<R>* __restrict__ ents) {
+__device__ __forceinline__ void apply_cplx(const typename Cplx<R>::T* __restrict__ src, typename Cplx<R>::T* __restrict__ dst,
+                                           int T, const DevOp& op, const EntC<R>* __restrict__ e0) {
   using C = typename Cplx<R>::T;
   constexpr int D = 1 << K;
   const uint32_t ngroups = 1u << (T - K);
-  const EntC<R>* e0 = ents + op.ent;
-  for (uint32_t g = threadIdx.x; g < ngroups; g += kSweepThreads) {
-    const uint32_t base = insert_zeros<K>(g, op.slb);
-    C out[D];
+  const uint32_t per = 32u * kILP;
+  const uint32_t nchunk = (ngroups + per - 1) / per;
+  const uint32_t nitems = (uint32_t)D * nchunk;
+  for (uint32_t item = threadIdx.x >> 5; item < nitems; item += kSweepThreads / 32) {
+    const uint32_t i = item / nchunk, c0 = (item % nchunk) * per;
+    const RowMeta rm = op.row[i];
+    uint32_t b[kILP];
+    bool valid[kILP];
+    group_bases<K>(c0, ngroups, op.slb, b, valid);
+    C acc[kILP];
+    if (rm.kind == ROW_ID) {
 #pragma unroll
-    for (int i = 0; i < D; i++) {
-      const RowMeta& rm = op.row[i];
-      if (rm.kind == ROW_ID) continue;
-      C acc = signed_base(tile[base + rm.boff], rm.base);
+      for (int u = 0; u < kILP; u++) acc[u] = src[b[u] + rm.out];
+    } else {
+#pragma unroll
+      for (int u = 0; u < kILP; u++) acc[u] = signed_base(src[b[u] + rm.boff], rm.base);
       if (rm.kind == ROW_GEN) {
         const EntC<R>* e = e0 + rm.beg;
-        const int c0 = rm.cnt[0], c1 = c0 + rm.cnt[1], c2 = c1 + rm.cnt[2];
+        const int c0n = rm.cnt[0], c1n = c0n + rm.cnt[1], c2n = c1n + rm.cnt[2];
         int c = 0;
 #pragma unroll 1
-        for (; c < c0; c++) {
-          const C x = tile[base + e[c].off];
+        for (; c < c0n; c++) {
           const R re = e[c].re;
-          acc.x = fma(re, x.x, acc.x);
-          acc.y = fma(re, x.y, acc.y);
+          const uint32_t off = e[c].off;
+#pragma unroll
+          for (int u = 0; u < kILP; u++) {
+            const C x = src[b[u] + off];
+            acc[u].x = fma(re, x.x, acc[u].x);
+            acc[u].y = fma(re, x.y, acc[u].y);
+          }
         }
 #pragma unroll 1
-        for (; c < c1; c++) {
-          const C x = tile[base + e[c].off];
+        for (; c < c1n; c++) {
           const R im = e[c].im;
-          acc.x = fma(-im, x.y, acc.x);
-          acc.y = fma(im, x.x, acc.y);
+          const uint32_t off = e[c].off;
+#pragma unroll
+          for (int u = 0; u < kILP; u++) {
+            const C x = src[b[u] + off];
+            acc[u].x = fma(-im, x.y, acc[u].x);
+            acc[u].y = fma(im, x.x, acc[u].y);
+          }
         }
 #pragma unroll 1
-        for (; c < c2; c++) {
-          const C x = tile[base + e[c].off];
+        for (; c < c2n; c++) {
           const R re = e[c].re, im = e[c].im;
-          acc.x = fma(re, x.x, fma(-im, x.y, acc.x));
-          acc.y = fma(re, x.y, fma(im, x.x, acc.y));
+          const uint32_t off = e[c].off;
+#pragma unroll
+          for (int u = 0; u < kILP; u++) {
+            const C x = src[b[u] + off];
+            acc[u].x = fma(re, x.x, fma(-im, x.y, acc[u].x));
+            acc[u].y = fma(re, x.y, fma(im, x.x, acc[u].y));
+          }
         }
       }
-      out[i] = acc;
     }
 #pragma unroll
-    for (int i = 0; i < D; i++)
-      if (op.row[i].kind != ROW_ID) tile[base + op.row[i].out] = out[i];
+    for (int u = 0; u < kILP; u++)
+      if (valid[u]) dst[b[u] + rm.out] = acc[u];
   }
 }
 
@@ -162,22 +208,39 @@ __device__ __forceinline__ uint64_t deposit(uint64_t v, uint64_t mask) {
   return out;
 }
 
-// Resident CTAs per SM the register budget is tuned for (no spills at these bounds).
 template <class R, bool CPLX>
-struct SweepOcc {
-  static constexpr int value = (sizeof(R) == 4 && !CPLX) ? 3 : ((sizeof(R) == 8 && CPLX) ? 1 : 2);
-};
+using ElemT = typename std::conditional<CPLX, typename Cplx<R>::T, R>::type;
+template <class R, bool CPLX>
+using EntT = typename std::conditional<CPLX, EntC<R>, EntR<R>>::type;
 
-template <class R, bool CPLX>
-__global__ void __launch_bounds__(kSweepThreads, SweepOcc<R, CPLX>::value) sweep_kernel(void* __restrict__ state_v, uint64_t ntiles,
-                                                                SweepDesc sd, const DevOp* __restrict__ ops,
-                                                                const void* __restrict__ ents_v) {
-  using E = typename std::conditional<CPLX, typename Cplx<R>::T, R>::type;
+// Shared memory: tile A | tile B | the sweep's operators | their entries (when
+// TBL; otherwise the tables are read from global memory through L1).
+template <class R, bool CPLX, bool TBL>
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(void* __restrict__ state_v, uint64_t ntiles, SweepDesc sd,
+                                                              const DevOp* __restrict__ ops_g,
+                                                              const void* __restrict__ ents_v) {
+  using E = ElemT<R, CPLX>;
+  using Ent = EntT<R, CPLX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  E* tile = reinterpret_cast<E*>(smem_raw);
+  const int T = sd.T;
+  E* tileA = reinterpret_cast<E*>(smem_raw);
+  E* tileB = tileA + (1u << T);
+  const DevOp* ops = ops_g + sd.op0;
+  const Ent* ents = reinterpret_cast<const Ent*>(ents_v) + sd.ent0;  // entry e of the sweep at ents[e - ent0]
+  if constexpr (TBL) {
+    DevOp* sops = reinterpret_cast<DevOp*>(tileB + (1u << T));
+    Ent* sents = reinterpret_cast<Ent*>(sops + sd.nops);
+    const uint4* s1 = reinterpret_cast<const uint4*>(ops_g + sd.op0);
+    uint4* d1 = reinterpret_cast<uint4*>(sops);
+    for (uint32_t v = threadIdx.x; v < sd.nops * (sizeof(DevOp) / 16); v += kSweepThreads) d1[v] = s1[v];
+    const uint32_t* s2 = reinterpret_cast<const uint32_t*>(reinterpret_cast<const Ent*>(ents_v) + sd.ent0);
+    uint32_t* d2 = reinterpret_cast<uint32_t*>(sents);
+    for (uint32_t v = threadIdx.x; v < sd.nent * (sizeof(Ent) / 4); v += kSweepThreads) d2[v] = s2[v];
+    ops = sops;
+    ents = sents;
+  }
   E* state = reinterpret_cast<E*>(state_v);
   constexpr int VPE = 16 / sizeof(E);  // elements per 16-byte vector
-  const int T = sd.T;
   const uint32_t nvec = (1u << T) / VPE;
   const int lvpc = sd.m - __ffs(VPE) + 1;  // log2(vectors per contiguous chunk)
   const uint32_t vpc_mask = (1u << lvpc) - 1u;
@@ -188,61 +251,77 @@ __global__ void __launch_bounds__(kSweepThreads, SweepOcc<R, CPLX>::value) sweep
     for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
       uint32_t j = v >> lvpc;
       uint64_t off = base + deposit(j, sd.hmask) + (uint64_t)(v & vpc_mask) * VPE;
-      reinterpret_cast<uint4*>(tile)[v] = __ldg(reinterpret_cast<const uint4*>(state + off));
+      reinterpret_cast<uint4*>(tileA)[v] = __ldg(reinterpret_cast<const uint4*>(state + off));
     }
     __syncthreads();
+    E* src = tileA;
+    E* dst = tileB;
     for (int o = 0; o < sd.nops; o++) {
-      const DevOp& op = ops[sd.op0 + o];
+      const DevOp& op = ops[o];
+      const Ent* e0 = ents + (op.ent - sd.ent0);
       if constexpr (CPLX) {
-        const EntC<R>* ents = reinterpret_cast<const EntC<R>*>(ents_v);
         switch (op.k) {
-          case 1: apply_cplx<1, R>(tile, T, op, ents); break;
-          case 2: apply_cplx<2, R>(tile, T, op, ents); break;
-          case 3: apply_cplx<3, R>(tile, T, op, ents); break;
-          default: apply_cplx<4, R>(tile, T, op, ents); break;
+          case 1: apply_cplx<1, R>(src, dst, T, op, e0); break;
+          case 2: apply_cplx<2, R>(src, dst, T, op, e0); break;
+          case 3: apply_cplx<3, R>(src, dst, T, op, e0); break;
+          default: apply_cplx<4, R>(src, dst, T, op, e0); break;
         }
       } else {
-        const EntR<R>* ents = reinterpret_cast<const EntR<R>*>(ents_v);
         switch (op.k) {
-          case 1: apply_real<1, R>(tile, T, op, ents); break;
-          case 2: apply_real<2, R>(tile, T, op, ents); break;
-          case 3: apply_real<3, R>(tile, T, op, ents); break;
-          default: apply_real<4, R>(tile, T, op, ents); break;
+          case 1: apply_real<1, R>(src, dst, T, op, e0); break;
+          case 2: apply_real<2, R>(src, dst, T, op, e0); break;
+          case 3: apply_real<3, R>(src, dst, T, op, e0); break;
+          default: apply_real<4, R>(src, dst, T, op, e0); break;
         }
       }
       __syncthreads();
+      E* t = src;
+      src = dst;
+      dst = t;
     }
     for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
       uint32_t j = v >> lvpc;
       uint64_t off = base + deposit(j, sd.hmask) + (uint64_t)(v & vpc_mask) * VPE;
-      reinterpret_cast<uint4*>(state + off)[0] = reinterpret_cast<const uint4*>(tile)[v];
+      reinterpret_cast<uint4*>(state + off)[0] = reinterpret_cast<const uint4*>(src)[v];
     }
     __syncthreads();
   }
 }
 
-template <class R, bool CPLX>
-static cudaError_t launch_sweep_t(void* state, int B, const SweepDesc& sd, const DevOp* ops, const void* ents,
-                                  int sm_count, cudaStream_t s) {
-  using E = typename std::conditional<CPLX, typename Cplx<R>::T, R>::type;
-  size_t smem = sizeof(E) << sd.T;
-  static bool attr_set = false;  // per instantiation
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <class R, bool CPLX, bool TBL>
+static cudaError_t launch_sweep_tt(void* state, int B, const SweepDesc& sd, const DevOp* ops, const void* ents,
+                                   size_t smem, int sm_count, cudaStream_t s) {
+  static int attr_dev = -1;  // per instantiation: the attribute is set once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, CPLX, TBL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxDynSmem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_dev = dev;
   }
   uint64_t ntiles = 1ull << (B - sd.T);
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, CPLX>, kSweepThreads, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<R, CPLX, TBL>, kSweepThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   uint64_t grid = (uint64_t)sm_count * per_sm;
   if (grid > ntiles) grid = ntiles;
-  sweep_kernel<R, CPLX><<<(unsigned)grid, kSweepThreads, smem, s>>>(state, ntiles, sd, ops, ents);
+  sweep_kernel<R, CPLX, TBL><<<(unsigned)grid, kSweepThreads, smem, s>>>(state, ntiles, sd, ops, ents);
   g_launches += 1;
   return cudaGetLastError();
+}
+
+template <class R, bool CPLX>
+static cudaError_t launch_sweep_t(void* state, int B, const SweepDesc& sd, const DevOp* ops, const void* ents,
+                                  int sm_count, cudaStream_t s) {
+  using E = ElemT<R, CPLX>;
+  using Ent = EntT<R, CPLX>;
+  size_t tiles = 2 * (sizeof(E) << sd.T);
+  size_t table = sd.nops * sizeof(DevOp) + sd.nent * sizeof(Ent);
+  if (tiles + table <= (size_t)kTableSmemLimit)
+    return launch_sweep_tt<R, CPLX, true>(state, B, sd, ops, ents, tiles + table, sm_count, s);
+  return launch_sweep_tt<R, CPLX, false>(state, B, sd, ops, ents, tiles, sm_count, s);
 }
 
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
