@@ -235,14 +235,56 @@ int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term* terms, siz
 
 /* ---------------------------------------------------------------- batched VQE */
 
-/* Evaluate one parametrised circuit on nsets parameter sets in one launch
- * (the VQE inner loop of paper Sec. III).  Each set starts from |0..0>, runs
- * the gates (gate k takes theta[0] = params[s * nparams + param_idx] when
- * param_idx >= 0), and produces ne energies
- *   out[s * ne + e] = sum_t coeffs[e * nt + t] <psi_s| P_t |psi_s>.
- * params: device, nsets * nparams doubles.  out: device, nsets * ne doubles.
- * terms: host (coeff field ignored).  coeffs: host, ne * nt doubles.
- * n <= 13 (F64) or 14 (F32).  Asynchronous on stream. */
+/* Batched evaluation of parametrised circuits: the inner loop of the VQE use
+ * case of paper Sec. III (VQE for the Ising model, where an optimiser such
+ * as COBYLA asks for energies of many parameter sets).  Every job starts
+ * from |0..0>, runs its template's gates with theta[0] of gate k taken from
+ * params[job * nparams + param_idx] when param_idx >= 0, and produces the
+ * template's ne energies
+ *   out[job * out_stride + e] = sum_t coeffs[e * nterms + t] <P_t> / <psi|psi>
+ * (the division removes the norm drift of FP32 storage; <psi|psi> is
+ * written to norms[job] when norms is not NULL).  One CTA evaluates one job
+ * with the whole 2^n state in shared memory; jobs of different templates
+ * (different qubit counts) share one launch.  Limits: n <= 13 (F64) or
+ * 14 (F32); gate kinds CX, CZ, SWAP, RZZ and every one-qubit kind (angles
+ * from parameters on RX, RY, RZ, P, U3 and RZZ); MAT2 is not supported. */
+typedef struct {
+  int32_t n;                    /* qubits */
+  const nwq_gate* gates;        /* host, read during nwq_batch_create */
+  size_t ngates;
+  const nwq_pauli_term* terms;  /* host; coeff fields ignored */
+  size_t nterms;
+  const double* coeffs;         /* host, ne * nterms energy weights */
+  int32_t ne;                   /* energies per job (>= 1) */
+} nwq_batch_template;
+
+typedef struct nwq_batch nwq_batch;
+
+enum nwq_batch_flags {
+  NWQ_BATCH_GRAPH = 1u  /* launch through a captured CUDA graph, captured on first use and
+                           recaptured when pointers or the job count change */
+};
+
+/* Validate and upload templates (synchronous; allocates device tables). */
+int nwq_batch_create(int dtype, const nwq_batch_template* templates, int ntemplates, int nparams,
+                     nwq_batch** out);
+
+/* Evaluate njobs jobs, asynchronous on stream.  params: device, njobs *
+ * nparams doubles.  job_template: device, njobs ints (template of each job;
+ * NULL = template 0 for all jobs, allowed only with one template; a job whose
+ * index is out of range gets NaN energies).  out:
+ * device, njobs * out_stride doubles (out_stride >= the largest ne).
+ * norms: device, njobs doubles, or NULL.  Runs of one batch object must not
+ * overlap (they share its work-queue counter). */
+int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* job_template, int njobs, double* out,
+                  int out_stride, double* norms, void* stream, uint32_t flags);
+
+/* Wait for the device and free the batch's tables. */
+int nwq_batch_destroy(nwq_batch* b);
+
+/* One template, nsets parameter sets: create + run + destroy.  params and
+ * out are device pointers (out: nsets * ne doubles); terms, coeffs host.
+ * Synchronises the stream before returning. */
 int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t ng, const double* params,
                      int nsets, int nparams, const nwq_pauli_term* terms, size_t nt,
                      const double* coeffs, int ne, double* out, void* stream);

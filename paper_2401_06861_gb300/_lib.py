@@ -22,6 +22,7 @@ PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE = 0, 1, 2, 4
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
 NOALLOC_MAX_TERMS = 256
+BATCH_GRAPH = 1
 
 GATE_KIND = {"ID": 1, "X": 2, "Y": 3, "Z": 4, "H": 5, "S": 6, "SDG": 7, "T": 8, "TDG": 9, "SX": 10,
              "RX": 11, "RY": 12, "RZ": 13, "P": 14, "U3": 15, "MAT1": 16,
@@ -43,6 +44,12 @@ class NoiseModel(ctypes.Structure):
                 ("T2_us", ctypes.POINTER(ctypes.c_double)), ("t1q_ns", ctypes.c_double),
                 ("t2q_ns", ctypes.c_double), ("p1", ctypes.c_double), ("p2", ctypes.c_double),
                 ("readout_e", ctypes.c_double)]
+
+
+class BatchTemplate(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("gates", ctypes.POINTER(Gate)), ("ngates", ctypes.c_size_t),
+                ("terms", ctypes.POINTER(PauliTerm)), ("nterms", ctypes.c_size_t),
+                ("coeffs", ctypes.POINTER(ctypes.c_double)), ("ne", ctypes.c_int32)]
 
 
 class NwqError(RuntimeError):
@@ -85,6 +92,9 @@ def lib():
         "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_probs": (i32, [vp, dbl, P(dbl)]),
         "nwq_batch_energy": (i32, [i32, i32, P(Gate), sz, vp, i32, i32, P(PauliTerm), sz, P(dbl), i32, vp, vp]),
+        "nwq_batch_create": (i32, [i32, P(BatchTemplate), i32, i32, pp]),
+        "nwq_batch_run": (i32, [vp, vp, vp, i32, vp, i32, vp, vp, u32]),
+        "nwq_batch_destroy": (i32, [vp]),
         "nwq_last_error": (ctypes.c_char_p, []),
         "nwq_device_sync": (i32, [vp]),
         "nwq_launch_count": (ctypes.c_uint64, []),

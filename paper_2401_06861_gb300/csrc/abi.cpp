@@ -528,10 +528,3 @@ extern "C" const char* nwq_last_error(void) { return g_err.c_str(); }
 
 extern "C" uint64_t nwq_launch_count(void) { return (uint64_t)g_launches.load(); }
 
-extern "C" int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t ng, const double* params, int nsets,
-                                int nparams, const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne,
-                                double* out, void* stream) {
-  (void)n; (void)dtype; (void)gates; (void)ng; (void)params; (void)nsets; (void)nparams;
-  (void)terms; (void)nt; (void)coeffs; (void)ne; (void)out; (void)stream;
-  return fail(NWQ_EUNSUPPORTED, "batched energy kernel not built");
-}

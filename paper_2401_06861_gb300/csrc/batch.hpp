@@ -1,0 +1,49 @@
+// Device tables of the batched parametrised-circuit kernel.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nwq {
+
+constexpr int kBatchThreads = 256;
+
+// Gate types of the batched kernel.
+enum : uint8_t { BT_FIXED1 = 0, BT_CX, BT_CZ, BT_SWAP, BT_RX, BT_RY, BT_RZ, BT_P, BT_U3, BT_RZZ };
+
+struct BGate {
+  uint8_t type;   // BT_*
+  uint8_t cls;    // BT_FIXED1: structure class of m (dense / real / diagonal)
+  uint8_t q0, q1;
+  int32_t pidx;   // parameter slot of theta[0], -1 = fixed
+  double th[3];
+  double m[8];    // BT_FIXED1: 2x2 complex, re/im interleaved
+};
+
+struct BTemplate {
+  int32_t n, g0, ng, t0, nt, c0, ne, pad;
+};
+
+struct BTerm {
+  uint32_t x, z;
+  int32_t y;  // |x & z| mod 4
+  int32_t pad;
+};
+
+struct BatchArgs {
+  const BGate* gates;
+  const BTemplate* templates;
+  const BTerm* terms;
+  const double* coeffs;
+  const double* params;
+  const int32_t* job_template;  // NULL = every job uses template 0
+  double* out;
+  double* norms;                // optional per-job <psi|psi>
+  int* counter;                 // work-queue head (reset before each launch)
+  int njobs, nparams, out_stride, ntemplates;
+  int max_n, max_gates, max_terms;
+};
+
+size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms);
+cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s);
+
+}  // namespace nwq

@@ -1,0 +1,256 @@
+// Host side of the batched parametrised-circuit evaluation: validation,
+// device tables, launches and CUDA-graph replay for repeated runs (a VQE
+// optimiser calls the same batch with new parameters every iteration).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nwqgb.h"
+#include "batch.hpp"
+#include "kernels.hpp"
+#include "planner.hpp"
+#include "state.hpp"
+
+using namespace nwq;
+
+struct nwq_batch {
+  int dtype = 0, nparams = 0, ntemplates = 0;
+  int max_n = 0, max_gates = 0, max_terms = 0, max_ne = 0;
+  int device = 0, sm_count = 1;
+  void* dev = nullptr;  // tables + work-queue counter
+  const BGate* gates = nullptr;
+  const BTemplate* templates = nullptr;
+  const BTerm* terms = nullptr;
+  const double* coeffs = nullptr;
+  int* counter = nullptr;
+  // captured launch for repeated runs with the same pointers and job count
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  BatchArgs cap_args{};
+};
+
+static bool lower_batch_gate(const nwq_gate& g, int n, int nparams, BGate& b, std::string& err) {
+  std::memset(&b, 0, sizeof(b));
+  b.pidx = g.param_idx;
+  b.q0 = (uint8_t)g.q[0];
+  b.q1 = (uint8_t)g.q[1];
+  for (int k = 0; k < 3; k++) b.th[k] = g.theta[k];
+  bool two = g.kind >= NWQ_GATE_CX;
+  if (g.q[0] < 0 || g.q[0] >= n || (two && (g.q[1] < 0 || g.q[1] >= n || g.q[1] == g.q[0]))) {
+    err = "gate qubit out of range";
+    return false;
+  }
+  if (g.param_idx >= nparams || g.param_idx < -1) {
+    err = "parameter index out of range";
+    return false;
+  }
+  bool param_ok = true;
+  switch (g.kind) {
+    case NWQ_GATE_CX: b.type = BT_CX; param_ok = false; break;
+    case NWQ_GATE_CZ: b.type = BT_CZ; param_ok = false; break;
+    case NWQ_GATE_SWAP: b.type = BT_SWAP; param_ok = false; break;
+    case NWQ_GATE_RZZ: b.type = BT_RZZ; break;
+    case NWQ_GATE_RX: b.type = BT_RX; break;
+    case NWQ_GATE_RY: b.type = BT_RY; break;
+    case NWQ_GATE_RZ: b.type = BT_RZ; break;
+    case NWQ_GATE_P: b.type = BT_P; break;
+    case NWQ_GATE_U3: b.type = BT_U3; break;
+    case NWQ_GATE_MAT2:
+      err = "MAT2 is not supported in batched evaluation";
+      return false;
+    default: {
+      cd U[16];
+      if (gate_matrix(g, g.theta[0], U) != 1) {
+        err = "unknown gate kind or missing matrix";
+        return false;
+      }
+      b.type = BT_FIXED1;
+      param_ok = false;
+      bool real = true, diag = U[1] == cd(0.0) && U[2] == cd(0.0);
+      for (int k = 0; k < 4; k++) {
+        b.m[2 * k] = U[k].real();
+        b.m[2 * k + 1] = U[k].imag();
+        real &= U[k].imag() == 0.0;
+      }
+      b.cls = diag ? 2 : (real ? 1 : 0);  // BG_DIAG / BG_REAL / BG_DENSE
+    }
+  }
+  if (!param_ok && g.param_idx >= 0) {
+    err = "parameter index on a gate without an angle";
+    return false;
+  }
+  return true;
+}
+
+extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntemplates, int nparams,
+                                nwq_batch** out) {
+  if (!out || !t || ntemplates < 1 || nparams < 0) return set_error(NWQ_EINVAL, "bad batch arguments");
+  *out = nullptr;
+  if (dtype != NWQ_F32 && dtype != NWQ_F64) return set_error(NWQ_EINVAL, "unsupported dtype");
+  const int nmax = dtype == NWQ_F64 ? 13 : 14;
+  std::vector<BGate> gates;
+  std::vector<BTemplate> tmpl;
+  std::vector<BTerm> terms;
+  std::vector<double> coeffs;
+  auto b = std::make_unique<nwq_batch>();
+  for (int k = 0; k < ntemplates; k++) {
+    const nwq_batch_template& tk = t[k];
+    if (tk.n < 1 || tk.n > nmax) return set_error(NWQ_EINVAL, "batch template qubit count outside [1, 13] (F64) / [1, 14] (F32)");
+    if ((tk.ngates && !tk.gates) || (tk.nterms && !tk.terms) || tk.ne < 1 || !tk.coeffs)
+      return set_error(NWQ_EINVAL, "batch template with NULL tables or no energies");
+    BTemplate bt{};
+    bt.n = tk.n;
+    bt.g0 = (int)gates.size();
+    bt.ng = (int)tk.ngates;
+    bt.t0 = (int)terms.size();
+    bt.nt = (int)tk.nterms;
+    bt.c0 = (int)coeffs.size();
+    bt.ne = tk.ne;
+    std::string err;
+    for (size_t i = 0; i < tk.ngates; i++) {
+      BGate g;
+      if (tk.gates[i].reserved || tk.gates[i].reserved2) return set_error(NWQ_EINVAL, "reserved gate field not 0");
+      if (!lower_batch_gate(tk.gates[i], tk.n, nparams, g, err)) return set_error(NWQ_EINVAL, err.c_str());
+      gates.push_back(g);
+    }
+    const uint64_t qmask = (1ull << tk.n) - 1;
+    for (size_t i = 0; i < tk.nterms; i++) {
+      const nwq_pauli_term& p = tk.terms[i];
+      if ((p.x_mask & ~qmask) || (p.z_mask & ~qmask)) return set_error(NWQ_EINVAL, "Pauli mask out of range");
+      terms.push_back(BTerm{(uint32_t)p.x_mask, (uint32_t)p.z_mask, __builtin_popcountll(p.x_mask & p.z_mask) & 3, 0});
+    }
+    coeffs.insert(coeffs.end(), tk.coeffs, tk.coeffs + (size_t)tk.ne * tk.nterms);
+    tmpl.push_back(bt);
+    b->max_n = std::max(b->max_n, tk.n);
+    b->max_gates = std::max(b->max_gates, (int)tk.ngates);
+    b->max_terms = std::max(b->max_terms, (int)tk.nterms);
+    b->max_ne = std::max(b->max_ne, tk.ne);
+  }
+  b->dtype = dtype;
+  b->nparams = nparams;
+  b->ntemplates = ntemplates;
+  if (batch_smem_bytes(dtype == NWQ_F64, b->max_n, std::max(b->max_gates, 1), b->max_terms) > 220 * 1024)
+    return set_error(NWQ_EUNSUPPORTED, "batch state plus gate tables exceed shared memory");
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+  if (e != cudaSuccess) return set_error(NWQ_ECUDA, cudaGetErrorString(e));
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t og = 0, ot = al(og + gates.size() * sizeof(BGate)), oterm = al(ot + tmpl.size() * sizeof(BTemplate));
+  size_t oc = al(oterm + terms.size() * sizeof(BTerm)), ocnt = al(oc + coeffs.size() * sizeof(double));
+  size_t total = ocnt + 256;
+  e = cudaMalloc(&b->dev, total);
+  if (e != cudaSuccess) return set_error(NWQ_ENOMEM, "batch table allocation failed");
+  char* d = (char*)b->dev;
+  if (!gates.empty()) e = cudaMemcpy(d + og, gates.data(), gates.size() * sizeof(BGate), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + ot, tmpl.data(), tmpl.size() * sizeof(BTemplate), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !terms.empty()) e = cudaMemcpy(d + oterm, terms.data(), terms.size() * sizeof(BTerm), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !coeffs.empty()) e = cudaMemcpy(d + oc, coeffs.data(), coeffs.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(b->dev);
+    return set_error(NWQ_ECUDA, cudaGetErrorString(e));
+  }
+  b->gates = (const BGate*)(d + og);
+  b->templates = (const BTemplate*)(d + ot);
+  b->terms = (const BTerm*)(d + oterm);
+  b->coeffs = (const double*)(d + oc);
+  b->counter = (int*)(d + ocnt);
+  *out = b.release();
+  return NWQ_OK;
+}
+
+extern "C" int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* job_template, int njobs,
+                             double* out, int out_stride, double* norms, void* stream, uint32_t flags) {
+  if (!b || (njobs > 0 && (!out || (b->nparams > 0 && !params)))) return set_error(NWQ_EINVAL, "NULL argument");
+  if (njobs < 0) return set_error(NWQ_EINVAL, "negative job count");
+  if (njobs == 0) return NWQ_OK;
+  if (out_stride < b->max_ne) return set_error(NWQ_EINVAL, "output stride below the largest energy count");
+  if (b->ntemplates > 1 && !job_template) return set_error(NWQ_EINVAL, "several templates need a job_template array");
+  BatchArgs a;
+  std::memset(&a, 0, sizeof(a));  // compared bytewise against the captured arguments
+  a.gates = b->gates;
+  a.templates = b->templates;
+  a.terms = b->terms;
+  a.coeffs = b->coeffs;
+  a.params = params;
+  a.job_template = job_template;
+  a.out = out;
+  a.norms = norms;
+  a.counter = b->counter;
+  a.njobs = njobs;
+  a.nparams = b->nparams;
+  a.out_stride = out_stride;
+  a.ntemplates = b->ntemplates;
+  a.max_n = b->max_n;
+  a.max_gates = std::max(b->max_gates, 1);
+  a.max_terms = b->max_terms;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = b->dtype == NWQ_F64;
+  if (!(flags & NWQ_BATCH_GRAPH)) {
+    cudaError_t e = launch_batch(f64, a, b->sm_count, s);
+    return e == cudaSuccess ? NWQ_OK : set_error(NWQ_ECUDA, cudaGetErrorString(e));
+  }
+  // Replay a captured graph (work-queue reset + launch); recapture when the
+  // pointers or the job count differ from the captured ones.
+  if (!b->exec || std::memcmp(&b->cap_args, &a, sizeof(a)) != 0) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b->cap_stream) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    // one direct launch first: kernel attributes are set outside the capture
+    if (e == cudaSuccess) e = launch_batch(f64, a, b->sm_count, b->cap_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->cap_stream);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t el = launch_batch(f64, a, b->sm_count, b->cap_stream);
+      e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_error(NWQ_ECUDA, cudaGetErrorString(e));
+    b->cap_args = a;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, s);
+  if (e == cudaSuccess) g_launches += 1;
+  return e == cudaSuccess ? NWQ_OK : set_error(NWQ_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" int nwq_batch_destroy(nwq_batch* b) {
+  if (!b) return NWQ_OK;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->dev) cudaFree(b->dev);
+  delete b;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t ng, const double* params, int nsets,
+                                int nparams, const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne,
+                                double* out, void* stream) {
+  nwq_batch_template t{};
+  t.n = n;
+  t.gates = gates;
+  t.ngates = ng;
+  t.terms = terms;
+  t.nterms = nt;
+  t.coeffs = coeffs;
+  t.ne = ne;
+  nwq_batch* b = nullptr;
+  int rc = nwq_batch_create(dtype, &t, 1, nparams, &b);
+  if (rc) return rc;
+  rc = nwq_batch_run(b, params, nullptr, nsets, out, ne, nullptr, stream, 0);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) rc = set_error(NWQ_ECUDA, cudaGetErrorString(e));
+  }
+  nwq_batch_destroy(b);
+  return rc;
+}

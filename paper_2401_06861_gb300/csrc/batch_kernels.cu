@@ -1,2 +1,268 @@
-// Batched parameter-set evaluation (filled in below).
+// Batched evaluation of parametrised circuits (the VQE inner loop of paper
+// Sec. III): one CTA per job (one parameter set of one circuit template),
+// the whole 2^n state resident in shared memory, gates applied in place,
+// Pauli-term expectations reduced in FP64, energies written per job.
+// Jobs are taken from an atomic work queue (a persistent grid), so templates
+// of different qubit counts and depths balance across SMs in one launch.
 #include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "batch.hpp"
+#include "kernels.hpp"
+
+namespace nwq {
+
+template <class R>
+struct C2;
+template <>
+struct C2<double> {
+  using T = double2;
+};
+template <>
+struct C2<float> {
+  using T = float2;
+};
+
+// Per-job gate matrix: 2x2 complex (or the 4 diagonal phases of a 2q
+// diagonal) with its structure class.
+template <class R>
+struct GateMat {
+  typename C2<R>::T m[4];
+  int cls;  // BG_* class below
+};
+
+enum : int { BG_DENSE = 0, BG_REAL = 1, BG_DIAG = 2, BG_CX = 3, BG_CZ = 4, BG_SWAP = 5, BG_DIAG2 = 6 };
+
+// Matrix of gate g for parameter vector p (FP64 trigonometry, stored in R).
+template <class R>
+__device__ void make_gate(const BGate& g, const double* __restrict__ p, GateMat<R>& out) {
+  using C = typename C2<R>::T;
+  if (g.type == BT_CX) { out.cls = BG_CX; return; }
+  if (g.type == BT_CZ) { out.cls = BG_CZ; return; }
+  if (g.type == BT_SWAP) { out.cls = BG_SWAP; return; }
+  if (g.type == BT_FIXED1) {
+    for (int k = 0; k < 4; k++) out.m[k] = C{(R)g.m[2 * k], (R)g.m[2 * k + 1]};
+    out.cls = g.cls;
+    return;
+  }
+  double th = g.pidx >= 0 ? p[g.pidx] : g.th[0];
+  double s, c;
+  sincos(0.5 * th, &s, &c);
+  switch (g.type) {
+    case BT_RX:
+      out.m[0] = C{(R)c, 0}; out.m[1] = C{0, (R)-s}; out.m[2] = C{0, (R)-s}; out.m[3] = C{(R)c, 0};
+      out.cls = BG_DENSE;
+      break;
+    case BT_RY:
+      out.m[0] = C{(R)c, 0}; out.m[1] = C{(R)-s, 0}; out.m[2] = C{(R)s, 0}; out.m[3] = C{(R)c, 0};
+      out.cls = BG_REAL;
+      break;
+    case BT_RZ:  // diag(e^{-i th/2}, e^{i th/2})
+      out.m[0] = C{(R)c, (R)-s}; out.m[3] = C{(R)c, (R)s};
+      out.cls = BG_DIAG;
+      break;
+    case BT_P: {  // diag(1, e^{i th})
+      double s2, c2;
+      sincos(th, &s2, &c2);
+      out.m[0] = C{1, 0}; out.m[3] = C{(R)c2, (R)s2};
+      out.cls = BG_DIAG;
+      break;
+    }
+    case BT_U3: {
+      double sp, cp, sl, cl, spl, cpl;
+      sincos(g.th[1], &sp, &cp);
+      sincos(g.th[2], &sl, &cl);
+      sincos(g.th[1] + g.th[2], &spl, &cpl);
+      out.m[0] = C{(R)c, 0};
+      out.m[1] = C{(R)(-cl * s), (R)(-sl * s)};
+      out.m[2] = C{(R)(cp * s), (R)(sp * s)};
+      out.m[3] = C{(R)(cpl * c), (R)(spl * c)};
+      out.cls = BG_DENSE;
+      break;
+    }
+    default:  // BT_RZZ: phases e^{-i th/2} on even parity, e^{+i th/2} on odd
+      out.m[0] = C{(R)c, (R)-s}; out.m[1] = C{(R)c, (R)s};
+      out.cls = BG_DIAG2;
+  }
+}
+
+template <class C, class R>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return C{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)};
+}
+
+template <class R>
+__device__ void apply_gate(typename C2<R>::T* __restrict__ psi, int n, const BGate& g, const GateMat<R>& G) {
+  using C = typename C2<R>::T;
+  const uint32_t half = 1u << (n - 1);
+  const uint32_t q0 = g.q0, q1 = g.q1;
+  const uint32_t m0 = 1u << q0, m1 = 1u << q1;
+  switch (G.cls) {
+    case BG_CX:
+    case BG_CZ:
+    case BG_SWAP: {
+      // quarter of the state: indices with both bits 0
+      const uint32_t lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
+      for (uint32_t t = threadIdx.x; t < (half >> 1); t += blockDim.x) {
+        uint32_t b = t;
+        b = ((b >> lo) << (lo + 1)) | (b & ((1u << lo) - 1));
+        b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1));
+        if (G.cls == BG_CX) {  // swap |c=1,t=0> and |c=1,t=1>
+          C a = psi[b | m0], d = psi[b | m0 | m1];
+          psi[b | m0] = d;
+          psi[b | m0 | m1] = a;
+        } else if (G.cls == BG_CZ) {
+          C a = psi[b | m0 | m1];
+          psi[b | m0 | m1] = C{-a.x, -a.y};
+        } else {
+          C a = psi[b | m0], d = psi[b | m1];
+          psi[b | m0] = d;
+          psi[b | m1] = a;
+        }
+      }
+      return;
+    }
+    case BG_DIAG2:  // parity phases
+      for (uint32_t b = threadIdx.x; b < 2 * half; b += blockDim.x) {
+        uint32_t par = ((b >> q0) ^ (b >> q1)) & 1u;
+        psi[b] = cmul<C, R>(G.m[par], psi[b]);
+      }
+      return;
+    case BG_DIAG:
+      for (uint32_t b = threadIdx.x; b < 2 * half; b += blockDim.x) psi[b] = cmul<C, R>(G.m[(b >> q0) & 1u ? 3 : 0], psi[b]);
+      return;
+    default:
+      break;
+  }
+  for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+    uint32_t i0 = ((t >> q0) << (q0 + 1)) | (t & (m0 - 1));
+    uint32_t i1 = i0 | m0;
+    C a = psi[i0], d = psi[i1];
+    C o0, o1;
+    if (G.cls == BG_REAL) {
+      o0 = C{fma(G.m[0].x, a.x, G.m[1].x * d.x), fma(G.m[0].x, a.y, G.m[1].x * d.y)};
+      o1 = C{fma(G.m[2].x, a.x, G.m[3].x * d.x), fma(G.m[2].x, a.y, G.m[3].x * d.y)};
+    } else {
+      C x0 = cmul<C, R>(G.m[0], a), x1 = cmul<C, R>(G.m[1], d);
+      C y0 = cmul<C, R>(G.m[2], a), y1 = cmul<C, R>(G.m[3], d);
+      o0 = C{x0.x + x1.x, x0.y + x1.y};
+      o1 = C{y0.x + y1.x, y0.y + y1.y};
+    }
+    psi[i0] = o0;
+    psi[i1] = o1;
+  }
+}
+
+// Block-wide FP64 sum; every thread gets the result.
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < nw; w++) s += red[w];
+  return s;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
+  using C = typename C2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* psi = reinterpret_cast<C*>(smem);
+  GateMat<R>* mats = reinterpret_cast<GateMat<R>*>(smem + ((size_t)sizeof(C) << a.max_n));
+  double* red = reinterpret_cast<double*>(mats + a.max_gates);  // 32 doubles
+  double* vals = red + 32;                                       // max_terms + 1 doubles
+  __shared__ int s_job;
+  for (int iter = 0; iter < a.njobs; iter++) {  // bounded: at most njobs jobs per CTA
+    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int job = s_job;
+    __syncthreads();
+    if (job >= a.njobs) break;
+    const int tid = a.job_template ? a.job_template[job] : 0;
+    if (tid < 0 || tid >= a.ntemplates) {  // invalid template index: NaN energies
+      for (int e = threadIdx.x; e < a.out_stride; e += blockDim.x) a.out[(size_t)job * a.out_stride + e] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
+    const BTemplate T = a.templates[tid];
+    const double* p = a.params + (size_t)job * a.nparams;
+    const int n = T.n;
+    const uint32_t N = 1u << n;
+    // |0..0>
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = C{b == 0 ? (R)1 : (R)0, 0};
+    // per-job gate matrices (each thread builds different gates)
+    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) make_gate<R>(a.gates[T.g0 + k], p, mats[k]);
+    __syncthreads();
+    for (int k = 0; k < T.ng; k++) {
+      apply_gate<R>(psi, n, a.gates[T.g0 + k], mats[k]);
+      __syncthreads();
+    }
+    // norm and per-term expectations in FP64
+    double nrm = 0;
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+      double re = psi[b].x, im = psi[b].y;
+      nrm = fma(re, re, fma(im, im, nrm));
+    }
+    nrm = block_sum(nrm, red);
+    for (int t = 0; t < T.nt; t++) {
+      const BTerm tm = a.terms[T.t0 + t];
+      double acc = 0;
+      for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+        double pr = psi[b].x, pi = psi[b].y;
+        double qr = pr, qi = pi;
+        if (tm.x) {
+          qr = psi[b ^ tm.x].x;
+          qi = psi[b ^ tm.x].y;
+        }
+        double wr = fma(qr, pr, qi * pi), wi = fma(qr, pi, -qi * pr);
+        double v = (tm.y & 1) ? wi : wr;
+        int neg = ((tm.y == 1) || (tm.y == 2)) ^ (__popc(b & tm.z) & 1);
+        acc += neg ? -v : v;
+      }
+      acc = block_sum(acc, red);
+      if (threadIdx.x == 0) vals[t] = acc / nrm;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < T.ne; e += blockDim.x) {
+      double s = 0;
+      for (int t = 0; t < T.nt; t++) s = fma(a.coeffs[T.c0 + e * T.nt + t], vals[t], s);
+      a.out[(size_t)job * a.out_stride + e] = s;
+    }
+    if (a.norms && threadIdx.x == 0) a.norms[job] = nrm;
+    __syncthreads();
+  }
+}
+
+size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
+  size_t c = f64 ? 16 : 8;
+  size_t gm = f64 ? sizeof(GateMat<double>) : sizeof(GateMat<float>);
+  return (c << max_n) + gm * (size_t)max_gates + 8 * (32 + (size_t)max_terms + 1);
+}
+
+cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s) {
+  size_t smem = batch_smem_bytes(f64, a.max_n, a.max_gates, a.max_terms);
+  cudaError_t e;
+  int per_sm = 0;
+  if (f64) {
+    e = cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double>, kBatchThreads, smem);
+  } else {
+    e = cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float>, kBatchThreads, smem);
+  }
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = sm_count * per_sm;
+  if (grid > a.njobs) grid = a.njobs;
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (f64) batch_kernel<double><<<grid, kBatchThreads, smem, s>>>(a);
+  else batch_kernel<float><<<grid, kBatchThreads, smem, s>>>(a);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace nwq

@@ -164,3 +164,52 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Batched parametrised circuits (nwq_batch_create / nwq_batch_run).
+
+    templates: list of dicts {n, gates, param_index, terms, coeffs (ne x nt)}.
+    run(params, out, job_template=None, norms=None): device tensors (torch or
+    raw pointers); asynchronous on ``stream``.
+    """
+
+    def __init__(self, templates, nparams, dtype=F64):
+        self.keep = []
+        arr = (L.BatchTemplate * len(templates))()
+        self.max_ne = 0
+        for i, t in enumerate(templates):
+            g, k1 = encode_gates(t["gates"], t.get("param_index"))
+            tr = encode_terms(t["terms"])
+            c = np.ascontiguousarray(t["coeffs"], np.float64).reshape(-1)
+            ne = int(np.asarray(t["coeffs"]).reshape(-1, max(len(t["terms"]), 1)).shape[0]) if len(t["terms"]) else 1
+            self.keep += [g, k1, tr, c]
+            arr[i].n = t["n"]
+            arr[i].gates = ctypes.cast(g, ctypes.POINTER(L.Gate))
+            arr[i].ngates = len(t["gates"])
+            arr[i].terms = ctypes.cast(tr, ctypes.POINTER(L.PauliTerm))
+            arr[i].nterms = len(t["terms"])
+            arr[i].coeffs = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[i].ne = ne
+            self.max_ne = max(self.max_ne, ne)
+        self.h = ctypes.c_void_p()
+        check(L.lib().nwq_batch_create(dtype, arr, len(templates), nparams, ctypes.byref(self.h)))
+        self.keep = None
+
+    def run(self, params_ptr, njobs, out_ptr, out_stride=None, job_template_ptr=None, norms_ptr=None,
+            stream=None, graph=False):
+        check(L.lib().nwq_batch_run(self.h, ctypes.c_void_p(params_ptr), ctypes.c_void_p(job_template_ptr)
+                                    if job_template_ptr else None, njobs, ctypes.c_void_p(out_ptr),
+                                    out_stride or self.max_ne, ctypes.c_void_p(norms_ptr) if norms_ptr else None,
+                                    ctypes.c_void_p(stream) if stream else None, L.BATCH_GRAPH if graph else 0))
+
+    def close(self):
+        if self.h:
+            L.lib().nwq_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

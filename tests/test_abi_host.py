@@ -111,3 +111,18 @@ def test_planner_tfim_sweep_counts():
     fused = sim.Plan(L.SV, 33, g, L.F32).info()
     plain = sim.Plan(L.SV, 33, g, L.F32, flags=L.PLAN_PLAIN).info()
     assert fused["bytes"] < plain["bytes"] / 20
+
+
+def test_batch_create_validates_without_device():
+    import ctypes
+    from paper_2401_06861_gb300.sim import Batch
+    g, pidx = inputs.hea_ansatz(4, 1)
+    ok = dict(n=4, gates=g, param_index=pidx, terms=inputs.z_terms(4), coeffs=np.ones((1, 4)))
+    for bad, msg in [(dict(ok, n=14), b"qubit count"), (dict(ok, n=2), b"qubit out of range"),
+                     (dict(ok, gates=[inputs.gate("MAT2", (0, 1), np.eye(4))], param_index=[-1]), b"MAT2"),
+                     (dict(ok, gates=[inputs.gate("CX", (0, 1))], param_index=[0]), b"without an angle"),
+                     (dict(ok, param_index=[99] * len(g)), b"parameter index")]:
+        with pytest.raises(L.NwqError) as ei:
+            Batch([bad], 8, L.F64)
+        assert ei.value.code == L.EINVAL
+        assert msg in L.lib().nwq_last_error()

@@ -1,0 +1,141 @@
+"""Batched VQE energies (nwq_batch_*) against the oracle, per parameter set."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_06861_gb300 import _lib as L
+from paper_2401_06861_gb300 import inputs
+from paper_2401_06861_gb300.sim import Batch, State
+
+pytestmark = pytest.mark.gpu
+H_LIST = (0.5, 1.0, 2.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2401_06861_gb300 import build
+    build.build()
+    yield
+
+
+def tfim_energy_template(n, gates, pidx):
+    """Terms Z_iZ_{i+1} and X_i with one energy row per h in H_LIST."""
+    terms = inputs.zz_terms(n) + inputs.x_terms(n)
+    coeffs = np.array([[-1.0] * (n - 1) + [-h] * n for h in H_LIST])
+    return dict(n=n, gates=gates, param_index=pidx, terms=terms, coeffs=coeffs)
+
+
+def oracle_energies(n, gates, pidx, params):
+    g = [(name, q, (params[k],) if k >= 0 else prm) for (name, q, prm), k in zip(gates, pidx)]
+    psi = oracle.sv_run(n, g)
+    out = []
+    for h in H_LIST:
+        t = inputs.tfim_terms(n, 1.0, h)
+        out.append(oracle.energy(oracle.sv_expect(psi, n, t), t) / np.vdot(psi, psi).real)
+    return np.array(out)
+
+
+def rel(e, eref, n, h):
+    return np.abs(e - eref) / np.maximum(np.abs(eref), (n - 1) + n * np.asarray(h))
+
+
+@pytest.mark.parametrize("dtype", [L.F64, L.F32])
+@pytest.mark.parametrize("n", [1, 5, 12])
+def test_batch_hea_matches_oracle(n, dtype):
+    import torch
+    layers, nsets = 4, 24
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    nparams = layers * 2 * n
+    params = inputs.hea_params(n, layers, nsets, seed=4096)
+    b = Batch([tfim_energy_template(n, gates, pidx)], nparams, dtype)
+    p = torch.from_numpy(params).cuda()
+    out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+    b.run(p.data_ptr(), nsets, out.data_ptr(), stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = np.array([oracle_energies(n, gates, pidx, params[s]) for s in range(nsets)])
+    err = rel(got, ref, n, np.array(H_LIST)[None, :]).max()
+    print(f"batch hea n={n} dtype={dtype}: max rel energy err {err:.3e}")
+    assert err <= (1e-12 if dtype == L.F64 else 1e-6)
+    b.close()
+
+
+def test_batch_uneven_templates_in_one_launch_and_graph_replay():
+    import torch
+    specs = []
+    for n, layers in ((4, 2), (9, 3), (13, 2)):
+        g, pidx = inputs.hea_ansatz(n, layers)
+        specs.append((n, g, pidx, layers * 2 * n))
+    # a Trotter template with fixed angles (no parameters) as the fourth
+    g4 = inputs.tfim_trotter(7, 1.0, 1.0, 0.05, 6)
+    specs.append((7, g4, [-1] * len(g4), 0))
+    nparams = max(s[3] for s in specs)
+    b = Batch([tfim_energy_template(n, g, pidx) for n, g, pidx, _ in specs], nparams, L.F64)
+    njobs = 40
+    rng = np.random.default_rng(5)
+    job_t = rng.integers(0, len(specs), njobs).astype(np.int32)
+    stream = torch.cuda.current_stream().cuda_stream
+    for it in range(2):  # second run: same pointers, new parameters -> graph replay
+        params = rng.uniform(0, 2 * np.pi, (njobs, nparams))
+        p = torch.from_numpy(params).cuda() if it == 0 else p.copy_(torch.from_numpy(params))
+        jt = torch.from_numpy(job_t).cuda() if it == 0 else jt
+        out = torch.zeros(njobs, 3, dtype=torch.float64, device="cuda") if it == 0 else out.zero_()
+        b.run(p.data_ptr(), njobs, out.data_ptr(), job_template_ptr=jt.data_ptr(), stream=stream, graph=True)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for j in range(njobs):
+            n, g, pidx, _ = specs[job_t[j]]
+            ref = oracle_energies(n, g, pidx, params[j])
+            assert rel(got[j], ref, n, np.array(H_LIST)).max() <= 1e-12, (it, j)
+    b.close()
+
+
+def test_batch_equals_per_circuit_plain_path():
+    import torch
+    n, layers, nsets = 10, 3, 6
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    params = inputs.hea_params(n, layers, nsets, seed=7)
+    b = Batch([tfim_energy_template(n, gates, pidx)], layers * 2 * n, L.F64)
+    p = torch.from_numpy(params).cuda()
+    out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+    b.run(p.data_ptr(), nsets, out.data_ptr(), stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for s in range(nsets):
+        g = [(name, q, (params[s][k],) if k >= 0 else prm) for (name, q, prm), k in zip(gates, pidx)]
+        with State(L.SV, n, L.F64) as st:
+            st.apply(g, flags=L.PLAN_PLAIN)
+            e = [st.expect(inputs.tfim_terms(n, 1.0, h), sum=True) for h in H_LIST]
+        assert np.max(np.abs(got[s] - e)) <= 1e-12
+    b.close()
+
+
+def test_batch_energy_convenience_and_invalid_template_index():
+    import torch
+    n, layers, nsets = 6, 2, 5
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    params = inputs.hea_params(n, layers, nsets, seed=9)
+    t = tfim_energy_template(n, gates, pidx)
+    garr, keep = L.encode_gates(gates, pidx)
+    tarr = L.encode_terms(t["terms"])
+    coeffs = np.ascontiguousarray(t["coeffs"]).reshape(-1)
+    p = torch.from_numpy(params).cuda()
+    out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+    import ctypes
+    L.check(L.lib().nwq_batch_energy(n, L.F64, garr, len(gates), ctypes.c_void_p(p.data_ptr()), nsets,
+                                      layers * 2 * n, tarr, len(t["terms"]),
+                                      coeffs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 3,
+                                      ctypes.c_void_p(out.data_ptr()), None))
+    ref = np.array([oracle_energies(n, gates, pidx, params[s]) for s in range(nsets)])
+    assert rel(out.cpu().numpy(), ref, n, np.array(H_LIST)[None, :]).max() <= 1e-12
+    # a job naming a template that does not exist gets NaN energies, the others are unaffected
+    b = Batch([t], layers * 2 * n, L.F64)
+    jt = torch.tensor([0, 3, 0, -1, 0], dtype=torch.int32, device="cuda")
+    out2 = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+    b.run(p.data_ptr(), nsets, out2.data_ptr(), job_template_ptr=jt.data_ptr())
+    torch.cuda.synchronize()
+    o = out2.cpu().numpy()
+    assert np.all(np.isnan(o[[1, 3]])) and np.allclose(o[[0, 2, 4]], ref[[0, 2, 4]], atol=1e-12)
+    b.close()
