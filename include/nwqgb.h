@@ -120,7 +120,8 @@ enum nwq_expect_flags { NWQ_EXPECT_TERMS = 0u, NWQ_EXPECT_SUM = 1u, NWQ_EXPECT_N
 size_t nwq_state_bytes(int kind, int n, int dtype);
 
 /* Create an n-qubit state vector |0..0> (paper Sec. II, SV-Sim).
- * dev_buf: NULL = the library allocates (and nwq_destroy frees) the state;
+ * dev_buf: NULL = the library allocates the state stream-ordered from the
+ *   device's default memory pool (nwq_destroy frees it);
  *   otherwise a caller-owned device buffer of >= nwq_state_bytes() bytes,
  *   16-byte aligned, which the library never frees.
  * stream: a cudaStream_t (NULL = the legacy default stream).
@@ -150,15 +151,18 @@ int nwq_state_copy(nwq_state* st, void* dst, size_t bytes, int dst_on_device);
 /* DM only: copy the raw Pauli-basis coefficients (4^n reals). */
 int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst_on_device);
 
-/* Free library-owned memory and the handle. */
+/* Free the handle.  Library-owned device memory is released stream-ordered
+ * on the state's stream (work queued there completes first; no device-wide
+ * synchronisation).  A caller-owned buffer is left alone. */
 int nwq_destroy(nwq_state* st);
 
 /* ---------------------------------------------------------------- circuits */
 
 /* Apply a circuit to a state vector: psi <- U_ng ... U_1 psi (paper Sec. II).
  * Gates are validated, lowered to sweeps (nwq_plan_create) and launched on
- * the state's stream; the call returns without waiting for the device.
- * gates: host array, read during the call only. */
+ * the state's stream; the operator tables are uploaded (the call waits for
+ * that copy) and released stream-ordered, and the call returns without
+ * waiting for the sweeps.  gates: host array, read during the call only. */
 int nwq_sv_apply_circuit(nwq_state* st, const nwq_gate* gates, size_t ng, uint32_t flags);
 
 /* Apply a circuit with the device noise model to a density matrix
@@ -265,9 +269,11 @@ enum nwq_batch_flags {
                            recaptured when pointers or the job count change */
 };
 
-/* Validate and upload templates (synchronous; allocates device tables). */
+/* Validate and upload templates.  The device tables are allocated and
+ * uploaded stream-ordered on stream (the call synchronises that stream) and
+ * freed on it by nwq_batch_destroy. */
 int nwq_batch_create(int dtype, const nwq_batch_template* templates, int ntemplates, int nparams,
-                     nwq_batch** out);
+                     void* stream, nwq_batch** out);
 
 /* Evaluate njobs jobs, asynchronous on stream.  params: device, njobs *
  * nparams doubles.  job_template: device, njobs ints (template of each job;
@@ -279,7 +285,9 @@ int nwq_batch_create(int dtype, const nwq_batch_template* templates, int ntempla
 int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* job_template, int njobs, double* out,
                   int out_stride, double* norms, void* stream, uint32_t flags);
 
-/* Wait for the device and free the batch's tables. */
+/* Free the batch: its tables are released stream-ordered on the creation
+ * stream, so runs queued on that stream complete first; runs on other
+ * streams must have completed (synchronise them) before this call. */
 int nwq_batch_destroy(nwq_batch* b);
 
 /* One template, nsets parameter sets: create + run + destroy.  params and

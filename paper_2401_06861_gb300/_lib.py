@@ -92,7 +92,7 @@ def lib():
         "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_probs": (i32, [vp, dbl, P(dbl)]),
         "nwq_batch_energy": (i32, [i32, i32, P(Gate), sz, vp, i32, i32, P(PauliTerm), sz, P(dbl), i32, vp, vp]),
-        "nwq_batch_create": (i32, [i32, P(BatchTemplate), i32, i32, pp]),
+        "nwq_batch_create": (i32, [i32, P(BatchTemplate), i32, i32, vp, pp]),
         "nwq_batch_run": (i32, [vp, vp, vp, i32, vp, i32, vp, vp, u32]),
         "nwq_batch_destroy": (i32, [vp]),
         "nwq_last_error": (ctypes.c_char_p, []),

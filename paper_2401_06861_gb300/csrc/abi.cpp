@@ -85,7 +85,12 @@ static int plan_upload(Plan& p, cudaStream_t s) {
   size_t ob = p.ops.size() * sizeof(DevOp);
   size_t total = ob + p.ents.size() + 16;
   void* d = nullptr;
-  CK(cudaMalloc(&d, total), "plan table allocation");
+  if (p.stream_ordered) {
+    CK(cudaMallocAsync(&d, total, s), "plan table allocation");
+    p.dev_stream = s;
+  } else {
+    CK(cudaMalloc(&d, total), "plan table allocation");
+  }
   if (ob) CK(cudaMemcpyAsync(d, p.ops.data(), ob, cudaMemcpyHostToDevice, s), "plan upload");
   if (!p.ents.empty())
     CK(cudaMemcpyAsync((char*)d + ob, p.ents.data(), p.ents.size(), cudaMemcpyHostToDevice, s), "plan upload");
@@ -109,7 +114,9 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
 }
 
 Plan::~Plan() {
-  if (dev) cudaFree(dev);
+  if (!dev) return;
+  if (stream_ordered) cudaFreeAsync(dev, dev_stream);
+  else cudaFree(dev);
 }
 
 // ------------------------------------------------------------------ states
@@ -132,13 +139,13 @@ static int create_state(int kind, int n, int dtype, void* dev_buf, size_t buf_by
   if (dev_buf) {
     st->buf = dev_buf;
   } else {
-    cudaError_t e = cudaMalloc(&st->buf, need);
+    cudaError_t e = cudaMallocAsync(&st->buf, need, st->stream);  // stream-ordered, pooled
     if (e != cudaSuccess) return fail(NWQ_ENOMEM, std::string("state allocation: ") + cudaGetErrorString(e));
     st->owned = true;
   }
   cudaError_t e = launch_init(kind == NWQ_SV, f64_of(dtype), st->buf, n, st->sm_count, st->stream);
   if (e != cudaSuccess) {
-    if (st->owned) cudaFree(st->buf);
+    if (st->owned) cudaFreeAsync(st->buf, st->stream);
     return cuda_fail(e, "state init");
   }
   *out = st.release();
@@ -160,10 +167,9 @@ extern "C" int nwq_state_reset(nwq_state* st) {
 
 extern "C" int nwq_destroy(nwq_state* st) {
   if (!st) return NWQ_OK;
-  if (st->stream) cudaStreamSynchronize(st->stream);
-  else cudaDeviceSynchronize();
-  if (st->owned && st->buf) cudaFree(st->buf);
-  delete st;
+  // stream-ordered release: work already queued on the state's stream finishes first
+  if (st->owned && st->buf) cudaFreeAsync(st->buf, st->stream);
+  delete st;  // the state's helper plans free their tables on the same stream
   return NWQ_OK;
 }
 
@@ -178,6 +184,7 @@ static nwq_plan* dm_conv_plan(nwq_state* st, bool to_rho) {
   std::unique_ptr<nwq_plan>& slot = to_rho ? st->p2r : st->r2p;
   if (slot) return slot.get();
   auto pl = std::make_unique<nwq_plan>();
+  pl->p.stream_ordered = true;
   init_plan_meta(pl->p, NWQ_SV, st->n, st->dtype, 2 * st->n);  // complex elements over 2n bits
   cd M[16];
   if (to_rho) pauli_to_rho_matrix(M);
@@ -330,35 +337,30 @@ extern "C" int nwq_plan_destroy(nwq_plan* plan) {
   return NWQ_OK;
 }
 
+// One-shot circuit: lower, run, and release the tables stream-ordered (the
+// host returns without waiting for the sweeps).
+static int apply_once(nwq_state* st, int kind, const nwq_gate* gates, size_t ng, const nwq_noise_model* nm,
+                      uint32_t flags) {
+  nwq_plan* pl = nullptr;
+  int rc = nwq_plan_create(kind, st->n, st->dtype, gates, ng, nm, flags, st->stream, &pl);
+  if (rc) return rc;
+  pl->p.stream_ordered = true;
+  rc = nwq_plan_run(st, pl);
+  nwq_plan_destroy(pl);
+  return rc;
+}
+
 extern "C" int nwq_sv_apply_circuit(nwq_state* st, const nwq_gate* gates, size_t ng, uint32_t flags) {
   if (!st) return fail(NWQ_EINVAL, "state is NULL");
   if (st->kind != NWQ_SV) return fail(NWQ_EINVAL, "not a state vector");
-  nwq_plan* pl = nullptr;
-  int rc = nwq_plan_create(NWQ_SV, st->n, st->dtype, gates, ng, nullptr, flags, st->stream, &pl);
-  if (rc) return rc;
-  rc = nwq_plan_run(st, pl);
-  if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(st->stream);  // tables are freed below
-    if (e != cudaSuccess) rc = cuda_fail(e, "apply circuit");
-  }
-  nwq_plan_destroy(pl);
-  return rc;
+  return apply_once(st, NWQ_SV, gates, ng, nullptr, flags);
 }
 
 extern "C" int nwq_dm_apply_circuit_noisy(nwq_state* st, const nwq_gate* gates, size_t ng,
                                           const nwq_noise_model* nm, uint32_t flags) {
   if (!st) return fail(NWQ_EINVAL, "state is NULL");
   if (st->kind != NWQ_DM) return fail(NWQ_EINVAL, "not a density matrix");
-  nwq_plan* pl = nullptr;
-  int rc = nwq_plan_create(NWQ_DM, st->n, st->dtype, gates, ng, nm, flags, st->stream, &pl);
-  if (rc) return rc;
-  rc = nwq_plan_run(st, pl);
-  if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(st->stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "apply circuit");
-  }
-  nwq_plan_destroy(pl);
-  return rc;
+  return apply_once(st, NWQ_DM, gates, ng, nm, flags);
 }
 
 // ------------------------------------------------------------------ measurement
@@ -478,6 +480,7 @@ static nwq_plan* probs_plan(nwq_state* st, double e, bool wht) {
   auto it = st->probs.find(key);
   if (it != st->probs.end()) return it->second.get();
   auto pl = std::make_unique<nwq_plan>();
+  pl->p.stream_ordered = true;
   init_plan_meta(pl->p, NWQ_DM, st->n, NWQ_F64, st->n);  // real f64 elements over n bits
   std::vector<BitOp> ops(st->n);
   for (int q = 0; q < st->n; q++) {

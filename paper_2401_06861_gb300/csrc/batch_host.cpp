@@ -27,6 +27,7 @@ struct nwq_batch {
   const BTerm* terms = nullptr;
   const double* coeffs = nullptr;
   int* counter = nullptr;
+  cudaStream_t stream = nullptr;  // tables are allocated and freed stream-ordered here
   // captured launch for repeated runs with the same pointers and job count
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -87,7 +88,7 @@ static bool lower_batch_gate(const nwq_gate& g, int n, int nparams, BGate& b, st
 }
 
 extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntemplates, int nparams,
-                                nwq_batch** out) {
+                                void* stream, nwq_batch** out) {
   if (!out || !t || ntemplates < 1 || nparams < 0) return set_error(NWQ_EINVAL, "bad batch arguments");
   *out = nullptr;
   if (dtype != NWQ_F32 && dtype != NWQ_F64) return set_error(NWQ_EINVAL, "unsupported dtype");
@@ -142,15 +143,20 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
   size_t og = 0, ot = al(og + gates.size() * sizeof(BGate)), oterm = al(ot + tmpl.size() * sizeof(BTemplate));
   size_t oc = al(oterm + terms.size() * sizeof(BTerm)), ocnt = al(oc + coeffs.size() * sizeof(double));
   size_t total = ocnt + 256;
-  e = cudaMalloc(&b->dev, total);
+  b->stream = (cudaStream_t)stream;
+  e = cudaMallocAsync(&b->dev, total, b->stream);
   if (e != cudaSuccess) return set_error(NWQ_ENOMEM, "batch table allocation failed");
   char* d = (char*)b->dev;
-  if (!gates.empty()) e = cudaMemcpy(d + og, gates.data(), gates.size() * sizeof(BGate), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d + ot, tmpl.data(), tmpl.size() * sizeof(BTemplate), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !terms.empty()) e = cudaMemcpy(d + oterm, terms.data(), terms.size() * sizeof(BTerm), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !coeffs.empty()) e = cudaMemcpy(d + oc, coeffs.data(), coeffs.size() * sizeof(double), cudaMemcpyHostToDevice);
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+  if (!gates.empty()) e = cudaMemcpyAsync(d + og, gates.data(), gates.size() * sizeof(BGate), h2d, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + ot, tmpl.data(), tmpl.size() * sizeof(BTemplate), h2d, b->stream);
+  if (e == cudaSuccess && !terms.empty())
+    e = cudaMemcpyAsync(d + oterm, terms.data(), terms.size() * sizeof(BTerm), h2d, b->stream);
+  if (e == cudaSuccess && !coeffs.empty())
+    e = cudaMemcpyAsync(d + oc, coeffs.data(), coeffs.size() * sizeof(double), h2d, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // host tables go out of scope
   if (e != cudaSuccess) {
-    cudaFree(b->dev);
+    cudaFreeAsync(b->dev, b->stream);
     return set_error(NWQ_ECUDA, cudaGetErrorString(e));
   }
   b->gates = (const BGate*)(d + og);
@@ -224,10 +230,10 @@ extern "C" int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* 
 
 extern "C" int nwq_batch_destroy(nwq_batch* b) {
   if (!b) return NWQ_OK;
-  cudaDeviceSynchronize();
+  if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  if (b->dev) cudaFree(b->dev);
+  if (b->dev) cudaFreeAsync(b->dev, b->stream);  // after the runs queued on the creation stream
   delete b;
   return NWQ_OK;
 }
@@ -244,7 +250,7 @@ extern "C" int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t 
   t.coeffs = coeffs;
   t.ne = ne;
   nwq_batch* b = nullptr;
-  int rc = nwq_batch_create(dtype, &t, 1, nparams, &b);
+  int rc = nwq_batch_create(dtype, &t, 1, nparams, stream, &b);
   if (rc) return rc;
   rc = nwq_batch_run(b, params, nullptr, nsets, out, ne, nullptr, stream, 0);
   if (!rc) {

@@ -9,6 +9,8 @@
 #include "../../include/nwqgb.h"
 #include "nwq_internal.h"
 
+#include <cuda_runtime.h>
+
 namespace nwq {
 
 using cd = std::complex<double>;
@@ -45,6 +47,10 @@ struct Plan {
   std::mutex mu;
   void* dev = nullptr;
   size_t dev_bytes = 0;
+  // Plans internal to one state allocate their tables stream-ordered on the
+  // state's stream and free them there (no device-wide synchronisation).
+  bool stream_ordered = false;
+  cudaStream_t dev_stream = nullptr;
   ~Plan();
 };
 

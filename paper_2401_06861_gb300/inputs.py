@@ -197,3 +197,40 @@ def large_sv_tfim(n, steps=10, seed=3334):
     rng = np.random.default_rng(seed)
     h = rng.uniform(0.5, 2.0, n)
     return tfim_trotter(n, 1.0, h, 0.05, steps), h
+
+
+# ---------------------------------------------------------------- serving stream
+def serve_requests(rate=200.0, duration=60.0, seed=200, sv_frac=0.7, sv_n=(8, 26), dm_n=(6, 12),
+                   trotter_steps=(5, 50), hea_layers=(2, 6)):
+    """Poisson request stream for the serving loop.
+
+    Each request is a dict: id, arrival (s), kind ("sv" or "dm"), n, family
+    ("trotter" or "hea"), gates, noise (dm only), z_terms and h_terms (TFIM,
+    J = h = 1).  Inter-arrival times are exponential with mean 1/rate; 70%
+    state-vector requests with n ~ U{8..26}, 30% density-matrix requests with
+    n ~ U{6..12}; half Trotter circuits (steps ~ U{5..50}), half hardware-
+    efficient ansatz circuits (layers ~ U{2..6}, angles ~ U(0, 2 pi)); the DM
+    requests carry the seeded device noise model of ``noise_params``.
+    """
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            break
+        kind = "sv" if rng.random() < sv_frac else "dm"
+        lo, hi = sv_n if kind == "sv" else dm_n
+        n = int(rng.integers(lo, hi + 1))
+        if rng.random() < 0.5:
+            fam = "trotter"
+            gates = tfim_trotter(n, 1.0, 1.0, 0.05, int(rng.integers(trotter_steps[0], trotter_steps[1] + 1)))
+        else:
+            fam = "hea"
+            layers = int(rng.integers(hea_layers[0], hea_layers[1] + 1))
+            gates, _ = hea_ansatz(n, layers, rng.uniform(0.0, 2.0 * np.pi, layers * 2 * n))
+        req = dict(id=len(out), arrival=t, kind=kind, n=n, family=fam, gates=gates,
+                   z_terms=z_terms(n), h_terms=tfim_terms(n))
+        if kind == "dm":
+            req["noise"] = noise_params(n, seed=int(rng.integers(1 << 30)))
+        out.append(req)
+    return out

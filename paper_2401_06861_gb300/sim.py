@@ -174,7 +174,7 @@ class Batch:
     raw pointers); asynchronous on ``stream``.
     """
 
-    def __init__(self, templates, nparams, dtype=F64):
+    def __init__(self, templates, nparams, dtype=F64, stream=None):
         self.keep = []
         arr = (L.BatchTemplate * len(templates))()
         self.max_ne = 0
@@ -193,7 +193,8 @@ class Batch:
             arr[i].ne = ne
             self.max_ne = max(self.max_ne, ne)
         self.h = ctypes.c_void_p()
-        check(L.lib().nwq_batch_create(dtype, arr, len(templates), nparams, ctypes.byref(self.h)))
+        check(L.lib().nwq_batch_create(dtype, arr, len(templates), nparams,
+                                       ctypes.c_void_p(stream) if stream else None, ctypes.byref(self.h)))
         self.keep = None
 
     def run(self, params_ptr, njobs, out_ptr, out_stride=None, job_template_ptr=None, norms_ptr=None,
