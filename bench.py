@@ -258,6 +258,154 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------- other workloads
+# These print one JSON line each for the design notes; the default run above
+# is the headline measurement.
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def run_sv(args):
+    """Large state vector: TFIM depth 10 with random h_i, fused sweeps vs one
+    gate per pass, FP32 and FP64; gate-updates/s and HBM GB/s."""
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, inputs
+    from paper_2401_06861_gb300.sim import Plan, State
+    build.build()
+    stream = torch.cuda.current_stream()
+    peak = _peaks()["hbm_gbs"]
+    cases = [(args.sv_n, L.F32, 0, args.steps), (args.sv_n - 1, L.F64, 0, max(1, args.steps // 3)),
+             (args.sv_n, L.F32, L.PLAN_PLAIN, 1)]
+    for n, dtype, flags, steps in cases:
+        gates, h = inputs.large_sv_tfim(n, steps=10)
+        plan = Plan(L.SV, n, gates, dtype, None, flags)
+        info = plan.info()
+        st = State(L.SV, n, dtype, stream=stream.cuda_stream)
+        st.run(plan)
+        st.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            st.reset()
+            a.record(stream)
+            st.run(plan)
+            b.record(stream)
+        torch.cuda.synchronize()
+        sec = sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
+        e = st.expect(inputs.tfim_terms(n, 1.0, h), sum=True, normalize=True)
+        nrm = st.norm()
+        st.close()
+        plan.close()
+        gb = info["bytes"] / sec / 1e9
+        line = {"workload": f"sv_tfim_n{n}_depth10", "plan": "plain" if flags else "fused",
+                "dtype": "c64" if dtype == L.F32 else "c128", "metric": "gate-updates/s",
+                "value": len(gates) * 2.0 ** n / sec, "unit": "gate-updates/s", "s_per_circuit": sec,
+                "sweeps": info["sweeps"], "operators": info["ops"],
+                "roofline": {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak,
+                             "fp_ops_per_amp": info["fma_per_elem"]},
+                "energy": e, "norm": nrm}
+        print(json.dumps(line), flush=True)
+        torch.cuda.empty_cache()
+
+
+def run_vqe(args):
+    """Batched VQE energies: n = 12 hardware-efficient ansatz (4 layers, 96
+    parameters), 4096 sets, energies for h in {0.5, 1, 2}; batched FP32 and
+    FP64 vs the per-circuit plain FP64 path."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, inputs
+    from paper_2401_06861_gb300.sim import Batch, State
+    build.build()
+    n, layers, nsets = 12, 4, 4096
+    hs = (0.5, 1.0, 2.0)
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    params = inputs.hea_params(n, layers, nsets, seed=4096)
+    terms = inputs.zz_terms(n) + inputs.x_terms(n)
+    coeffs = np.array([[-1.0] * (n - 1) + [-h] * n for h in hs])
+    stream = torch.cuda.current_stream()
+    p = torch.from_numpy(params).cuda()
+    res = {}
+    for dtype in (L.F32, L.F64):
+        b = Batch([dict(n=n, gates=gates, param_index=pidx, terms=terms, coeffs=coeffs)], layers * 2 * n, dtype,
+                  stream=stream.cuda_stream)
+        out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            b.run(p.data_ptr(), nsets, out.data_ptr(), stream=stream.cuda_stream, graph=True)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            b.run(p.data_ptr(), nsets, out.data_ptr(), stream=stream.cuda_stream, graph=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        sec = t0.elapsed_time(t1) / args.steps / 1e3
+        res[dtype] = (out.cpu().numpy(), sec)
+        b.close()
+    # per-circuit plain FP64 path on a sample of the sets
+    sample = 64
+    t0 = time.perf_counter()
+    plain = []
+    for s in range(sample):
+        g = [(name, q, (params[s][k],) if k >= 0 else prm) for (name, q, prm), k in zip(gates, pidx)]
+        with State(L.SV, n, L.F64, stream=stream.cuda_stream) as st:
+            st.apply(g, flags=L.PLAN_PLAIN)
+            plain.append([st.expect(inputs.tfim_terms(n, 1.0, h), sum=True) for h in hs])
+    psec = (time.perf_counter() - t0) / sample
+    plain = np.array(plain)
+    ref = res[L.F64][0]
+    norm1 = np.array([(n - 1) + n * h for h in hs])
+    for dtype, name in ((L.F32, "f32"), (L.F64, "f64")):
+        out, sec = res[dtype]
+        err = float(np.max(np.abs(out - ref) / np.maximum(np.abs(ref), norm1)))
+        line = {"workload": "vqe_hea_n12_4layers_4096sets", "path": f"batched_{name}", "metric": "energies/s",
+                "value": 3 * nsets / sec, "unit": "energies/s", "ms_per_batch": sec * 1e3,
+                "rel_energy_err_vs_batched_f64": err,
+                "vs_plain_f64_per_circuit": (3 * nsets / sec) / (3 / psec)}
+        print(json.dumps(line), flush=True)
+    err = float(np.max(np.abs(plain - ref[:sample]) / np.maximum(np.abs(ref[:sample]), norm1)))
+    print(json.dumps({"workload": "vqe_hea_n12_4layers_4096sets", "path": "plain_f64_per_circuit",
+                      "metric": "energies/s", "value": 3 / psec, "unit": "energies/s",
+                      "sample": f"{sample} sets, host wall clock", "rel_energy_err_vs_batched_f64": err}), flush=True)
+
+
+def run_serve(args):
+    """Serving: Poisson stream (200 circuits/s for --serve-seconds), 70% SV
+    n ~ U{8..26}, 30% DM n ~ U{6..12}; served FP32 (continuous batching,
+    8 streams) vs plain FP64 serial on the first seconds of the same stream."""
+    import numpy as np
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, inputs
+    from paper_2401_06861_gb300.serve import GpuExecutor, Server, summarize
+    build.build()
+    reqs = inputs.serve_requests(rate=200.0, duration=args.serve_seconds, seed=200)
+    warm = inputs.serve_requests(rate=200.0, duration=1.0, seed=7, sv_n=(8, 20), dm_n=(6, 9))
+    Server(GpuExecutor(L.F32), slots=8, dtype=L.F32).serve(warm)
+    srv = Server(GpuExecutor(L.F32), slots=8, dtype=L.F32, budget_bytes=150e9)
+    res = srv.serve(reqs)
+    s = summarize(res, srv.wall)
+    s.update(workload=f"serve_poisson200_{args.serve_seconds:g}s", path="served_f32", metric="circuits/s",
+             value=s["circuits_per_s"], unit="circuits/s", offered=len(reqs) / args.serve_seconds,
+             peak_budget_bytes=srv.ledger.peak,
+             batched=sum(1 for r in res.values() if r["path"] == "batch"))
+    print(json.dumps(s), flush=True)
+    window = min(args.serve_seconds, args.serial_seconds)
+    sub = [r for r in reqs if r["arrival"] < window]
+    ser = Server(GpuExecutor(L.F64, plan_flags=L.PLAN_PLAIN), slots=1, batch_max_n=0, dtype=L.F64)
+    res2 = ser.serve(sub)
+    s2 = summarize(res2, ser.wall)
+    s2.update(workload=f"serve_poisson200_first{window:g}s", path="plain_f64_serial", metric="circuits/s",
+              value=s2["circuits_per_s"], unit="circuits/s", offered=len(sub) / window)
+    print(json.dumps(s2), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -265,6 +413,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "serve"])
+    ap.add_argument("--sv-n", type=int, default=34)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serial-seconds", type=float, default=5.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_init()
@@ -274,6 +426,12 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return rc
+    if args.workload == "sv":
+        return run_sv(args)
+    if args.workload == "vqe":
+        return run_vqe(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args, ws, rank, local)
 
 

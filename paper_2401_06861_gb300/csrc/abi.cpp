@@ -83,7 +83,11 @@ static int plan_upload(Plan& p, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(p.mu);
   if (p.dev) return NWQ_OK;
   size_t ob = p.ops.size() * sizeof(DevOp);
-  size_t total = ob + p.ents.size() + 16;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t o_ph = al(ob + p.ents.size());
+  size_t o_po = al(o_ph + p.phases.size() * sizeof(PhaseDesc));
+  size_t o_pc = al(o_po + p.pops.size() * sizeof(PhaseOp));
+  size_t total = al(o_pc + p.pcoef.size()) + 16;
   void* d = nullptr;
   if (p.stream_ordered) {
     CK(cudaMallocAsync(&d, total, s), "plan table allocation");
@@ -94,6 +98,17 @@ static int plan_upload(Plan& p, cudaStream_t s) {
   if (ob) CK(cudaMemcpyAsync(d, p.ops.data(), ob, cudaMemcpyHostToDevice, s), "plan upload");
   if (!p.ents.empty())
     CK(cudaMemcpyAsync((char*)d + ob, p.ents.data(), p.ents.size(), cudaMemcpyHostToDevice, s), "plan upload");
+  if (!p.phases.empty())
+    CK(cudaMemcpyAsync((char*)d + o_ph, p.phases.data(), p.phases.size() * sizeof(PhaseDesc), cudaMemcpyHostToDevice, s),
+       "plan upload");
+  if (!p.pops.empty())
+    CK(cudaMemcpyAsync((char*)d + o_po, p.pops.data(), p.pops.size() * sizeof(PhaseOp), cudaMemcpyHostToDevice, s),
+       "plan upload");
+  if (!p.pcoef.empty())
+    CK(cudaMemcpyAsync((char*)d + o_pc, p.pcoef.data(), p.pcoef.size(), cudaMemcpyHostToDevice, s), "plan upload");
+  p.pt_off[0] = o_ph;
+  p.pt_off[1] = o_po;
+  p.pt_off[2] = o_pc;
   CK(cudaStreamSynchronize(s), "plan upload");
   p.dev = d;
   p.dev_bytes = total;
@@ -105,9 +120,12 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
   if (rc) return rc;
   const DevOp* ops = (const DevOp*)p.dev;
   const void* ents = (const char*)p.dev + p.ops.size() * sizeof(DevOp);
+  PhaseTables pt{(const PhaseDesc*)((const char*)p.dev + p.pt_off[0]), (const PhaseOp*)((const char*)p.dev + p.pt_off[1]),
+                 (const char*)p.dev + p.pt_off[2]};
   for (const SweepDesc& sd : p.sweeps) {
     if (sd.nops == 0) continue;
-    cudaError_t e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents, sm_count, s);
+    cudaError_t e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents,
+                                 p.phases.empty() ? nullptr : &pt, sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   }
   return NWQ_OK;

@@ -17,8 +17,16 @@ constexpr int kExpectChunk = 16;         // terms per expectation launch
 constexpr int kMaxDynSmem = 200 * 1024;      // dynamic shared memory cap of the sweep kernel
 constexpr int kTableSmemLimit = 112 * 1024;  // stage a sweep's tables in shared memory up to this total
 
+struct PhaseTables {
+  const PhaseDesc* ph;
+  const PhaseOp* po;
+  const void* pc;
+};
+
+// Complex sweeps with register phases run the phase kernel; everything else
+// (real DM sweeps, tiny tiles) the row kernel.
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
-                         const void* ents, int sm_count, cudaStream_t s);
+                         const void* ents, const PhaseTables* pt, int sm_count, cudaStream_t s);
 cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s);
 cudaError_t launch_real_to_cplx(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_cplx_to_real(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);

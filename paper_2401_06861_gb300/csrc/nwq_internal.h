@@ -74,8 +74,52 @@ struct SweepDesc {
   uint32_t op0;    // index of the first operator
   uint32_t ent0;   // index of the first entry of the sweep's operators
   uint32_t nent;   // number of entries of the sweep's operators
+  uint32_t ph0;    // complex sweeps: first phase (absolute index)
+  uint32_t nph;    //                 number of phases
+  uint32_t pop0;   //                 first phase operator
+  uint32_t npop;   //                 number of phase operators
+  uint32_t pc0;    //                 first coefficient
+  uint32_t npc;    //                 number of coefficients
   uint8_t hpos[kMaxHigh];  // global position of high tile bit i (ascending, >= m)
   uint8_t pad;
 };
+
+}  // namespace nwq
+
+namespace nwq {
+
+// ---------------------------------------------------------------- register phases
+// Complex (state-vector) sweeps run as *phases*: a phase fixes 4 tile bits U;
+// every thread holds the 16 elements of a group (all values of the U bits)
+// in registers and applies the phase's operators there, so shared memory is
+// read and written once per phase instead of once per operator.  Dense and
+// permutation operators act on a subset of U; diagonal operators may act on
+// any tile bits (their factor depends only on the element's index).
+enum : uint8_t { PO_DIAG = 0, PO_PERM = 1, PO_DENSE = 2 };
+
+// DENSE structure classes (select the arithmetic at compile time).
+enum : uint8_t { PD_GEN = 0, PD_REAL = 1, PD_XROT = 2 };
+
+struct PhaseOp {
+  uint8_t cls;       // PO_*
+  uint8_t k;         // operator bits
+  uint8_t mask;      // PERM / DENSE: positions inside U (bit p set = U[p]); operator bit t is the t-th set bit
+  uint8_t form;      // DENSE: PD_* (PD_XROT: k = 1, real diagonal, imaginary off-diagonal)
+  uint8_t dpos[4];   // DIAG: tile-local bit position of operator bit t
+  uint32_t coef;     // DIAG: 2^k factors; DENSE: 2^k x 2^k row-major (complex entries)
+  uint8_t dnu;       // DIAG: operator bits t outside the register bits (bit t set)
+  uint8_t pad[3];
+  uint64_t uidx;     // DIAG: 4-bit factor-index contribution of register element i at bits 4i..4i+3
+  uint8_t perm[8];   // PERM: output i = (perm[i] & 0x80 ? -1 : 1) * input (perm[i] & 15), k <= 2
+};
+static_assert(sizeof(PhaseOp) == 32, "PhaseOp must be 32 bytes");
+
+struct alignas(16) PhaseDesc {
+  uint8_t u[4];      // tile-local positions of the register bits, ascending
+  uint32_t op0;      // first PhaseOp (absolute index)
+  uint32_t nops;
+  uint32_t pad;      // 16-byte records keep the shared-memory copies aligned
+};
+static_assert(sizeof(PhaseDesc) == 16, "PhaseDesc must be 16 bytes");
 
 }  // namespace nwq

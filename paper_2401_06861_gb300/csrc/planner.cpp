@@ -477,6 +477,14 @@ static uint64_t op_mask(const BitOp& op) {
   return m;
 }
 
+static bool is_diagonal(const BitOp& op) {
+  int d = 1 << op.k;
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++)
+      if (i != j && op.m[(size_t)i * d + j] != cd(0.0)) return false;
+  return true;
+}
+
 static void merge_ops(std::vector<BitOp>& ops, bool is_complex, int max_bits) {
   if (ops.empty()) return;
   std::vector<BitOp> out;
@@ -487,6 +495,14 @@ static void merge_ops(std::vector<BitOp>& ops, bool is_complex, int max_bits) {
     BitOp C;
     bool share = (op_mask(cur) & op_mask(ops[i])) != 0;
     if (share && compose(cur, ops[i], max_bits, C)) {
+      // complex operators run in register phases: keep non-diagonal products
+      // within 2 bits (diagonal ones may use all 4)
+      if (is_complex && C.k > 2 && !is_diagonal(C)) {
+        out.push_back(std::move(cur));
+        cur = std::move(ops[i]);
+        ccur = op_cost(cur, is_complex);
+        continue;
+      }
       double cc = op_cost(C, is_complex);
       double cb = op_cost(ops[i], is_complex);
       if (cc <= ccur + cb + 1e-12) {
@@ -503,10 +519,171 @@ static void merge_ops(std::vector<BitOp>& ops, bool is_complex, int max_bits) {
   ops.swap(out);
 }
 
+// ------------------------------------------------------------------ register phases
+static bool is_signed_perm(const BitOp& op) {
+  int d = 1 << op.k;
+  for (int i = 0; i < d; i++) {
+    int cnt = 0;
+    for (int j = 0; j < d; j++) {
+      cd v = op.m[(size_t)i * d + j];
+      if (v == cd(0.0)) continue;
+      if (!is_unit(v)) return false;
+      cnt++;
+    }
+    if (cnt != 1) return false;
+  }
+  return true;
+}
+
+// Group each complex sweep's operators into phases of RB register bits.
+static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& order, Plan& plan) {
+  const bool f64 = plan.dtype == NWQ_F64;
+  const int RB = f64 ? 3 : 4;  // register bits: 8 complex128 or 16 complex64 elements per thread
+  plan.phases.clear();
+  plan.pops.clear();
+  plan.pcoef.clear();
+  size_t ncoef = 0;
+  auto push_coef = [&](cd v) {
+    if (f64) {
+      double c[2] = {v.real(), v.imag()};
+      plan.pcoef.insert(plan.pcoef.end(), (unsigned char*)c, (unsigned char*)c + sizeof(c));
+    } else {
+      float c[2] = {(float)v.real(), (float)v.imag()};
+      plan.pcoef.insert(plan.pcoef.end(), (unsigned char*)c, (unsigned char*)c + sizeof(c));
+    }
+    ncoef++;
+  };
+  for (SweepDesc& sd : plan.sweeps) {
+    sd.ph0 = (uint32_t)plan.phases.size();
+    sd.pop0 = (uint32_t)plan.pops.size();
+    sd.pc0 = (uint32_t)ncoef;
+    bool ok = sd.T >= RB;  // register groups need RB tile bits
+    for (int s = 0; s < sd.nops && ok; s++) {
+      const BitOp& op = ops[order[sd.op0 + s]];
+      ok = is_diagonal(op) || op.k <= 2;  // register operators act on at most 2 bits
+    }
+    if (!ok) {  // the row kernel runs this sweep
+      sd.nph = sd.npop = sd.npc = 0;
+      continue;
+    }
+    int local[64];
+    for (int b = 0; b < 64; b++) local[b] = -1;
+    for (int b = 0; b < sd.m; b++) local[b] = b;
+    for (int i = 0; i < sd.h; i++) local[sd.hpos[i]] = sd.m + i;
+    std::vector<std::pair<uint32_t, std::vector<int>>> groups;  // (U mask, op indices)
+    uint32_t U = 0;
+    std::vector<int> cur;
+    for (int s = 0; s < sd.nops; s++) {
+      const BitOp& op = ops[order[sd.op0 + s]];
+      if (!is_diagonal(op)) {
+        uint32_t bm = 0;
+        for (int t = 0; t < op.k; t++) bm |= 1u << local[op.bits[t]];
+        if (__builtin_popcount(U | bm) > RB) {
+          groups.push_back({U, cur});
+          U = 0;
+          cur.clear();
+        }
+        U |= bm;
+      }
+      cur.push_back(order[sd.op0 + s]);
+    }
+    if (!cur.empty()) groups.push_back({U, cur});
+    for (auto& gr : groups) {
+      uint32_t Um = gr.first;
+      // fill to RB register bits from the highest tile bits (the low bits stay
+      // with the lanes of a warp, for conflict-free shared-memory access)
+      for (int b = sd.T - 1; b >= 0 && __builtin_popcount(Um) < RB; b--) Um |= 1u << b;
+      PhaseDesc pd;
+      std::memset(&pd, 0, sizeof(pd));
+      int upos[4] = {0, 0, 0, 0}, nu = 0;
+      for (int b = 0; b < sd.T; b++)
+        if ((Um >> b) & 1) upos[nu++] = b;
+      for (int p = 0; p < RB; p++) pd.u[p] = (uint8_t)upos[p];
+      pd.op0 = (uint32_t)plan.pops.size();
+      for (int oi : gr.second) {
+        const BitOp& op = ops[oi];
+        PhaseOp po;
+        std::memset(&po, 0, sizeof(po));
+        po.k = (uint8_t)op.k;
+        po.coef = (uint32_t)ncoef;
+        int dim = 1 << op.k;
+        if (is_diagonal(op)) {
+          po.cls = PO_DIAG;
+          for (int t = 0; t < op.k; t++) po.dpos[t] = (uint8_t)local[op.bits[t]];
+          // factor index = (bits of the group base outside U) | uidx[register element]
+          uint64_t uidx = 0;
+          for (int t = 0; t < op.k; t++) {
+            int p = -1;
+            for (int q = 0; q < RB; q++)
+              if (upos[q] == local[op.bits[t]]) p = q;
+            if (p < 0) {
+              po.dnu |= (uint8_t)(1u << t);
+              continue;
+            }
+            for (int i = 0; i < (1 << RB); i++)
+              if ((i >> p) & 1) uidx |= (uint64_t)1 << (4 * i + t);
+          }
+          po.uidx = uidx;
+          for (int i = 0; i < dim; i++) push_coef(op.m[(size_t)i * dim + i]);
+        } else {
+          // operator bit t -> register position; reorder to ascending positions
+          int rp[4];
+          for (int t = 0; t < op.k; t++)
+            for (int p = 0; p < RB; p++)
+              if (upos[p] == local[op.bits[t]]) rp[t] = p;
+          int ord[4];
+          for (int t = 0; t < op.k; t++) ord[t] = t;
+          std::sort(ord, ord + op.k, [&](int a, int b) { return rp[a] < rp[b]; });
+          uint8_t mask = 0;
+          for (int t = 0; t < op.k; t++) mask |= (uint8_t)(1u << rp[t]);
+          po.mask = mask;
+          auto remap = [&](int inew) {  // new index (bit t = ord[t]) -> old index
+            int iold = 0;
+            for (int t = 0; t < op.k; t++) iold |= ((inew >> t) & 1) << ord[t];
+            return iold;
+          };
+          if (is_signed_perm(op)) {
+            po.cls = PO_PERM;
+            for (int i = 0; i < dim; i++) {
+              int oi2 = remap(i);
+              for (int j = 0; j < dim; j++) {
+                cd v = op.m[(size_t)oi2 * dim + remap(j)];
+                if (v != cd(0.0)) po.perm[i] = (uint8_t)(j | (v.real() < 0 ? 0x80 : 0));
+              }
+            }
+          } else {
+            po.cls = PO_DENSE;
+            bool real = true;
+            for (int i = 0; i < dim; i++)
+              for (int j = 0; j < dim; j++) {
+                cd v = op.m[(size_t)remap(i) * dim + remap(j)];
+                real &= v.imag() == 0.0;
+                push_coef(v);
+              }
+            bool xrot = op.k == 1 && op.m[0].imag() == 0.0 && op.m[3].imag() == 0.0 && op.m[1].real() == 0.0 &&
+                        op.m[2].real() == 0.0;
+            po.form = real ? PD_REAL : (xrot ? PD_XROT : PD_GEN);
+          }
+        }
+        plan.pops.push_back(po);
+      }
+      pd.nops = (uint32_t)plan.pops.size() - pd.op0;
+      plan.phases.push_back(pd);
+    }
+    sd.nph = (uint32_t)plan.phases.size() - sd.ph0;
+    sd.npop = (uint32_t)plan.pops.size() - sd.pop0;
+    sd.npc = (uint32_t)ncoef - sd.pc0;
+  }
+}
+
 // ------------------------------------------------------------------ sweeps
 void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
   const bool cplx = plan.is_complex;
-  if (opt.merge && !opt.plain) merge_ops(ops, cplx, opt.max_merge_bits);
+  if (opt.merge && !opt.plain) {
+    merge_ops(ops, cplx, opt.max_merge_bits);
+    // complex: a second pass joins diagonal operators that became adjacent
+    if (cplx) merge_ops(ops, cplx, opt.max_merge_bits);
+  }
   if (!cplx && opt.rescale_qubits > 0) rescale_dm(ops, opt.rescale_qubits, plan.dtype == NWQ_F64 ? 0x1p-40 : 0x1p-6);
 
   const int B = plan.B;
@@ -658,6 +835,7 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
     sd.ent0 = (uint32_t)sweep_ent0;
     sd.nent = (uint32_t)(nent - sweep_ent0);
   }
+  if (cplx) build_phases(ops, order, plan);
   double state_bytes = (double)plan.elem_bytes * (double)(1ull << B);
   plan.bytes = 2.0 * state_bytes * (double)plan.sweeps.size();
 }

@@ -41,6 +41,11 @@ struct Plan {
   std::vector<DevOp> ops;
   std::vector<unsigned char> ents;  // EntR<R> or EntC<R> records
   std::vector<int> op_gate0, op_ngates;
+  // complex plans: register phases (see nwq_internal.h)
+  std::vector<PhaseDesc> phases;
+  std::vector<PhaseOp> pops;
+  std::vector<unsigned char> pcoef;  // complex coefficients (float2 or double2)
+  size_t pt_off[3] = {0, 0, 0};      // device offsets of phases, phase operators, coefficients
   double fma_per_elem = 0.0;  // summed over operators, per state element
   double bytes = 0.0;         // algorithmic bytes per run
   // device copy (lazy upload on first run)

@@ -208,6 +208,47 @@ __device__ __forceinline__ uint64_t deposit(uint64_t v, uint64_t mask) {
   return out;
 }
 
+// Padded tile layout: one 16-byte pad after every 128 bytes of elements, so
+// lanes whose indices differ by multiples of 128 bytes fall on different
+// banks.  pad(a | b) = pad(a) + pad(b) for indices with disjoint bits, which
+// lets a phase precompute per-register offsets (an element address is then
+// one add) and keeps 16-byte vectors contiguous and aligned.
+template <class C>
+__device__ __forceinline__ uint32_t swz(uint32_t l) {
+  if constexpr (sizeof(C) == 16) return l + (l >> 3);       // 8 complex128 + 1 pad
+  else return l + ((l >> 4) << 1);                          // 16 complex64 + 2 pad
+}
+template <class C>
+__host__ __device__ constexpr size_t padded_elems(int T) {
+  return sizeof(C) == 16 ? ((size_t)1 << T) + ((size_t)1 << T) / 8 : ((size_t)1 << T) + ((size_t)1 << T) / 8;
+}
+
+// 16-byte asynchronous global -> shared copies (completion by group waits).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Byte offset of the chunk-offset table in shared memory: after the tile(s)
+// (tile_bytes_per_elem << T) and, when the tables are staged, after them.
+__host__ __device__ inline size_t hoff_offset(const SweepDesc& sd, size_t tile_bytes_per_elem, bool tbl,
+                                              size_t table_bytes) {
+  size_t o = (tile_bytes_per_elem << sd.T) + (tbl ? table_bytes : 0);
+  return (o + 15) & ~(size_t)15;
+}
+
+template <class C>
+__host__ __device__ inline size_t phase_hoff_offset(const SweepDesc& sd, bool tbl) {
+  size_t o = 2 * sizeof(C) * padded_elems<C>(sd.T);
+  if (tbl) o += sizeof(PhaseDesc) * sd.nph + sizeof(PhaseOp) * sd.npop + sizeof(C) * sd.npc;
+  return (o + 15) & ~(size_t)15;
+}
+
 template <class R, bool CPLX>
 using ElemT = typename std::conditional<CPLX, typename Cplx<R>::T, R>::type;
 template <class R, bool CPLX>
@@ -244,13 +285,17 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(void* __restrict__
   const uint32_t nvec = (1u << T) / VPE;
   const int lvpc = sd.m - __ffs(VPE) + 1;  // log2(vectors per contiguous chunk)
   const uint32_t vpc_mask = (1u << lvpc) - 1u;
+  // global offset of each strided chunk of the tile, computed once per CTA
+  uint64_t* hoff = reinterpret_cast<uint64_t*>(smem_raw + hoff_offset(sd, 2 * sizeof(E), TBL,
+                                                                     sizeof(DevOp) * sd.nops + sizeof(Ent) * sd.nent));
+  for (uint32_t j = threadIdx.x; j < (1u << sd.h); j += kSweepThreads) hoff[j] = deposit(j, sd.hmask);
+  __syncthreads();
 
   for (uint64_t tileid = blockIdx.x; tileid < ntiles; tileid += gridDim.x) {
     // base = tile id scattered onto the non-tile bits
     const uint64_t base = deposit(tileid, sd.fmask);
     for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
-      uint32_t j = v >> lvpc;
-      uint64_t off = base + deposit(j, sd.hmask) + (uint64_t)(v & vpc_mask) * VPE;
+      uint64_t off = base + hoff[v >> lvpc] + (uint64_t)(v & vpc_mask) * VPE;
       reinterpret_cast<uint4*>(tileA)[v] = __ldg(reinterpret_cast<const uint4*>(state + off));
     }
     __syncthreads();
@@ -280,12 +325,278 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(void* __restrict__
       dst = t;
     }
     for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
-      uint32_t j = v >> lvpc;
-      uint64_t off = base + deposit(j, sd.hmask) + (uint64_t)(v & vpc_mask) * VPE;
+      uint64_t off = base + hoff[v >> lvpc] + (uint64_t)(v & vpc_mask) * VPE;
       reinterpret_cast<uint4*>(state + off)[0] = reinterpret_cast<const uint4*>(src)[v];
     }
     __syncthreads();
   }
+}
+
+// ------------------------------------------------------------------ register-phase kernel (complex)
+// One shared-memory tile per CTA (XOR-swizzled so that lanes differing only in
+// higher index bits hit different banks).  Per phase every thread loads the
+// 16 elements of a group (all values of the phase's 4 register bits) into
+// registers, applies the phase's operators there and stores them back.
+__host__ __device__ constexpr int dep4(int v, int mask) {  // deposit v's low bits on mask's set bits
+  int out = 0, bit = 0;
+  for (int p = 0; p < 4; p++)
+    if ((mask >> p) & 1) {
+      if ((v >> bit) & 1) out |= 1 << p;
+      bit++;
+    }
+  return out;
+}
+__host__ __device__ constexpr int popc4(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
+
+template <class R>
+__device__ __forceinline__ typename Cplx<R>::T cfma(typename Cplx<R>::T c, typename Cplx<R>::T x, typename Cplx<R>::T acc) {
+  acc.x = fma(c.x, x.x, fma(-c.y, x.y, acc.x));
+  acc.y = fma(c.x, x.y, fma(c.y, x.x, acc.y));
+  return acc;
+}
+
+// Dense operator on register bits MASK (k <= 2) of NR-element groups, with the
+// arithmetic fixed by its structure form: general complex (4 FMA per entry),
+// real (2 FMA per entry) or X-rotation [[a, i b], [i c, d]] (2 FMA per entry).
+template <int NR, int MASK, int FORM, class R>
+__device__ __forceinline__ void phase_dense(typename Cplx<R>::T (&r)[NR], const typename Cplx<R>::T* __restrict__ c) {
+  using C = typename Cplx<R>::T;
+  constexpr int K = popc4(MASK), D = 1 << K;
+  C m[D * D];
+#pragma unroll
+  for (int e = 0; e < D * D; e++) m[e] = c[e];
+#pragma unroll
+  for (int o = 0; o < NR; o++) {
+    if (o & MASK) continue;
+    C in[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) in[j] = r[o | dep4(j, MASK)];
+    if constexpr (FORM == PD_XROT) {  // K == 1
+      const C a = in[0], b = in[1];
+      r[o] = C{fma(m[0].x, a.x, -m[1].y * b.y), fma(m[0].x, a.y, m[1].y * b.x)};
+      r[o | MASK] = C{fma(m[3].x, b.x, -m[2].y * a.y), fma(m[3].x, b.y, m[2].y * a.x)};
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        C acc{R(0), R(0)};
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+          if constexpr (FORM == PD_REAL) {
+            acc.x = fma(m[i * D + j].x, in[j].x, acc.x);
+            acc.y = fma(m[i * D + j].x, in[j].y, acc.y);
+          } else {
+            acc = cfma<R>(m[i * D + j], in[j], acc);
+          }
+        }
+        r[o | dep4(i, MASK)] = acc;
+      }
+    }
+  }
+}
+
+// Signed permutation on register bits MASK (k <= 2): integer moves only.
+template <int NR, int MASK, class R>
+__device__ __forceinline__ void phase_perm(typename Cplx<R>::T (&r)[NR], const uint8_t* perm) {
+  using C = typename Cplx<R>::T;
+  constexpr int K = popc4(MASK), D = 1 << K;
+  uint8_t pm[D];
+#pragma unroll
+  for (int i = 0; i < D; i++) pm[i] = perm[i];
+#pragma unroll
+  for (int o = 0; o < NR; o++) {
+    if (o & MASK) continue;
+    C in[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) in[j] = r[o | dep4(j, MASK)];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      C v = in[0];
+#pragma unroll
+      for (int j = 1; j < D; j++) v = ((pm[i] & 15) == j) ? in[j] : v;
+      r[o | dep4(i, MASK)] = signed_base(v, (pm[i] & 0x80) ? 2 : 1);
+    }
+  }
+}
+
+template <int NR, int MASK, class R>
+__device__ __forceinline__ void phase_dense_any(typename Cplx<R>::T (&r)[NR], const typename Cplx<R>::T* c, int form) {
+  if (form == PD_REAL) phase_dense<NR, MASK, PD_REAL, R>(r, c);
+  else if (MASK == 1 || MASK == 2 || MASK == 4 || MASK == 8) {
+    if (form == PD_XROT) phase_dense<NR, MASK, PD_XROT, R>(r, c);
+    else phase_dense<NR, MASK, PD_GEN, R>(r, c);
+  } else {
+    phase_dense<NR, MASK, PD_GEN, R>(r, c);
+  }
+}
+
+#define NWQ_MASKS3(F) F(1) F(2) F(4) F(3) F(5) F(6)
+#define NWQ_MASKS4(F) F(1) F(2) F(4) F(8) F(3) F(5) F(6) F(9) F(10) F(12)
+
+template <class R, int RB, bool TBL>
+__global__ void __launch_bounds__(kSweepThreads) phase_kernel(void* __restrict__ state_v, uint64_t ntiles, SweepDesc sd,
+                                                              const PhaseDesc* __restrict__ ph_g,
+                                                              const PhaseOp* __restrict__ po_g,
+                                                              const void* __restrict__ pc_v) {
+  using C = typename Cplx<R>::T;
+  constexpr int NR = 1 << RB;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int T = sd.T;
+  const uint32_t PE = (uint32_t)padded_elems<C>(T);
+  C* tile = reinterpret_cast<C*>(smem_raw);    // current tile (padded layout)
+  C* ntile = tile + PE;                         // next tile, filled asynchronously
+  const PhaseDesc* phases = ph_g + sd.ph0;
+  const PhaseOp* pops = po_g + sd.pop0;
+  const C* coefs = reinterpret_cast<const C*>(pc_v) + sd.pc0;
+  if constexpr (TBL) {
+    PhaseDesc* sph = reinterpret_cast<PhaseDesc*>(tile + 2 * PE);
+    PhaseOp* spo = reinterpret_cast<PhaseOp*>(sph + sd.nph);  // 16-byte records: stays aligned
+    C* sc = reinterpret_cast<C*>(spo + sd.npop);
+    const uint4* a1 = reinterpret_cast<const uint4*>(phases);
+    uint4* b1 = reinterpret_cast<uint4*>(sph);
+    for (uint32_t v = threadIdx.x; v < sd.nph * (sizeof(PhaseDesc) / 16); v += kSweepThreads) b1[v] = a1[v];
+    const uint4* a2 = reinterpret_cast<const uint4*>(pops);
+    uint4* b2 = reinterpret_cast<uint4*>(spo);
+    for (uint32_t v = threadIdx.x; v < sd.npop * (sizeof(PhaseOp) / 16); v += kSweepThreads) b2[v] = a2[v];
+    for (uint32_t v = threadIdx.x; v < sd.npc; v += kSweepThreads) sc[v] = coefs[v];
+    phases = sph;
+    pops = spo;
+    coefs = sc;
+  }
+  C* state = reinterpret_cast<C*>(state_v);
+  constexpr int VPE = 16 / sizeof(C);
+  const uint32_t nvec = (1u << T) / VPE;
+  const int lvpc = sd.m - __ffs(VPE) + 1;
+  const uint32_t vpc_mask = (1u << lvpc) - 1u;
+  const uint32_t ngroups = 1u << (T - RB);
+  // global offset of each strided chunk of the tile, computed once per CTA
+  uint64_t* hoff = reinterpret_cast<uint64_t*>(smem_raw + phase_hoff_offset<C>(sd, TBL));
+  for (uint32_t j = threadIdx.x; j < (1u << sd.h); j += kSweepThreads) hoff[j] = deposit(j, sd.hmask);
+  __syncthreads();
+
+  auto prefetch = [&](uint64_t tid, C* dst) {
+    const uint64_t b = deposit(tid, sd.fmask);
+    for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads)
+      cp_async16(dst + swz<C>(v * VPE), state + b + hoff[v >> lvpc] + (uint64_t)(v & vpc_mask) * VPE);
+    cp_async_commit();
+  };
+  if (blockIdx.x < ntiles) prefetch(blockIdx.x, tile);
+  for (uint64_t tileid = blockIdx.x; tileid < ntiles; tileid += gridDim.x) {
+    const uint64_t base = deposit(tileid, sd.fmask);
+    const uint64_t next = tileid + gridDim.x;
+    if (next < ntiles) {
+      prefetch(next, ntile);  // overlaps with the phases below
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    for (uint32_t ph = 0; ph < sd.nph; ph++) {
+      const PhaseDesc P = phases[ph];
+      uint32_t roff[NR];  // padded offset of register element i inside its group
+#pragma unroll
+      for (int i = 0; i < NR; i++) {
+        uint32_t l = 0;
+#pragma unroll
+        for (int p = 0; p < RB; p++)
+          if ((i >> p) & 1) l |= 1u << P.u[p];
+        roff[i] = swz<C>(l);
+      }
+      const PhaseOp* pop = pops + (P.op0 - sd.pop0);
+      for (uint32_t g = threadIdx.x; g < ngroups; g += kSweepThreads) {
+        const uint32_t gb = insert_zeros<RB>(g, P.u);
+        const C* gt = tile + swz<C>(gb);
+        C r[NR];
+#pragma unroll
+        for (int i = 0; i < NR; i++) r[i] = gt[roff[i]];
+        for (uint32_t q = 0; q < P.nops; q++) {
+          const PhaseOp& o = pop[q];
+          if (o.cls == PO_DIAG) {
+            const C* d = coefs + (o.coef - sd.pc0);
+            uint32_t ig = 0;
+#pragma unroll
+            for (int t = 0; t < 4; t++)
+              if ((o.dnu >> t) & 1) ig |= ((gb >> o.dpos[t]) & 1u) << t;
+            const uint64_t ux = o.uidx;
+#pragma unroll
+            for (int i = 0; i < NR; i++) {
+              const C f = d[ig | (uint32_t)((ux >> (4 * i)) & 15u)];
+              r[i] = C{fma(f.x, r[i].x, -f.y * r[i].y), fma(f.x, r[i].y, f.y * r[i].x)};
+            }
+          } else if (o.cls == PO_PERM) {
+            switch (o.mask) {
+#define NWQ_PERM_CASE(M) \
+  case M: phase_perm<NR, M, R>(r, o.perm); break;
+              NWQ_MASKS3(NWQ_PERM_CASE)
+#undef NWQ_PERM_CASE
+#define NWQ_PERM_CASE4(M) \
+  case M: if constexpr (RB == 4) phase_perm<NR, M, R>(r, o.perm); break;
+              NWQ_PERM_CASE4(8) NWQ_PERM_CASE4(9) NWQ_PERM_CASE4(10) NWQ_PERM_CASE4(12)
+#undef NWQ_PERM_CASE4
+              default: break;
+            }
+          } else {
+            const C* c = coefs + (o.coef - sd.pc0);
+            switch (o.mask) {
+#define NWQ_DENSE_CASE(M) \
+  case M: phase_dense_any<NR, M, R>(r, c, o.form); break;
+              NWQ_MASKS3(NWQ_DENSE_CASE)
+#undef NWQ_DENSE_CASE
+#define NWQ_DENSE_CASE4(M) \
+  case M: if constexpr (RB == 4) phase_dense_any<NR, M, R>(r, c, o.form); break;
+              NWQ_DENSE_CASE4(8) NWQ_DENSE_CASE4(9) NWQ_DENSE_CASE4(10) NWQ_DENSE_CASE4(12)
+#undef NWQ_DENSE_CASE4
+              default: break;
+            }
+          }
+        }
+        C* gw = tile + swz<C>(gb);
+#pragma unroll
+        for (int i = 0; i < NR; i++) gw[roff[i]] = r[i];
+      }
+      __syncthreads();
+    }
+    for (uint32_t v = threadIdx.x; v < nvec; v += kSweepThreads) {
+      uint64_t off = base + hoff[v >> lvpc] + (uint64_t)(v & vpc_mask) * VPE;
+      *reinterpret_cast<uint4*>(state + off) = *reinterpret_cast<const uint4*>(tile + swz<C>(v * VPE));
+    }
+    __syncthreads();  // the current tile is refilled by the prefetch of the next iteration
+    C* t = tile;
+    tile = ntile;
+    ntile = t;
+  }
+  cp_async_wait<0>();
+}
+
+template <class R>
+static cudaError_t launch_phase_t(void* state, int B, const SweepDesc& sd, const PhaseTables& pt, int sm_count,
+                                  cudaStream_t s) {
+  using C = typename Cplx<R>::T;
+  constexpr int RB = sizeof(R) == 8 ? 3 : 4;
+  size_t tile = 2 * sizeof(C) * padded_elems<C>(sd.T);  // current + prefetched tile
+  size_t table = sd.nph * sizeof(PhaseDesc) + sd.npop * sizeof(PhaseOp) + sd.npc * sizeof(C);
+  const bool tbl = tile + table <= (size_t)kTableSmemLimit;
+  size_t smem = (tbl ? phase_hoff_offset<C>(sd, true) : phase_hoff_offset<C>(sd, false)) + ((size_t)8 << sd.h);
+  static int attr_dev[2] = {-1, -1};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev[tbl] != dev) {
+    cudaError_t e = tbl ? cudaFuncSetAttribute(phase_kernel<R, RB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)
+                        : cudaFuncSetAttribute(phase_kernel<R, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    attr_dev[tbl] = dev;
+  }
+  uint64_t ntiles = 1ull << (B - sd.T);
+  int per_sm = 0;
+  cudaError_t e = tbl ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_kernel<R, RB, true>, kSweepThreads, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, phase_kernel<R, RB, false>, kSweepThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)sm_count * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  if (tbl) phase_kernel<R, RB, true><<<(unsigned)grid, kSweepThreads, smem, s>>>(state, ntiles, sd, pt.ph, pt.po, pt.pc);
+  else phase_kernel<R, RB, false><<<(unsigned)grid, kSweepThreads, smem, s>>>(state, ntiles, sd, pt.ph, pt.po, pt.pc);
+  g_launches += 1;
+  return cudaGetLastError();
 }
 
 template <class R, bool CPLX, bool TBL>
@@ -319,13 +630,20 @@ static cudaError_t launch_sweep_t(void* state, int B, const SweepDesc& sd, const
   using Ent = EntT<R, CPLX>;
   size_t tiles = 2 * (sizeof(E) << sd.T);
   size_t table = sd.nops * sizeof(DevOp) + sd.nent * sizeof(Ent);
+  size_t hbytes = (size_t)8 << sd.h;
   if (tiles + table <= (size_t)kTableSmemLimit)
-    return launch_sweep_tt<R, CPLX, true>(state, B, sd, ops, ents, tiles + table, sm_count, s);
-  return launch_sweep_tt<R, CPLX, false>(state, B, sd, ops, ents, tiles, sm_count, s);
+    return launch_sweep_tt<R, CPLX, true>(state, B, sd, ops, ents,
+                                          hoff_offset(sd, 2 * sizeof(E), true, table) + hbytes, sm_count, s);
+  return launch_sweep_tt<R, CPLX, false>(state, B, sd, ops, ents, hoff_offset(sd, 2 * sizeof(E), false, 0) + hbytes,
+                                         sm_count, s);
 }
 
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
-                         const void* ents, int sm_count, cudaStream_t s) {
+                         const void* ents, const PhaseTables* pt, int sm_count, cudaStream_t s) {
+  if (cplx && pt && sd.nph > 0) {
+    if (f64) return launch_phase_t<double>(state, B, sd, *pt, sm_count, s);
+    return launch_phase_t<float>(state, B, sd, *pt, sm_count, s);
+  }
   if (cplx) {
     if (f64) return launch_sweep_t<double, true>(state, B, sd, ops, ents, sm_count, s);
     return launch_sweep_t<float, true>(state, B, sd, ops, ents, sm_count, s);
