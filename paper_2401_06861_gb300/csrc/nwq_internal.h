@@ -107,8 +107,9 @@ struct PhaseOp {
   uint8_t form;      // DENSE: PD_* (PD_XROT: k = 1, real diagonal, imaginary off-diagonal)
   uint8_t dpos[4];   // DIAG: tile-local bit position of operator bit t
   uint32_t coef;     // DIAG: 2^k factors; DENSE: 2^k x 2^k row-major (complex entries)
-  uint8_t dnu;       // DIAG: operator bits t outside the register bits (bit t set)
-  uint8_t pad[3];
+  uint8_t dnu;       // DIAG: number of operator bits outside the register bits
+  uint8_t code;      // dispatch code: DIAG 0..15 (mask), PERM 16 + mask, DENSE 32 + 16 * form + mask
+  uint8_t pad[2];
   uint64_t uidx;     // DIAG: 4-bit factor-index contribution of register element i at bits 4i..4i+3
   uint8_t perm[8];   // PERM: output i = (perm[i] & 0x80 ? -1 : 1) * input (perm[i] & 15), k <= 2
 };

@@ -609,22 +609,42 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
         int dim = 1 << op.k;
         if (is_diagonal(op)) {
           po.cls = PO_DIAG;
-          for (int t = 0; t < op.k; t++) po.dpos[t] = (uint8_t)local[op.bits[t]];
-          // factor index = (bits of the group base outside U) | uidx[register element]
-          uint64_t uidx = 0;
+          // Factor table reindexed as (bits outside the register bits, in
+          // operator order) << kU | (register bits, in ascending position order),
+          // so the kernel indexes it with a compile-time register offset.
+          int upos_of[4], nout = 0, kU = 0;
+          int outt[4];
+          uint8_t SU = 0;
           for (int t = 0; t < op.k; t++) {
-            int p = -1;
+            upos_of[t] = -1;
             for (int q = 0; q < RB; q++)
-              if (upos[q] == local[op.bits[t]]) p = q;
-            if (p < 0) {
-              po.dnu |= (uint8_t)(1u << t);
-              continue;
+              if (upos[q] == local[op.bits[t]]) upos_of[t] = q;
+            if (upos_of[t] < 0) {
+              outt[nout] = t;
+              po.dpos[nout++] = (uint8_t)local[op.bits[t]];
+            } else {
+              SU |= (uint8_t)(1u << upos_of[t]);
             }
-            for (int i = 0; i < (1 << RB); i++)
-              if ((i >> p) & 1) uidx |= (uint64_t)1 << (4 * i + t);
           }
-          po.uidx = uidx;
-          for (int i = 0; i < dim; i++) push_coef(op.m[(size_t)i * dim + i]);
+          kU = __builtin_popcount(SU);
+          po.mask = SU;
+          po.dnu = (uint8_t)nout;
+          for (int nidx = 0; nidx < dim; nidx++) {
+            int uval = nidx & ((1 << kU) - 1), oval = nidx >> kU;
+            int old = 0;
+            // register part: the c-th set bit of SU carries bit c of uval
+            int c = 0;
+            for (int q = 0; q < RB; q++)
+              if ((SU >> q) & 1) {
+                if ((uval >> c) & 1)
+                  for (int t = 0; t < op.k; t++)
+                    if (upos_of[t] == q) old |= 1 << t;
+                c++;
+              }
+            for (int o2 = 0; o2 < nout; o2++)
+              if ((oval >> o2) & 1) old |= 1 << outt[o2];
+            push_coef(op.m[(size_t)old * dim + old]);
+          }
         } else {
           // operator bit t -> register position; reorder to ascending positions
           int rp[4];
@@ -665,6 +685,7 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
             po.form = real ? PD_REAL : (xrot ? PD_XROT : PD_GEN);
           }
         }
+        po.code = po.cls == PO_DIAG ? po.mask : (po.cls == PO_PERM ? 16 + po.mask : 32 + 16 * po.form + po.mask);
         plan.pops.push_back(po);
       }
       pd.nops = (uint32_t)plan.pops.size() - pd.op0;

@@ -394,6 +394,28 @@ __device__ __forceinline__ void phase_dense(typename Cplx<R>::T (&r)[NR], const 
   }
 }
 
+__host__ __device__ constexpr int pext4(int v, int mask) {  // gather v's bits at mask positions
+  int out = 0, bit = 0;
+  for (int p = 0; p < 4; p++)
+    if ((mask >> p) & 1) {
+      if ((v >> p) & 1) out |= 1 << bit;
+      bit++;
+    }
+  return out;
+}
+
+// Diagonal operator whose register-bit part is SU: factor of register
+// element i is dg[pext(i, SU)] (compile-time offset; no integer work).
+template <int NR, int SU, class R>
+__device__ __forceinline__ void phase_diag(typename Cplx<R>::T (&r)[NR], const typename Cplx<R>::T* __restrict__ dg) {
+  using C = typename Cplx<R>::T;
+#pragma unroll
+  for (int i = 0; i < NR; i++) {
+    const C f = dg[pext4(i, SU)];
+    r[i] = C{fma(f.x, r[i].x, -f.y * r[i].y), fma(f.x, r[i].y, f.y * r[i].x)};
+  }
+}
+
 // Signed permutation on register bits MASK (k <= 2): integer moves only.
 template <int NR, int MASK, class R>
 __device__ __forceinline__ void phase_perm(typename Cplx<R>::T (&r)[NR], const uint8_t* perm) {
@@ -418,19 +440,6 @@ __device__ __forceinline__ void phase_perm(typename Cplx<R>::T (&r)[NR], const u
   }
 }
 
-template <int NR, int MASK, class R>
-__device__ __forceinline__ void phase_dense_any(typename Cplx<R>::T (&r)[NR], const typename Cplx<R>::T* c, int form) {
-  if (form == PD_REAL) phase_dense<NR, MASK, PD_REAL, R>(r, c);
-  else if (MASK == 1 || MASK == 2 || MASK == 4 || MASK == 8) {
-    if (form == PD_XROT) phase_dense<NR, MASK, PD_XROT, R>(r, c);
-    else phase_dense<NR, MASK, PD_GEN, R>(r, c);
-  } else {
-    phase_dense<NR, MASK, PD_GEN, R>(r, c);
-  }
-}
-
-#define NWQ_MASKS3(F) F(1) F(2) F(4) F(3) F(5) F(6)
-#define NWQ_MASKS4(F) F(1) F(2) F(4) F(8) F(3) F(5) F(6) F(9) F(10) F(12)
 
 template <class R, int RB, bool TBL>
 __global__ void __launch_bounds__(kSweepThreads) phase_kernel(void* __restrict__ state_v, uint64_t ntiles, SweepDesc sd,
@@ -510,43 +519,32 @@ __global__ void __launch_bounds__(kSweepThreads) phase_kernel(void* __restrict__
         for (int i = 0; i < NR; i++) r[i] = gt[roff[i]];
         for (uint32_t q = 0; q < P.nops; q++) {
           const PhaseOp& o = pop[q];
-          if (o.cls == PO_DIAG) {
-            const C* d = coefs + (o.coef - sd.pc0);
+          const C* cf = coefs + (o.coef - sd.pc0);
+          const int code = o.code;
+          if (code < 16) {  // diagonal: factor table offset by the out-of-register bits
             uint32_t ig = 0;
 #pragma unroll
-            for (int t = 0; t < 4; t++)
-              if ((o.dnu >> t) & 1) ig |= ((gb >> o.dpos[t]) & 1u) << t;
-            const uint64_t ux = o.uidx;
-#pragma unroll
-            for (int i = 0; i < NR; i++) {
-              const C f = d[ig | (uint32_t)((ux >> (4 * i)) & 15u)];
-              r[i] = C{fma(f.x, r[i].x, -f.y * r[i].y), fma(f.x, r[i].y, f.y * r[i].x)};
-            }
-          } else if (o.cls == PO_PERM) {
-            switch (o.mask) {
-#define NWQ_PERM_CASE(M) \
-  case M: phase_perm<NR, M, R>(r, o.perm); break;
-              NWQ_MASKS3(NWQ_PERM_CASE)
-#undef NWQ_PERM_CASE
-#define NWQ_PERM_CASE4(M) \
-  case M: if constexpr (RB == 4) phase_perm<NR, M, R>(r, o.perm); break;
-              NWQ_PERM_CASE4(8) NWQ_PERM_CASE4(9) NWQ_PERM_CASE4(10) NWQ_PERM_CASE4(12)
-#undef NWQ_PERM_CASE4
-              default: break;
-            }
-          } else {
-            const C* c = coefs + (o.coef - sd.pc0);
-            switch (o.mask) {
-#define NWQ_DENSE_CASE(M) \
-  case M: phase_dense_any<NR, M, R>(r, c, o.form); break;
-              NWQ_MASKS3(NWQ_DENSE_CASE)
-#undef NWQ_DENSE_CASE
-#define NWQ_DENSE_CASE4(M) \
-  case M: if constexpr (RB == 4) phase_dense_any<NR, M, R>(r, c, o.form); break;
-              NWQ_DENSE_CASE4(8) NWQ_DENSE_CASE4(9) NWQ_DENSE_CASE4(10) NWQ_DENSE_CASE4(12)
-#undef NWQ_DENSE_CASE4
-              default: break;
-            }
+            for (int t = 0; t < 4; t++) ig |= (t < (int)o.dnu ? ((gb >> o.dpos[t]) & 1u) : 0u) << t;
+            cf += ig << popc4(code);
+          }
+          switch (code) {
+#define NWQ_D(M) case M: if constexpr (M < NR) phase_diag<NR, M, R>(r, cf); break;
+#define NWQ_P(M) case 16 + M: if constexpr (M < NR) phase_perm<NR, M, R>(r, o.perm); break;
+#define NWQ_G(M) case 32 + M: if constexpr (M < NR) phase_dense<NR, M, PD_GEN, R>(r, cf); break;
+#define NWQ_R(M) case 48 + M: if constexpr (M < NR) phase_dense<NR, M, PD_REAL, R>(r, cf); break;
+#define NWQ_X(M) case 64 + M: if constexpr (M < NR) phase_dense<NR, M, PD_XROT, R>(r, cf); break;
+            NWQ_D(0) NWQ_D(1) NWQ_D(2) NWQ_D(3) NWQ_D(4) NWQ_D(5) NWQ_D(6) NWQ_D(7)
+            NWQ_D(8) NWQ_D(9) NWQ_D(10) NWQ_D(11) NWQ_D(12) NWQ_D(13) NWQ_D(14) NWQ_D(15)
+            NWQ_P(1) NWQ_P(2) NWQ_P(4) NWQ_P(8) NWQ_P(3) NWQ_P(5) NWQ_P(6) NWQ_P(9) NWQ_P(10) NWQ_P(12)
+            NWQ_G(1) NWQ_G(2) NWQ_G(4) NWQ_G(8) NWQ_G(3) NWQ_G(5) NWQ_G(6) NWQ_G(9) NWQ_G(10) NWQ_G(12)
+            NWQ_R(1) NWQ_R(2) NWQ_R(4) NWQ_R(8) NWQ_R(3) NWQ_R(5) NWQ_R(6) NWQ_R(9) NWQ_R(10) NWQ_R(12)
+            NWQ_X(1) NWQ_X(2) NWQ_X(4) NWQ_X(8)
+#undef NWQ_D
+#undef NWQ_P
+#undef NWQ_G
+#undef NWQ_R
+#undef NWQ_X
+            default: break;
           }
         }
         C* gw = tile + swz<C>(gb);
