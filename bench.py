@@ -282,7 +282,7 @@ def run_sv(args):
     cases = [(args.sv_n, L.F32, 0, args.steps), (args.sv_n - 1, L.F64, 0, max(1, args.steps // 3)),
              (args.sv_n, L.F32, L.PLAN_PLAIN, 1)]
     for n, dtype, flags, steps in cases:
-        gates, h = inputs.large_sv_tfim(n, steps=10)
+        gates, h = inputs.large_sv_tfim(n, steps=args.sv_depth)
         plan = Plan(L.SV, n, gates, dtype, None, flags)
         info = plan.info()
         st = State(L.SV, n, dtype, stream=stream.cuda_stream)
@@ -301,7 +301,7 @@ def run_sv(args):
         st.close()
         plan.close()
         gb = info["bytes"] / sec / 1e9
-        line = {"workload": f"sv_tfim_n{n}_depth10", "plan": "plain" if flags else "fused",
+        line = {"workload": f"sv_tfim_n{n}_depth{args.sv_depth}", "plan": "plain" if flags else "fused",
                 "dtype": "c64" if dtype == L.F32 else "c128", "metric": "gate-updates/s",
                 "value": len(gates) * 2.0 ** n / sec, "unit": "gate-updates/s", "s_per_circuit": sec,
                 "sweeps": info["sweeps"], "operators": info["ops"],
@@ -391,6 +391,11 @@ def run_serve(args):
     srv = Server(GpuExecutor(L.F32), slots=8, dtype=L.F32, budget_bytes=150e9)
     res = srv.serve(reqs)
     s = summarize(res, srv.wall)
+    errs = {}
+    for r in res.values():
+        if r["error"]:
+            errs[r["error"][:120]] = errs.get(r["error"][:120], 0) + 1
+    s["errors"] = errs
     s.update(workload=f"serve_poisson200_{args.serve_seconds:g}s", path="served_f32", metric="circuits/s",
              value=s["circuits_per_s"], unit="circuits/s", offered=len(reqs) / args.serve_seconds,
              peak_budget_bytes=srv.ledger.peak,
@@ -415,6 +420,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "serve"])
     ap.add_argument("--sv-n", type=int, default=34)
+    ap.add_argument("--sv-depth", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serial-seconds", type=float, default=5.0)
     args = ap.parse_args()
