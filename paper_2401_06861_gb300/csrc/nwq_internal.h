@@ -81,7 +81,7 @@ struct SweepDesc {
   uint32_t pc0;    //                 first coefficient
   uint32_t npc;    //                 number of coefficients
   uint8_t hpos[kMaxHigh];  // global position of high tile bit i (ascending, >= m)
-  uint8_t pad;
+  uint8_t prb;             // complex sweeps: register bits per thread group (3 or 4)
 };
 
 }  // namespace nwq
@@ -95,22 +95,28 @@ namespace nwq {
 // read and written once per phase instead of once per operator.  Dense and
 // permutation operators act on a subset of U; diagonal operators may act on
 // any tile bits (their factor depends only on the element's index).
-enum : uint8_t { PO_DIAG = 0, PO_PERM = 1, PO_DENSE = 2 };
+enum : uint8_t { PO_DIAG = 0, PO_PERM = 1, PO_DENSE = 2, PO_KRON = 3 };
 
 // DENSE structure classes (select the arithmetic at compile time).
 enum : uint8_t { PD_GEN = 0, PD_REAL = 1, PD_XROT = 2 };
 
+// Dispatch code of a phase operator (one switch in the kernel):
+//   0..15   DIAG, register-bit mask SU       16 + m  PERM on register mask m
+//   32 + m  DENSE general   48 + m  real     64 + m  X-rotation form
+//   80      KRON: one 2x2 matrix per register bit set in `mask`
+constexpr uint8_t PCODE_KRON = 80;
+
 struct PhaseOp {
   uint8_t cls;       // PO_*
-  uint8_t k;         // operator bits
-  uint8_t mask;      // PERM / DENSE: positions inside U (bit p set = U[p]); operator bit t is the t-th set bit
-  uint8_t form;      // DENSE: PD_* (PD_XROT: k = 1, real diagonal, imaginary off-diagonal)
-  uint8_t dpos[4];   // DIAG: tile-local bit position of operator bit t
-  uint32_t coef;     // DIAG: 2^k factors; DENSE: 2^k x 2^k row-major (complex entries)
-  uint8_t dnu;       // DIAG: number of operator bits outside the register bits
-  uint8_t code;      // dispatch code: DIAG 0..15 (mask), PERM 16 + mask, DENSE 32 + 16 * form + mask
-  uint8_t pad[2];
-  uint64_t uidx;     // DIAG: 4-bit factor-index contribution of register element i at bits 4i..4i+3
+  uint8_t k;         // operator bits (DIAG: up to 8)
+  uint8_t mask;      // PERM / DENSE: register positions (operator bit t = t-th set bit);
+                     // DIAG: register part SU; KRON: register bits that carry a matrix
+  uint8_t form;      // DENSE: PD_*; KRON: 2 bits per register bit
+  uint32_t coef;     // DIAG: 2^k factors; DENSE: 2^k x 2^k row-major; KRON: 4 entries per register bit
+  uint8_t dnu;       // DIAG: operator bits outside the register bits (their positions in dpos)
+  uint8_t code;      // dispatch code (above)
+  uint8_t pad[6];
+  uint8_t dpos[8];   // DIAG: tile-local bit positions of the out-of-register bits, low to high
   uint8_t perm[8];   // PERM: output i = (perm[i] & 0x80 ? -1 : 1) * input (perm[i] & 15), k <= 2
 };
 static_assert(sizeof(PhaseOp) == 32, "PhaseOp must be 32 bytes");

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <unordered_map>
 
@@ -535,10 +536,29 @@ static bool is_signed_perm(const BitOp& op) {
   return true;
 }
 
-// Group each complex sweep's operators into phases of RB register bits.
+// Group each complex sweep's operators into phases of RB register bits, then
+// within a phase merge consecutive diagonal operators into one diagonal of at
+// most 8 bits and consecutive one-bit dense operators on distinct register
+// bits into one KRON operator, so one dispatch does the work of several.
+// Register bits per thread group (elements per thread = 2^RB); NWQ_PHASE_RB
+// overrides it for tuning experiments.
+static int phase_register_bits(bool f64) {
+  if (const char* e = std::getenv("NWQ_PHASE_RB")) {
+    int v = std::atoi(e);
+    if (v == 3 || v == 4) return v;
+  }
+  return f64 ? 3 : 4;
+}
+
+struct PDiag {  // diagonal over up to 8 tile-local bits
+  int k = 0;
+  int lbits[8];
+  std::vector<cd> f;  // 2^k factors, operator index bit t = lbits[t]
+};
+
 static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& order, Plan& plan) {
   const bool f64 = plan.dtype == NWQ_F64;
-  const int RB = f64 ? 3 : 4;  // register bits: 8 complex128 or 16 complex64 elements per thread
+  const int RB = phase_register_bits(f64);
   plan.phases.clear();
   plan.pops.clear();
   plan.pcoef.clear();
@@ -553,7 +573,16 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
     }
     ncoef++;
   };
+  auto form_of = [](const cd* m, int k) -> uint8_t {
+    int d = 1 << k;
+    bool real = true;
+    for (int e = 0; e < d * d; e++) real &= m[e].imag() == 0.0;
+    if (real) return PD_REAL;
+    if (k == 1 && m[0].imag() == 0.0 && m[3].imag() == 0.0 && m[1].real() == 0.0 && m[2].real() == 0.0) return PD_XROT;
+    return PD_GEN;
+  };
   for (SweepDesc& sd : plan.sweeps) {
+    sd.prb = (uint8_t)RB;
     sd.ph0 = (uint32_t)plan.phases.size();
     sd.pop0 = (uint32_t)plan.pops.size();
     sd.pc0 = (uint32_t)ncoef;
@@ -591,7 +620,7 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
     for (auto& gr : groups) {
       uint32_t Um = gr.first;
       // fill to RB register bits from the highest tile bits (the low bits stay
-      // with the lanes of a warp, for conflict-free shared-memory access)
+      // with the lanes of a warp)
       for (int b = sd.T - 1; b >= 0 && __builtin_popcount(Um) < RB; b--) Um |= 1u << b;
       PhaseDesc pd;
       std::memset(&pd, 0, sizeof(pd));
@@ -600,94 +629,181 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
         if ((Um >> b) & 1) upos[nu++] = b;
       for (int p = 0; p < RB; p++) pd.u[p] = (uint8_t)upos[p];
       pd.op0 = (uint32_t)plan.pops.size();
+      auto rpos = [&](int lb) {
+        for (int q = 0; q < RB; q++)
+          if (upos[q] == lb) return q;
+        return -1;
+      };
+
+      // ---- pending macro-operators
+      PDiag dg;          // dg.k == 0: none
+      bool kron_any = false;
+      cd kron[4][4];     // per register bit: 2x2 (identity when absent)
+      uint8_t kron_mask = 0;
+      auto flush_diag = [&]() {
+        if (dg.k == 0) return;
+        PhaseOp po;
+        std::memset(&po, 0, sizeof(po));
+        po.cls = PO_DIAG;
+        po.k = (uint8_t)dg.k;
+        po.coef = (uint32_t)ncoef;
+        int upos_of[8], outt[8], nout = 0;
+        uint8_t SU = 0;
+        for (int t = 0; t < dg.k; t++) {
+          upos_of[t] = rpos(dg.lbits[t]);
+          if (upos_of[t] < 0) {
+            outt[nout] = t;
+            po.dpos[nout++] = (uint8_t)dg.lbits[t];
+          } else {
+            SU |= (uint8_t)(1u << upos_of[t]);
+          }
+        }
+        int kU = __builtin_popcount(SU);
+        po.mask = SU;
+        po.dnu = (uint8_t)nout;
+        po.code = SU;
+        int dim = 1 << dg.k;
+        for (int nidx = 0; nidx < dim; nidx++) {
+          int uval = nidx & ((1 << kU) - 1), oval = nidx >> kU, old = 0, c = 0;
+          for (int q = 0; q < RB; q++)
+            if ((SU >> q) & 1) {
+              if ((uval >> c) & 1)
+                for (int t = 0; t < dg.k; t++)
+                  if (upos_of[t] == q) old |= 1 << t;
+              c++;
+            }
+          for (int o2 = 0; o2 < nout; o2++)
+            if ((oval >> o2) & 1) old |= 1 << outt[o2];
+          push_coef(dg.f[old]);
+        }
+        plan.pops.push_back(po);
+        dg = PDiag();
+      };
+      auto flush_kron = [&]() {
+        if (!kron_any) return;
+        PhaseOp po;
+        std::memset(&po, 0, sizeof(po));
+        po.cls = PO_KRON;
+        po.k = 1;
+        po.coef = (uint32_t)ncoef;
+        po.mask = kron_mask;
+        po.code = PCODE_KRON;
+        for (int p = 0; p < RB; p++) {
+          po.form |= (uint8_t)(form_of(kron[p], 1) << (2 * p));
+          for (int e = 0; e < 4; e++) push_coef(kron[p][e]);
+        }
+        plan.pops.push_back(po);
+        kron_any = false;
+        kron_mask = 0;
+      };
+      auto kron_reset = [&]() {
+        for (int p = 0; p < 4; p++) {
+          kron[p][0] = 1; kron[p][1] = 0; kron[p][2] = 0; kron[p][3] = 1;
+        }
+      };
+      kron_reset();
       for (int oi : gr.second) {
         const BitOp& op = ops[oi];
+        int dim = 1 << op.k;
+        if (is_diagonal(op)) {
+          flush_kron();
+          kron_reset();
+          // union of bits with the pending diagonal
+          int ub[8], nub = dg.k;
+          for (int t = 0; t < dg.k; t++) ub[t] = dg.lbits[t];
+          for (int t = 0; t < op.k; t++) {
+            int lb = local[op.bits[t]];
+            bool have = false;
+            for (int u = 0; u < nub; u++) have |= ub[u] == lb;
+            if (!have) {
+              if (nub == 8) {
+                nub = 9;
+                break;
+              }
+              ub[nub++] = lb;
+            }
+          }
+          if (nub > 8) {
+            flush_diag();
+            nub = 0;
+            for (int t = 0; t < op.k; t++) ub[nub++] = local[op.bits[t]];
+          }
+          PDiag nd;
+          nd.k = nub;
+          for (int u = 0; u < nub; u++) nd.lbits[u] = ub[u];
+          nd.f.assign((size_t)1 << nub, cd(1.0));
+          for (int idx = 0; idx < (1 << nub); idx++) {
+            cd v = 1.0;
+            if (dg.k) {  // pending factor
+              int sub = 0;
+              for (int t = 0; t < dg.k; t++)
+                for (int u = 0; u < nub; u++)
+                  if (ub[u] == dg.lbits[t] && ((idx >> u) & 1)) sub |= 1 << t;
+              v *= dg.f[sub];
+            }
+            int sub = 0;
+            for (int t = 0; t < op.k; t++)
+              for (int u = 0; u < nub; u++)
+                if (ub[u] == local[op.bits[t]] && ((idx >> u) & 1)) sub |= 1 << t;
+            v *= op.m[(size_t)sub * dim + sub];
+            nd.f[idx] = v;
+          }
+          dg = nd;
+          continue;
+        }
+        flush_diag();
+        if (op.k == 1) {  // one-bit dense or permutation: into the KRON group
+          int p = rpos(local[op.bits[0]]);
+          if ((kron_mask >> p) & 1) {
+            flush_kron();
+            kron_reset();
+          }
+          for (int e = 0; e < 4; e++) kron[p][e] = op.m[e];
+          kron_mask |= (uint8_t)(1u << p);
+          kron_any = true;
+          continue;
+        }
+        flush_kron();
+        kron_reset();
+        // two-bit dense / permutation: operator bits in ascending register order
         PhaseOp po;
         std::memset(&po, 0, sizeof(po));
         po.k = (uint8_t)op.k;
         po.coef = (uint32_t)ncoef;
-        int dim = 1 << op.k;
-        if (is_diagonal(op)) {
-          po.cls = PO_DIAG;
-          // Factor table reindexed as (bits outside the register bits, in
-          // operator order) << kU | (register bits, in ascending position order),
-          // so the kernel indexes it with a compile-time register offset.
-          int upos_of[4], nout = 0, kU = 0;
-          int outt[4];
-          uint8_t SU = 0;
-          for (int t = 0; t < op.k; t++) {
-            upos_of[t] = -1;
-            for (int q = 0; q < RB; q++)
-              if (upos[q] == local[op.bits[t]]) upos_of[t] = q;
-            if (upos_of[t] < 0) {
-              outt[nout] = t;
-              po.dpos[nout++] = (uint8_t)local[op.bits[t]];
-            } else {
-              SU |= (uint8_t)(1u << upos_of[t]);
+        int rp[4];
+        for (int t = 0; t < op.k; t++) rp[t] = rpos(local[op.bits[t]]);
+        int ord[4];
+        for (int t = 0; t < op.k; t++) ord[t] = t;
+        std::sort(ord, ord + op.k, [&](int a, int b) { return rp[a] < rp[b]; });
+        uint8_t mask = 0;
+        for (int t = 0; t < op.k; t++) mask |= (uint8_t)(1u << rp[t]);
+        po.mask = mask;
+        auto remap = [&](int inew) {
+          int iold = 0;
+          for (int t = 0; t < op.k; t++) iold |= ((inew >> t) & 1) << ord[t];
+          return iold;
+        };
+        if (is_signed_perm(op)) {
+          po.cls = PO_PERM;
+          for (int i = 0; i < dim; i++)
+            for (int j = 0; j < dim; j++) {
+              cd v = op.m[(size_t)remap(i) * dim + remap(j)];
+              if (v != cd(0.0)) po.perm[i] = (uint8_t)(j | (v.real() < 0 ? 0x80 : 0));
             }
-          }
-          kU = __builtin_popcount(SU);
-          po.mask = SU;
-          po.dnu = (uint8_t)nout;
-          for (int nidx = 0; nidx < dim; nidx++) {
-            int uval = nidx & ((1 << kU) - 1), oval = nidx >> kU;
-            int old = 0;
-            // register part: the c-th set bit of SU carries bit c of uval
-            int c = 0;
-            for (int q = 0; q < RB; q++)
-              if ((SU >> q) & 1) {
-                if ((uval >> c) & 1)
-                  for (int t = 0; t < op.k; t++)
-                    if (upos_of[t] == q) old |= 1 << t;
-                c++;
-              }
-            for (int o2 = 0; o2 < nout; o2++)
-              if ((oval >> o2) & 1) old |= 1 << outt[o2];
-            push_coef(op.m[(size_t)old * dim + old]);
-          }
+          po.code = (uint8_t)(16 + mask);
         } else {
-          // operator bit t -> register position; reorder to ascending positions
-          int rp[4];
-          for (int t = 0; t < op.k; t++)
-            for (int p = 0; p < RB; p++)
-              if (upos[p] == local[op.bits[t]]) rp[t] = p;
-          int ord[4];
-          for (int t = 0; t < op.k; t++) ord[t] = t;
-          std::sort(ord, ord + op.k, [&](int a, int b) { return rp[a] < rp[b]; });
-          uint8_t mask = 0;
-          for (int t = 0; t < op.k; t++) mask |= (uint8_t)(1u << rp[t]);
-          po.mask = mask;
-          auto remap = [&](int inew) {  // new index (bit t = ord[t]) -> old index
-            int iold = 0;
-            for (int t = 0; t < op.k; t++) iold |= ((inew >> t) & 1) << ord[t];
-            return iold;
-          };
-          if (is_signed_perm(op)) {
-            po.cls = PO_PERM;
-            for (int i = 0; i < dim; i++) {
-              int oi2 = remap(i);
-              for (int j = 0; j < dim; j++) {
-                cd v = op.m[(size_t)oi2 * dim + remap(j)];
-                if (v != cd(0.0)) po.perm[i] = (uint8_t)(j | (v.real() < 0 ? 0x80 : 0));
-              }
-            }
-          } else {
-            po.cls = PO_DENSE;
-            bool real = true;
-            for (int i = 0; i < dim; i++)
-              for (int j = 0; j < dim; j++) {
-                cd v = op.m[(size_t)remap(i) * dim + remap(j)];
-                real &= v.imag() == 0.0;
-                push_coef(v);
-              }
-            bool xrot = op.k == 1 && op.m[0].imag() == 0.0 && op.m[3].imag() == 0.0 && op.m[1].real() == 0.0 &&
-                        op.m[2].real() == 0.0;
-            po.form = real ? PD_REAL : (xrot ? PD_XROT : PD_GEN);
-          }
+          po.cls = PO_DENSE;
+          std::vector<cd> mm((size_t)dim * dim);
+          for (int i = 0; i < dim; i++)
+            for (int j = 0; j < dim; j++) mm[(size_t)i * dim + j] = op.m[(size_t)remap(i) * dim + remap(j)];
+          po.form = form_of(mm.data(), op.k);
+          for (auto& v : mm) push_coef(v);
+          po.code = (uint8_t)(32 + 16 * po.form + mask);
         }
-        po.code = po.cls == PO_DIAG ? po.mask : (po.cls == PO_PERM ? 16 + po.mask : 32 + 16 * po.form + po.mask);
         plan.pops.push_back(po);
       }
+      flush_diag();
+      flush_kron();
       pd.nops = (uint32_t)plan.pops.size() - pd.op0;
       plan.phases.push_back(pd);
     }

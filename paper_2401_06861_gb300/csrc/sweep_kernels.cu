@@ -394,6 +394,22 @@ __device__ __forceinline__ void phase_dense(typename Cplx<R>::T (&r)[NR], const 
   }
 }
 
+// KRON operator: register bit P carries its own 2x2 matrix (cf + 4P) when
+// bit P of mask is set; its arithmetic form is 2 bits of `form`.
+template <int NR, int P, class R>
+__device__ __forceinline__ void kron_bit(typename Cplx<R>::T (&r)[NR], const typename Cplx<R>::T* cf, int mask,
+                                         int form) {
+  if constexpr ((1 << P) < NR) {
+    if ((mask >> P) & 1) {
+      const typename Cplx<R>::T* m = cf + 4 * P;
+      const int f = (form >> (2 * P)) & 3;
+      if (f == PD_XROT) phase_dense<NR, 1 << P, PD_XROT, R>(r, m);
+      else if (f == PD_REAL) phase_dense<NR, 1 << P, PD_REAL, R>(r, m);
+      else phase_dense<NR, 1 << P, PD_GEN, R>(r, m);
+    }
+  }
+}
+
 __host__ __device__ constexpr int pext4(int v, int mask) {  // gather v's bits at mask positions
   int out = 0, bit = 0;
   for (int p = 0; p < 4; p++)
@@ -523,8 +539,8 @@ __global__ void __launch_bounds__(kSweepThreads) phase_kernel(void* __restrict__
           const int code = o.code;
           if (code < 16) {  // diagonal: factor table offset by the out-of-register bits
             uint32_t ig = 0;
-#pragma unroll
-            for (int t = 0; t < 4; t++) ig |= (t < (int)o.dnu ? ((gb >> o.dpos[t]) & 1u) : 0u) << t;
+            const int dn = o.dnu;
+            for (int t = 0; t < dn; t++) ig |= ((gb >> o.dpos[t]) & 1u) << t;
             cf += ig << popc4(code);
           }
           switch (code) {
@@ -533,6 +549,12 @@ __global__ void __launch_bounds__(kSweepThreads) phase_kernel(void* __restrict__
 #define NWQ_G(M) case 32 + M: if constexpr (M < NR) phase_dense<NR, M, PD_GEN, R>(r, cf); break;
 #define NWQ_R(M) case 48 + M: if constexpr (M < NR) phase_dense<NR, M, PD_REAL, R>(r, cf); break;
 #define NWQ_X(M) case 64 + M: if constexpr (M < NR) phase_dense<NR, M, PD_XROT, R>(r, cf); break;
+            case PCODE_KRON:
+              kron_bit<NR, 0, R>(r, cf, o.mask, o.form);
+              kron_bit<NR, 1, R>(r, cf, o.mask, o.form);
+              kron_bit<NR, 2, R>(r, cf, o.mask, o.form);
+              kron_bit<NR, 3, R>(r, cf, o.mask, o.form);
+              break;
             NWQ_D(0) NWQ_D(1) NWQ_D(2) NWQ_D(3) NWQ_D(4) NWQ_D(5) NWQ_D(6) NWQ_D(7)
             NWQ_D(8) NWQ_D(9) NWQ_D(10) NWQ_D(11) NWQ_D(12) NWQ_D(13) NWQ_D(14) NWQ_D(15)
             NWQ_P(1) NWQ_P(2) NWQ_P(4) NWQ_P(8) NWQ_P(3) NWQ_P(5) NWQ_P(6) NWQ_P(9) NWQ_P(10) NWQ_P(12)
@@ -565,11 +587,10 @@ __global__ void __launch_bounds__(kSweepThreads) phase_kernel(void* __restrict__
   cp_async_wait<0>();
 }
 
-template <class R>
+template <class R, int RB>
 static cudaError_t launch_phase_t(void* state, int B, const SweepDesc& sd, const PhaseTables& pt, int sm_count,
                                   cudaStream_t s) {
   using C = typename Cplx<R>::T;
-  constexpr int RB = sizeof(R) == 8 ? 3 : 4;
   size_t tile = 2 * sizeof(C) * padded_elems<C>(sd.T);  // current + prefetched tile
   size_t table = sd.nph * sizeof(PhaseDesc) + sd.npop * sizeof(PhaseOp) + sd.npc * sizeof(C);
   const bool tbl = tile + table <= (size_t)kTableSmemLimit;
@@ -638,9 +659,11 @@ static cudaError_t launch_sweep_t(void* state, int B, const SweepDesc& sd, const
 
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
                          const void* ents, const PhaseTables* pt, int sm_count, cudaStream_t s) {
-  if (cplx && pt && sd.nph > 0) {
-    if (f64) return launch_phase_t<double>(state, B, sd, *pt, sm_count, s);
-    return launch_phase_t<float>(state, B, sd, *pt, sm_count, s);
+  if (cplx && pt && sd.nph > 0) {  // the register-group width is fixed by the plan (SweepDesc::prb)
+    if (f64) return sd.prb == 4 ? launch_phase_t<double, 4>(state, B, sd, *pt, sm_count, s)
+                                : launch_phase_t<double, 3>(state, B, sd, *pt, sm_count, s);
+    return sd.prb == 3 ? launch_phase_t<float, 3>(state, B, sd, *pt, sm_count, s)
+                       : launch_phase_t<float, 4>(state, B, sd, *pt, sm_count, s);
   }
   if (cplx) {
     if (f64) return launch_sweep_t<double, true>(state, B, sd, ops, ents, sm_count, s);
