@@ -388,7 +388,8 @@ def run_serve(args):
     reqs = inputs.serve_requests(rate=200.0, duration=args.serve_seconds, seed=200)
     warm = inputs.serve_requests(rate=200.0, duration=1.0, seed=7, sv_n=(8, 20), dm_n=(6, 9))
     Server(GpuExecutor(L.F32), slots=8, dtype=L.F32).serve(warm)
-    srv = Server(GpuExecutor(L.F32), slots=8, dtype=L.F32, budget_bytes=150e9)
+    ex = GpuExecutor(L.F32)
+    srv = Server(ex, slots=args.serve_slots, dtype=L.F32, budget_bytes=150e9)
     res = srv.serve(reqs)
     s = summarize(res, srv.wall)
     errs = {}
@@ -396,6 +397,8 @@ def run_serve(args):
         if r["error"]:
             errs[r["error"][:120]] = errs.get(r["error"][:120], 0) + 1
     s["errors"] = errs
+    s["plan_cache"] = {"hits": ex.hits, "misses": ex.misses}
+    s["slots"] = args.serve_slots
     s.update(workload=f"serve_poisson200_{args.serve_seconds:g}s", path="served_f32", metric="circuits/s",
              value=s["circuits_per_s"], unit="circuits/s", offered=len(reqs) / args.serve_seconds,
              peak_budget_bytes=srv.ledger.peak,
@@ -423,6 +426,7 @@ def main():
     ap.add_argument("--sv-depth", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serial-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_init()

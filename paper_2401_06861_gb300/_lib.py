@@ -114,6 +114,36 @@ def check(rc):
 
 
 # ------------------------------------------------------------------ marshalling
+# numpy mirror of nwq_gate (56 bytes) for vectorised marshalling
+GATE_DTYPE = np.dtype({"names": ["kind", "reserved", "q", "theta", "param_idx", "reserved2", "mat"],
+                       "formats": [np.uint16, np.uint16, (np.int32, 2), (np.float64, 3), np.int32, np.int32,
+                                   np.uint64],
+                       "offsets": [0, 2, 4, 16, 40, 44, 48], "itemsize": 56})
+
+
+def encode_gates_np(gates, param_index=None):
+    """Gate tuples -> numpy array laid out as nwq_gate[] (plus keep-alive list).
+    Column-wise; MAT1/MAT2 matrices are pointed to by address."""
+    ng = len(gates)
+    a = np.zeros(max(ng, 1), GATE_DTYPE)
+    if ng == 0:
+        return a, []
+    a["kind"][:ng] = np.fromiter((GATE_KIND[g[0]] for g in gates), np.uint16, ng)
+    a["q"][:ng, 0] = np.fromiter((g[1][0] for g in gates), np.int32, ng)
+    a["q"][:ng, 1] = np.fromiter((g[1][1] if len(g[1]) > 1 else 0 for g in gates), np.int32, ng)
+    keep = []
+    mats = [i for i, g in enumerate(gates) if g[0].startswith("MAT")]
+    if len(mats) < ng:
+        a["theta"][:ng] = np.array([(tuple(g[2]) + (0.0, 0.0, 0.0))[:3] if not g[0].startswith("MAT") else (0.0, 0.0, 0.0)
+                                    for g in gates], np.float64)
+    for i in mats:
+        m = np.ascontiguousarray(np.asarray(gates[i][2], np.complex128)).view(np.float64).copy()
+        keep.append(m)
+        a["mat"][i] = m.ctypes.data
+    a["param_idx"][:ng] = -1 if param_index is None else np.asarray(param_index, np.int32)
+    return a, keep
+
+
 def encode_gates(gates, param_index=None):
     """Gate tuples (name, qubits, params) -> (ctypes array, keep-alive list)."""
     arr = (Gate * max(len(gates), 1))()

@@ -6,6 +6,7 @@
 namespace nwq {
 
 constexpr int kBatchThreads = 256;
+constexpr int kBatchMaxSmem = 220 * 1024;  // per-CTA dynamic shared memory cap of the batched kernel
 
 // Gate types of the batched kernel.
 enum : uint8_t { BT_FIXED1 = 0, BT_CX, BT_CZ, BT_SWAP, BT_RX, BT_RY, BT_RZ, BT_P, BT_U3, BT_RZZ };

@@ -134,7 +134,7 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
   b->dtype = dtype;
   b->nparams = nparams;
   b->ntemplates = ntemplates;
-  if (batch_smem_bytes(dtype == NWQ_F64, b->max_n, std::max(b->max_gates, 1), b->max_terms) > 220 * 1024)
+  if (batch_smem_bytes(dtype == NWQ_F64, b->max_n, std::max(b->max_gates, 1), b->max_terms) > (size_t)kBatchMaxSmem)
     return set_error(NWQ_EUNSUPPORTED, "batch state plus gate tables exceed shared memory");
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "batch.hpp"
@@ -244,15 +245,27 @@ size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
 
 cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s) {
   size_t smem = batch_smem_bytes(f64, a.max_n, a.max_gates, a.max_terms);
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   int per_sm = 0;
-  if (f64) {
-    e = cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double>, kBatchThreads, smem);
-  } else {
-    e = cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float>, kBatchThreads, smem);
+  // The attribute is a per-function maximum shared by every caller (several
+  // host threads may launch concurrently): set it once to the largest size any
+  // batch may use, never per call.
+  static int attr_dev[2] = {-1, -1};
+  static std::mutex attr_mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (attr_dev[f64] != dev) {
+      e = f64 ? cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem)
+              : cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
+      if (e == cudaSuccess) attr_dev[f64] = dev;
+    }
   }
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)kBatchMaxSmem) return cudaErrorInvalidValue;
+  if (f64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double>, kBatchThreads, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float>, kBatchThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = sm_count * per_sm;

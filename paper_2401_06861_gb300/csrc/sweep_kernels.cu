@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "nwq_internal.h"
@@ -595,10 +596,10 @@ static cudaError_t launch_phase_t(void* state, int B, const SweepDesc& sd, const
   size_t table = sd.nph * sizeof(PhaseDesc) + sd.npop * sizeof(PhaseOp) + sd.npc * sizeof(C);
   const bool tbl = tile + table <= (size_t)kTableSmemLimit;
   size_t smem = (tbl ? phase_hoff_offset<C>(sd, true) : phase_hoff_offset<C>(sd, false)) + ((size_t)8 << sd.h);
-  static int attr_dev[2] = {-1, -1};
+  static std::atomic<int> attr_dev[2] = {-1, -1};  // setting the same maximum twice is harmless
   int dev = 0;
   cudaGetDevice(&dev);
-  if (attr_dev[tbl] != dev) {
+  if (attr_dev[tbl].load() != dev) {
     cudaError_t e = tbl ? cudaFuncSetAttribute(phase_kernel<R, RB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem)
                         : cudaFuncSetAttribute(phase_kernel<R, RB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e != cudaSuccess) return e;
@@ -621,10 +622,10 @@ static cudaError_t launch_phase_t(void* state, int B, const SweepDesc& sd, const
 template <class R, bool CPLX, bool TBL>
 static cudaError_t launch_sweep_tt(void* state, int B, const SweepDesc& sd, const DevOp* ops, const void* ents,
                                    size_t smem, int sm_count, cudaStream_t s) {
-  static int attr_dev = -1;  // per instantiation: the attribute is set once per device
+  static std::atomic<int> attr_dev{-1};  // per instantiation: the attribute is set once per device
   int dev = 0;
   cudaGetDevice(&dev);
-  if (attr_dev != dev) {
+  if (attr_dev.load() != dev) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<R, CPLX, TBL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxDynSmem);
     if (e != cudaSuccess) return e;

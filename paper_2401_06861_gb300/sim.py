@@ -69,6 +69,17 @@ class State:
                                                       ctypes.byref(nm) if nm is not None else None, flags))
         return self
 
+    def apply_encoded(self, arr, ng, noise=None, flags=0):
+        """apply() from an ``_lib.encode_gates_np`` array (one-shot lowering)."""
+        g = ctypes.cast(ctypes.c_void_p(arr.ctypes.data), ctypes.POINTER(L.Gate))
+        if self.kind == SV:
+            check(L.lib().nwq_sv_apply_circuit(self.h, g, ng, flags))
+        else:
+            nm, keep2 = encode_noise(noise, self.n)
+            check(L.lib().nwq_dm_apply_circuit_noisy(self.h, g, ng, ctypes.byref(nm) if nm is not None else None,
+                                                      flags))
+        return self
+
     def run(self, plan):
         check(L.lib().nwq_plan_run(self.h, plan.h))
         return self
@@ -130,13 +141,20 @@ class State:
 
 
 class Plan:
-    def __init__(self, kind, n, gates, dtype=F64, noise=None, flags=0):
-        arr, keep = encode_gates(gates)
+    def __init__(self, kind, n, gates, dtype=F64, noise=None, flags=0, encoded=None):
+        """Lower ``gates`` (tuples), or an ``encoded`` nwq_gate array from
+        ``_lib.encode_gates_np``, once for repeated runs."""
+        if encoded is None:
+            arr, keep = encode_gates(gates)
+            ng = len(gates)
+        else:
+            arr = ctypes.cast(ctypes.c_void_p(encoded.ctypes.data), ctypes.POINTER(L.Gate))
+            ng = len(encoded) if gates is None else len(gates)
         nm, keep2 = encode_noise(noise, n)
         self.h = ctypes.c_void_p()
-        check(L.lib().nwq_plan_create(kind, n, dtype, arr, len(gates), ctypes.byref(nm) if nm is not None else None,
+        check(L.lib().nwq_plan_create(kind, n, dtype, arr, ng, ctypes.byref(nm) if nm is not None else None,
                                       flags, None, ctypes.byref(self.h)))
-        self.ngates = len(gates)
+        self.ngates = ng
 
     def info(self):
         s, o = ctypes.c_int(), ctypes.c_int()
@@ -179,13 +197,15 @@ class Batch:
         arr = (L.BatchTemplate * len(templates))()
         self.max_ne = 0
         for i, t in enumerate(templates):
-            g, k1 = encode_gates(t["gates"], t.get("param_index"))
+            ga, k1 = L.encode_gates_np(t["gates"], t.get("param_index"))
+            g = ctypes.cast(ctypes.c_void_p(ga.ctypes.data), ctypes.POINTER(L.Gate))
+            k1 = (ga, k1)
             tr = encode_terms(t["terms"])
             c = np.ascontiguousarray(t["coeffs"], np.float64).reshape(-1)
             ne = int(np.asarray(t["coeffs"]).reshape(-1, max(len(t["terms"]), 1)).shape[0]) if len(t["terms"]) else 1
             self.keep += [g, k1, tr, c]
             arr[i].n = t["n"]
-            arr[i].gates = ctypes.cast(g, ctypes.POINTER(L.Gate))
+            arr[i].gates = g
             arr[i].ngates = len(t["gates"])
             arr[i].terms = ctypes.cast(tr, ctypes.POINTER(L.PauliTerm))
             arr[i].nterms = len(t["terms"])
