@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnwqgb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["sweep_kernels.cu", "batch_kernels.cu", "noalloc.cu", "planner.cpp", "abi.cpp", "batch_host.cpp"]
+SOURCES = ["sweep_kernels.cu", "expect_kernels.cu", "batch_kernels.cu", "noalloc.cu", "planner.cpp", "expect_host.cpp", "abi.cpp", "batch_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -33,7 +33,7 @@ def _flags(src):
 def _compile(src):
     obj = os.path.join(BUILD, src + ".o")
     path = os.path.join(CSRC, src)
-    deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".hpp"))]
+    deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".hpp", ".cuh"))]
     deps.append(os.path.join(ROOT, "include", "nwqgb.h"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj

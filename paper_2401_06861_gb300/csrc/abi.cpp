@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/nwqgb.h"
+#include "expect_host.hpp"
 #include "kernels.hpp"
 #include "planner.hpp"
 #include "state.hpp"
@@ -421,73 +422,28 @@ extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, 
     return rc;
   }
 
-  // SV: group terms by x mask, chunks of kExpectChunk terms per launch.
-  std::map<uint64_t, std::vector<int>> groups;
-  for (size_t t = 0; t < nt; t++) groups[terms[t].x_mask].push_back((int)t);
-  struct Chunk {
-    uint64_t x;
-    std::vector<int> idx;
-  };
-  std::vector<Chunk> chunks;
-  for (auto& g : groups)
-    for (size_t i = 0; i < g.second.size(); i += kExpectChunk)
-      chunks.push_back({g.first, std::vector<int>(g.second.begin() + i,
-                                                  g.second.begin() + std::min(g.second.size(), i + kExpectChunk))});
-  if (norm) chunks.push_back({0ull, std::vector<int>{-1}});  // identity string: <psi|psi>
-  uint64_t N = 1ull << st->n;
-  int nblocks = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)st->sm_count * 4);
-  // host staging: per chunk z masks (16 u64) + y (16 int) ; coefficients in group order
-  size_t nchunk = chunks.size();
-  std::vector<uint64_t> hz(nchunk * kExpectChunk, 0);
-  std::vector<int> hy(nchunk * kExpectChunk, 0);
-  std::vector<double> hcoef;
-  std::vector<int> order;
-  const nwq_pauli_term ident{0ull, 0ull, 0.0};
-  for (size_t c = 0; c < nchunk; c++)
-    for (size_t j = 0; j < chunks[c].idx.size(); j++) {
-      int ti = chunks[c].idx[j];
-      const nwq_pauli_term& tm = ti < 0 ? ident : terms[ti];
-      hz[c * kExpectChunk + j] = tm.z_mask;
-      hy[c * kExpectChunk + j] = __builtin_popcountll(tm.x_mask & tm.z_mask) & 3;
-      if (ti < 0) continue;
-      hcoef.push_back(tm.coeff);
-      order.push_back(ti);
-    }
-  size_t bz = hz.size() * 8, by = hy.size() * 4, bc = nt * 8, bv = nt * 8 + 16;
-  size_t bp = (size_t)nblocks * kExpectChunk * 8;
+  // SV: tiled passes, then the general kernel for terms no tile can hold.
+  std::vector<ExpPass> passes(nt + 1);
+  std::vector<ExpTerm> eterms(nt + 1);
+  std::vector<int> fb(nt), work(2 * nt + 2);
+  std::vector<SvChunk> chunks(nt);
+  SvExpectHost h{passes.data(), eterms.data(), fb.data(), chunks.data(), work.data()};
+  SvExpectCounts c{};
+  plan_sv_expect(st->n, terms, nt, norm, h, c);
+  int grid = (int)std::min<uint64_t>(1ull << (st->n - std::min(st->n, kExpTileBits)),
+                                     (uint64_t)st->sm_count * (f64 ? 2 : 4));
+  const uint64_t N = 1ull << st->n;
+  const int fblocks = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)st->sm_count * 4);
+  std::vector<unsigned char> stage(sv_expect_stage_bytes(nt));
   void* d = nullptr;
-  CK(cudaMallocAsync(&d, bz + by + bc + bv + bp + 64, s), "scratch allocation");
-  char* base = (char*)d;
-  uint64_t* dz = (uint64_t*)base;
-  int* dy = (int*)(base + bz);
-  double* dc = (double*)(base + ((bz + by + 7) & ~(size_t)7));
-  double* dv = dc + nt;       // values in chunk order; dv[nt] = norm, dv[nt+1] = sum
-  double* dpart = dv + nt + 2;
+  CK(cudaMallocAsync(&d, sv_expect_scratch_bytes(nt, grid, fblocks), s), "scratch allocation");
   int rc = NWQ_OK;
-  cudaError_t e = cudaMemcpyAsync(dz, hz.data(), bz, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy.data(), by, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, hcoef.data(), bc, cudaMemcpyHostToDevice, s);
-  size_t done = 0;
-  for (size_t c = 0; c < nchunk && e == cudaSuccess; c++) {
-    int cnt = (int)chunks[c].idx.size();
-    e = launch_sv_expect_group(f64, st->buf, st->n, chunks[c].x, dz + c * kExpectChunk, dy + c * kExpectChunk, cnt,
-                               dpart, nblocks, dv + done, s);
-    done += cnt;
-  }
-  std::vector<double> vals(nt);
-  if (e == cudaSuccess && norm) e = launch_scale(dv, (int)nt, dv + nt, s);
-  if (e == cudaSuccess && sum) {
-    e = launch_weighted_sum(dv, dc, (int)nt, dv + nt + 1, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dv + nt + 1, 8, cudaMemcpyDeviceToHost, s);
-  } else if (e == cudaSuccess) {
-    e = cudaMemcpyAsync(vals.data(), dv, nt * 8, cudaMemcpyDeviceToHost, s);
-  }
+  cudaError_t e = sv_expect_enqueue(st, terms, nt, flags, out_host, h, c, grid, fblocks, stage.data(),
+                                    (unsigned char*)d);
   if (e != cudaSuccess) rc = cuda_fail(e, "expectation");
   cudaFreeAsync(d, s);
   e = cudaStreamSynchronize(s);
   if (!rc && e != cudaSuccess) rc = cuda_fail(e, "expectation");
-  if (!rc && !sum)
-    for (size_t k = 0; k < nt; k++) out_host[order[k]] = vals[k];
   return rc;
 }
 

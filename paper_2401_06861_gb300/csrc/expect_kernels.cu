@@ -1,0 +1,263 @@
+// Pauli-string expectations of a state vector (paper Sec. III: VQE energies
+// and observables are weighted sums of Pauli-string expectations).
+//
+//   <psi| P(x, z) |psi> = sum_b Re( conj(psi[b ^ x]) i^y (-1)^{|b & z|} psi[b] ),
+//   y = |x & z| mod 4 (one factor i per Y).
+//
+// sv_expect_tiled: one launch per pass.  A pass stages tiles of 2^T
+// amplitudes (2^m contiguous elements x 2^(T-m) strided chunks at the pass's
+// high bit positions) in shared memory, and evaluates every term whose X
+// support lies inside the tile's bits: the partner psi[b ^ x] of each element
+// is then in the same tile, so one read of the state serves all those terms.
+// Each thread keeps |psi|^2 of its E = 2^T / 128 elements in registers for the
+// diagonal (Z-type) terms; off-diagonal terms read both amplitudes from shared
+// memory.  The sign of element j is bit j of a per-term word built with one
+// warp ballot, so the inner loops carry no population counts.
+//
+// Precision: products and sums over one warp's 32 x E elements are taken in
+// the state's precision, everything above (per warp across tiles, per block,
+// across blocks) in FP64.  Per-block sums go to part[block * ncols + column];
+// reduce_partials adds the blocks in order, so results are deterministic.
+//
+// sv_expect_group: the general kernel for terms whose X support does not fit
+// a tile: one pass per group of at most kExpectChunk terms sharing x, each
+// thread reading psi[b] and psi[b ^ x] from global memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "nwq_internal.h"
+#include "kernels.hpp"
+#include "device_util.cuh"
+
+namespace nwq {
+
+namespace {
+
+// Flip the sign of v when s = 0x80000000 (s = 0: unchanged).
+__device__ __forceinline__ float flip_sign(float v, uint32_t s) { return __int_as_float(__float_as_int(v) ^ (int)s); }
+__device__ __forceinline__ double flip_sign(double v, uint32_t s) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)((unsigned long long)s << 32));
+}
+
+template <class R, int E>
+__global__ void __launch_bounds__(kExpThreads) sv_expect_tiled(const typename Cplx<R>::T* __restrict__ psi,
+                                                               uint64_t ntiles, ExpPass P,
+                                                               const ExpTerm* __restrict__ terms,
+                                                               double* __restrict__ part, int ncols) {
+  using C = typename Cplx<R>::T;
+  constexpr int VPE = 16 / sizeof(C);  // elements per 16-byte vector
+  constexpr int kLogVPE = VPE == 2 ? 1 : 0;
+  constexpr int kWarps = kExpThreads / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t nel = 1u << P.T;
+  C* tile = reinterpret_cast<C*>(smem_raw);
+  uint64_t* hoff = reinterpret_cast<uint64_t*>(smem_raw + sizeof(C) * (size_t)nel);
+  ExpTerm* st = reinterpret_cast<ExpTerm*>(hoff + (1u << P.h));
+  double* red = reinterpret_cast<double*>(st + P.nk);  // [warp][term] FP64 sums
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int i = tid; i < P.nk; i += kExpThreads) st[i] = terms[P.k0 + i];
+  for (uint32_t j = tid; j < (1u << P.h); j += kExpThreads) hoff[j] = deposit(j, P.hmask);
+  for (int i = tid; i < kWarps * P.nk; i += kExpThreads) red[i] = 0.0;
+  const uint32_t lowmask = (1u << P.m) - 1u;
+
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = deposit(t, P.fmask);
+    __syncthreads();  // tables staged; previous tile consumed
+    if (P.m >= kLogVPE) {  // 16-byte vectors along the contiguous low bits
+      for (uint32_t v = tid; v < nel / VPE; v += kExpThreads) {
+        const uint32_t l = v * VPE;
+        cp_async16(tile + l, psi + base + hoff[l >> P.m] + (l & lowmask));
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+    } else {
+      for (uint32_t l = tid; l < nel; l += kExpThreads) tile[l] = psi[base + hoff[l >> P.m] + (l & lowmask)];
+    }
+    __syncthreads();
+
+    R p[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+      const uint32_t l = tid + kExpThreads * j;
+      C a = tile[l < nel ? l : 0];
+      p[j] = (l < nel) ? a.x * a.x + a.y * a.y : R(0);
+    }
+    for (int k = 0; k < P.nk; k++) {
+      const ExpTerm tm = st[k];
+      // bit j of W: sign of element tid + 128 j, i.e. parity of its bits in
+      // z (tile-local and the tile's base) plus the sign of i^y (y = 1, 2).
+      const uint32_t hi = (uint32_t)__popc((uint32_t)lane & (tm.zl >> 7)) & 1u;
+      uint32_t W = __ballot_sync(0xffffffffu, hi);
+      const uint32_t flip = ((uint32_t)__popc((uint32_t)tid & tm.zl & 127u) + (uint32_t)__popcll(base & tm.zh) +
+                             (uint32_t)(tm.y == 1 || tm.y == 2)) & 1u;
+      W ^= 0u - flip;
+      R a = R(0);
+      if (tm.xl == 0) {
+#pragma unroll
+        for (int j = 0; j < E; j++) a += flip_sign(p[j], (W << (31 - j)) & 0x80000000u);
+      } else if ((tm.y & 1) == 0) {  // Re(conj(q) s)
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+          const uint32_t l = tid + kExpThreads * j;
+          if (E > 1 || l < nel) {
+            const C s = tile[l], q = tile[l ^ tm.xl];
+            a += flip_sign(fma(q.x, s.x, q.y * s.y), (W << (31 - j)) & 0x80000000u);
+          }
+        }
+      } else {  // Im(conj(q) s)
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+          const uint32_t l = tid + kExpThreads * j;
+          if (E > 1 || l < nel) {
+            const C s = tile[l], q = tile[l ^ tm.xl];
+            a += flip_sign(fma(q.x, s.y, -q.y * s.x), (W << (31 - j)) & 0x80000000u);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[warp * P.nk + k] += (double)a;
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < P.nk; k += kExpThreads) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) v += red[w * P.nk + k];
+    part[(size_t)blockIdx.x * ncols + st[k].out] = v;
+  }
+}
+
+// One group of terms sharing x; per-block partial sums to part[block * nt + t].
+template <class R>
+__global__ void __launch_bounds__(256) sv_expect_group(const typename Cplx<R>::T* __restrict__ psi, uint64_t N,
+                                                       uint64_t x, const uint64_t* __restrict__ zm,
+                                                       const int* __restrict__ ym, int nt,
+                                                       double* __restrict__ part) {
+  double acc[kExpectChunk];
+#pragma unroll
+  for (int t = 0; t < kExpectChunk; t++) acc[t] = 0.0;
+  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < N; b += (uint64_t)gridDim.x * blockDim.x) {
+    double pr = psi[b].x, pi = psi[b].y;
+    double qr = pr, qi = pi;
+    if (x) {
+      qr = psi[b ^ x].x;
+      qi = psi[b ^ x].y;
+    }
+    // w = conj(q) * p
+    double wr = fma(qr, pr, qi * pi);
+    double wi = fma(qr, pi, -qi * pr);
+#pragma unroll
+    for (int t = 0; t < kExpectChunk; t++) {
+      if (t < nt) {
+        // Re(i^y w): y=0 wr, y=1 -wi, y=2 -wr, y=3 wi
+        int y = ym[t];
+        double v = (y & 1) ? wi : wr;
+        int neg = ((y == 1) || (y == 2)) ^ (__popcll(b & zm[t]) & 1);
+        acc[t] += neg ? -v : v;
+      }
+    }
+  }
+  __shared__ double red[kExpectChunk][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kExpectChunk; t++) {
+    if (t >= nt) break;
+    double v = acc[t];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[t][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nt) {
+    double v = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
+    part[(size_t)blockIdx.x * nt + threadIdx.x] = v;
+  }
+}
+
+// out[idx ? idx[t] : t] = sum over blocks (in order) of part[block * nt + t].
+__global__ void reduce_partials(const double* __restrict__ part, int nblocks, int nt, const int* __restrict__ idx,
+                                double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double v = 0;
+  for (int b = 0; b < nblocks; b++) v += part[(size_t)b * nt + t];
+  out[idx ? idx[t] : t] = v;
+}
+
+template <class R, int E>
+cudaError_t launch_tiled_e(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
+                           int ncols, int grid, size_t smem, cudaStream_t s) {
+  using C = typename Cplx<R>::T;
+  static std::atomic<int> attr_dev{-1};  // setting the same maximum twice is harmless
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev.load() != dev) {
+    cudaError_t e = cudaFuncSetAttribute(sv_expect_tiled<R, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  sv_expect_tiled<R, E><<<grid, kExpThreads, smem, s>>>((const C*)psi, ntiles, P, terms, part, ncols);
+  return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_tiled_r(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
+                           int ncols, int grid, size_t smem, cudaStream_t s) {
+  switch (P.T <= 7 ? 0 : P.T - 7) {
+    case 0: return launch_tiled_e<R, 1>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+    case 1: return launch_tiled_e<R, 2>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+    case 2: return launch_tiled_e<R, 4>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+    case 3: return launch_tiled_e<R, 8>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+    case 4: return launch_tiled_e<R, 16>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+    case 5: return launch_tiled_e<R, 32>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t sv_expect_tiled_smem(bool f64, const ExpPass& P) {
+  return ((size_t)(f64 ? 16 : 8) << P.T) + ((size_t)8 << P.h) + (size_t)P.nk * sizeof(ExpTerm) +
+         (size_t)(kExpThreads / 32) * P.nk * sizeof(double);
+}
+
+cudaError_t launch_sv_expect_tiled(bool f64, const void* psi, int n, const ExpPass& P, const ExpTerm* terms,
+                                   double* part, int ncols, int grid, cudaStream_t s) {
+  // tile bits (low m plus hmask) and tile-index bits (fmask) partition the index bits
+  const uint64_t lowmask = (1ull << P.m) - 1;
+  if (P.T < 0 || P.T > kExpTileBits || P.m < 0 || P.m + P.h != P.T || P.T > n || P.nk < 1 ||
+      P.nk > kExpPassTerms || __builtin_popcountll(P.hmask) != P.h || __builtin_popcountll(P.fmask) != n - P.T ||
+      ((P.hmask | P.fmask) & lowmask) || (P.hmask & P.fmask) || ((P.hmask | P.fmask | lowmask) >> n) || grid < 1)
+    return cudaErrorInvalidValue;
+  const uint64_t ntiles = 1ull << (n - P.T);
+  const size_t smem = sv_expect_tiled_smem(f64, P);
+  cudaError_t e = f64 ? launch_tiled_r<double>(psi, ntiles, P, terms, part, ncols, grid, smem, s)
+                      : launch_tiled_r<float>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
+  g_launches += 1;
+  return e;
+}
+
+cudaError_t launch_sv_expect_group(bool f64, const void* psi, int n, uint64_t x, const uint64_t* zm, const int* ym,
+                                   int nt, double* part, int nblocks, const int* idx, double* out, cudaStream_t s) {
+  uint64_t N = 1ull << n;
+  if (f64) sv_expect_group<double><<<nblocks, 256, 0, s>>>((const double2*)psi, N, x, zm, ym, nt, part);
+  else sv_expect_group<float><<<nblocks, 256, 0, s>>>((const float2*)psi, N, x, zm, ym, nt, part);
+  cudaError_t e = cudaGetLastError();
+  g_launches += 1;
+  if (e != cudaSuccess) return e;
+  return launch_reduce_partials(part, nblocks, nt, idx, out, s);
+}
+
+cudaError_t launch_reduce_partials(const double* part, int nblocks, int nt, const int* idx, double* out,
+                                   cudaStream_t s) {
+  reduce_partials<<<(nt + 63) / 64, 64, 0, s>>>(part, nblocks, nt, idx, out);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace nwq

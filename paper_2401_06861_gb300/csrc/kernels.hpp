@@ -17,6 +17,24 @@ constexpr int kExpectChunk = 16;         // terms per expectation launch
 constexpr int kMaxDynSmem = 200 * 1024;      // dynamic shared memory cap of the sweep kernel
 constexpr int kTableSmemLimit = 112 * 1024;  // stage a sweep's tables in shared memory up to this total
 
+// Tiled SV expectations: 128 threads, tiles of at most 2^12 amplitudes, at
+// most 256 terms per pass.  A pass's tile holds the low m bits (contiguous) and
+// h = T - m high bits (hmask); fmask holds the remaining bits of the index.
+constexpr int kExpThreads = 128;
+constexpr int kExpTileBits = 12;
+constexpr int kExpPassTerms = 256;
+struct ExpTerm {
+  uint64_t zh;      // z bits outside the tile (global positions)
+  uint32_t xl, zl;  // x and z bits inside the tile (tile-local positions)
+  int32_t y;        // |x & z| mod 4
+  int32_t out;      // output column
+};
+struct ExpPass {
+  uint64_t hmask, fmask;
+  int32_t T, m, h, k0, nk, pad;
+};
+static_assert(sizeof(ExpTerm) == 24, "ExpTerm layout");
+
 struct PhaseTables {
   const PhaseDesc* ph;
   const PhaseOp* po;
@@ -33,7 +51,12 @@ cudaError_t launch_cplx_to_real(bool f64, const void* in, void* out, uint64_t co
 cudaError_t launch_sv_abs2(bool f64, const void* psi, double* p, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, int sm_count, cudaStream_t s);
 cudaError_t launch_sv_expect_group(bool f64, const void* psi, int n, uint64_t x, const uint64_t* zm, const int* ym,
-                                   int nt, double* part, int nblocks, double* out, cudaStream_t s);
+                                   int nt, double* part, int nblocks, const int* idx, double* out, cudaStream_t s);
+size_t sv_expect_tiled_smem(bool f64, const ExpPass& P);
+cudaError_t launch_sv_expect_tiled(bool f64, const void* psi, int n, const ExpPass& P, const ExpTerm* terms,
+                                   double* part, int ncols, int grid, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* part, int nblocks, int nt, const int* idx, double* out,
+                                   cudaStream_t s);
 cudaError_t launch_dm_expect(bool f64, const void* r, int n, const uint64_t* xm, const uint64_t* zm,
                              const double* coef, int nt, double* out, int sum, int normalize, cudaStream_t s);
 cudaError_t launch_weighted_sum(const double* v, const double* coef, int nt, double* out, cudaStream_t s);

@@ -9,8 +9,10 @@
 // Its scratch (term tables, per-block partial sums, results) lives in one
 // file-scope device array of kScratchBytes bytes.  Every GPU that loads the
 // library holds that array until the process exits.  All calls share it and
-// it keeps the last call's contents; the kernels below overwrite every slot
-// they read, so nothing has to start at zero.  Calls that overlap on the GPU
+// it keeps the last call's contents; each call clears or writes every slot
+// before reading it.  State vectors take the same passes and kernels as
+// nwq_expect_pauli_sum (host tables on the stack), with the tiled grid
+// reduced until its per-block partial sums fit the array.  Calls that overlap on the GPU
 // (two host threads, or two streams) race on the array and must be
 // serialised by the caller.
 #include <cuda_runtime.h>
@@ -19,6 +21,7 @@
 #include <mutex>
 
 #include "../../include/nwqgb.h"
+#include "expect_host.hpp"
 #include "kernels.hpp"
 #include "state.hpp"
 
@@ -26,18 +29,14 @@ namespace nwq {
 namespace {
 
 constexpr int kMaxTerms = NWQ_NOALLOC_MAX_TERMS;
-constexpr int kMaxBlocks = 1024;                // partial sums per expectation pass
-constexpr int kMaxChunks = kMaxTerms + 1;       // one chunk per term, plus the norm
-constexpr size_t kAlign = 256;
-constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-constexpr size_t kPartBytes = align_up((size_t)kMaxBlocks * kExpectChunk * sizeof(double));
-constexpr size_t kValBytes = align_up((kMaxTerms + 2) * sizeof(double));
-constexpr size_t kZBytes = align_up((size_t)kMaxChunks * kExpectChunk * sizeof(uint64_t));
-constexpr size_t kYBytes = align_up((size_t)kMaxChunks * kExpectChunk * sizeof(int));
-constexpr size_t kCoefBytes = align_up(kMaxTerms * sizeof(double));
-constexpr size_t kScratchBytes = kPartBytes + kValBytes + kZBytes + kYBytes + kCoefBytes;
-static_assert(kScratchBytes <= 192 * 1024, "scratch must stay at most 192 KiB");
-static_assert(3 * kMaxTerms * sizeof(uint64_t) <= kZBytes, "DM term table must fit the z region");
+constexpr size_t kScratchBytes = 192 * 1024;
+constexpr int kMaxGeneralBlocks = 256;  // partial sums per general-kernel pass
+// DM: term table (x, z, coefficient per term) then the values
+constexpr size_t kDmTable = 3 * kMaxTerms * sizeof(uint64_t);
+static_assert(kDmTable + (kMaxTerms + 2) * sizeof(double) <= kScratchBytes, "DM scratch");
+// SV: the tables and general partials for kMaxTerms terms leave room for the
+// tiled partials of at least 32 blocks
+static_assert(sv_expect_scratch_bytes(kMaxTerms, 32, kMaxGeneralBlocks) <= kScratchBytes, "SV scratch");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -87,11 +86,8 @@ extern "C" int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term*
   unsigned char* base = nullptr;
   int rc = scratch_address(st->device, &base);
   if (rc) return rc;
-  double* dpart = (double*)base;
-  double* dv = (double*)(base + kPartBytes);  // values; dv[nt] = norm, dv[nt+1] = weighted sum
-  uint64_t* dz = (uint64_t*)(base + kPartBytes + kValBytes);
-  int* dy = (int*)(base + kPartBytes + kValBytes + kZBytes);
-  double* dc = (double*)(base + kPartBytes + kValBytes + kZBytes + kYBytes);
+  uint64_t* dz = (uint64_t*)base;           // DM term table
+  double* dv = (double*)(base + kDmTable);  // DM values
   const bool f64 = st->dtype == NWQ_F64;
   cudaStream_t s = st->stream;
   cudaError_t e = cudaSuccess;
@@ -113,67 +109,26 @@ extern "C" int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term*
     return e == cudaSuccess ? NWQ_OK : set_error(NWQ_ECUDA, cudaGetErrorString(e));
   }
 
-  // SV: order terms by x mask (insertion sort on a stack array), then chunks
-  // of at most kExpectChunk terms sharing x; the norm chunk goes last.
-  int idx[kMaxTerms];
-  for (size_t t = 0; t < nt; t++) {
-    size_t k = t;
-    while (k > 0 && terms[idx[k - 1]].x_mask > terms[t].x_mask) {
-      idx[k] = idx[k - 1];
-      k--;
-    }
-    idx[k] = (int)t;
-  }
-  uint64_t hz[kMaxChunks * kExpectChunk];
-  int hy[kMaxChunks * kExpectChunk];
-  double hc[kMaxTerms];
-  uint64_t cx[kMaxChunks];
-  int ccnt[kMaxChunks];
-  int nchunk = 0;
-  for (size_t t = 0; t < nt; t++) {
-    const nwq_pauli_term& tm = terms[idx[t]];
-    if (nchunk == 0 || cx[nchunk - 1] != tm.x_mask || ccnt[nchunk - 1] == kExpectChunk) {
-      cx[nchunk] = tm.x_mask;
-      ccnt[nchunk] = 0;
-      nchunk++;
-    }
-    int c = nchunk - 1, j = ccnt[c]++;
-    hz[c * kExpectChunk + j] = tm.z_mask;
-    hy[c * kExpectChunk + j] = __builtin_popcountll(tm.x_mask & tm.z_mask) & 3;
-    hc[t] = tm.coeff;
-  }
-  if (norm) {  // identity string: <psi|psi>, written to dv[nt]
-    cx[nchunk] = 0;
-    ccnt[nchunk] = 1;
-    hz[nchunk * kExpectChunk] = 0;
-    hy[nchunk * kExpectChunk] = 0;
-    nchunk++;
-  }
+  // SV: the same passes and kernels as nwq_expect_pauli_sum, tables on the
+  // stack, scratch in g_scratch; the tiled grid shrinks until its partial sums fit.
+  ExpPass passes[kMaxTerms + 1];
+  ExpTerm eterms[kMaxTerms + 1];
+  int fb[kMaxTerms], work[2 * kMaxTerms + 2];
+  SvChunk chunks[kMaxTerms];
+  alignas(16) unsigned char stage[sv_expect_stage_bytes(kMaxTerms)];
+  SvExpectHost h{passes, eterms, fb, chunks, work};
+  SvExpectCounts c{};
+  plan_sv_expect(st->n, terms, nt, norm, h, c);
   const uint64_t N = 1ull << st->n;
-  uint64_t nb = (N + 255) / 256;
-  if (nb > (uint64_t)st->sm_count * 4) nb = (uint64_t)st->sm_count * 4;
-  if (nb > (uint64_t)kMaxBlocks) nb = kMaxBlocks;
-  e = cudaMemcpyAsync(dz, hz, (size_t)nchunk * kExpectChunk * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, hy, (size_t)nchunk * kExpectChunk * sizeof(int), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dc, hc, nt * sizeof(double), cudaMemcpyHostToDevice, s);
-  size_t done = 0;
-  for (int c = 0; c < nchunk && e == cudaSuccess; c++) {
-    e = launch_sv_expect_group(f64, st->buf, st->n, cx[c], dz + c * kExpectChunk, dy + c * kExpectChunk, ccnt[c],
-                               dpart, (int)nb, dv + done, s);
-    done += ccnt[c];
-  }
-  double vals[kMaxTerms];
-  if (e == cudaSuccess && norm) e = launch_scale(dv, (int)nt, dv + nt, s);
-  if (e == cudaSuccess && sum) {
-    e = launch_weighted_sum(dv, dc, (int)nt, dv + nt + 1, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dv + nt + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
-  } else if (e == cudaSuccess) {
-    e = cudaMemcpyAsync(vals, dv, nt * sizeof(double), cudaMemcpyDeviceToHost, s);
-  }
+  uint64_t fblocks = (N + 255) / 256;
+  if (fblocks > (uint64_t)st->sm_count * 4) fblocks = (uint64_t)st->sm_count * 4;
+  if (fblocks > (uint64_t)kMaxGeneralBlocks) fblocks = kMaxGeneralBlocks;
+  uint64_t grid = 1ull << (st->n - (st->n < kExpTileBits ? st->n : kExpTileBits));
+  if (grid > (uint64_t)st->sm_count * (f64 ? 2 : 4)) grid = (uint64_t)st->sm_count * (f64 ? 2 : 4);
+  while (grid > 1 && sv_expect_scratch_bytes(nt, (int)grid, (int)fblocks) > kScratchBytes) grid--;
+  e = sv_expect_enqueue(st, terms, nt, flags, out_host, h, c, (int)grid, (int)fblocks, stage, base);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return set_error(NWQ_ECUDA, cudaGetErrorString(e));
-  if (!sum)
-    for (size_t t = 0; t < nt; t++) out_host[idx[t]] = vals[t];
   return NWQ_OK;
 }

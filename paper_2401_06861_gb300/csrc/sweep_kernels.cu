@@ -20,21 +20,11 @@
 
 #include "nwq_internal.h"
 #include "kernels.hpp"
+#include "device_util.cuh"
 
 namespace nwq {
 
 std::atomic<unsigned long long> g_launches{0};
-
-template <class R>
-struct Cplx;
-template <>
-struct Cplx<double> {
-  using T = double2;
-};
-template <>
-struct Cplx<float> {
-  using T = float2;
-};
 
 // Insert a zero bit at each position of `pos` (ascending) into g.
 template <int K>
@@ -197,18 +187,6 @@ __device__ __forceinline__ void apply_cplx(const typename Cplx<R>::T* __restrict
 }
 
 // ------------------------------------------------------------------ sweep kernel
-// Scatter the low bits of v onto the set bits of mask (ascending).
-__device__ __forceinline__ uint64_t deposit(uint64_t v, uint64_t mask) {
-  uint64_t out = 0;
-  while (v && mask) {
-    uint64_t lowbit = mask & (~mask + 1ull);
-    if (v & 1ull) out |= lowbit;
-    v >>= 1;
-    mask ^= lowbit;
-  }
-  return out;
-}
-
 // Padded tile layout: one 16-byte pad after every 128 bytes of elements, so
 // lanes whose indices differ by multiples of 128 bytes fall on different
 // banks.  pad(a | b) = pad(a) + pad(b) for indices with disjoint bits, which
@@ -222,17 +200,6 @@ __device__ __forceinline__ uint32_t swz(uint32_t l) {
 template <class C>
 __host__ __device__ constexpr size_t padded_elems(int T) {
   return sizeof(C) == 16 ? ((size_t)1 << T) + ((size_t)1 << T) / 8 : ((size_t)1 << T) + ((size_t)1 << T) / 8;
-}
-
-// 16-byte asynchronous global -> shared copies (completion by group waits).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // Byte offset of the chunk-offset table in shared memory: after the tile(s)
@@ -773,77 +740,7 @@ cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, 
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ expectations
-// SV, one group of terms sharing x: sum_b Re( conj(psi[b^x]) i^{y_t} (-1)^{|b & z_t|} psi[b] ),
-// FP64 accumulation; per-block partial sums written to part[block * nt + t];
-// a second kernel adds the partials in block order (deterministic).
-template <class R>
-__global__ void __launch_bounds__(256) sv_expect_group(const typename Cplx<R>::T* __restrict__ psi, uint64_t N,
-                                                       uint64_t x, const uint64_t* __restrict__ zm,
-                                                       const int* __restrict__ ym, int nt,
-                                                       double* __restrict__ part) {
-  double acc[kExpectChunk];
-#pragma unroll
-  for (int t = 0; t < kExpectChunk; t++) acc[t] = 0.0;
-  for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < N; b += (uint64_t)gridDim.x * blockDim.x) {
-    double pr = psi[b].x, pi = psi[b].y;
-    double qr = pr, qi = pi;
-    if (x) {
-      qr = psi[b ^ x].x;
-      qi = psi[b ^ x].y;
-    }
-    // w = conj(q) * p
-    double wr = fma(qr, pr, qi * pi);
-    double wi = fma(qr, pi, -qi * pr);
-#pragma unroll
-    for (int t = 0; t < kExpectChunk; t++) {
-      if (t < nt) {
-        // Re(i^y w): y=0 wr, y=1 -wi, y=2 -wr, y=3 wi
-        int y = ym[t];
-        double v = (y & 1) ? wi : wr;
-        int neg = ((y == 1) || (y == 2)) ^ (__popcll(b & zm[t]) & 1);
-        acc[t] += neg ? -v : v;
-      }
-    }
-  }
-  __shared__ double red[kExpectChunk][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int t = 0; t < kExpectChunk; t++) {
-    if (t >= nt) break;
-    double v = acc[t];
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[t][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nt) {
-    double v = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
-    part[(size_t)blockIdx.x * nt + threadIdx.x] = v;
-  }
-}
-
-__global__ void reduce_partials(const double* __restrict__ part, int nblocks, int nt, double* __restrict__ out) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nt) return;
-  double v = 0;
-  for (int b = 0; b < nblocks; b++) v += part[(size_t)b * nt + t];
-  out[t] = v;
-}
-
-cudaError_t launch_sv_expect_group(bool f64, const void* psi, int n, uint64_t x, const uint64_t* zm, const int* ym,
-                                   int nt, double* part, int nblocks, double* out, cudaStream_t s) {
-  uint64_t N = 1ull << n;
-  if (f64) sv_expect_group<double><<<nblocks, 256, 0, s>>>((const double2*)psi, N, x, zm, ym, nt, part);
-  else sv_expect_group<float><<<nblocks, 256, 0, s>>>((const float2*)psi, N, x, zm, ym, nt, part);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  reduce_partials<<<(nt + 63) / 64, 64, 0, s>>>(part, nblocks, nt, out);
-  g_launches += 2;
-  return cudaGetLastError();
-}
-
-// DM: <P(x,z)> = r[x + 2^n z]; optional weighted sum in term order.
+// ------------------------------------------------------------------ DM expectations
 template <class R>
 __global__ void dm_expect_gather(const R* __restrict__ r, int n, const uint64_t* __restrict__ xm,
                                  const uint64_t* __restrict__ zm, const double* __restrict__ coef, int nt,

@@ -106,7 +106,7 @@ def test_tfim_n10_40_steps(dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("n", [1, 2, 4, 11, 15])
+@pytest.mark.parametrize("n", [1, 2, 4, 7, 8, 11, 12, 13, 15, 17])
 def test_sv_expectations(n, dtype):
     psi0 = inputs.random_state(n, 300 + n)
     terms = inputs.random_pauli_terms(n, 40, 400 + n) + inputs.z_terms(n) + inputs.x_terms(n)
@@ -121,6 +121,55 @@ def test_sv_expectations(n, dtype):
     assert maxerr(got, ref) <= tol
     assert abs(tot - oracle.energy(ref, terms)) <= tol * len(terms)
     assert maxerr(gotn, ref) <= tol and abs(totn - oracle.energy(ref, terms)) <= tol * len(terms)
+
+
+def _wide_terms(n, rng):
+    """Strings whose X support spans many high bits (some wider than any
+    shared-memory tile), with Y factors, the identity and a duplicate."""
+    full = (1 << n) - 1
+    t = [(full, 0, 0.5), (full, full, -0.25), (full & 0xAAAAAAAAA, full & 0x555555555, 0.75), (0, 0, 1.5)]
+    for w in (5, 8, 9, 11, 12, 13):
+        bits = rng.choice(np.arange(4, n), size=min(w, n - 4), replace=False)
+        x = int(sum(1 << int(b) for b in bits)) | int(rng.integers(0, 16))
+        t.append((x, int(rng.integers(0, 1 << n)), float(rng.uniform(-1, 1))))
+    t.append(t[5])
+    return t
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [13, 16, 18])
+def test_sv_expectations_tile_passes(n, dtype):
+    # terms spread over the low tile, several high-bit tiles and the general kernel
+    rng = np.random.default_rng(500 + n)
+    psi0 = inputs.random_state(n, 310 + n)
+    terms = (inputs.random_pauli_terms(n, 30, 410 + n) + inputs.tfim_terms(n) + inputs.x_terms(n)
+             + [(1 << (n - 1), 1, 1.0), ((1 << (n - 1)) | 1, (1 << (n - 1)) | 2, -1.0)] + _wide_terms(n, rng))
+    ref = oracle.sv_expect(psi0, n, terms)
+    with State(L.SV, n, dtype) as st:
+        st.load(psi0)
+        got = st.expect(terms)
+        gotn = st.expect(terms, normalize=True)
+        tot = st.expect(terms, sum=True, normalize=True)
+    tol = 1e-12 if dtype == L.F64 else 2e-6
+    assert maxerr(got, ref) <= tol
+    assert maxerr(gotn, ref) <= tol
+    assert abs(tot - oracle.energy(ref, terms)) <= tol * len(terms)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_sv_expectations_many_terms_one_pass(dtype):
+    # more terms than one launch takes (256) inside the same tile
+    n = 10
+    psi0 = inputs.random_state(n, 320)
+    terms = inputs.random_pauli_terms(n, 700, 420)
+    ref = oracle.sv_expect(psi0, n, terms)
+    with State(L.SV, n, dtype) as st:
+        st.load(psi0)
+        got = st.expect(terms)
+        tot = st.expect(terms, sum=True)
+    tol = 1e-12 if dtype == L.F64 else 2e-6
+    assert maxerr(got, ref) <= tol
+    assert abs(tot - oracle.energy(ref, terms)) <= tol * len(terms)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
