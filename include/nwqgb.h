@@ -104,7 +104,8 @@ enum nwq_plan_flags {
   NWQ_PLAN_FUSED = 0u,      /* default: gates fused into shared-memory sweeps */
   NWQ_PLAN_PLAIN = 1u,      /* one gate (plus its noise) per pass over the state */
   NWQ_PLAN_NO_MERGE = 2u,   /* fused sweeps, but no algebraic merging of operators */
-  NWQ_PLAN_NO_RESCALE = 4u  /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
+  NWQ_PLAN_NO_RESCALE = 4u, /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
+  NWQ_PLAN_INTERPRETED = 8u /* complex sweeps: never the run-time specialised kernels (see nwq_plan_jit_check) */
 };
 
 /* Expectation flags.  NWQ_EXPECT_NORMALIZE divides every value by the FP64
@@ -200,6 +201,17 @@ int nwq_plan_info(const nwq_plan* plan, int* sweeps, int* ops, double* bytes, do
  * gate folded into operator k (operators listed sweep by sweep).  Sizes from
  * nwq_plan_info.  Host-only; needs no device. */
 int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op_ngates);
+
+/* Test hook: generate and compile (host only; nothing is loaded on a device)
+ * the run-time specialised kernel of every eligible sweep of a complex plan.
+ * Complex sweeps of states with at least NWQ_JIT_MIN_BITS qubits (default 18)
+ * run such kernels: one per distinct sweep structure, compiled by NVRTC for
+ * sm_103a on first use and cached for the process; set NWQ_JIT=0 to run the
+ * interpreted kernel instead.  *eligible: sweeps whose structure and tables
+ * fit the specialised kernel; *built: those compiled.  NWQ_EUNSUPPORTED when
+ * NVRTC cannot be loaded, with the reason (or the first compiler message) in
+ * nwq_last_error(). */
+int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* built);
 
 int nwq_plan_destroy(nwq_plan* plan);
 

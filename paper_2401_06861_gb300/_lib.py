@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libnwqgb.so")
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 F32, F64 = 1, 2
 SV, DM = 1, 2
-PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE = 0, 1, 2, 4
+PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED = 0, 1, 2, 4, 8
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
 NOALLOC_MAX_TERMS = 256
@@ -88,6 +88,7 @@ def lib():
         "nwq_plan_info": (i32, [vp, P(i32), P(i32), P(dbl), P(dbl), P(sz)]),
         "nwq_plan_layout": (i32, [vp, P(i32), P(i32), P(i32)]),
         "nwq_plan_destroy": (i32, [vp]),
+        "nwq_plan_jit_check": (i32, [vp, P(i32), P(i32)]),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_probs": (i32, [vp, dbl, P(dbl)]),

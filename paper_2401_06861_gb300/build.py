@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnwqgb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["sweep_kernels.cu", "expect_kernels.cu", "batch_kernels.cu", "noalloc.cu", "planner.cpp", "expect_host.cpp", "abi.cpp", "batch_host.cpp"]
+SOURCES = ["sweep_kernels.cu", "expect_kernels.cu", "batch_kernels.cu", "noalloc.cu", "planner.cpp", "jit.cpp", "expect_host.cpp", "abi.cpp", "batch_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -51,7 +51,7 @@ def build(verbose=False):
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -15,6 +15,7 @@
 
 #include "../../include/nwqgb.h"
 #include "expect_host.hpp"
+#include "jit.hpp"
 #include "kernels.hpp"
 #include "planner.hpp"
 #include "state.hpp"
@@ -123,10 +124,13 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
   const void* ents = (const char*)p.dev + p.ops.size() * sizeof(DevOp);
   PhaseTables pt{(const PhaseDesc*)((const char*)p.dev + p.pt_off[0]), (const PhaseOp*)((const char*)p.dev + p.pt_off[1]),
                  (const char*)p.dev + p.pt_off[2]};
-  for (const SweepDesc& sd : p.sweeps) {
+  for (size_t i = 0; i < p.sweeps.size(); i++) {
+    const SweepDesc& sd = p.sweeps[i];
     if (sd.nops == 0) continue;
-    cudaError_t e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents,
-                                 p.phases.empty() ? nullptr : &pt, sm_count, s);
+    cudaError_t e = cudaSuccess;
+    if (!(p.is_complex && sd.nph > 0 && jit_launch_sweep(p, i, pt, data, sm_count, s, &e)))
+      e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents, p.phases.empty() ? nullptr : &pt,
+                       sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   }
   return NWQ_OK;
@@ -315,6 +319,7 @@ extern "C" int nwq_plan_create(int kind, int n, int dtype, const nwq_gate* gates
   plan_options(kind, dtype, flags, o);
   if (kind == NWQ_DM && !(flags & NWQ_PLAN_NO_RESCALE)) o.rescale_qubits = n;
   build_plan(ops, o, pl->p);
+  pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
   *out = pl.release();
   return NWQ_OK;
 }
@@ -348,6 +353,14 @@ extern "C" int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_ga
     if (op_gate) op_gate[k] = plan->p.op_gate0[k];
     if (op_ngates) op_ngates[k] = plan->p.op_ngates[k];
   }
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* built) {
+  if (!plan || !eligible || !built) return fail(NWQ_EINVAL, "NULL argument");
+  std::string log;
+  jit_build_check(plan->p, eligible, built, &log);
+  if (*built < *eligible) return fail(NWQ_EUNSUPPORTED, log.empty() ? "specialised kernel compilation failed" : log);
   return NWQ_OK;
 }
 

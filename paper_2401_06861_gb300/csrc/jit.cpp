@@ -1,0 +1,538 @@
+// Run-time specialised phase kernels (NVRTC).
+//
+// The register-phase kernel interprets each sweep's operator list: for every
+// group of 16 amplitudes it reads operator records, branches on their codes
+// and derives register offsets from the phase's bit positions.  On large
+// complex64 states that interpretation, not the arithmetic and not HBM, bounds
+// the sweeps.  This file writes, for each distinct sweep structure, CUDA
+// source in which the structure is fixed (tile geometry, register offsets,
+// the operator sequence with its masks, forms, permutations and diagonal index
+// bits), compiles it once with NVRTC for sm_103a and caches the kernel by its
+// source text, so sweeps that differ only in angles share one kernel.
+// Coefficients of dense, KRON and register-indexed diagonal operators travel
+// in the kernel's parameter bank (read directly as FMA operands); diagonal
+// tables indexed by bits outside the registers are staged in shared memory.
+// Every operator uses the interpreted kernel's arithmetic in the same order.
+#include "jit.hpp"
+
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <vector>
+
+namespace nwq {
+
+namespace {
+
+constexpr int kJitThreads = 256;
+constexpr size_t kParamLimit = 28 * 1024;  // packed coefficients per launch (kernel parameter bank)
+constexpr int kDefaultMinBits = 18;        // smaller states: interpreted kernel (no compile latency)
+
+// ------------------------------------------------------------------ NVRTC (loaded on first use)
+struct Nvrtc {
+  bool ok = false;
+  nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*) = nullptr;
+  nvrtcResult (*compile)(nvrtcProgram, int, const char* const*) = nullptr;
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t*) = nullptr;
+  nvrtcResult (*cubin)(nvrtcProgram, char*) = nullptr;
+  nvrtcResult (*log_size)(nvrtcProgram, size_t*) = nullptr;
+  nvrtcResult (*log)(nvrtcProgram, char*) = nullptr;
+  nvrtcResult (*destroy)(nvrtcProgram*) = nullptr;
+};
+
+Nvrtc& nvrtc() {
+  static Nvrtc N;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* h = dlopen("libnvrtc.so.13", RTLD_NOW | RTLD_LOCAL);
+    if (!h) h = dlopen("libnvrtc.so", RTLD_NOW | RTLD_LOCAL);
+    if (!h) return;
+    N.create = (decltype(N.create))dlsym(h, "nvrtcCreateProgram");
+    N.compile = (decltype(N.compile))dlsym(h, "nvrtcCompileProgram");
+    N.cubin_size = (decltype(N.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+    N.cubin = (decltype(N.cubin))dlsym(h, "nvrtcGetCUBIN");
+    N.log_size = (decltype(N.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+    N.log = (decltype(N.log))dlsym(h, "nvrtcGetProgramLog");
+    N.destroy = (decltype(N.destroy))dlsym(h, "nvrtcDestroyProgram");
+    N.ok = N.create && N.compile && N.cubin_size && N.cubin && N.log_size && N.log && N.destroy;
+  });
+  return N;
+}
+
+bool jit_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("NWQ_JIT");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+int jit_min_bits() {
+  static const int b = [] {
+    const char* e = std::getenv("NWQ_JIT_MIN_BITS");
+    return e ? std::atoi(e) : kDefaultMinBits;
+  }();
+  return b;
+}
+
+// ------------------------------------------------------------------ compiled kernels
+struct JitKernel {
+  std::mutex mu;
+  bool done = false, ok = false;
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t k = nullptr;
+  std::atomic<int> attr_dev{-1};
+};
+
+std::mutex g_cache_mu;
+std::map<std::string, std::shared_ptr<JitKernel>> g_cache;
+std::atomic<int> g_compiled{0}, g_failed{0};
+
+// Source -> sm_103a cubin (host only; needs no device).
+bool compile_cubin(const std::string& src, std::vector<char>& bin, std::string* log) {
+  Nvrtc& N = nvrtc();
+  if (!N.ok) {
+    if (log) *log = "libnvrtc not found";
+    return false;
+  }
+  nvrtcProgram prog;
+  if (N.create(&prog, src.c_str(), "nwq_jit_sweep.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device"};
+  bool ok = N.compile(prog, 3, opts) == NVRTC_SUCCESS;
+  if (!ok && log) {
+    size_t ls = 0;
+    if (N.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
+      log->resize(ls);
+      N.log(prog, &(*log)[0]);
+    }
+  }
+  if (ok) {
+    size_t sz = 0;
+    ok = N.cubin_size(prog, &sz) == NVRTC_SUCCESS && sz > 0;
+    if (ok) {
+      bin.resize(sz);
+      ok = N.cubin(prog, bin.data()) == NVRTC_SUCCESS;
+    }
+  }
+  N.destroy(&prog);
+  return ok;
+}
+
+bool compile(const std::string& src, JitKernel& jk) {
+  std::vector<char> bin;
+  if (!compile_cubin(src, bin, nullptr)) return false;
+  if (cudaLibraryLoadData(&jk.lib, bin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaLibraryGetKernel(&jk.k, jk.lib, "nwq_jit_sweep") != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+std::shared_ptr<JitKernel> kernel_for(const std::string& src) {
+  std::shared_ptr<JitKernel> jk;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto& slot = g_cache[src];
+    if (!slot) slot = std::make_shared<JitKernel>();
+    jk = slot;
+  }
+  std::lock_guard<std::mutex> lk(jk->mu);
+  if (!jk->done) {
+    jk->ok = compile(src, *jk);
+    jk->done = true;
+    (jk->ok ? g_compiled : g_failed) += 1;
+  }
+  return jk;
+}
+
+// ------------------------------------------------------------------ source generation
+int popc(unsigned v) { return __builtin_popcount(v); }
+int dep4(int v, int mask) {  // deposit v's low bits on mask's set bits
+  int out = 0, bit = 0;
+  for (int p = 0; p < 4; p++)
+    if ((mask >> p) & 1) {
+      if ((v >> bit) & 1) out |= 1 << p;
+      bit++;
+    }
+  return out;
+}
+int pext4(int v, int mask) {  // gather v's bits at mask positions
+  int out = 0, bit = 0;
+  for (int p = 0; p < 4; p++)
+    if ((mask >> p) & 1) {
+      if ((v >> p) & 1) out |= 1 << bit;
+      bit++;
+    }
+  return out;
+}
+uint32_t swz(bool c128, uint32_t l) { return c128 ? l + (l >> 3) : l + ((l >> 4) << 1); }
+size_t padded_elems(int T) { return ((size_t)1 << T) + ((size_t)1 << T) / 8; }
+
+struct Gen {
+  const Plan& p;
+  const SweepDesc& sd;
+  bool c128;
+  size_t cs;                        // bytes per coefficient
+  std::vector<unsigned char> param; // packed coefficients
+  struct Tab {
+    uint32_t src, cnt, dst;  // sweep-relative source index, count, shared-memory index
+  };
+  std::vector<Tab> tabs;
+  uint32_t ntab = 0;
+  std::ostringstream o;
+  bool ok = true;
+
+  Gen(const Plan& p_, const SweepDesc& sd_) : p(p_), sd(sd_), c128(p_.dtype == NWQ_F64), cs(c128 ? 16 : 8) {}
+
+  // Pack cnt coefficients starting at absolute index a; returns the packed index.
+  uint32_t pack(uint32_t a, uint32_t cnt) {
+    if ((size_t)(a + cnt) * cs > p.pcoef.size()) {
+      ok = false;
+      return 0;
+    }
+    uint32_t at = (uint32_t)(param.size() / cs);
+    param.insert(param.end(), p.pcoef.begin() + (size_t)a * cs, p.pcoef.begin() + (size_t)(a + cnt) * cs);
+    return at;
+  }
+  uint32_t table(uint32_t a, uint32_t cnt) {
+    if ((size_t)(a + cnt) * cs > p.pcoef.size() || a < sd.pc0) {
+      ok = false;
+      return 0;
+    }
+    tabs.push_back({a - sd.pc0, cnt, ntab});
+    ntab += cnt;
+    return ntab - cnt;
+  }
+
+  std::string K(uint32_t i) { return "K.c[" + std::to_string(i) + "]"; }
+  std::string r(int i) { return "r" + std::to_string(i); }
+
+  // Dense operator on register mask M (form f), coefficients at packed index pb.
+  void dense(int NR, int M, int f, uint32_t pb) {
+    const int D = 1 << popc(M);
+    for (int ob = 0; ob < NR; ob++) {
+      if (ob & M) continue;
+      o << "    {";
+      for (int j = 0; j < D; j++) o << " const C i" << j << " = " << r(ob | dep4(j, M)) << ";";
+      o << "\n";
+      if (f == PD_XROT) {
+        o << "      " << r(ob) << " = C{fma(" << K(pb) << ".x, i0.x, -" << K(pb + 1) << ".y * i1.y), fma(" << K(pb)
+          << ".x, i0.y, " << K(pb + 1) << ".y * i1.x)};\n";
+        o << "      " << r(ob | M) << " = C{fma(" << K(pb + 3) << ".x, i1.x, -" << K(pb + 2) << ".y * i0.y), fma("
+          << K(pb + 3) << ".x, i1.y, " << K(pb + 2) << ".y * i0.x)};\n";
+      } else {
+        for (int i = 0; i < D; i++) {
+          o << "      { C a{R(0), R(0)};";
+          for (int j = 0; j < D; j++) {
+            const std::string c = K(pb + i * D + j);
+            if (f == PD_REAL)
+              o << " a.x = fma(" << c << ".x, i" << j << ".x, a.x); a.y = fma(" << c << ".x, i" << j << ".y, a.y);";
+            else
+              o << " a.x = fma(" << c << ".x, i" << j << ".x, fma(-" << c << ".y, i" << j << ".y, a.x)); a.y = fma("
+                << c << ".x, i" << j << ".y, fma(" << c << ".y, i" << j << ".x, a.y));";
+          }
+          o << " " << r(ob | dep4(i, M)) << " = a; }\n";
+        }
+      }
+      o << "    }\n";
+    }
+  }
+
+  void op(int NR, const PhaseOp& po) {
+    const int code = po.code;
+    if (code < 16) {  // diagonal, register part SU
+      const int SU = code, ks = popc(SU);
+      if (SU >= NR || po.dnu > 8) {
+        ok = false;
+        return;
+      }
+      if (po.dnu == 0) {
+        const uint32_t pb = pack(po.coef, 1u << ks);
+        for (int i = 0; i < NR; i++)
+          o << "    { const C f = " << K(pb + pext4(i, SU)) << "; const C v = " << r(i) << "; " << r(i)
+            << " = C{fma(f.x, v.x, -f.y * v.y), fma(f.x, v.y, f.y * v.x)}; }\n";
+      } else {
+        const uint32_t tb = table(po.coef, 1u << (ks + po.dnu));
+        o << "    { unsigned ig = 0u";
+        for (int t = 0; t < po.dnu; t++) o << " | (((gb >> " << (int)po.dpos[t] << ") & 1u) << " << t << ")";
+        o << ";\n      const C* dg = dtab + " << tb << " + (ig << " << ks << ");\n";
+        for (int i = 0; i < NR; i++)
+          o << "      { const C f = dg[" << pext4(i, SU) << "]; const C v = " << r(i) << "; " << r(i)
+            << " = C{fma(f.x, v.x, -f.y * v.y), fma(f.x, v.y, f.y * v.x)}; }\n";
+        o << "    }\n";
+      }
+      return;
+    }
+    if (code == PCODE_KRON) {
+      for (int P = 0; P < 4; P++) {
+        if (!((po.mask >> P) & 1)) continue;
+        if ((1 << P) >= NR) {
+          ok = false;
+          return;
+        }
+        const uint32_t pb = pack(po.coef + 4 * P, 4);
+        dense(NR, 1 << P, (po.form >> (2 * P)) & 3, pb);
+      }
+      return;
+    }
+    const int M = code & 15, cls = code >> 4;
+    if (M == 0 || M >= NR || popc(M) > 2 || cls > 4) {
+      ok = false;
+      return;
+    }
+    if (cls == 1) {  // signed permutation: register moves and negations only
+      const int D = 1 << popc(M);
+      for (int ob = 0; ob < NR; ob++) {
+        if (ob & M) continue;
+        o << "    {";
+        for (int j = 0; j < D; j++) o << " const C i" << j << " = " << r(ob | dep4(j, M)) << ";";
+        for (int i = 0; i < D; i++) {
+          const int src = po.perm[i] & 15;
+          if (src >= D) {
+            ok = false;
+            return;
+          }
+          if (po.perm[i] & 0x80) o << " " << r(ob | dep4(i, M)) << " = C{-i" << src << ".x, -i" << src << ".y};";
+          else o << " " << r(ob | dep4(i, M)) << " = i" << src << ";";
+        }
+        o << " }\n";
+      }
+      return;
+    }
+    const int form = cls == 2 ? PD_GEN : (cls == 3 ? PD_REAL : PD_XROT);
+    const int D = 1 << popc(M);
+    if (form == PD_XROT && D != 2) {
+      ok = false;
+      return;
+    }
+    dense(NR, M, form, pack(po.coef, (uint32_t)(D * D)));
+  }
+
+  bool run(std::string& src) {
+    const int T = sd.T, m = sd.m, h = sd.h, RB = sd.prb, NR = 1 << RB;
+    const int lvpe = c128 ? 0 : 1;
+    if (RB < 1 || RB > 4 || T < RB || T > 13 || m < lvpe || m + h != T) return false;
+    const size_t PE = padded_elems(T);
+    const uint32_t NG = 1u << (T - RB);
+    std::ostringstream body;
+    o.swap(body);
+    for (uint32_t ph = 0; ph < sd.nph && ok; ph++) {
+      const PhaseDesc& P = p.phases[sd.ph0 + ph];
+      o << "    // phase " << ph << "\n";
+      o << "    for (unsigned g = threadIdx.x; g < " << NG << "u; g += " << kJitThreads << "u) {\n";
+      o << "    unsigned gb = g;\n";
+      for (int t = 0; t < RB; t++) {
+        const uint32_t lowm = (1u << P.u[t]) - 1u;
+        o << "    gb = ((gb & " << (~lowm) << "u) << 1) | (gb & " << lowm << "u);\n";
+      }
+      o << "    C* gt = tile + " << (c128 ? "(gb + (gb >> 3))" : "(gb + ((gb >> 4) << 1))") << ";\n";
+      uint32_t roff[16];
+      for (int i = 0; i < NR; i++) {
+        uint32_t l = 0;
+        for (int b = 0; b < RB; b++)
+          if ((i >> b) & 1) l |= 1u << P.u[b];
+        roff[i] = swz(c128, l);
+        o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
+      }
+      for (uint32_t q = 0; q < P.nops && ok; q++) op(NR, p.pops[P.op0 + q]);
+      for (int i = 0; i < NR; i++) o << "    gt[" << roff[i] << "] = " << r(i) << ";\n";
+      o << "    }\n    __syncthreads();\n";
+    }
+    if (!ok) return false;
+    if (param.size() > kParamLimit) return false;
+    o.swap(body);
+    const size_t npk = param.empty() ? 1 : param.size() / cs;
+    const size_t hoff_byte = ((2 * PE + ntab) * cs + 15) & ~(size_t)15;
+    smem = hoff_byte + ((size_t)8 << h);
+    if (smem > (size_t)kMaxDynSmem) return false;
+    const char* RT = c128 ? "double" : "float";
+    const char* CT = c128 ? "double2" : "float2";
+    o << "typedef " << RT << " R;\ntypedef " << CT << " C;\n"
+      << "struct Coef { C c[" << npk << "]; };\n"
+      << "__device__ __forceinline__ unsigned long long dep(unsigned long long v, unsigned long long mask) {\n"
+      << "  unsigned long long out = 0;\n"
+      << "  while (v && mask) { unsigned long long lb = mask & (~mask + 1ull); if (v & 1ull) out |= lb; v >>= 1; mask ^= lb; }\n"
+      << "  return out;\n}\n"
+      << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
+      << "  unsigned a = (unsigned)__cvta_generic_to_shared(s);\n"
+      << "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(a), \"l\"(g) : \"memory\");\n}\n"
+      << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 2) nwq_jit_sweep(C* __restrict__ state, "
+      << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const C* __restrict__ pcs, "
+      << "const Coef K) {\n"
+      << "  extern __shared__ __align__(16) unsigned char sm[];\n"
+      << "  C* tile = (C*)sm;\n  C* ntile = tile + " << PE << ";\n  C* dtab = tile + " << 2 * PE << ";\n"
+      << "  unsigned long long* hoff = (unsigned long long*)(sm + " << hoff_byte << ");\n"
+      << "  for (unsigned j = threadIdx.x; j < " << (1u << h) << "u; j += " << kJitThreads << "u) hoff[j] = dep(j, hmask);\n";
+    for (const Tab& t : tabs)
+      o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << kJitThreads << "u) dtab[" << t.dst
+        << " + j] = pcs[" << t.src << " + j];\n";
+    const int VPE = c128 ? 1 : 2, lvpc = m - lvpe;
+    const uint32_t nvec = (1u << T) / VPE;
+    o << "  __syncthreads();\n"
+      << "  if (blockIdx.x < ntiles) {\n"
+      << "    const unsigned long long b = dep(blockIdx.x, fmask);\n"
+      << "    for (unsigned v = threadIdx.x; v < " << nvec << "u; v += " << kJitThreads << "u) {\n"
+      << "      const unsigned l = v * " << VPE << "u;\n"
+      << "      cpa16(tile + " << (c128 ? "(l + (l >> 3))" : "(l + ((l >> 4) << 1))")
+      << ", state + b + hoff[v >> " << lvpc << "] + (unsigned long long)(v & " << ((1u << lvpc) - 1u) << "u) * "
+      << VPE << ");\n    }\n"
+      << "    asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n  }\n"
+      << "  for (unsigned long long tileid = blockIdx.x; tileid < ntiles; tileid += gridDim.x) {\n"
+      << "    const unsigned long long base = dep(tileid, fmask);\n"
+      << "    const unsigned long long next = tileid + gridDim.x;\n"
+      << "    if (next < ntiles) {\n"
+      << "      const unsigned long long nb = dep(next, fmask);\n"
+      << "      for (unsigned v = threadIdx.x; v < " << nvec << "u; v += " << kJitThreads << "u) {\n"
+      << "        const unsigned l = v * " << VPE << "u;\n"
+      << "        cpa16(ntile + " << (c128 ? "(l + (l >> 3))" : "(l + ((l >> 4) << 1))")
+      << ", state + nb + hoff[v >> " << lvpc << "] + (unsigned long long)(v & " << ((1u << lvpc) - 1u) << "u) * "
+      << VPE << ");\n      }\n"
+      << "      asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n"
+      << "      asm volatile(\"cp.async.wait_group 1;\\n\" ::: \"memory\");\n"
+      << "    } else {\n"
+      << "      asm volatile(\"cp.async.wait_group 0;\\n\" ::: \"memory\");\n"
+      << "    }\n"
+      << "    __syncthreads();\n"
+      << body.str()
+      << "    for (unsigned v = threadIdx.x; v < " << nvec << "u; v += " << kJitThreads << "u) {\n"
+      << "      const unsigned l = v * " << VPE << "u;\n"
+      << "      *reinterpret_cast<uint4*>(state + base + hoff[v >> " << lvpc << "] + (unsigned long long)(v & "
+      << ((1u << lvpc) - 1u) << "u) * " << VPE << ") = *reinterpret_cast<const uint4*>(tile + "
+      << (c128 ? "(l + (l >> 3))" : "(l + ((l >> 4) << 1))") << ");\n"
+      << "    }\n"
+      << "    __syncthreads();\n"
+      << "    C* t = tile; tile = ntile; ntile = t;\n"
+      << "  }\n"
+      << "  asm volatile(\"cp.async.wait_group 0;\\n\" ::: \"memory\");\n"
+      << "}\n";
+    src = o.str();
+    return true;
+  }
+  size_t smem = 0;
+};
+
+// Per-plan state: one entry per sweep, built on the plan's first launch.
+struct JitSweep {
+  std::shared_ptr<JitKernel> k;  // null: run the interpreted kernel
+  std::vector<unsigned char> param;
+  size_t smem = 0;
+  int per_sm = 0;
+};
+struct JitPlan {
+  std::mutex mu;
+  bool built = false;
+  std::vector<JitSweep> sw;
+};
+
+}  // namespace
+
+bool jit_source(const Plan& p, size_t sweep, std::string& src, size_t* param_bytes, size_t* smem_bytes) {
+  src.clear();
+  if (!p.is_complex || sweep >= p.sweeps.size() || p.sweeps[sweep].nph == 0) return false;
+  Gen g(p, p.sweeps[sweep]);
+  if (!g.run(src)) {
+    src.clear();
+    return false;
+  }
+  if (param_bytes) *param_bytes = g.param.size();
+  if (smem_bytes) *smem_bytes = g.smem;
+  return true;
+}
+
+int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log) {
+  *eligible = *built = 0;
+  std::map<std::string, bool> seen;  // one compile per distinct structure, as at run time
+  for (size_t i = 0; i < p.sweeps.size(); i++) {
+    std::string src;
+    if (!jit_source(p, i, src, nullptr, nullptr)) continue;
+    (*eligible)++;
+    auto it = seen.find(src);
+    if (it == seen.end()) {
+      std::vector<char> bin;
+      it = seen.emplace(src, compile_cubin(src, bin, log)).first;
+    }
+    if (!it->second) return 0;
+    (*built)++;
+  }
+  return 0;
+}
+
+void jit_stats(int* compiled, int* failed) {
+  if (compiled) *compiled = g_compiled.load();
+  if (failed) *failed = g_failed.load();
+}
+
+bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state, int sm_count, cudaStream_t s,
+                      cudaError_t* err) {
+  if (!jit_enabled() || p.interpreted || !p.is_complex || p.B < jit_min_bits() || sweep >= p.sweeps.size())
+    return false;
+  if (!p.jit) p.jit = std::make_shared<JitPlan>();
+  JitPlan& jp = *std::static_pointer_cast<JitPlan>(p.jit);
+  {
+    std::lock_guard<std::mutex> lk(jp.mu);
+    if (!jp.built) {
+      jp.sw.resize(p.sweeps.size());
+      for (size_t i = 0; i < p.sweeps.size(); i++) {
+        const SweepDesc& sd = p.sweeps[i];
+        if (sd.nops == 0 || sd.nph == 0) continue;
+        Gen g(p, sd);
+        std::string src;
+        if (!g.run(src)) continue;
+        std::shared_ptr<JitKernel> k = kernel_for(src);
+        if (!k->ok) continue;
+        JitSweep& js = jp.sw[i];
+        js.k = k;
+        js.param = std::move(g.param);
+        if (js.param.empty()) js.param.resize(g.cs, 0);
+        js.smem = g.smem;
+      }
+      jp.built = true;
+    }
+  }
+  JitSweep& js = jp.sw[sweep];
+  if (!js.k) return false;
+  const void* fn = (const void*)js.k->k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaError_t e = cudaSuccess;
+  if (js.k->attr_dev.load() != dev) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) {
+      *err = e;
+      return true;
+    }
+    js.k->attr_dev = dev;
+  }
+  if (js.per_sm == 0) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kJitThreads, js.smem);
+    if (e != cudaSuccess) {
+      *err = e;
+      return true;
+    }
+    js.per_sm = per_sm < 1 ? 1 : per_sm;
+  }
+  const SweepDesc& sd = p.sweeps[sweep];
+  unsigned long long ntiles = 1ull << (p.B - sd.T);
+  unsigned long long grid = (unsigned long long)sm_count * js.per_sm;
+  if (grid > ntiles) grid = ntiles;
+  unsigned long long hmask = sd.hmask, fmask = sd.fmask;
+  const void* pcs = (const char*)pt.pc + (size_t)sd.pc0 * (p.dtype == NWQ_F64 ? 16 : 8);
+  void* args[] = {&state, &ntiles, &hmask, &fmask, (void*)&pcs, js.param.data()};
+  e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kJitThreads), args, js.smem, s);
+  g_launches += 1;
+  *err = e;
+  return true;
+}
+
+}  // namespace nwq

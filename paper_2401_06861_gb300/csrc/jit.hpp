@@ -1,0 +1,33 @@
+// Run-time specialised phase kernels (see jit.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "kernels.hpp"
+#include "planner.hpp"
+
+namespace nwq {
+
+// Run sweep sd of plan p through a kernel compiled for its structure.
+// Returns false, launching nothing, when the sweep is not eligible (real
+// plans, no phases, states below the size threshold, tables over the
+// parameter or shared-memory budget) or NVRTC is unavailable or failed: the
+// caller then runs the interpreted phase kernel.  When it returns true, *err
+// holds the launch status.
+bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state, int sm_count, cudaStream_t s,
+                      cudaError_t* err);
+
+// Source of the specialised kernel for sweep `sweep` of p (empty if not
+// eligible) and its packed parameter bytes: a host-only hook for tests.
+bool jit_source(const Plan& p, size_t sweep, std::string& src, size_t* param_bytes, size_t* smem_bytes);
+
+// Host-only check: generate and compile (to cubin, nothing loaded) every
+// eligible sweep of p; *eligible sweeps, *built compiled.  log: the first
+// compiler error.
+int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log);
+
+// Kernels compiled so far in this process, and compile failures.
+void jit_stats(int* compiled, int* failed);
+
+}  // namespace nwq

@@ -2,6 +2,7 @@
 #pragma once
 #include <complex>
 #include <cstddef>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -56,6 +57,9 @@ struct Plan {
   // state's stream and free them there (no device-wide synchronisation).
   bool stream_ordered = false;
   cudaStream_t dev_stream = nullptr;
+  // run-time specialised kernels of this plan's sweeps (built on first launch)
+  std::shared_ptr<void> jit;
+  bool interpreted = false;  // never use them
   ~Plan();
 };
 

@@ -172,6 +172,13 @@ class Plan:
         check(L.lib().nwq_plan_layout(self.h, sw, og, on))
         return list(sw)[:info["sweeps"]], list(og)[:info["ops"]], list(on)[:info["ops"]]
 
+    def jit_check(self):
+        """Compile (host only) the specialised kernels of this plan's sweeps:
+        returns (eligible sweeps, compiled sweeps)."""
+        e, b = ctypes.c_int(), ctypes.c_int()
+        check(L.lib().nwq_plan_jit_check(self.h, ctypes.byref(e), ctypes.byref(b)))
+        return e.value, b.value
+
     def close(self):
         if self.h:
             L.lib().nwq_plan_destroy(self.h)

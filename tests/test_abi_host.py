@@ -126,3 +126,19 @@ def test_batch_create_validates_without_device():
             Batch([bad], 8, L.F64)
         assert ei.value.code == L.EINVAL
         assert msg in L.lib().nwq_last_error()
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F64])
+def test_specialised_sweep_kernels_compile(dtype):
+    # NVRTC needs no device: every eligible sweep's generated source must compile
+    plans = [(20, inputs.large_sv_tfim(20, 3)[0], 0), (19, inputs.random_circuit(19, 400, 23), 0),
+             (18, inputs.hea_ansatz(18, 3, inputs.hea_params(18, 3, 1)[0])[0], 0),
+             (20, inputs.random_circuit(20, 60, 29), L.PLAN_NO_MERGE)]
+    total = 0
+    for n, gates, flags in plans:
+        p = sim.Plan(L.SV, n, gates, dtype, flags=flags)
+        eligible, built = p.jit_check()
+        assert built == eligible, L.lib().nwq_last_error()
+        total += eligible
+        p.close()
+    assert total >= 10

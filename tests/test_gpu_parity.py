@@ -55,6 +55,37 @@ def test_sv_random_circuits(n, flags, dtype):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,family", [(18, "random"), (19, "random_mat"), (20, "tfim"), (18, "hea"),
+                                      (19, "no_merge")])
+def test_sv_specialised_kernels(n, family, dtype):
+    # states of >= 18 qubits run run-time compiled sweep kernels: against the
+    # oracle and against the interpreted kernel on the same plan structure
+    flags = 0
+    if family == "random":
+        gates = inputs.random_circuit(n, 300, 3000 + n, names=[g for g in inputs.GATE_NAMES if not g.startswith("MAT")])
+    elif family == "random_mat":
+        gates = inputs.random_circuit(n, 150, 3100 + n)
+    elif family == "tfim":
+        gates = inputs.large_sv_tfim(n, 4)[0]
+    elif family == "hea":
+        gates = inputs.hea_ansatz(n, 4, inputs.hea_params(n, 4, 1)[0])[0]
+    else:
+        gates, flags = inputs.random_circuit(n, 120, 3200 + n), L.PLAN_NO_MERGE
+    psi0 = inputs.random_state(n, 2100 + n)
+    out = {}
+    for extra in (0, L.PLAN_INTERPRETED):
+        with State(L.SV, n, dtype) as st:
+            st.load(psi0)
+            st.apply(gates, flags=flags | extra)
+            out[extra] = st.copy()
+    ref = oracle.sv_run(n, gates, psi0)
+    err, err_i = maxerr(out[0], ref), maxerr(out[0], out[L.PLAN_INTERPRETED])
+    print(f"sv n={n} {family} dtype={dtype} specialised err {err:.3e}, vs interpreted {err_i:.3e}")
+    assert err <= TOL[dtype]
+    assert err_i <= (1e-14 if dtype == L.F64 else 1e-6)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
 def test_sv_every_gate_on_every_qubit_position(dtype):
     # each gate kind on low, tile-boundary and top qubits of a 15-qubit state
     n = 15
