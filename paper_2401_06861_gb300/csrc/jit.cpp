@@ -321,7 +321,7 @@ struct Gen {
   bool run(std::string& src) {
     const int T = sd.T, m = sd.m, h = sd.h, RB = sd.prb, NR = 1 << RB;
     const int lvpe = c128 ? 0 : 1;
-    if (RB < 1 || RB > 4 || T < RB || T > 13 || m < lvpe || m + h != T) return false;
+    if (RB < 1 || RB > 4 || T < RB || T > 13 || m < lvpe || m + h != T || p.B - T > 24) return false;
     const size_t PE = padded_elems(T);
     const uint32_t NG = 1u << (T - RB);
     std::ostringstream body;
@@ -353,7 +353,8 @@ struct Gen {
     o.swap(body);
     const size_t npk = param.empty() ? 1 : param.size() / cs;
     const size_t hoff_byte = ((2 * PE + ntab) * cs + 15) & ~(size_t)15;
-    smem = hoff_byte + ((size_t)8 << h);
+    const size_t btab_byte = hoff_byte + ((size_t)8 << h);  // 4 x 64 tile-base pieces
+    smem = btab_byte + 4 * 64 * 8;
     if (smem > (size_t)kMaxDynSmem) return false;
     const char* RT = c128 ? "double" : "float";
     const char* CT = c128 ? "double2" : "float2";
@@ -372,45 +373,66 @@ struct Gen {
       << "  extern __shared__ __align__(16) unsigned char sm[];\n"
       << "  C* tile = (C*)sm;\n  C* ntile = tile + " << PE << ";\n  C* dtab = tile + " << 2 * PE << ";\n"
       << "  unsigned long long* hoff = (unsigned long long*)(sm + " << hoff_byte << ");\n"
-      << "  for (unsigned j = threadIdx.x; j < " << (1u << h) << "u; j += " << kJitThreads << "u) hoff[j] = dep(j, hmask);\n";
+      << "  unsigned long long* btab = (unsigned long long*)(sm + " << btab_byte << ");\n"
+      << "  for (unsigned j = threadIdx.x; j < " << (1u << h) << "u; j += " << kJitThreads << "u) hoff[j] = dep(j, hmask);\n"
+      << "  // tile base = OR of 4 pieces, each depositing 6 bits of the tile index on fmask\n"
+      << "  for (unsigned j = threadIdx.x; j < 256u; j += " << kJitThreads
+      << "u) btab[j] = dep((unsigned long long)(j & 63u) << (6u * (j >> 6)), fmask);\n";
     for (const Tab& t : tabs)
       o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << kJitThreads << "u) dtab[" << t.dst
         << " + j] = pcs[" << t.src << " + j];\n";
     const int VPE = c128 ? 1 : 2, lvpc = m - lvpe;
     const uint32_t nvec = (1u << T) / VPE;
+    const uint32_t NVT = (nvec + kJitThreads - 1) / kJitThreads;  // vectors per thread
+    const bool ragged = nvec % kJitThreads != 0;
+    // per-thread vector offsets inside a tile (global, registers) and shared-memory slots
+    // (swz is additive over the disjoint bits of threadIdx.x * VPE and 256 * i * VPE)
     o << "  __syncthreads();\n"
-      << "  if (blockIdx.x < ntiles) {\n"
-      << "    const unsigned long long b = dep(blockIdx.x, fmask);\n"
-      << "    for (unsigned v = threadIdx.x; v < " << nvec << "u; v += " << kJitThreads << "u) {\n"
-      << "      const unsigned l = v * " << VPE << "u;\n"
-      << "      cpa16(tile + " << (c128 ? "(l + (l >> 3))" : "(l + ((l >> 4) << 1))")
-      << ", state + b + hoff[v >> " << lvpc << "] + (unsigned long long)(v & " << ((1u << lvpc) - 1u) << "u) * "
-      << VPE << ");\n    }\n"
-      << "    asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n  }\n"
+      << "  const unsigned s0 = " << (c128 ? "threadIdx.x + (threadIdx.x >> 3)" : "threadIdx.x * 2u + ((threadIdx.x >> 3) << 1)")
+      << ";\n";
+    for (uint32_t i = 0; i < NVT; i++) {
+      const std::string v = "(threadIdx.x + " + std::to_string(i * kJitThreads) + "u)";
+      const std::string off = "hoff[" + v + " >> " + std::to_string(lvpc) + "] + (unsigned long long)(" + v + " & " +
+                              std::to_string((1u << lvpc) - 1u) + "u) * " + std::to_string(VPE);
+      if (ragged && i == NVT - 1)  // threads past the last vector read no table entry
+        o << "  const unsigned long long o" << i << " = " << v << " < " << nvec << "u ? " << off << " : 0ull;\n";
+      else
+        o << "  const unsigned long long o" << i << " = " << off << ";\n";
+    }
+    auto sidx = [&](uint32_t i) { return std::to_string(swz(c128, i * kJitThreads * VPE)); };
+    auto guard = [&](uint32_t i) -> std::string {
+      return (ragged && i == NVT - 1) ? "if (threadIdx.x + " + std::to_string(i * kJitThreads) + "u < " +
+                                            std::to_string(nvec) + "u) "
+                                      : "";
+    };
+    auto base_of = [](const char* t) {
+      return std::string("(btab[") + t + " & 63u] | btab[64u + ((" + t + " >> 6) & 63u)] | btab[128u + ((" + t +
+             " >> 12) & 63u)] | btab[192u + ((" + t + " >> 18) & 63u)])";
+    };
+    o << "  if (blockIdx.x < ntiles) {\n"
+      << "    const unsigned long long tb = blockIdx.x;\n"
+      << "    const unsigned long long b = " << base_of("tb") << ";\n";
+    for (uint32_t i = 0; i < NVT; i++)
+      o << "    " << guard(i) << "cpa16(tile + s0 + " << sidx(i) << ", state + b + o" << i << ");\n";
+    o << "    asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n  }\n"
       << "  for (unsigned long long tileid = blockIdx.x; tileid < ntiles; tileid += gridDim.x) {\n"
-      << "    const unsigned long long base = dep(tileid, fmask);\n"
+      << "    const unsigned long long base = " << base_of("tileid") << ";\n"
       << "    const unsigned long long next = tileid + gridDim.x;\n"
       << "    if (next < ntiles) {\n"
-      << "      const unsigned long long nb = dep(next, fmask);\n"
-      << "      for (unsigned v = threadIdx.x; v < " << nvec << "u; v += " << kJitThreads << "u) {\n"
-      << "        const unsigned l = v * " << VPE << "u;\n"
-      << "        cpa16(ntile + " << (c128 ? "(l + (l >> 3))" : "(l + ((l >> 4) << 1))")
-      << ", state + nb + hoff[v >> " << lvpc << "] + (unsigned long long)(v & " << ((1u << lvpc) - 1u) << "u) * "
-      << VPE << ");\n      }\n"
-      << "      asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n"
+      << "      const unsigned long long nb = " << base_of("next") << ";\n";
+    for (uint32_t i = 0; i < NVT; i++)
+      o << "      " << guard(i) << "cpa16(ntile + s0 + " << sidx(i) << ", state + nb + o" << i << ");\n";
+    o << "      asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\");\n"
       << "      asm volatile(\"cp.async.wait_group 1;\\n\" ::: \"memory\");\n"
       << "    } else {\n"
       << "      asm volatile(\"cp.async.wait_group 0;\\n\" ::: \"memory\");\n"
       << "    }\n"
       << "    __syncthreads();\n"
-      << body.str()
-      << "    for (unsigned v = threadIdx.x; v < " << nvec << "u; v += " << kJitThreads << "u) {\n"
-      << "      const unsigned l = v * " << VPE << "u;\n"
-      << "      *reinterpret_cast<uint4*>(state + base + hoff[v >> " << lvpc << "] + (unsigned long long)(v & "
-      << ((1u << lvpc) - 1u) << "u) * " << VPE << ") = *reinterpret_cast<const uint4*>(tile + "
-      << (c128 ? "(l + (l >> 3))" : "(l + ((l >> 4) << 1))") << ");\n"
-      << "    }\n"
-      << "    __syncthreads();\n"
+      << body.str();
+    for (uint32_t i = 0; i < NVT; i++)
+      o << "    " << guard(i) << "*reinterpret_cast<uint4*>(state + base + o" << i
+        << ") = *reinterpret_cast<const uint4*>(tile + s0 + " << sidx(i) << ");\n";
+    o << "    __syncthreads();\n"
       << "    C* t = tile; tile = ntile; ntile = t;\n"
       << "  }\n"
       << "  asm volatile(\"cp.async.wait_group 0;\\n\" ::: \"memory\");\n"
