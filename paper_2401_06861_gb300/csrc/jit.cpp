@@ -19,7 +19,10 @@
 #include <nvrtc.h>
 
 #include <atomic>
+#include <condition_variable>
 #include <cstdlib>
+#include <deque>
+#include <thread>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -73,6 +76,13 @@ bool jit_enabled() {
   }();
   return on;
 }
+bool jit_sync_all() {  // compile one-shot plans' kernels before running them too
+  static const bool on = [] {
+    const char* e = std::getenv("NWQ_JIT_SYNC");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
 int jit_min_bits() {
   static const int b = [] {
     const char* e = std::getenv("NWQ_JIT_MIN_BITS");
@@ -84,7 +94,7 @@ int jit_min_bits() {
 // ------------------------------------------------------------------ compiled kernels
 struct JitKernel {
   std::mutex mu;
-  bool done = false, ok = false;
+  std::atomic<bool> done{false}, ok{false}, queued{false};
   cudaLibrary_t lib = nullptr;
   cudaKernel_t k = nullptr;
   std::atomic<int> attr_dev{-1};
@@ -138,7 +148,61 @@ bool compile(const std::string& src, JitKernel& jk) {
   return true;
 }
 
-std::shared_ptr<JitKernel> kernel_for(const std::string& src) {
+void build_kernel(const std::string& src, JitKernel& jk) {
+  std::lock_guard<std::mutex> lk(jk.mu);
+  if (jk.done) return;
+  jk.ok = compile(src, jk);
+  jk.done = true;
+  (jk.ok ? g_compiled : g_failed) += 1;
+}
+
+// One background thread compiles kernels queued by one-shot plans; it is
+// stopped and joined when the library unloads.
+struct AsyncCompiler {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<std::pair<std::string, std::shared_ptr<JitKernel>>> q;
+  bool stop = false;
+  std::thread th;
+  AsyncCompiler() : th([this] { run(); }) {}
+  ~AsyncCompiler() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    th.join();
+  }
+  void push(const std::string& src, std::shared_ptr<JitKernel> jk) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      q.emplace_back(src, std::move(jk));
+    }
+    cv.notify_one();
+  }
+  void run() {
+    for (;;) {
+      std::pair<std::string, std::shared_ptr<JitKernel>> job;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [this] { return stop || !q.empty(); });
+        if (stop) return;
+        job = std::move(q.front());
+        q.pop_front();
+      }
+      build_kernel(job.first, *job.second);
+    }
+  }
+};
+AsyncCompiler& async_compiler() {
+  static AsyncCompiler ac;
+  return ac;
+}
+
+// Cached kernel for src.  Synchronous: compiled before returning.
+// Asynchronous: queued for the background compiler on first request; until
+// it is ready the caller runs the interpreted kernel.
+std::shared_ptr<JitKernel> kernel_for(const std::string& src, bool async) {
   std::shared_ptr<JitKernel> jk;
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -146,11 +210,11 @@ std::shared_ptr<JitKernel> kernel_for(const std::string& src) {
     if (!slot) slot = std::make_shared<JitKernel>();
     jk = slot;
   }
-  std::lock_guard<std::mutex> lk(jk->mu);
-  if (!jk->done) {
-    jk->ok = compile(src, *jk);
-    jk->done = true;
-    (jk->ok ? g_compiled : g_failed) += 1;
+  if (jk->done) return jk;
+  if (!async) {
+    build_kernel(src, *jk);
+  } else if (!jk->queued.exchange(true)) {
+    async_compiler().push(src, jk);
   }
   return jk;
 }
@@ -510,8 +574,10 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
         Gen g(p, sd);
         std::string src;
         if (!g.run(src)) continue;
-        std::shared_ptr<JitKernel> k = kernel_for(src);
-        if (!k->ok) continue;
+        // one-shot plans never wait for a compile: their sweeps run interpreted
+        // until the kernel of that structure is ready
+        std::shared_ptr<JitKernel> k = kernel_for(src, p.stream_ordered && !jit_sync_all());
+        if (k->done && !k->ok) continue;
         JitSweep& js = jp.sw[i];
         js.k = k;
         js.param = std::move(g.param);
@@ -522,7 +588,7 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
     }
   }
   JitSweep& js = jp.sw[sweep];
-  if (!js.k) return false;
+  if (!js.k || !js.k->done || !js.k->ok) return false;
   const void* fn = (const void*)js.k->k;
   int dev = 0;
   cudaGetDevice(&dev);

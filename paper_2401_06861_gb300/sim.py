@@ -172,6 +172,12 @@ class Plan:
         check(L.lib().nwq_plan_layout(self.h, sw, og, on))
         return list(sw)[:info["sweeps"]], list(og)[:info["ops"]], list(on)[:info["ops"]]
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
     def jit_check(self):
         """Compile (host only) the specialised kernels of this plan's sweeps:
         returns (eligible sweeps, compiled sweeps)."""

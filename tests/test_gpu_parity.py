@@ -74,9 +74,10 @@ def test_sv_specialised_kernels(n, family, dtype):
     psi0 = inputs.random_state(n, 2100 + n)
     out = {}
     for extra in (0, L.PLAN_INTERPRETED):
-        with State(L.SV, n, dtype) as st:
+        # a reusable plan compiles its kernels before its first run
+        with State(L.SV, n, dtype) as st, Plan(L.SV, n, gates, dtype, flags=flags | extra) as plan:
             st.load(psi0)
-            st.apply(gates, flags=flags | extra)
+            st.run(plan)
             out[extra] = st.copy()
     ref = oracle.sv_run(n, gates, psi0)
     err, err_i = maxerr(out[0], ref), maxerr(out[0], out[L.PLAN_INTERPRETED])
