@@ -29,7 +29,7 @@ TROTTER_STEPS = 20
 METRIC = "gate-updates/s"
 UNIT = "gate-updates/s"
 WORKLOAD = f"dm_noisy_tfim_n{N}_{TROTTER_STEPS}steps"
-KERNEL_SRC = os.path.join(ROOT, "paper_2401_06861_gb300", "csrc", "sweep_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2401_06861_gb300", "csrc", f) for f in ("sweep_kernels.cu", "device_util.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_sweep_f64_n13_traffic.json")
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flop x max clock
 
@@ -91,7 +91,7 @@ def traffic_per_launch():
     kernel source changed since the counters were taken."""
     try:
         rec = json.load(open(TRAFFIC_FILE))
-        h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRCS)).hexdigest()[:16]
         return rec["traffic_bytes_per_launch"] if rec.get("kernel_sha") == h else None
     except (OSError, ValueError, KeyError):
         return None
