@@ -375,6 +375,30 @@ def run_vqe(args):
                       "sample": f"{sample} sets, host wall clock", "rel_energy_err_vs_batched_f64": err}), flush=True)
 
 
+def run_vqe_cobyla(args):
+    """VQE outer loop (COBYLA) on the Ising chain: noise-free n = 12 (4 layers,
+    96 parameters; 256 batched starts, then COBYLA with one launch per energy)
+    and noisy n = 6 (density matrix with the device noise model, 3 layers)."""
+    import numpy as np
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, inputs, vqe
+    build.build()
+    cases = [("noise_free", 12, 4, None, L.F64, 256), ("noisy", 6, 3, inputs.noise_params(6, seed=2401), L.F64, 1)]
+    for name, n, layers, noise, dtype, starts in cases:
+        ef = vqe.NoiseFreeEnergy(n, layers, dtype=dtype) if noise is None else vqe.NoisyEnergy(n, layers, noise, dtype)
+        t0 = time.perf_counter()
+        r = vqe.minimize(ef, ef.nparams, starts=starts, batch_energy=getattr(ef, "batch", None),
+                         maxiter=args.vqe_maxiter, tol=1e-6)
+        sec = time.perf_counter() - t0
+        line = {"workload": f"vqe_cobyla_{name}_n{n}_{layers}layers", "metric": "energies/s",
+                "value": ef.nevals / sec, "unit": "energies/s", "wall_s": sec, "evaluations": ef.nevals,
+                "cobyla_nfev": r["nfev"], "energy": r["energy"], "dtype": "f64",
+                "note": "host wall clock of the whole optimisation (scipy COBYLA + one library call per energy)"}
+        print(json.dumps(line), flush=True)
+        ef.close()
+
+
 def run_serve(args):
     """Serving: Poisson stream (200 circuits/s for --serve-seconds), 70% SV
     n ~ U{8..26}, 30% DM n ~ U{6..12}; served FP32 (continuous batching,
@@ -421,7 +445,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "serve"])
+    ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "vqe-cobyla", "serve"])
+    ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
@@ -438,6 +463,8 @@ def main():
         return rc
     if args.workload == "sv":
         return run_sv(args)
+    if args.workload == "vqe-cobyla":
+        return run_vqe_cobyla(args)
     if args.workload == "vqe":
         return run_vqe(args)
     if args.workload == "serve":
