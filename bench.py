@@ -399,6 +399,44 @@ def run_vqe_cobyla(args):
         ef.close()
 
 
+def serve_oracle_check(reqs, res, budget_s=20.0, every=100):
+    """cpu_baseline leg of the serving line: the CPU oracle on a sample of the
+    served requests (every 100th completed request with SV n <= 16 or DM n <= 9,
+    until about 20 s of CPU work), timed, and the largest error of the served
+    FP32 results against it."""
+    import numpy as np
+
+    import oracle
+    oracle.lib()
+    byid = {q["id"]: q for q in reqs}
+    cand = [i for i in sorted(res) if res[i]["error"] is None and
+            ((byid[i]["kind"] == "sv" and byid[i]["n"] <= 16) or (byid[i]["kind"] == "dm" and byid[i]["n"] <= 9))]
+    zerr = eerr = 0.0
+    done = 0
+    t0 = time.perf_counter()
+    for i in cand[::every]:
+        q, n = byid[i], byid[i]["n"]
+        if q["kind"] == "sv":
+            psi = oracle.sv_run(n, q["gates"])
+            z, ev = oracle.sv_expect(psi, n, q["z_terms"]), oracle.sv_expect(psi, n, q["h_terms"])
+        else:
+            rho = oracle.dm_run(n, q["gates"], q["noise"])
+            z, ev = oracle.dm_expect(rho, n, q["z_terms"]), oracle.dm_expect(rho, n, q["h_terms"])
+        e = oracle.energy(ev, q["h_terms"])
+        norm1 = sum(abs(t[2]) for t in q["h_terms"])
+        zerr = max(zerr, float(np.max(np.abs(np.asarray(res[i]["z"]) - np.asarray(z)))))
+        eerr = max(eerr, abs(res[i]["energy"] - e) / max(abs(e), norm1))
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    sec = time.perf_counter() - t0
+    check = {"requests": done, "max_z_err": zerr, "max_rel_energy_err": eerr,
+             "tolerance": {"z": 1e-5, "rel_energy": 1e-6}}
+    base = {"value": done / sec if sec > 0 else 0.0, "unit": "circuits/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{done} served requests (every {every}th completed with SV n<=16 or DM n<=9), {sec:.1f} s"}
+    return check, base
+
+
 def run_serve(args):
     """Serving: Poisson stream (200 circuits/s for --serve-seconds), 70% SV
     n ~ U{8..26}, 30% DM n ~ U{6..12}; served FP32 (continuous batching,
@@ -422,6 +460,8 @@ def run_serve(args):
             errs[r["error"][:120]] = errs.get(r["error"][:120], 0) + 1
     s["errors"] = errs
     s["plan_cache"] = {"hits": ex.hits, "misses": ex.misses}
+    if not args.no_cpu_baseline:
+        s["oracle_check"], s["cpu_baseline"] = serve_oracle_check(reqs, res)
     s["slots"] = args.serve_slots
     s.update(workload=f"serve_poisson200_{args.serve_seconds:g}s", path="served_f32", metric="circuits/s",
              value=s["circuits_per_s"], unit="circuits/s", offered=len(reqs) / args.serve_seconds,
