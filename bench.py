@@ -29,8 +29,18 @@ TROTTER_STEPS = 20
 METRIC = "gate-updates/s"
 UNIT = "gate-updates/s"
 WORKLOAD = f"dm_noisy_tfim_n{N}_{TROTTER_STEPS}steps"
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2401_06861_gb300", "csrc", f) for f in ("sweep_kernels.cu", "device_util.cuh")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_sweep_f64_n13_traffic.json")
+# The DM sweeps run the run-time specialised kernel (generated by jit.cpp from
+# the plan of planner.cpp) unless NWQ_JIT=0 selects the interpreted one.
+JIT = os.environ.get("NWQ_JIT", "1") != "0"
+_CSRC = os.path.join(ROOT, "paper_2401_06861_gb300", "csrc")
+if JIT:
+    KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("jit.cpp", "planner.cpp")]
+    TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_jit_sweep_f64_n13_traffic.json")
+    KERNEL_NAME = "nwq_jit_sweep (run-time specialised FP64 Pauli-basis DM sweep)"
+else:
+    KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("sweep_kernels.cu", "device_util.cuh")]
+    TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_sweep_f64_n13_traffic.json")
+    KERNEL_NAME = "sweep_kernel<double,real> (FP64 Pauli-basis DM sweep, interpreted)"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flop x max clock
 
 
@@ -226,7 +236,7 @@ def run_ours(args, ws, rank, local):
     achieved = flops_per_launch / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(),
-                "kernel": "sweep_kernel<double,real> (FP64 Pauli-basis DM sweep)",
+                "kernel": KERNEL_NAME,
                 "launches_per_step": nlaunch, "ms_per_launch": launch_s * 1e3,
                 "algorithmic_bytes_per_launch": info["bytes"] / nlaunch,
                 "hbm_gbs": info["bytes"] / nlaunch / launch_s / 1e9}

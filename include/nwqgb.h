@@ -213,6 +213,19 @@ int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op
  * nwq_last_error(). */
 int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* built);
 
+/* Queue background compilation of the plan's specialised sweep kernels that
+ * are not compiled yet (one compiler thread per process) and return at once;
+ * *pending (may be NULL): sweeps whose kernel is queued or still compiling.  Sweeps whose
+ * kernel is not ready run the interpreted kernel; a serving loop can call
+ * this ahead of time for circuit structures it expects.  Host only. */
+int nwq_plan_jit_prefetch(const nwq_plan* plan, int* pending);
+
+/* Stop the background kernel compiler: queued compiles are dropped, the one
+ * in progress finishes, its thread is joined; later one-shot plans run the
+ * interpreted kernel for structures not compiled yet.  Call before the
+ * process exits (the Python binding does so from atexit); idempotent. */
+int nwq_jit_shutdown(void);
+
 int nwq_plan_destroy(nwq_plan* plan);
 
 /* ---------------------------------------------------------------- measurement */

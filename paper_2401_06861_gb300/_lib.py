@@ -7,6 +7,7 @@ there is no CPU fallback.  Device memory and streams may come from PyTorch
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 
@@ -89,6 +90,8 @@ def lib():
         "nwq_plan_layout": (i32, [vp, P(i32), P(i32), P(i32)]),
         "nwq_plan_destroy": (i32, [vp]),
         "nwq_plan_jit_check": (i32, [vp, P(i32), P(i32)]),
+        "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
+        "nwq_jit_shutdown": (i32, []),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_probs": (i32, [vp, dbl, P(dbl)]),
@@ -105,6 +108,9 @@ def lib():
         f.restype = res
         f.argtypes = args
     _lib = L
+    # stop the library's background kernel compiler while the interpreter is
+    # still alive, before any C-level exit handler tears its dependencies down
+    atexit.register(L.nwq_jit_shutdown)
     return L
 
 

@@ -128,7 +128,7 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
     const SweepDesc& sd = p.sweeps[i];
     if (sd.nops == 0) continue;
     cudaError_t e = cudaSuccess;
-    if (!(p.is_complex && sd.nph > 0 && jit_launch_sweep(p, i, pt, data, sm_count, s, &e)))
+    if (!((!p.is_complex || sd.nph > 0) && jit_launch_sweep(p, i, pt, data, sm_count, s, &e)))
       e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents, p.phases.empty() ? nullptr : &pt,
                        sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
@@ -361,6 +361,18 @@ extern "C" int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* buil
   std::string log;
   jit_build_check(plan->p, eligible, built, &log);
   if (*built < *eligible) return fail(NWQ_EUNSUPPORTED, log.empty() ? "specialised kernel compilation failed" : log);
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_jit_prefetch(const nwq_plan* plan, int* pending) {
+  if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
+  const int q = jit_prefetch(plan->p);
+  if (pending) *pending = q;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_jit_shutdown(void) {
+  jit_shutdown();
   return NWQ_OK;
 }
 

@@ -18,6 +18,7 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <array>
 #include <atomic>
 #include <condition_variable>
 #include <cstdlib>
@@ -165,20 +166,23 @@ struct AsyncCompiler {
   bool stop = false;
   std::thread th;
   AsyncCompiler() : th([this] { run(); }) {}
-  ~AsyncCompiler() {
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      stop = true;
-    }
-    cv.notify_all();
-    th.join();
-  }
+  ~AsyncCompiler() { shutdown(); }
   void push(const std::string& src, std::shared_ptr<JitKernel> jk) {
     {
       std::lock_guard<std::mutex> lk(mu);
+      if (stop) return;  // after shutdown: the kernel stays interpreted
       q.emplace_back(src, std::move(jk));
     }
     cv.notify_one();
+  }
+  void shutdown() {  // drop queued jobs, finish the one in progress, join
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+      q.clear();
+    }
+    cv.notify_all();
+    if (th.joinable()) th.join();
   }
   void run() {
     for (;;) {
@@ -195,9 +199,19 @@ struct AsyncCompiler {
   }
 };
 AsyncCompiler& async_compiler() {
-  static AsyncCompiler ac;
-  return ac;
+  // NVRTC is loaded and has compiled once on this thread (its lazily built
+  // state and helper libraries exist) before the compiler thread does, so at
+  // exit the compiler is stopped and joined before NVRTC's own teardown runs:
+  // exit handlers run in reverse order of registration.
+  static AsyncCompiler* ac = [] {
+    std::vector<char> bin;
+    compile_cubin("extern \"C\" __global__ void nwq_jit_warm() {}\n", bin, nullptr);
+    static AsyncCompiler a;
+    return &a;
+  }();
+  return *ac;
 }
+std::atomic<bool> g_async_started{false};
 
 // Cached kernel for src.  Synchronous: compiled before returning.
 // Asynchronous: queued for the background compiler on first request; until
@@ -214,6 +228,7 @@ std::shared_ptr<JitKernel> kernel_for(const std::string& src, bool async) {
   if (!async) {
     build_kernel(src, *jk);
   } else if (!jk->queued.exchange(true)) {
+    g_async_started = true;
     async_compiler().push(src, jk);
   }
   return jk;
@@ -256,7 +271,108 @@ struct Gen {
   std::ostringstream o;
   bool ok = true;
 
-  Gen(const Plan& p_, const SweepDesc& sd_) : p(p_), sd(sd_), c128(p_.dtype == NWQ_F64), cs(c128 ? 16 : 8) {}
+  // complex plans: complex64 / complex128 elements; real (density-matrix)
+  // plans: FP64 elements.  8-byte elements share the complex64 tile layout.
+  bool real;
+  Gen(const Plan& p_, const SweepDesc& sd_)
+      : p(p_), sd(sd_), c128(p_.is_complex && p_.dtype == NWQ_F64), cs(c128 ? 16 : 8), real(!p_.is_complex) {}
+
+  uint32_t pack_real(double v) {  // one FP64 coefficient
+    uint32_t at = (uint32_t)(param.size() / cs);
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    param.insert(param.end(), b, b + 8);
+    return at;
+  }
+
+  // Real operator (DevOp rows + entries) on the register bits u[0..3]: every
+  // output row is its unit entry (+-input or 0) followed by one FMA per
+  // remaining entry, in the row kernel's order; identity rows cost nothing.
+  void op_real(const DevOp& d, const uint8_t* u) {
+    auto regbit = [&](int pos) {
+      for (int q = 0; q < 4; q++)
+        if (u[q] == pos) return q;
+      return -1;
+    };
+    auto reg = [&](uint32_t off) {  // register index of a tile-local offset over the operator bits
+      uint32_t x = 0;
+      for (int q = 0; q < 4; q++)
+        if ((off >> u[q]) & 1u) x |= 1u << q;
+      return x;
+    };
+    if (d.k < 1 || d.k > 4) {
+      ok = false;
+      return;
+    }
+    uint32_t rmask = 0;
+    for (int t = 0; t < d.k; t++) {
+      const int q = regbit(d.lb[t]);
+      if (q < 0) {
+        ok = false;
+        return;
+      }
+      rmask |= 1u << q;
+    }
+    const int D = 1 << d.k;
+    const size_t esz = p.ent_bytes;
+    for (int ob = 0; ob < 16; ob++) {
+      if (ob & rmask) continue;
+      o << "    {";
+      for (int s = 0; s < 16; s++)
+        if ((s & ~(int)rmask) == 0) o << " const R t" << (ob | s) << " = " << r(ob | s) << ";";
+      o << "\n";
+      for (int i = 0; i < D; i++) {
+        const RowMeta& rm = d.row[i];
+        if (rm.kind == ROW_ID) continue;
+        std::string ex = rm.base == 0 ? std::string("R(0)")
+                                      : (rm.base == 1 ? "t" : "-t") + std::to_string(ob | reg(rm.boff));
+        if (rm.kind == ROW_GEN) {
+          for (int e = 0; e < rm.cnt[0]; e++) {
+            const size_t at = ((size_t)d.ent + rm.beg + e) * esz;
+            if (at + esz > p.ents.size()) {
+              ok = false;
+              return;
+            }
+            double c;
+            uint32_t off;
+            std::memcpy(&c, &p.ents[at], 8);
+            std::memcpy(&off, &p.ents[at + 8], 4);
+            ex = "fma(" + K(pack_real(c)) + ", t" + std::to_string(ob | reg(off)) + ", " + ex + ")";
+          }
+        }
+        o << "      " << r(ob | reg(rm.out)) << " = " << ex << ";\n";
+      }
+      o << "    }\n";
+    }
+  }
+
+  // Register phases of a real sweep: consecutive operators while their bits
+  // fit 4 register bits (padded with the lowest unused tile bits).
+  bool real_phases(std::vector<std::pair<std::array<uint8_t, 4>, std::vector<int>>>& out) {
+    uint32_t U = 0;
+    std::vector<int> cur;
+    auto flush = [&]() {
+      if (cur.empty()) return;
+      for (int b = 0; b < sd.T && __builtin_popcount(U) < 4; b++) U |= 1u << b;
+      std::array<uint8_t, 4> u{};
+      int q = 0;
+      for (int b = 0; b < sd.T; b++)
+        if ((U >> b) & 1u) u[q++] = (uint8_t)b;
+      out.emplace_back(u, cur);
+      cur.clear();
+      U = 0;
+    };
+    for (int o2 = 0; o2 < sd.nops; o2++) {
+      const DevOp& d = p.ops[sd.op0 + o2];
+      if (d.k < 1 || d.k > 4) return false;
+      uint32_t bits = 0;
+      for (int t = 0; t < d.k; t++) bits |= 1u << d.lb[t];
+      if (__builtin_popcount(U | bits) > 4) flush();
+      U |= bits;
+      cur.push_back(o2);
+    }
+    flush();
+    return true;
+  }
 
   // Pack cnt coefficients starting at absolute index a; returns the packed index.
   uint32_t pack(uint32_t a, uint32_t cnt) {
@@ -383,15 +499,24 @@ struct Gen {
   }
 
   bool run(std::string& src) {
-    const int T = sd.T, m = sd.m, h = sd.h, RB = sd.prb, NR = 1 << RB;
+    const int T = sd.T, m = sd.m, h = sd.h, RB = real ? 4 : sd.prb, NR = 1 << RB;
     const int lvpe = c128 ? 0 : 1;
     if (RB < 1 || RB > 4 || T < RB || T > 13 || m < lvpe || m + h != T || p.B - T > 24) return false;
+    if (real && (p.dtype != NWQ_F64 || p.ent_bytes != 16)) return false;
     const size_t PE = padded_elems(T);
     const uint32_t NG = 1u << (T - RB);
+    std::vector<std::pair<std::array<uint8_t, 4>, std::vector<int>>> rph;
+    if (real && !real_phases(rph)) return false;
+    const uint32_t nphase = real ? (uint32_t)rph.size() : sd.nph;
     std::ostringstream body;
     o.swap(body);
-    for (uint32_t ph = 0; ph < sd.nph && ok; ph++) {
-      const PhaseDesc& P = p.phases[sd.ph0 + ph];
+    for (uint32_t ph = 0; ph < nphase && ok; ph++) {
+      PhaseDesc P{};
+      if (real) {
+        for (int q = 0; q < 4; q++) P.u[q] = rph[ph].first[q];
+      } else {
+        P = p.phases[sd.ph0 + ph];
+      }
       o << "    // phase " << ph << "\n";
       o << "    for (unsigned g = threadIdx.x; g < " << NG << "u; g += " << kJitThreads << "u) {\n";
       o << "    unsigned gb = g;\n";
@@ -408,7 +533,11 @@ struct Gen {
         roff[i] = swz(c128, l);
         o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
       }
-      for (uint32_t q = 0; q < P.nops && ok; q++) op(NR, p.pops[P.op0 + q]);
+      if (real) {
+        for (int oi : rph[ph].second) op_real(p.ops[sd.op0 + oi], P.u);
+      } else {
+        for (uint32_t q = 0; q < P.nops && ok; q++) op(NR, p.pops[P.op0 + q]);
+      }
       for (int i = 0; i < NR; i++) o << "    gt[" << roff[i] << "] = " << r(i) << ";\n";
       o << "    }\n    __syncthreads();\n";
     }
@@ -420,8 +549,8 @@ struct Gen {
     const size_t btab_byte = hoff_byte + ((size_t)8 << h);  // 4 x 64 tile-base pieces
     smem = btab_byte + 4 * 64 * 8;
     if (smem > (size_t)kMaxDynSmem) return false;
-    const char* RT = c128 ? "double" : "float";
-    const char* CT = c128 ? "double2" : "float2";
+    const char* RT = (c128 || real) ? "double" : "float";
+    const char* CT = real ? "double" : (c128 ? "double2" : "float2");
     o << "typedef " << RT << " R;\ntypedef " << CT << " C;\n"
       << "struct Coef { C c[" << npk << "]; };\n"
       << "__device__ __forceinline__ unsigned long long dep(unsigned long long v, unsigned long long mask) {\n"
@@ -524,7 +653,8 @@ struct JitPlan {
 
 bool jit_source(const Plan& p, size_t sweep, std::string& src, size_t* param_bytes, size_t* smem_bytes) {
   src.clear();
-  if (!p.is_complex || sweep >= p.sweeps.size() || p.sweeps[sweep].nph == 0) return false;
+  if (sweep >= p.sweeps.size() || p.sweeps[sweep].nops == 0 || (p.is_complex && p.sweeps[sweep].nph == 0))
+    return false;
   Gen g(p, p.sweeps[sweep]);
   if (!g.run(src)) {
     src.clear();
@@ -553,6 +683,21 @@ int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log) 
   return 0;
 }
 
+void jit_shutdown() {
+  if (g_async_started) async_compiler().shutdown();
+}
+
+int jit_prefetch(const Plan& p) {
+  if (!jit_enabled()) return 0;
+  int queued = 0;
+  for (size_t i = 0; i < p.sweeps.size(); i++) {
+    std::string src;
+    if (!jit_source(p, i, src, nullptr, nullptr)) continue;
+    if (!kernel_for(src, true)->done) queued++;
+  }
+  return queued;
+}
+
 void jit_stats(int* compiled, int* failed) {
   if (compiled) *compiled = g_compiled.load();
   if (failed) *failed = g_failed.load();
@@ -560,8 +705,7 @@ void jit_stats(int* compiled, int* failed) {
 
 bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state, int sm_count, cudaStream_t s,
                       cudaError_t* err) {
-  if (!jit_enabled() || p.interpreted || !p.is_complex || p.B < jit_min_bits() || sweep >= p.sweeps.size())
-    return false;
+  if (!jit_enabled() || p.interpreted || p.B < jit_min_bits() || sweep >= p.sweeps.size()) return false;
   if (!p.jit) p.jit = std::make_shared<JitPlan>();
   JitPlan& jp = *std::static_pointer_cast<JitPlan>(p.jit);
   {
@@ -570,7 +714,7 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
       jp.sw.resize(p.sweeps.size());
       for (size_t i = 0; i < p.sweeps.size(); i++) {
         const SweepDesc& sd = p.sweeps[i];
-        if (sd.nops == 0 || sd.nph == 0) continue;
+        if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
         Gen g(p, sd);
         std::string src;
         if (!g.run(src)) continue;
@@ -615,7 +759,8 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
   unsigned long long grid = (unsigned long long)sm_count * js.per_sm;
   if (grid > ntiles) grid = ntiles;
   unsigned long long hmask = sd.hmask, fmask = sd.fmask;
-  const void* pcs = (const char*)pt.pc + (size_t)sd.pc0 * (p.dtype == NWQ_F64 ? 16 : 8);
+  const void* pcs = p.is_complex && pt.pc ? (const char*)pt.pc + (size_t)sd.pc0 * (p.dtype == NWQ_F64 ? 16 : 8)
+                                          : nullptr;
   void* args[] = {&state, &ntiles, &hmask, &fmask, (void*)&pcs, js.param.data()};
   e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kJitThreads), args, js.smem, s);
   g_launches += 1;

@@ -27,6 +27,14 @@ bool jit_source(const Plan& p, size_t sweep, std::string& src, size_t* param_byt
 // compiler error.
 int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log);
 
+// Queue background compilation of every eligible sweep kernel of p that is
+// not compiled yet; returns how many are pending.  Never waits.
+int jit_prefetch(const Plan& p);
+
+// Stop the background compiler (queued kernels stay uncompiled; the one in
+// progress finishes) and join its thread.  Idempotent.
+void jit_shutdown();
+
 // Kernels compiled so far in this process, and compile failures.
 void jit_stats(int* compiled, int* failed);
 

@@ -185,6 +185,13 @@ class Plan:
         check(L.lib().nwq_plan_jit_check(self.h, ctypes.byref(e), ctypes.byref(b)))
         return e.value, b.value
 
+    def jit_prefetch(self):
+        """Queue background compilation of this plan's specialised kernels;
+        returns the number pending (does not wait)."""
+        q = ctypes.c_int()
+        check(L.lib().nwq_plan_jit_prefetch(self.h, ctypes.byref(q)))
+        return q.value
+
     def close(self):
         if self.h:
             L.lib().nwq_plan_destroy(self.h)

@@ -142,3 +142,20 @@ def test_specialised_sweep_kernels_compile(dtype):
         total += eligible
         p.close()
     assert total >= 10
+
+
+def test_exit_while_kernels_compile_in_the_background():
+    # a process that queues specialised-kernel compiles and exits at once must
+    # exit cleanly (the compiler thread is joined before NVRTC is torn down)
+    import subprocess
+    import sys
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_2401_06861_gb300 import _lib as L, inputs, sim\n"
+        "g, noise = inputs.dm_noisy_tfim(13, 20)\n"
+        "p = sim.Plan(L.DM, 13, g, L.F64, noise)\n"
+        "print('pending', p.jit_prefetch())\n" % ROOT)
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+        assert "pending" in r.stdout
