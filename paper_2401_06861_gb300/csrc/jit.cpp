@@ -84,6 +84,14 @@ bool jit_sync_all() {  // compile one-shot plans' kernels before running them to
   }();
   return on;
 }
+int jit_min_blocks() {  // __launch_bounds__ minimum resident blocks per SM
+  static const int b = [] {
+    const char* e = std::getenv("NWQ_JIT_MINB");
+    const int v = e ? std::atoi(e) : 2;
+    return v < 1 ? 1 : (v > 4 ? 4 : v);
+  }();
+  return b;
+}
 int jit_min_bits() {
   static const int b = [] {
     const char* e = std::getenv("NWQ_JIT_MIN_BITS");
@@ -546,8 +554,10 @@ struct Gen {
     o.swap(body);
     const size_t npk = param.empty() ? 1 : param.size() / cs;
     const size_t hoff_byte = ((2 * PE + ntab) * cs + 15) & ~(size_t)15;
-    const size_t btab_byte = hoff_byte + ((size_t)8 << h);  // 4 x 64 tile-base pieces
-    smem = btab_byte + 4 * 64 * 8;
+    const size_t btab_byte = hoff_byte + ((size_t)8 << h);  // 4 x 2^pb tile-base pieces
+    const int F = p.B - T, pb = F <= 4 ? 1 : (F + 3) / 4;     // tile-index bits per piece
+    const uint32_t nb = 1u << pb;
+    smem = btab_byte + 4 * (size_t)nb * 8;
     if (smem > (size_t)kMaxDynSmem) return false;
     const char* RT = (c128 || real) ? "double" : "float";
     const char* CT = real ? "double" : (c128 ? "double2" : "float2");
@@ -560,7 +570,8 @@ struct Gen {
       << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
       << "  unsigned a = (unsigned)__cvta_generic_to_shared(s);\n"
       << "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(a), \"l\"(g) : \"memory\");\n}\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", 2) nwq_jit_sweep(C* __restrict__ state, "
+      << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << jit_min_blocks()
+      << ") nwq_jit_sweep(C* __restrict__ state, "
       << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const C* __restrict__ pcs, "
       << "const Coef K) {\n"
       << "  extern __shared__ __align__(16) unsigned char sm[];\n"
@@ -568,9 +579,10 @@ struct Gen {
       << "  unsigned long long* hoff = (unsigned long long*)(sm + " << hoff_byte << ");\n"
       << "  unsigned long long* btab = (unsigned long long*)(sm + " << btab_byte << ");\n"
       << "  for (unsigned j = threadIdx.x; j < " << (1u << h) << "u; j += " << kJitThreads << "u) hoff[j] = dep(j, hmask);\n"
-      << "  // tile base = OR of 4 pieces, each depositing 6 bits of the tile index on fmask\n"
-      << "  for (unsigned j = threadIdx.x; j < 256u; j += " << kJitThreads
-      << "u) btab[j] = dep((unsigned long long)(j & 63u) << (6u * (j >> 6)), fmask);\n";
+      << "  // tile base = OR of 4 pieces, each depositing " << pb << " bits of the tile index on fmask\n"
+      << "  for (unsigned j = threadIdx.x; j < " << 4 * nb << "u; j += " << kJitThreads
+      << "u) btab[j] = dep((unsigned long long)(j & " << nb - 1 << "u) << (" << pb << "u * (j >> " << pb
+      << ")), fmask);\n";
     for (const Tab& t : tabs)
       o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << kJitThreads << "u) dtab[" << t.dst
         << " + j] = pcs[" << t.src << " + j];\n";
@@ -598,9 +610,14 @@ struct Gen {
                                             std::to_string(nvec) + "u) "
                                       : "";
     };
-    auto base_of = [](const char* t) {
-      return std::string("(btab[") + t + " & 63u] | btab[64u + ((" + t + " >> 6) & 63u)] | btab[128u + ((" + t +
-             " >> 12) & 63u)] | btab[192u + ((" + t + " >> 18) & 63u)])";
+    auto base_of = [&](const char* t) {
+      std::string s = "(";
+      for (int q = 0; q < 4; q++) {
+        if (q) s += " | ";
+        s += "btab[" + std::to_string(q * nb) + "u + ((" + t + " >> " + std::to_string(q * pb) + ") & " +
+             std::to_string(nb - 1) + "u)]";
+      }
+      return s + ")";
     };
     o << "  if (blockIdx.x < ntiles) {\n"
       << "    const unsigned long long tb = blockIdx.x;\n"
