@@ -202,6 +202,35 @@ int nwq_plan_info(const nwq_plan* plan, int* sweeps, int* ops, double* bytes, do
  * nwq_plan_info.  Host-only; needs no device. */
 int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op_ngates);
 
+/* Plan shape, chosen by nwq_plan_autotune or by hand (0 = the default):
+ *   tile_bits      shared-memory tile of a sweep = 2^tile_bits state elements
+ *                  (default 11 for 16-byte, 12 for 8-byte, 13 for 4-byte elements);
+ *   fusion_bits    widest operator the planner merges gates into, in state-index
+ *                  bits, 2..4 (default 4; a density-matrix qubit spans 2 bits);
+ *   register_bits  complex sweeps: state elements per thread group = 2^register_bits,
+ *                  3 or 4 (default 3 for complex128, 4 for complex64). */
+typedef struct {
+  int tile_bits, fusion_bits, register_bits;
+} nwq_plan_tuning;
+
+/* nwq_plan_create with an explicit plan shape (tuning may be NULL). */
+int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate* gates, size_t ng,
+                          const nwq_noise_model* noise, uint32_t flags, const nwq_plan_tuning* tuning,
+                          void* cuda_stream, nwq_plan** out);
+
+/* Autotuner: build the circuit's plan for each candidate shape (tile bits of
+ * the default -1, +0, +1; fusion bits 3 and 4 (density matrix: 2 and 4);
+ * register bits 3 and 4 for state vectors), run each on `scratch` (a state of
+ * the circuit's kind, size and dtype; its contents are overwritten) once to
+ * warm up and `reps` times under CUDA events on the state's stream, and return
+ * the fastest shape in *best with its mean time in *best_ms.  When `tried` is
+ * not NULL the first max_tried candidates and their times (ms; negative when
+ * the shape could not be built or run) are written there, their count in
+ * *ntried.  Synchronises the stream. */
+int nwq_plan_autotune(nwq_state* scratch, const nwq_gate* gates, size_t ng, const nwq_noise_model* noise,
+                      uint32_t flags, int reps, nwq_plan_tuning* best, double* best_ms,
+                      nwq_plan_tuning* tried, double* tried_ms, int max_tried, int* ntried);
+
 /* Test hook: generate and compile (host only; nothing is loaded on a device)
  * the run-time specialised kernel of every eligible sweep of a complex plan.
  * Complex sweeps of states with at least NWQ_JIT_MIN_BITS qubits (default 18)

@@ -47,6 +47,13 @@ class NoiseModel(ctypes.Structure):
                 ("readout_e", ctypes.c_double)]
 
 
+class PlanTuning(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int32), ("fusion_bits", ctypes.c_int32), ("register_bits", ctypes.c_int32)]
+
+    def as_dict(self):
+        return dict(tile_bits=self.tile_bits, fusion_bits=self.fusion_bits, register_bits=self.register_bits)
+
+
 class BatchTemplate(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("gates", ctypes.POINTER(Gate)), ("ngates", ctypes.c_size_t),
                 ("terms", ctypes.POINTER(PauliTerm)), ("nterms", ctypes.c_size_t),
@@ -89,6 +96,9 @@ def lib():
         "nwq_plan_info": (i32, [vp, P(i32), P(i32), P(dbl), P(dbl), P(sz)]),
         "nwq_plan_layout": (i32, [vp, P(i32), P(i32), P(i32)]),
         "nwq_plan_destroy": (i32, [vp]),
+        "nwq_plan_create_tuned": (i32, [i32, i32, i32, P(Gate), sz, P(NoiseModel), u32, P(PlanTuning), vp, pp]),
+        "nwq_plan_autotune": (i32, [vp, P(Gate), sz, P(NoiseModel), u32, i32, P(PlanTuning), P(dbl),
+                                    P(PlanTuning), P(dbl), i32, P(i32)]),
         "nwq_plan_jit_check": (i32, [vp, P(i32), P(i32)]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),

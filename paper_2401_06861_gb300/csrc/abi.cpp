@@ -301,6 +301,12 @@ extern "C" int nwq_state_load(nwq_state* st, const void* src, size_t bytes, int 
 // ------------------------------------------------------------------ plans
 extern "C" int nwq_plan_create(int kind, int n, int dtype, const nwq_gate* gates, size_t ng,
                                const nwq_noise_model* nm, uint32_t flags, void* stream, nwq_plan** out) {
+  return nwq_plan_create_tuned(kind, n, dtype, gates, ng, nm, flags, nullptr, stream, out);
+}
+
+extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate* gates, size_t ng,
+                                     const nwq_noise_model* nm, uint32_t flags, const nwq_plan_tuning* tuning,
+                                     void* stream, nwq_plan** out) {
   (void)stream;
   if (!out) return fail(NWQ_EINVAL, "out is NULL");
   *out = nullptr;
@@ -317,6 +323,24 @@ extern "C" int nwq_plan_create(int kind, int n, int dtype, const nwq_gate* gates
   if (!ok) return fail(NWQ_EINVAL, err);
   PlanOptions o;
   plan_options(kind, dtype, flags, o);
+  if (tuning) {
+    const size_t esz = pl->p.elem_bytes;
+    if (tuning->tile_bits) {
+      if (tuning->tile_bits < 4 || tuning->tile_bits > kMaxTileBits ||
+          (2 * esz << tuning->tile_bits) > (size_t)kMaxDynSmem)
+        return fail(NWQ_EINVAL, "tile_bits out of range for this element size");
+      o.tile_bits = tuning->tile_bits;
+    }
+    if (tuning->fusion_bits) {
+      if (tuning->fusion_bits < 2 || tuning->fusion_bits > 4) return fail(NWQ_EINVAL, "fusion_bits must be 2..4");
+      o.max_merge_bits = tuning->fusion_bits;
+    }
+    if (tuning->register_bits) {
+      if (tuning->register_bits != 3 && tuning->register_bits != 4)
+        return fail(NWQ_EINVAL, "register_bits must be 3 or 4");
+      o.register_bits = tuning->register_bits;
+    }
+  }
   if (kind == NWQ_DM && !(flags & NWQ_PLAN_NO_RESCALE)) o.rescale_qubits = n;
   build_plan(ops, o, pl->p);
   pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
@@ -329,6 +353,60 @@ extern "C" int nwq_plan_run(nwq_state* st, const nwq_plan* plan) {
   const Plan& p = plan->p;
   if (p.kind != st->kind || p.n != st->n || p.dtype != st->dtype) return fail(NWQ_EINVAL, "plan does not match state");
   return plan_launch(const_cast<Plan&>(p), st->buf, st->stream, st->sm_count);
+}
+
+extern "C" int nwq_plan_autotune(nwq_state* st, const nwq_gate* gates, size_t ng, const nwq_noise_model* nm,
+                                 uint32_t flags, int reps, nwq_plan_tuning* best, double* best_ms,
+                                 nwq_plan_tuning* tried, double* tried_ms, int max_tried, int* ntried) {
+  if (!st || !best || (ng && !gates)) return fail(NWQ_EINVAL, "NULL argument");
+  if (reps < 1) return fail(NWQ_EINVAL, "reps must be >= 1");
+  const size_t esz = (st->kind == NWQ_SV ? 2 : 1) * (st->dtype == NWQ_F64 ? 8 : 4);
+  const int t0 = esz == 16 ? 11 : esz == 8 ? 12 : 13;
+  std::vector<nwq_plan_tuning> cand;
+  for (int dt = -1; dt <= 1; dt++) {
+    const int tb = t0 + dt;
+    if ((2 * esz << tb) > (size_t)kMaxDynSmem) continue;
+    for (int fb : (st->kind == NWQ_DM ? std::vector<int>{2, 4} : std::vector<int>{3, 4}))
+      for (int rb : (st->kind == NWQ_SV ? std::vector<int>{3, 4} : std::vector<int>{0})) cand.push_back({tb, fb, rb});
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a), "event");
+  CK(cudaEventCreate(&b), "event");
+  double bms = -1.0;
+  int nt = 0;
+  for (const nwq_plan_tuning& c : cand) {
+    double ms = -1.0;
+    nwq_plan* pl = nullptr;
+    if (nwq_plan_create_tuned(st->kind, st->n, st->dtype, gates, ng, nm, flags, &c, st->stream, &pl) == NWQ_OK) {
+      bool ok = nwq_plan_run(st, pl) == NWQ_OK && cudaStreamSynchronize(st->stream) == cudaSuccess;  // warm-up
+      if (ok) {
+        cudaEventRecord(a, st->stream);
+        for (int r = 0; r < reps && ok; r++) ok = nwq_plan_run(st, pl) == NWQ_OK;
+        cudaEventRecord(b, st->stream);
+        float f = 0.f;
+        ok = ok && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&f, a, b) == cudaSuccess;
+        if (ok) ms = f / reps;
+      }
+      nwq_plan_destroy(pl);
+    }
+    cudaGetLastError();  // a failed candidate leaves no sticky launch error behind
+    if (tried && nt < max_tried) {
+      tried[nt] = c;
+      if (tried_ms) tried_ms[nt] = ms;
+    }
+    nt++;
+    if (ms >= 0 && (bms < 0 || ms < bms)) {
+      bms = ms;
+      *best = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (ntried) *ntried = nt < max_tried ? nt : max_tried;
+  if (best_ms) *best_ms = bms;
+  nwq_state_reset(st);
+  if (bms < 0) return fail(NWQ_ECUDA, "no candidate plan shape could be run");
+  return NWQ_OK;
 }
 
 extern "C" int nwq_plan_info(const nwq_plan* plan, int* sweeps, int* ops, double* bytes, double* fma_per_elem,

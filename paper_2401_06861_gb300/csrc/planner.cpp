@@ -450,13 +450,14 @@ static void embed(const BitOp& op, const int* ubits, int ku, std::vector<cd>& E)
 // B after A, as one operator on the union of their bits (or false if the
 // union is wider than max_bits).
 static bool compose(const BitOp& A, const BitOp& B, int max_bits, BitOp& C) {
+  if (A.k > max_bits || B.k > max_bits) return false;  // an operand is already wider than the limit
   int ubits[8], ku = 0;
   for (int t = 0; t < A.k; t++) ubits[ku++] = A.bits[t];
   for (int t = 0; t < B.k; t++) {
     bool have = false;
     for (int u = 0; u < ku; u++) have |= ubits[u] == B.bits[t];
     if (!have) {
-      if (ku == max_bits) return false;
+      if (ku >= max_bits) return false;
       ubits[ku++] = B.bits[t];
     }
   }
@@ -542,7 +543,8 @@ static bool is_signed_perm(const BitOp& op) {
 // bits into one KRON operator, so one dispatch does the work of several.
 // Register bits per thread group (elements per thread = 2^RB); NWQ_PHASE_RB
 // overrides it for tuning experiments.
-static int phase_register_bits(bool f64) {
+static int phase_register_bits(bool f64, int requested) {
+  if (requested == 3 || requested == 4) return requested;
   if (const char* e = std::getenv("NWQ_PHASE_RB")) {
     int v = std::atoi(e);
     if (v == 3 || v == 4) return v;
@@ -556,9 +558,9 @@ struct PDiag {  // diagonal over up to 8 tile-local bits
   std::vector<cd> f;  // 2^k factors, operator index bit t = lbits[t]
 };
 
-static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& order, Plan& plan) {
+static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& order, Plan& plan, int rb) {
   const bool f64 = plan.dtype == NWQ_F64;
-  const int RB = phase_register_bits(f64);
+  const int RB = phase_register_bits(f64, rb);
   plan.phases.clear();
   plan.pops.clear();
   plan.pcoef.clear();
@@ -972,7 +974,7 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
     sd.ent0 = (uint32_t)sweep_ent0;
     sd.nent = (uint32_t)(nent - sweep_ent0);
   }
-  if (cplx) build_phases(ops, order, plan);
+  if (cplx) build_phases(ops, order, plan, opt.register_bits);
   double state_bytes = (double)plan.elem_bytes * (double)(1ull << B);
   plan.bytes = 2.0 * state_bytes * (double)plan.sweeps.size();
 }

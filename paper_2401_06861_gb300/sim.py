@@ -140,10 +140,34 @@ class State:
         check(L.lib().nwq_state_load(self.h, _ptr(a), a.nbytes, 0))
 
 
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, L.PlanTuning):
+        return t
+    return L.PlanTuning(int(t.get("tile_bits", 0)), int(t.get("fusion_bits", 0)), int(t.get("register_bits", 0)))
+
+
+def autotune(state, gates, noise=None, flags=0, reps=3):
+    """Time the circuit's plan for each candidate shape on ``state`` (a State
+    of the circuit's kind, size and dtype; overwritten) and return
+    dict(best=tuning dict, best_ms, tried=[(tuning dict, ms)])."""
+    arr, keep = encode_gates(gates)
+    nm, keep2 = encode_noise(noise, state.n)
+    best, bms = L.PlanTuning(), ctypes.c_double()
+    tried, tms, nt = (L.PlanTuning * 32)(), (ctypes.c_double * 32)(), ctypes.c_int()
+    check(L.lib().nwq_plan_autotune(state.h, arr, len(gates), ctypes.byref(nm) if nm is not None else None, flags,
+                                    reps, ctypes.byref(best), ctypes.byref(bms), tried, tms, 32, ctypes.byref(nt)))
+    return dict(best=best.as_dict(), best_ms=bms.value,
+                tried=[(tried[i].as_dict(), tms[i]) for i in range(nt.value)])
+
+
 class Plan:
-    def __init__(self, kind, n, gates, dtype=F64, noise=None, flags=0, encoded=None):
+    def __init__(self, kind, n, gates, dtype=F64, noise=None, flags=0, encoded=None, tuning=None):
         """Lower ``gates`` (tuples), or an ``encoded`` nwq_gate array from
-        ``_lib.encode_gates_np``, once for repeated runs."""
+        ``_lib.encode_gates_np``, once for repeated runs; ``tuning`` (a dict
+        of tile_bits / fusion_bits / register_bits, e.g. ``autotune(...)["best"]``)
+        fixes the plan shape."""
         if encoded is None:
             arr, keep = encode_gates(gates)
             ng = len(gates)
@@ -152,8 +176,10 @@ class Plan:
             ng = len(encoded) if gates is None else len(gates)
         nm, keep2 = encode_noise(noise, n)
         self.h = ctypes.c_void_p()
-        check(L.lib().nwq_plan_create(kind, n, dtype, arr, ng, ctypes.byref(nm) if nm is not None else None,
-                                      flags, None, ctypes.byref(self.h)))
+        tu = _tuning(tuning)
+        check(L.lib().nwq_plan_create_tuned(kind, n, dtype, arr, ng, ctypes.byref(nm) if nm is not None else None,
+                                            flags, ctypes.byref(tu) if tu is not None else None, None,
+                                            ctypes.byref(self.h)))
         self.ngates = ng
 
     def info(self):

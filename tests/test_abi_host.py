@@ -159,3 +159,26 @@ def test_exit_while_kernels_compile_in_the_background():
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
         assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
         assert "pending" in r.stdout
+
+
+def test_plan_tuning_shapes_and_validation():
+    g, _ = inputs.large_sv_tfim(20, 4)
+    base = sim.Plan(L.SV, 20, g, L.F32).info()
+    t11 = sim.Plan(L.SV, 20, g, L.F32, tuning=dict(tile_bits=11)).info()
+    t13 = sim.Plan(L.SV, 20, g, L.F32, tuning=dict(tile_bits=13)).info()
+    assert t11["sweeps"] >= base["sweeps"] >= t13["sweeps"]  # larger tiles, fewer passes
+    f2 = sim.Plan(L.SV, 20, g, L.F32, tuning=dict(fusion_bits=2)).info()
+    assert f2["ops"] >= base["ops"]  # narrower fusion, more operators
+    gd, noise = inputs.dm_noisy_tfim(8, 5)
+    d2 = sim.Plan(L.DM, 8, gd, L.F64, noise, tuning=dict(fusion_bits=2)).info()
+    d4 = sim.Plan(L.DM, 8, gd, L.F64, noise).info()
+    assert d2["ops"] > d4["ops"]  # two-qubit noisy blocks are only merged at 4 bits
+    for bad, msg in [(dict(tile_bits=3), b"tile_bits"), (dict(tile_bits=16), b"tile_bits"),
+                     (dict(fusion_bits=5), b"fusion_bits"), (dict(register_bits=2), b"register_bits")]:
+        with pytest.raises(L.NwqError):
+            sim.Plan(L.SV, 20, g, L.F32, tuning=bad)
+        assert msg in L.lib().nwq_last_error()
+    for rb in (3, 4):
+        p = sim.Plan(L.SV, 20, g, L.F64, tuning=dict(register_bits=rb, tile_bits=12))
+        e, b = p.jit_check()
+        assert e == b and e > 0

@@ -86,6 +86,32 @@ def test_sv_specialised_kernels(n, family, dtype):
     assert err_i <= (1e-14 if dtype == L.F64 else 1e-6)
 
 
+@pytest.mark.parametrize("kind,dtype", [(L.SV, L.F32), (L.SV, L.F64), (L.DM, L.F64), (L.DM, L.F32)])
+def test_autotuned_plan_shapes_all_agree_with_the_oracle(kind, dtype):
+    from paper_2401_06861_gb300.sim import autotune
+    if kind == L.SV:
+        n = 19
+        gates = inputs.random_circuit(n, 150, 4000, names=[g for g in inputs.GATE_NAMES if not g.startswith("MAT")])
+        noise, ref = None, oracle.sv_run(n, gates)
+    else:
+        n = 9
+        gates, noise = inputs.random_circuit(n, 80, 4100), inputs.noise_params(n, seed=4101)
+        ref = oracle.dm_run(n, gates, noise)
+    with State(kind, n, dtype) as st:
+        res = autotune(st, gates, noise, reps=2)
+        timed = [(t, ms) for t, ms in res["tried"] if ms >= 0]
+        assert len(timed) == len(res["tried"]) >= 4
+        assert res["best_ms"] == min(ms for _, ms in timed)
+        for t, _ in res["tried"]:  # every candidate shape computes the same state
+            with Plan(kind, n, gates, dtype, noise, tuning=t) as plan:
+                st.reset()
+                st.run(plan)
+                got = st.copy()
+            err = maxerr(got, ref)
+            assert err <= (TOL[dtype] if kind == L.SV else (1e-12 if dtype == L.F64 else 1e-5)), (t, err)
+    print(f"autotune kind={kind} dtype={dtype}: best {res['best']} {res['best_ms']:.3f} ms of {len(timed)}")
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_sv_every_gate_on_every_qubit_position(dtype):
     # each gate kind on low, tile-boundary and top qubits of a 15-qubit state
