@@ -346,6 +346,7 @@ def run_vqe(args):
         b = Batch([dict(n=n, gates=gates, param_index=pidx, terms=terms, coeffs=coeffs)], layers * 2 * n, dtype,
                   stream=stream.cuda_stream)
         out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+        shape = b.autotune(p.data_ptr(), nsets, out.data_ptr(), reps=3, stream=stream.cuda_stream)
         for _ in range(3):
             b.run(p.data_ptr(), nsets, out.data_ptr(), stream=stream.cuda_stream, graph=True)
         torch.cuda.synchronize()
@@ -356,7 +357,7 @@ def run_vqe(args):
         t1.record(stream)
         torch.cuda.synchronize()
         sec = t0.elapsed_time(t1) / args.steps / 1e3
-        res[dtype] = (out.cpu().numpy(), sec)
+        res[dtype] = (out.cpu().numpy(), sec, shape)
         b.close()
     # per-circuit plain FP64 path on a sample of the sets
     sample = 64
@@ -372,12 +373,13 @@ def run_vqe(args):
     ref = res[L.F64][0]
     norm1 = np.array([(n - 1) + n * h for h in hs])
     for dtype, name in ((L.F32, "f32"), (L.F64, "f64")):
-        out, sec = res[dtype]
+        out, sec, shape = res[dtype]
         err = float(np.max(np.abs(out - ref) / np.maximum(np.abs(ref), norm1)))
         line = {"workload": "vqe_hea_n12_4layers_4096sets", "path": f"batched_{name}", "metric": "energies/s",
                 "value": 3 * nsets / sec, "unit": "energies/s", "ms_per_batch": sec * 1e3,
                 "rel_energy_err_vs_batched_f64": err,
-                "vs_plain_f64_per_circuit": (3 * nsets / sec) / (3 / psec)}
+                "vs_plain_f64_per_circuit": (3 * nsets / sec) / (3 / psec),
+                "kernel_shape": {"threads": shape["threads"], "gate_fusion": shape["fusion"], "autotuned": True}}
         print(json.dumps(line), flush=True)
     err = float(np.max(np.abs(plain - ref[:sample]) / np.maximum(np.abs(ref[:sample]), norm1)))
     print(json.dumps({"workload": "vqe_hea_n12_4layers_4096sets", "path": "plain_f64_per_circuit",

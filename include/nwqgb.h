@@ -342,6 +342,20 @@ int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* job_templat
 /* Free the batch: its tables are released stream-ordered on the creation
  * stream, so runs queued on that stream complete first; runs on other
  * streams must have completed (synchronise them) before this call. */
+/* Kernel shape of a batch: threads per CTA (128, 256 or 512; default 256)
+ * and gate-fusion width (0, default: gates applied one by one; 1: every run
+ * of one-qubit gates on a qubit, up to the next two-qubit gate on it, is one
+ * 2x2 matrix per job, multiplied out in FP64 when the job starts). */
+int nwq_batch_set_shape(nwq_batch* b, int threads, int fusion);
+
+/* Autotuner of the batched kernel: run (params, job_template, njobs, out)
+ * once to warm up and `reps` times timed (CUDA events on `stream`) for every
+ * shape, keep the fastest on b and return it (best_* may be NULL).  `out` is
+ * overwritten; synchronises the stream. */
+int nwq_batch_autotune(nwq_batch* b, const double* params, const int32_t* job_template, int njobs, double* out,
+                       int out_stride, int reps, void* stream, int* best_threads, int* best_fusion,
+                       double* best_ms);
+
 int nwq_batch_destroy(nwq_batch* b);
 
 /* One template, nsets parameter sets: create + run + destroy.  params and

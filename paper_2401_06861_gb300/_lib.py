@@ -109,6 +109,8 @@ def lib():
         "nwq_batch_create": (i32, [i32, P(BatchTemplate), i32, i32, vp, pp]),
         "nwq_batch_run": (i32, [vp, vp, vp, i32, vp, i32, vp, vp, u32]),
         "nwq_batch_destroy": (i32, [vp]),
+        "nwq_batch_set_shape": (i32, [vp, i32, i32]),
+        "nwq_batch_autotune": (i32, [vp, vp, vp, i32, vp, i32, i32, vp, P(i32), P(i32), P(dbl)]),
         "nwq_last_error": (ctypes.c_char_p, []),
         "nwq_device_sync": (i32, [vp]),
         "nwq_launch_count": (ctypes.c_uint64, []),

@@ -5,11 +5,14 @@
 
 namespace nwq {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 256;  // default threads per CTA
 constexpr int kBatchMaxSmem = 220 * 1024;  // per-CTA dynamic shared memory cap of the batched kernel
 
 // Gate types of the batched kernel.
-enum : uint8_t { BT_FIXED1 = 0, BT_CX, BT_CZ, BT_SWAP, BT_RX, BT_RY, BT_RZ, BT_P, BT_U3, BT_RZZ };
+enum : uint8_t { BT_FIXED1 = 0, BT_CX, BT_CZ, BT_SWAP, BT_RX, BT_RY, BT_RZ, BT_P, BT_U3, BT_RZZ, BT_FUSED };
+// BT_FUSED: a run of one-qubit gates on qubit q0, applied as the one 2x2 matrix
+// product computed per job in FP64; its `cls` members are the gates
+// gates[pidx .. pidx + cls) in application order.
 
 struct BGate {
   uint8_t type;   // BT_*
@@ -42,7 +45,9 @@ struct BatchArgs {
   int* counter;                 // work-queue head (reset before each launch)
   int njobs, nparams, out_stride, ntemplates;
   int max_n, max_gates, max_terms;
+  int threads;  // threads per CTA: 128, 256 or 512
 };
+constexpr int kBatchThreadChoices[3] = {128, 256, 512};
 
 size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms);
 cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s);

@@ -24,6 +24,8 @@ struct nwq_batch {
   void* dev = nullptr;  // tables + work-queue counter
   const BGate* gates = nullptr;
   const BTemplate* templates = nullptr;
+  const BTemplate* templates_fused = nullptr;  // the same templates with one-qubit runs fused
+  int threads = kBatchThreads, fusion = 0;      // kernel shape (nwq_batch_set_shape)
   const BTerm* terms = nullptr;
   const double* coeffs = nullptr;
   int* counter = nullptr;
@@ -87,6 +89,49 @@ static bool lower_batch_gate(const nwq_gate& g, int n, int nparams, BGate& b, st
   return true;
 }
 
+static bool is_one_qubit(const BGate& g) {
+  return g.type == BT_FIXED1 || g.type == BT_RX || g.type == BT_RY || g.type == BT_RZ || g.type == BT_P ||
+         g.type == BT_U3;
+}
+
+// Fusion of one template's gates g[0, ng): each run of one-qubit gates on a
+// qubit, up to the next two-qubit gate touching that qubit, becomes one
+// BT_FUSED entry at the position of its first gate (the gates it moves past
+// act on other qubits, so the order of operations on every qubit is kept).
+// members[i] lists the gates of fused entry i (empty for other entries).
+static void fuse_runs(const BGate* g, size_t ng, std::vector<BGate>& out, std::vector<std::vector<BGate>>& members) {
+  const size_t first = out.size();
+  int open[64];
+  for (int& o : open) o = -1;
+  for (size_t k = 0; k < ng; k++) {
+    const BGate& x = g[k];
+    if (is_one_qubit(x)) {
+      const int q = x.q0;
+      if (open[q] >= 0 && members[open[q]].size() < 255) {
+        members[open[q]].push_back(x);
+      } else {
+        BGate f;
+        std::memset(&f, 0, sizeof(f));
+        f.type = BT_FUSED;
+        f.q0 = f.q1 = x.q0;
+        f.pidx = -1;
+        out.push_back(f);
+        members.push_back({x});
+        open[q] = (int)(out.size() - 1);
+      }
+    } else {
+      open[x.q0] = open[x.q1] = -1;
+      out.push_back(x);
+      members.push_back({});
+    }
+  }
+  for (size_t i = first; i < out.size(); i++)
+    if (members[i].size() == 1) {  // a run of one gate stays that gate
+      out[i] = members[i][0];
+      members[i].clear();
+    }
+}
+
 extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntemplates, int nparams,
                                 void* stream, nwq_batch** out) {
   if (!out || !t || ntemplates < 1 || nparams < 0) return set_error(NWQ_EINVAL, "bad batch arguments");
@@ -131,6 +176,25 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
     b->max_terms = std::max(b->max_terms, (int)tk.nterms);
     b->max_ne = std::max(b->max_ne, tk.ne);
   }
+  // fused variant: gates = [plain | fused | members of the fused runs]
+  std::vector<BGate> fused;
+  std::vector<std::vector<BGate>> members;
+  std::vector<BTemplate> tmplf = tmpl;
+  for (int k = 0; k < ntemplates; k++) {
+    tmplf[k].g0 = (int)(gates.size() + fused.size());
+    fuse_runs(gates.data() + tmpl[k].g0, (size_t)tmpl[k].ng, fused, members);
+    tmplf[k].ng = (int)(gates.size() + fused.size()) - tmplf[k].g0;
+  }
+  const size_t nplain = gates.size();
+  std::vector<BGate> runs;
+  for (size_t i = 0; i < fused.size(); i++) {
+    if (members[i].empty()) continue;
+    fused[i].pidx = (int32_t)(nplain + fused.size() + runs.size());
+    fused[i].cls = (uint8_t)members[i].size();
+    runs.insert(runs.end(), members[i].begin(), members[i].end());
+  }
+  gates.insert(gates.end(), fused.begin(), fused.end());
+  gates.insert(gates.end(), runs.begin(), runs.end());
   b->dtype = dtype;
   b->nparams = nparams;
   b->ntemplates = ntemplates;
@@ -140,7 +204,8 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
   if (e != cudaSuccess) return set_error(NWQ_ECUDA, cudaGetErrorString(e));
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  size_t og = 0, ot = al(og + gates.size() * sizeof(BGate)), oterm = al(ot + tmpl.size() * sizeof(BTemplate));
+  size_t og = 0, ot = al(og + gates.size() * sizeof(BGate)), otf = al(ot + tmpl.size() * sizeof(BTemplate));
+  size_t oterm = al(otf + tmplf.size() * sizeof(BTemplate));
   size_t oc = al(oterm + terms.size() * sizeof(BTerm)), ocnt = al(oc + coeffs.size() * sizeof(double));
   size_t total = ocnt + 256;
   b->stream = (cudaStream_t)stream;
@@ -150,6 +215,7 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
   const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
   if (!gates.empty()) e = cudaMemcpyAsync(d + og, gates.data(), gates.size() * sizeof(BGate), h2d, b->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d + ot, tmpl.data(), tmpl.size() * sizeof(BTemplate), h2d, b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d + otf, tmplf.data(), tmplf.size() * sizeof(BTemplate), h2d, b->stream);
   if (e == cudaSuccess && !terms.empty())
     e = cudaMemcpyAsync(d + oterm, terms.data(), terms.size() * sizeof(BTerm), h2d, b->stream);
   if (e == cudaSuccess && !coeffs.empty())
@@ -161,6 +227,7 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
   }
   b->gates = (const BGate*)(d + og);
   b->templates = (const BTemplate*)(d + ot);
+  b->templates_fused = (const BTemplate*)(d + otf);
   b->terms = (const BTerm*)(d + oterm);
   b->coeffs = (const double*)(d + oc);
   b->counter = (int*)(d + ocnt);
@@ -178,7 +245,8 @@ extern "C" int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* 
   BatchArgs a;
   std::memset(&a, 0, sizeof(a));  // compared bytewise against the captured arguments
   a.gates = b->gates;
-  a.templates = b->templates;
+  a.templates = b->fusion ? b->templates_fused : b->templates;
+  a.threads = b->threads;
   a.terms = b->terms;
   a.coeffs = b->coeffs;
   a.params = params;
@@ -226,6 +294,56 @@ extern "C" int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* 
   cudaError_t e = cudaGraphLaunch(b->exec, s);
   if (e == cudaSuccess) g_launches += 1;
   return e == cudaSuccess ? NWQ_OK : set_error(NWQ_ECUDA, cudaGetErrorString(e));
+}
+
+extern "C" int nwq_batch_set_shape(nwq_batch* b, int threads, int fusion) {
+  if (!b) return set_error(NWQ_EINVAL, "batch is NULL");
+  if (threads != 128 && threads != 256 && threads != 512) return set_error(NWQ_EINVAL, "threads must be 128, 256 or 512");
+  if (fusion != 0 && fusion != 1) return set_error(NWQ_EINVAL, "fusion must be 0 or 1");
+  b->threads = threads;
+  b->fusion = fusion;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_batch_autotune(nwq_batch* b, const double* params, const int32_t* job_template, int njobs,
+                                  double* out, int out_stride, int reps, void* stream, int* best_threads,
+                                  int* best_fusion, double* best_ms) {
+  if (!b || reps < 1 || njobs < 1) return set_error(NWQ_EINVAL, "bad autotune arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_error(NWQ_ECUDA, "event creation failed");
+  double bms = -1.0;
+  int bt = b->threads, bf = b->fusion;
+  int rc = NWQ_OK;
+  for (int f = 0; f <= 1 && !rc; f++)
+    for (int th : kBatchThreadChoices) {
+      b->threads = th;
+      b->fusion = f;
+      rc = nwq_batch_run(b, params, job_template, njobs, out, out_stride, nullptr, stream, 0);  // warm-up
+      if (rc) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && !rc; r++)
+        rc = nwq_batch_run(b, params, job_template, njobs, out, out_stride, nullptr, stream, 0);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = set_error(NWQ_ECUDA, "timing failed");
+      if (rc) break;
+      if (bms < 0 || ms / reps < bms) {
+        bms = ms / reps;
+        bt = th;
+        bf = f;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->threads = bt;
+  b->fusion = bf;
+  if (best_threads) *best_threads = bt;
+  if (best_fusion) *best_fusion = bf;
+  if (best_ms) *best_ms = bms;
+  return rc;
 }
 
 extern "C" int nwq_batch_destroy(nwq_batch* b) {

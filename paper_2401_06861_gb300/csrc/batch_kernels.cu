@@ -36,57 +36,95 @@ struct GateMat {
 
 enum : int { BG_DENSE = 0, BG_REAL = 1, BG_DIAG = 2, BG_CX = 3, BG_CZ = 4, BG_SWAP = 5, BG_DIAG2 = 6 };
 
-// Matrix of gate g for parameter vector p (FP64 trigonometry, stored in R).
-template <class R>
-__device__ void make_gate(const BGate& g, const double* __restrict__ p, GateMat<R>& out) {
-  using C = typename C2<R>::T;
-  if (g.type == BT_CX) { out.cls = BG_CX; return; }
-  if (g.type == BT_CZ) { out.cls = BG_CZ; return; }
-  if (g.type == BT_SWAP) { out.cls = BG_SWAP; return; }
+// One-qubit gate g as a full 2x2 matrix in FP64 (FP64 trigonometry) with its
+// structure class.
+__device__ void gate1_d(const BGate& g, const double* __restrict__ p, double2 (&m)[4], int& cls) {
   if (g.type == BT_FIXED1) {
-    for (int k = 0; k < 4; k++) out.m[k] = C{(R)g.m[2 * k], (R)g.m[2 * k + 1]};
-    out.cls = g.cls;
+    for (int k = 0; k < 4; k++) m[k] = make_double2(g.m[2 * k], g.m[2 * k + 1]);
+    cls = g.cls;
     return;
   }
-  double th = g.pidx >= 0 ? p[g.pidx] : g.th[0];
+  const double th = g.pidx >= 0 ? p[g.pidx] : g.th[0];
   double s, c;
   sincos(0.5 * th, &s, &c);
+  m[1] = m[2] = make_double2(0.0, 0.0);
   switch (g.type) {
     case BT_RX:
-      out.m[0] = C{(R)c, 0}; out.m[1] = C{0, (R)-s}; out.m[2] = C{0, (R)-s}; out.m[3] = C{(R)c, 0};
-      out.cls = BG_DENSE;
+      m[0] = make_double2(c, 0); m[1] = make_double2(0, -s); m[2] = make_double2(0, -s); m[3] = make_double2(c, 0);
+      cls = BG_DENSE;
       break;
     case BT_RY:
-      out.m[0] = C{(R)c, 0}; out.m[1] = C{(R)-s, 0}; out.m[2] = C{(R)s, 0}; out.m[3] = C{(R)c, 0};
-      out.cls = BG_REAL;
+      m[0] = make_double2(c, 0); m[1] = make_double2(-s, 0); m[2] = make_double2(s, 0); m[3] = make_double2(c, 0);
+      cls = BG_REAL;
       break;
     case BT_RZ:  // diag(e^{-i th/2}, e^{i th/2})
-      out.m[0] = C{(R)c, (R)-s}; out.m[3] = C{(R)c, (R)s};
-      out.cls = BG_DIAG;
+      m[0] = make_double2(c, -s); m[3] = make_double2(c, s);
+      cls = BG_DIAG;
       break;
     case BT_P: {  // diag(1, e^{i th})
       double s2, c2;
       sincos(th, &s2, &c2);
-      out.m[0] = C{1, 0}; out.m[3] = C{(R)c2, (R)s2};
-      out.cls = BG_DIAG;
+      m[0] = make_double2(1, 0); m[3] = make_double2(c2, s2);
+      cls = BG_DIAG;
       break;
     }
-    case BT_U3: {
+    default: {  // BT_U3
       double sp, cp, sl, cl, spl, cpl;
       sincos(g.th[1], &sp, &cp);
       sincos(g.th[2], &sl, &cl);
       sincos(g.th[1] + g.th[2], &spl, &cpl);
-      out.m[0] = C{(R)c, 0};
-      out.m[1] = C{(R)(-cl * s), (R)(-sl * s)};
-      out.m[2] = C{(R)(cp * s), (R)(sp * s)};
-      out.m[3] = C{(R)(cpl * c), (R)(spl * c)};
-      out.cls = BG_DENSE;
-      break;
+      m[0] = make_double2(c, 0);
+      m[1] = make_double2(-cl * s, -sl * s);
+      m[2] = make_double2(cp * s, sp * s);
+      m[3] = make_double2(cpl * c, spl * c);
+      cls = BG_DENSE;
     }
-    default:  // BT_RZZ: phases e^{-i th/2} on even parity, e^{+i th/2} on odd
-      out.m[0] = C{(R)c, (R)-s}; out.m[1] = C{(R)c, (R)s};
-      out.cls = BG_DIAG2;
   }
+}
+
+// Matrix of gate g for parameter vector p (FP64 trigonometry and, for fused
+// runs, FP64 products; stored in R).
+template <class R>
+__device__ void make_gate(const BGate& g, const BGate* __restrict__ all, const double* __restrict__ p,
+                          GateMat<R>& out) {
+  using C = typename C2<R>::T;
+  if (g.type == BT_CX) { out.cls = BG_CX; return; }
+  if (g.type == BT_CZ) { out.cls = BG_CZ; return; }
+  if (g.type == BT_SWAP) { out.cls = BG_SWAP; return; }
+  if (g.type == BT_RZZ) {  // phases e^{-i th/2} on even parity, e^{+i th/2} on odd
+    const double th = g.pidx >= 0 ? p[g.pidx] : g.th[0];
+    double s, c;
+    sincos(0.5 * th, &s, &c);
+    out.m[0] = C{(R)c, (R)-s}; out.m[1] = C{(R)c, (R)s};
+    out.cls = BG_DIAG2;
+    return;
+  }
+  double2 m[4];
+  int cls;
+  if (g.type == BT_FUSED) {  // M = G_last ... G_first
+    gate1_d(all[g.pidx], p, m, cls);
+    bool diag = cls == BG_DIAG, real = cls == BG_REAL;
+    for (int k = 1; k < g.cls; k++) {
+      double2 a[4];
+      int ca;
+      gate1_d(all[g.pidx + k], p, a, ca);
+      diag &= ca == BG_DIAG;
+      real &= ca == BG_REAL;
+      double2 r[4];
+      for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) {
+          const double2 x = a[2 * i], y = m[j], u = a[2 * i + 1], v = m[2 + j];
+          r[2 * i + j] = make_double2(fma(x.x, y.x, fma(-x.y, y.y, fma(u.x, v.x, -u.y * v.y))),
+                                      fma(x.x, y.y, fma(x.y, y.x, fma(u.x, v.y, u.y * v.x))));
+        }
+      for (int e = 0; e < 4; e++) m[e] = r[e];
+    }
+    cls = diag ? BG_DIAG : (real ? BG_REAL : BG_DENSE);
+  } else {
+    gate1_d(g, p, m, cls);
+  }
+  for (int k = 0; k < 4; k++) out.m[k] = C{(R)m[k].x, (R)m[k].y};
+  out.cls = cls;
 }
 
 template <class C, class R>
@@ -168,8 +206,8 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-template <class R>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
+template <class R, int TH>
+__global__ void __launch_bounds__(TH) batch_kernel(BatchArgs a) {
   using C = typename C2<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   C* psi = reinterpret_cast<C*>(smem);
@@ -195,7 +233,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(BatchArgs a) {
     // |0..0>
     for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = C{b == 0 ? (R)1 : (R)0, 0};
     // per-job gate matrices (each thread builds different gates)
-    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) make_gate<R>(a.gates[T.g0 + k], p, mats[k]);
+    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) make_gate<R>(a.gates[T.g0 + k], a.gates, p, mats[k]);
     __syncthreads();
     for (int k = 0; k < T.ng; k++) {
       apply_gate<R>(psi, n, a.gates[T.g0 + k], mats[k]);
@@ -243,39 +281,46 @@ size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
   return (c << max_n) + gm * (size_t)max_gates + 8 * (32 + (size_t)max_terms + 1);
 }
 
-cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s) {
-  size_t smem = batch_smem_bytes(f64, a.max_n, a.max_gates, a.max_terms);
-  cudaError_t e = cudaSuccess;
-  int per_sm = 0;
+template <class R, int TH>
+static cudaError_t launch_batch_t(const BatchArgs& a, size_t smem, int sm_count, cudaStream_t s) {
   // The attribute is a per-function maximum shared by every caller (several
   // host threads may launch concurrently): set it once to the largest size any
   // batch may use, never per call.
-  static int attr_dev[2] = {-1, -1};
+  static int attr_dev = -1;
   static std::mutex attr_mu;
   int dev = 0;
   cudaGetDevice(&dev);
+  cudaError_t e = cudaSuccess;
   {
     std::lock_guard<std::mutex> lk(attr_mu);
-    if (attr_dev[f64] != dev) {
-      e = f64 ? cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem)
-              : cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
-      if (e == cudaSuccess) attr_dev[f64] = dev;
+    if (attr_dev != dev) {
+      e = cudaFuncSetAttribute(batch_kernel<R, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
+      if (e == cudaSuccess) attr_dev = dev;
     }
   }
   if (e != cudaSuccess) return e;
-  if (smem > (size_t)kBatchMaxSmem) return cudaErrorInvalidValue;
-  if (f64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<double>, kBatchThreads, smem);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<float>, kBatchThreads, smem);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<R, TH>, TH, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = sm_count * per_sm;
   if (grid > a.njobs) grid = a.njobs;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  if (f64) batch_kernel<double><<<grid, kBatchThreads, smem, s>>>(a);
-  else batch_kernel<float><<<grid, kBatchThreads, smem, s>>>(a);
+  batch_kernel<R, TH><<<grid, TH, smem, s>>>(a);
   g_launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s) {
+  const size_t smem = batch_smem_bytes(f64, a.max_n, a.max_gates, a.max_terms);
+  if (smem > (size_t)kBatchMaxSmem) return cudaErrorInvalidValue;
+  switch (a.threads) {
+    case 128: return f64 ? launch_batch_t<double, 128>(a, smem, sm_count, s) : launch_batch_t<float, 128>(a, smem, sm_count, s);
+    case 256: return f64 ? launch_batch_t<double, 256>(a, smem, sm_count, s) : launch_batch_t<float, 256>(a, smem, sm_count, s);
+    case 512: return f64 ? launch_batch_t<double, 512>(a, smem, sm_count, s) : launch_batch_t<float, 512>(a, smem, sm_count, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace nwq

@@ -270,6 +270,21 @@ class Batch:
                                     out_stride or self.max_ne, ctypes.c_void_p(norms_ptr) if norms_ptr else None,
                                     ctypes.c_void_p(stream) if stream else None, L.BATCH_GRAPH if graph else 0))
 
+    def set_shape(self, threads=256, fusion=0):
+        """Threads per CTA (128 / 256 / 512) and gate-fusion width (0 / 1)."""
+        check(L.lib().nwq_batch_set_shape(self.h, threads, fusion))
+
+    def autotune(self, params_ptr, njobs, out_ptr, out_stride=None, job_template_ptr=None, reps=3, stream=None):
+        """Time every kernel shape on these jobs, keep the fastest; returns
+        dict(threads, fusion, ms)."""
+        th, fu, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        check(L.lib().nwq_batch_autotune(self.h, ctypes.c_void_p(params_ptr),
+                                         ctypes.c_void_p(job_template_ptr) if job_template_ptr else None, njobs,
+                                         ctypes.c_void_p(out_ptr), out_stride or self.max_ne, reps,
+                                         ctypes.c_void_p(stream) if stream else None, ctypes.byref(th),
+                                         ctypes.byref(fu), ctypes.byref(ms)))
+        return dict(threads=th.value, fusion=fu.value, ms=ms.value)
+
     def close(self):
         if self.h:
             L.lib().nwq_batch_destroy(self.h)

@@ -139,3 +139,68 @@ def test_batch_energy_convenience_and_invalid_template_index():
     o = out2.cpu().numpy()
     assert np.all(np.isnan(o[[1, 3]])) and np.allclose(o[[0, 2, 4]], ref[[0, 2, 4]], atol=1e-12)
     b.close()
+
+
+def _mixed_template(n, seed):
+    """Parametrised layers of one-qubit gates of every class (fixed, RX, RY,
+    RZ, P, U3) between two-qubit gates (CX, CZ, SWAP, RZZ)."""
+    rng = np.random.default_rng(seed)
+    g, pidx, k = [], [], 0
+    one = ["H", "S", "T", "SX", "RX", "RY", "RZ", "P", "U3"]
+    two = ["CX", "CZ", "SWAP", "RZZ"]
+    for _ in range(6):
+        for q in range(n):
+            for _ in range(int(rng.integers(1, 4))):
+                name = one[int(rng.integers(len(one)))]
+                prm = tuple(rng.uniform(-np.pi, np.pi, inputs.N_PARAMS.get(name, 0)))
+                g.append(inputs.gate(name, (q,), prm))
+                if name in ("RX", "RY", "RZ", "P"):
+                    pidx.append(k)
+                    k += 1
+                else:
+                    pidx.append(-1)
+        for q in range(0, n - 1, 2 if rng.random() < 0.5 else 1):
+            name = two[int(rng.integers(len(two)))]
+            g.append(inputs.gate(name, (q, q + 1), (0.37,) if name == "RZZ" else ()))
+            pidx.append(-1)
+    return g, pidx, k
+
+
+@pytest.mark.parametrize("dtype", [L.F64, L.F32])
+def test_batch_shapes_agree_and_autotune(dtype):
+    import torch
+    tmpl, nps = [], []
+    for i, n in enumerate((3, 7, 10)):
+        g, pidx, k = _mixed_template(n, 50 + i)
+        tmpl.append((n, g, pidx))
+        nps.append(k)
+    nparams, njobs = max(nps), 60
+    params = np.random.default_rng(51).uniform(-np.pi, np.pi, (njobs, nparams))
+    jt = np.arange(njobs, dtype=np.int32) % 3
+    b = Batch([tfim_energy_template(n, g, pidx) for n, g, pidx in tmpl], nparams, dtype)
+    s = torch.cuda.current_stream().cuda_stream
+    p = torch.from_numpy(params).cuda()
+    j = torch.from_numpy(jt).cuda()
+    ref = np.array([oracle_energies(tmpl[t][0], tmpl[t][1], tmpl[t][2], params[i]) for i, t in enumerate(jt)])
+    nref = np.array([tmpl[t][0] for t in jt])[:, None]
+    tol = 1e-12 if dtype == L.F64 else 1e-6
+    for fusion in (0, 1):
+        for threads in (128, 256, 512):
+            b.set_shape(threads, fusion)
+            out = torch.zeros(njobs, 3, dtype=torch.float64, device="cuda")
+            b.run(p.data_ptr(), njobs, out.data_ptr(), job_template_ptr=j.data_ptr(), stream=s, graph=True)
+            torch.cuda.synchronize()
+            err = rel(out.cpu().numpy(), ref, nref, np.array(H_LIST)[None, :]).max()
+            assert err <= tol, (threads, fusion, err)
+    out = torch.zeros(njobs, 3, dtype=torch.float64, device="cuda")
+    best = b.autotune(p.data_ptr(), njobs, out.data_ptr(), job_template_ptr=j.data_ptr(), reps=2, stream=s)
+    assert best["threads"] in (128, 256, 512) and best["fusion"] in (0, 1) and best["ms"] > 0
+    out.zero_()
+    b.run(p.data_ptr(), njobs, out.data_ptr(), job_template_ptr=j.data_ptr(), stream=s)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy(), ref, nref, np.array(H_LIST)[None, :]).max() <= tol
+    print(f"batch autotune dtype={dtype}: {best}")
+    for bad in ((64, 0), (256, 2)):
+        with pytest.raises(L.NwqError):
+            b.set_shape(*bad)
+    b.close()
