@@ -66,6 +66,9 @@ def lib():
         _lib.oracle_dm_expect.argtypes = [D, c_int, c_int, U64, U64, D]
         _lib.oracle_sv_probs.argtypes = [D, c_int, c_dbl, D]
         _lib.oracle_dm_probs.argtypes = [D, c_int, c_dbl, D]
+        _lib.oracle_traj_run.argtypes = [D, c_int, c_int, Ip, Ip, D, D, c_int, D, D, c_dbl, c_dbl, c_dbl, c_dbl,
+                                         ctypes.c_uint, D, c_int]
+        _lib.oracle_traj_draws.argtypes = [c_int, Ip, c_int, c_dbl, c_dbl, c_dbl, c_dbl, ctypes.c_uint]
     return _lib
 
 
@@ -142,6 +145,38 @@ def dm_run(n, gates, noise=None, rho0=None):
     if rc:
         raise ValueError(f"oracle_dm_run failed ({rc})")
     return rho
+
+
+def _noise_args(n, noise):
+    if noise is None:
+        T1 = T2 = np.ones(max(n, 1))
+        return (0, T1, T2, 0.0, 0.0, 0.0, 0.0, 0)
+    T1 = np.ascontiguousarray(noise["T1_us"], np.float64)
+    T2 = np.ascontiguousarray(noise["T2_us"], np.float64)
+    flags = (1 if noise.get("rz_virtual") else 0) | (2 if noise.get("depol_pauli_form") else 0)
+    return (1, T1, T2, noise["t1q_ns"], noise["t2q_ns"], noise["p1"], noise["p2"], flags)
+
+
+def traj_draws(gates, noise):
+    """Uniform draws one quantum trajectory of ``gates`` under ``noise`` consumes."""
+    ng, kinds, qs, th, mats = _encode(gates)
+    noisy, T1, T2, t1, t2, p1, p2, flags = _noise_args(1, noise)
+    return int(lib().oracle_traj_draws(ng, _p(kinds, ctypes.c_int), noisy, ctypes.c_double(t1), ctypes.c_double(t2),
+                                       ctypes.c_double(p1), ctypes.c_double(p2), flags))
+
+
+def traj_run(n, gates, noise, uniforms):
+    """One quantum trajectory (final normalised state) driven by ``uniforms``."""
+    psi = np.array(zero_state(n), dtype=np.complex128, copy=True)
+    ng, kinds, qs, th, mats = _encode(gates)
+    noisy, T1, T2, t1, t2, p1, p2, flags = _noise_args(n, noise)
+    u = np.ascontiguousarray(uniforms, np.float64)
+    rc = lib().oracle_traj_run(_p(psi.view(np.float64)), n, ng, _p(kinds, ctypes.c_int), _p(qs, ctypes.c_int),
+                               _p(th), _p(mats), noisy, _p(T1), _p(T2), ctypes.c_double(t1), ctypes.c_double(t2),
+                               ctypes.c_double(p1), ctypes.c_double(p2), flags, _p(u), len(u))
+    if rc < 0:
+        raise ValueError(f"oracle_traj_run failed ({rc})")
+    return psi
 
 
 def dm_depolarize(rho, n, qubits, p):

@@ -325,6 +325,114 @@ int oracle_dm_run(double *rho_reim, int n, int ng, const int *kinds, const int *
   return 0;
 }
 
+/* ------------------------------------------------------------------ quantum trajectories
+ * One trajectory of the Monte-Carlo unravelling of the same noise model on a
+ * state vector (its average over trajectories is the density matrix of
+ * oracle_dm_run).  The random draws are inputs: u[] holds uniforms in [0, 1),
+ * consumed in this order, gate by gate, after the gate is applied:
+ *   - depolarising with parameter p on the gate's k qubits (if p > 0), one
+ *     draw: each of the 4^k - 1 non-identity Pauli strings has probability
+ *     p / 4^k; string s = 1 + floor(u 4^k / p) (at most 4^k - 1) is applied
+ *     when u < (4^k - 1) p / 4^k, else none.  s & 3 is the Pauli on q0 and
+ *     s >> 2 the Pauli on q1 (0 I, 1 X, 2 Y, 3 Z).
+ *   - thermal relaxation on each gate qubit q (if t > 0), two draws: amplitude
+ *     damping (gamma) then phase damping (lambda, with sqrt(1-gamma)
+ *     sqrt(1-lambda) = eta).  With P1 = the probability of q = 1 in the
+ *     current state, the jump operator (|0><1| resp. |1><1|) is applied when
+ *     u < gamma P1 (resp. lambda P1), else diag(1, sqrt(1 - gamma)) (resp.
+ *     sqrt(1 - lambda)); the state is then renormalised (its norm after the
+ *     Kraus operator is the probability of the branch taken).
+ * Returns the number of draws consumed, -1 for an unknown gate, -2 when T2 >
+ * 2 T1, -3 when more than nu draws would be needed. */
+static double prob_one(const cx *psi, int n, int q) {
+  size_t N = (size_t)1 << n, m = (size_t)1 << q;
+  double s = 0.0;
+  for (size_t b = 0; b < N; b++)
+    if (b & m) s += creal(psi[b]) * creal(psi[b]) + cimag(psi[b]) * cimag(psi[b]);
+  return s;
+}
+
+static void scale_vec(cx *psi, int n, double f) {
+  size_t N = (size_t)1 << n;
+  for (size_t b = 0; b < N; b++) psi[b] *= f;
+}
+
+int oracle_traj_run(double *psi_reim, int n, int ng, const int *kinds, const int *qs, const double *th,
+                    const double *mats, int noisy, const double *T1_us, const double *T2_us, double t1q_ns,
+                    double t2q_ns, double p1, double p2, unsigned flags, const double *u, int nu) {
+  const cx *P1[4] = {PI_, PX_, PY_, PZ_};
+  cx *psi = (cx *)psi_reim;
+  int used = 0;
+  for (int g = 0; g < ng; g++) {
+    cx U[16];
+    int k = gate_matrix(kinds[g], th + 3 * g, mats + 32 * g, U);
+    if (!k) return -1;
+    const int *q = qs + 2 * g;
+    apply_vec(psi, n, 1, k, q, U);
+    if (!noisy) continue;
+    if ((flags & 1u) && kinds[g] == OG_RZ) continue;
+    int np = 1 << (2 * k);
+    double p = k == 2 ? p2 : p1;
+    if (flags & 2u) p = p * np / (np - 1.0);
+    if (p > 0) {
+      if (used >= nu) return -3;
+      double x = u[used++];
+      if (x < (np - 1) * p / np) {
+        int s = 1 + (int)floor(x * np / p);
+        if (s > np - 1) s = np - 1;
+        for (int w = 0; w < k; w++) {
+          int a = (s >> (2 * w)) & 3;
+          if (a) apply_vec(psi, n, 1, 1, q + w, P1[a]);
+        }
+      }
+    }
+    double t = k == 2 ? t2q_ns : t1q_ns;
+    if (t > 0)
+      for (int w = 0; w < k; w++) {
+        int qq = q[w];
+        double gamma = 1.0 - exp(-t / (T1_us[qq] * 1e3));
+        double eta = exp(-t / (T2_us[qq] * 1e3));
+        double oml = eta * eta / (1.0 - gamma);
+        if (oml > 1.0 + 1e-15) return -2;
+        if (oml > 1.0) oml = 1.0;
+        double rate[2] = {gamma, 1.0 - oml};
+        for (int step = 0; step < 2; step++) {  /* amplitude damping, then phase damping */
+          if (used >= nu) return -3;
+          double x = u[used++];
+          double pr1 = prob_one(psi, n, qq);
+          size_t N = (size_t)1 << n, m = (size_t)1 << qq;
+          if (x < rate[step] * pr1) {
+            for (size_t b = 0; b < N; b++) {
+              if (b & m) continue;
+              psi[b] = step == 0 ? psi[b | m] : 0.0;  /* |0><1| moves the |1> part down; |1><1| keeps it */
+              if (step == 0) psi[b | m] = 0.0;
+            }
+            scale_vec(psi, n, 1.0 / sqrt(pr1));
+          } else {
+            double f = sqrt(1.0 - rate[step]);
+            for (size_t b = 0; b < N; b++)
+              if (b & m) psi[b] *= f;
+            scale_vec(psi, n, 1.0 / sqrt(1.0 - rate[step] * pr1));
+          }
+        }
+      }
+  }
+  return used;
+}
+
+/* Draws one trajectory of oracle_traj_run consumes (independent of them). */
+int oracle_traj_draws(int ng, const int *kinds, int noisy, double t1q_ns, double t2q_ns, double p1, double p2,
+                      unsigned flags) {
+  int c = 0;
+  for (int g = 0; g < ng; g++) {
+    if (!noisy || ((flags & 1u) && kinds[g] == OG_RZ)) continue;
+    int k = is_two_qubit(kinds[g]) ? 2 : 1;
+    if ((k == 2 ? p2 : p1) > 0) c += 1;
+    if ((k == 2 ? t2q_ns : t1q_ns) > 0) c += 2 * k;
+  }
+  return c;
+}
+
 /* ------------------------------------------------------------------ Pauli strings
  * P(x, z) |b> = i^{|x&z|} (-1)^{|b&z|} |b ^ x>. */
 static cx pauli_phase(uint64_t x, uint64_t z, uint64_t b) {
