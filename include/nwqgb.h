@@ -358,6 +358,31 @@ int nwq_batch_autotune(nwq_batch* b, const double* params, const int32_t* job_te
 
 int nwq_batch_destroy(nwq_batch* b);
 
+/* ---------------------------------------------------------------- trajectories */
+
+/* Noisy state vectors by quantum trajectories: the Monte-Carlo unravelling of
+ * the device noise model of nwq_dm_apply_circuit_noisy (paper Sec. III), a
+ * stochastic alternative to the density matrix whose memory grows as 2^n
+ * instead of 4^n; the average over trajectories of <psi|P|psi> converges to
+ * Tr(rho P).  Every trajectory starts from |0..0> and, after each gate:
+ *   - depolarising p (one draw x when p > 0): if x < (4^k - 1) p / 4^k the
+ *     Pauli string s = 1 + floor(x 4^k / p) (<= 4^k - 1) is applied, s & 3
+ *     on the gate's first qubit and s >> 2 on its second (0 I, 1 X, 2 Y, 3 Z);
+ *   - thermal relaxation on each gate qubit q (when the gate time > 0):
+ *     amplitude damping gamma then phase damping lambda (sqrt(1-gamma)
+ *     sqrt(1-lambda) = exp(-t/T2); needs T2 <= 2 T1), one draw x each: with
+ *     P1 = prob(q = 1), the jump |0><1| (resp. |1><1|) when x < rate P1, else
+ *     diag(1, sqrt(1 - rate)); the state is renormalised in FP64.
+ * The random draws are inputs: `uniforms` (device) holds ntraj rows of
+ * nwq_traj_draws(...) values in [0, 1), consumed in the order above.
+ * out (device) [t * ne + e] = sum_k coeffs[e * nt + k] <P_k> / <psi|psi> of
+ * trajectory t.  Gates: the kinds of the batched kernel with fixed angles
+ * (param_idx = -1), no MAT2; n <= 13 (F64) / 14 (F32).  Synchronises the stream. */
+int nwq_traj_draws(const nwq_gate* gates, size_t ng, int n, const nwq_noise_model* noise, size_t* draws);
+int nwq_traj_run(int n, int dtype, const nwq_gate* gates, size_t ng, const nwq_noise_model* noise,
+                 const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne, const double* uniforms,
+                 int ntraj, double* out, void* stream);
+
 /* One template, nsets parameter sets: create + run + destroy.  params and
  * out are device pointers (out: nsets * ne doubles); terms, coeffs host.
  * Synchronises the stream before returning. */

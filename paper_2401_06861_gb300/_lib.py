@@ -110,6 +110,8 @@ def lib():
         "nwq_batch_run": (i32, [vp, vp, vp, i32, vp, i32, vp, vp, u32]),
         "nwq_batch_destroy": (i32, [vp]),
         "nwq_batch_set_shape": (i32, [vp, i32, i32]),
+        "nwq_traj_draws": (i32, [P(Gate), sz, i32, P(NoiseModel), P(sz)]),
+        "nwq_traj_run": (i32, [i32, i32, P(Gate), sz, P(NoiseModel), P(PauliTerm), sz, P(dbl), i32, vp, i32, vp, vp]),
         "nwq_batch_autotune": (i32, [vp, vp, vp, i32, vp, i32, i32, vp, P(i32), P(i32), P(dbl)]),
         "nwq_last_error": (ctypes.c_char_p, []),
         "nwq_device_sync": (i32, [vp]),

@@ -49,7 +49,29 @@ struct BatchArgs {
 };
 constexpr int kBatchThreadChoices[3] = {128, 256, 512};
 
+// Noise after one gate of a quantum-trajectory circuit: the depolarising
+// parameter (one draw when > 0) and, when `relax` is set, amplitude damping
+// then phase damping on each gate qubit (two draws each).
+struct TNoise {
+  double pdep;
+  double gamma[2], lambda[2];
+  int32_t k, relax;
+};
+
+struct TrajArgs {
+  const BGate* gates;
+  const TNoise* noise;
+  const BTerm* terms;
+  const double* coeffs;
+  const double* u;  // draws, `draws` per trajectory
+  double* out;      // ntraj x ne energies
+  int* counter;
+  int n, ng, nt, ne, draws, ntraj, threads;
+};
+
 size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms);
+size_t traj_smem_bytes(bool f64, int n, int ng, int nt);
+cudaError_t launch_traj(bool f64, const TrajArgs& a, int sm_count, cudaStream_t s);
 cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s);
 
 }  // namespace nwq

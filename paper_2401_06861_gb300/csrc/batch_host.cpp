@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -354,6 +355,122 @@ extern "C" int nwq_batch_destroy(nwq_batch* b) {
   if (b->dev) cudaFreeAsync(b->dev, b->stream);  // after the runs queued on the creation stream
   delete b;
   return NWQ_OK;
+}
+
+// ------------------------------------------------------------------ quantum trajectories
+// Noise descriptor of every gate (the device noise model of
+// nwq_dm_apply_circuit_noisy), or an error.
+static int traj_noise(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, std::vector<TNoise>& out,
+                      int* draws) {
+  out.assign(ng, TNoise{});
+  *draws = 0;
+  if (!nm) return NWQ_OK;
+  if (nm->n < n || !nm->T1_us || !nm->T2_us) return set_error(NWQ_EINVAL, "noise model does not cover the qubits");
+  for (size_t i = 0; i < ng; i++) {
+    TNoise& T = out[i];
+    const bool two = g[i].kind >= NWQ_GATE_CX;
+    T.k = two ? 2 : 1;
+    if ((nm->flags & NWQ_NOISE_RZ_VIRTUAL) && g[i].kind == NWQ_GATE_RZ) continue;
+    const int np = 1 << (2 * T.k);
+    double p = two ? nm->p2 : nm->p1;
+    if (nm->flags & NWQ_NOISE_DEPOL_PAULI_FORM) p = p * np / (np - 1.0);
+    if (p < 0 || p > np / (np - 1.0)) return set_error(NWQ_EINVAL, "depolarising parameter out of range");
+    T.pdep = p;
+    if (p > 0) *draws += 1;
+    const double tns = two ? nm->t2q_ns : nm->t1q_ns;
+    if (tns > 0) {
+      T.relax = 1;
+      for (int w = 0; w < T.k; w++) {
+        const int q = g[i].q[w];
+        const double T1 = nm->T1_us[q], T2 = nm->T2_us[q];
+        if (!(T1 > 0) || !(T2 > 0)) return set_error(NWQ_EINVAL, "T1 and T2 must be positive");
+        const double gamma = 1.0 - std::exp(-tns / (T1 * 1e3)), eta = std::exp(-tns / (T2 * 1e3));
+        double oml = eta * eta / (1.0 - gamma);
+        if (oml > 1.0 + 1e-15) return set_error(NWQ_EINVAL, "trajectories need T2 <= 2 T1 (amplitude plus phase damping)");
+        if (oml > 1.0) oml = 1.0;
+        T.gamma[w] = gamma;
+        T.lambda[w] = 1.0 - oml;
+      }
+      *draws += 2 * T.k;
+    }
+  }
+  return NWQ_OK;
+}
+
+extern "C" int nwq_traj_draws(const nwq_gate* gates, size_t ng, int n, const nwq_noise_model* noise, size_t* draws) {
+  if (!draws || (ng && !gates)) return set_error(NWQ_EINVAL, "NULL argument");
+  std::vector<TNoise> tn;
+  int d = 0;
+  int rc = traj_noise(gates, ng, n, noise, tn, &d);
+  if (rc) return rc;
+  *draws = (size_t)d;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_traj_run(int n, int dtype, const nwq_gate* gates, size_t ng, const nwq_noise_model* noise,
+                            const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne,
+                            const double* uniforms, int ntraj, double* out, void* stream) {
+  if ((ng && !gates) || (nt && !terms) || ne < 1 || !coeffs || ntraj < 1 || !out) return set_error(NWQ_EINVAL, "bad trajectory arguments");
+  if (dtype != NWQ_F32 && dtype != NWQ_F64) return set_error(NWQ_EINVAL, "unsupported dtype");
+  if (n < 1 || n > (dtype == NWQ_F64 ? 13 : 14)) return set_error(NWQ_EINVAL, "trajectory qubit count outside [1, 13] (F64) / [1, 14] (F32)");
+  std::vector<BGate> bg(ng);
+  std::string err;
+  for (size_t i = 0; i < ng; i++) {
+    if (gates[i].reserved || gates[i].reserved2) return set_error(NWQ_EINVAL, "reserved gate field not 0");
+    if (!lower_batch_gate(gates[i], n, 0, bg[i], err)) return set_error(NWQ_EINVAL, err.c_str());
+  }
+  std::vector<TNoise> tn;
+  int draws = 0;
+  int rc = traj_noise(gates, ng, n, noise, tn, &draws);
+  if (rc) return rc;
+  if (draws > 0 && !uniforms) return set_error(NWQ_EINVAL, "uniforms is NULL");
+  const uint64_t qmask = (1ull << n) - 1;
+  std::vector<BTerm> bt;
+  for (size_t i = 0; i < nt; i++) {
+    if ((terms[i].x_mask & ~qmask) || (terms[i].z_mask & ~qmask)) return set_error(NWQ_EINVAL, "Pauli mask out of range");
+    bt.push_back(BTerm{(uint32_t)terms[i].x_mask, (uint32_t)terms[i].z_mask,
+                       __builtin_popcountll(terms[i].x_mask & terms[i].z_mask) & 3, 0});
+  }
+  const bool f64 = dtype == NWQ_F64;
+  if (traj_smem_bytes(f64, n, (int)ng, (int)nt) > (size_t)kBatchMaxSmem)
+    return set_error(NWQ_EUNSUPPORTED, "trajectory state plus gate tables exceed shared memory");
+  int dev = 0, sms = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_error(NWQ_ECUDA, cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)stream;
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t og = 0, on = al(og + bg.size() * sizeof(BGate)), ot = al(on + tn.size() * sizeof(TNoise));
+  const size_t oc = al(ot + bt.size() * sizeof(BTerm)), ocnt = al(oc + (size_t)ne * nt * sizeof(double));
+  void* d = nullptr;
+  if (cudaMallocAsync(&d, ocnt + 256, s) != cudaSuccess) return set_error(NWQ_ENOMEM, "trajectory table allocation failed");
+  char* dc = (char*)d;
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+  if (!bg.empty()) e = cudaMemcpyAsync(dc + og, bg.data(), bg.size() * sizeof(BGate), h2d, s);
+  if (e == cudaSuccess && !tn.empty()) e = cudaMemcpyAsync(dc + on, tn.data(), tn.size() * sizeof(TNoise), h2d, s);
+  if (e == cudaSuccess && !bt.empty()) e = cudaMemcpyAsync(dc + ot, bt.data(), bt.size() * sizeof(BTerm), h2d, s);
+  if (e == cudaSuccess && nt) e = cudaMemcpyAsync(dc + oc, coeffs, (size_t)ne * nt * sizeof(double), h2d, s);
+  if (e == cudaSuccess) {
+    TrajArgs a{};
+    a.gates = (const BGate*)(dc + og);
+    a.noise = (const TNoise*)(dc + on);
+    a.terms = (const BTerm*)(dc + ot);
+    a.coeffs = (const double*)(dc + oc);
+    a.u = uniforms;
+    a.out = out;
+    a.counter = (int*)(dc + ocnt);
+    a.n = n;
+    a.ng = (int)ng;
+    a.nt = (int)nt;
+    a.ne = ne;
+    a.draws = draws;
+    a.ntraj = ntraj;
+    a.threads = 256;
+    e = launch_traj(f64, a, sms, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables go out of scope
+  cudaFreeAsync(d, s);
+  return e == cudaSuccess ? NWQ_OK : set_error(NWQ_ECUDA, cudaGetErrorString(e));
 }
 
 extern "C" int nwq_batch_energy(int n, int dtype, const nwq_gate* gates, size_t ng, const double* params, int nsets,

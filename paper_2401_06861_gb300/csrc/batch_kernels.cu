@@ -275,6 +275,190 @@ __global__ void __launch_bounds__(TH) batch_kernel(BatchArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ quantum trajectories
+// Noisy state vectors by Monte-Carlo unravelling of the device noise model
+// (the stochastic alternative to the density matrix of paper Sec. II/III):
+// one CTA per trajectory, the state in shared memory.  After each gate, with
+// the trajectory's draws u (inputs, consumed in order):
+//   depolarising p on k qubits: one draw x; if x < (4^k - 1) p / 4^k the
+//     Pauli string s = 1 + floor(x 4^k / p) (<= 4^k - 1) is applied,
+//     s & 3 on q0 and s >> 2 on q1 (0 I, 1 X, 2 Y, 3 Z);
+//   relaxation on each gate qubit: amplitude damping (gamma) then phase
+//     damping (lambda), one draw x each: with P1 = prob(q = 1) (FP64 block
+//     sum), the jump |0><1| (resp. |1><1|) when x < rate P1, else
+//     diag(1, sqrt(1 - rate)); the state is renormalised in FP64.
+// Every thread reads the same draw and the same P1, so branches are uniform.
+template <class C>
+__device__ void apply_pauli(C* __restrict__ psi, int n, int q, int a) {
+  const uint32_t half = 1u << (n - 1), m = 1u << q;
+  for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+    const uint32_t b0 = ((t >> q) << (q + 1)) | (t & (m - 1)), b1 = b0 | m;
+    const C x0 = psi[b0], x1 = psi[b1];
+    if (a == 1) {  // X
+      psi[b0] = x1;
+      psi[b1] = x0;
+    } else if (a == 2) {  // Y: (x0, x1) -> (-i x1, i x0)
+      psi[b0] = C{x1.y, -x1.x};
+      psi[b1] = C{-x0.y, x0.x};
+    } else {  // Z
+      psi[b1] = C{-x1.x, -x1.y};
+    }
+  }
+}
+
+template <class R, int TH>
+__global__ void __launch_bounds__(TH) traj_kernel(TrajArgs a) {
+  using C = typename C2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* psi = reinterpret_cast<C*>(smem);
+  GateMat<R>* mats = reinterpret_cast<GateMat<R>*>(smem + ((size_t)sizeof(C) << a.n));
+  double* red = reinterpret_cast<double*>(mats + a.ng);  // 32 doubles
+  double* vals = red + 32;                                // nt doubles
+  __shared__ int s_job;
+  const int n = a.n;
+  const uint32_t N = 1u << n, half = N >> 1;
+  // fixed circuit: gate matrices once per CTA
+  for (int k = threadIdx.x; k < a.ng; k += blockDim.x) make_gate<R>(a.gates[k], a.gates, nullptr, mats[k]);
+  __syncthreads();
+  for (int iter = 0; iter < a.ntraj; iter++) {  // bounded: at most ntraj trajectories per CTA
+    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int job = s_job;
+    __syncthreads();
+    if (job >= a.ntraj) break;
+    const double* u = a.u + (size_t)job * a.draws;
+    int used = 0;
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = C{b == 0 ? (R)1 : (R)0, 0};
+    __syncthreads();
+    for (int g = 0; g < a.ng; g++) {
+      const BGate& G = a.gates[g];
+      apply_gate<R>(psi, n, G, mats[g]);
+      __syncthreads();
+      const TNoise& T = a.noise[g];
+      if (T.pdep > 0) {
+        const double x = u[used++];
+        const int np = 1 << (2 * T.k);
+        if (x < (np - 1) * T.pdep / np) {
+          int s = 1 + (int)floor(x * np / T.pdep);
+          if (s > np - 1) s = np - 1;
+          for (int w = 0; w < T.k; w++) {
+            const int pa = (s >> (2 * w)) & 3;
+            if (pa) {
+              apply_pauli<C>(psi, n, w == 0 ? G.q0 : G.q1, pa);
+              __syncthreads();
+            }
+          }
+        }
+      }
+      if (!T.relax) continue;
+      for (int w = 0; w < T.k; w++) {
+        const int q = w == 0 ? G.q0 : G.q1;
+        const uint32_t m = 1u << q;
+        for (int step = 0; step < 2; step++) {
+          const double rate = step == 0 ? T.gamma[w] : T.lambda[w];
+          const double x = u[used++];
+          double p1 = 0.0;
+          for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+            const C v = psi[((t >> q) << (q + 1)) | (t & (m - 1)) | m];
+            p1 = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, p1));
+          }
+          p1 = block_sum(p1, red);
+          const bool jump = x < rate * p1;
+          const double f0 = jump ? 0.0 : 1.0 / sqrt(1.0 - rate * p1);  // |0> part
+          const double f1 = jump ? 1.0 / sqrt(p1) : sqrt(1.0 - rate) * f0;
+          for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+            const uint32_t b0 = ((t >> q) << (q + 1)) | (t & (m - 1)), b1 = b0 | m;
+            const C x0 = psi[b0], x1 = psi[b1];
+            if (jump && step == 0) {  // |0><1|: the |1> part moves down
+              psi[b0] = C{(R)(x1.x * f1), (R)(x1.y * f1)};
+              psi[b1] = C{0, 0};
+            } else if (jump) {  // |1><1|: the |0> part vanishes
+              psi[b0] = C{0, 0};
+              psi[b1] = C{(R)(x1.x * f1), (R)(x1.y * f1)};
+            } else {
+              psi[b0] = C{(R)(x0.x * f0), (R)(x0.y * f0)};
+              psi[b1] = C{(R)(x1.x * f1), (R)(x1.y * f1)};
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+    // energies of the (normalised) final state, FP64 accumulation
+    double nrm = 0;
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+      double re = psi[b].x, im = psi[b].y;
+      nrm = fma(re, re, fma(im, im, nrm));
+    }
+    nrm = block_sum(nrm, red);
+    for (int t = 0; t < a.nt; t++) {
+      const BTerm tm = a.terms[t];
+      double acc = 0;
+      for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+        double pr = psi[b].x, pi = psi[b].y;
+        double qr = pr, qi = pi;
+        if (tm.x) {
+          qr = psi[b ^ tm.x].x;
+          qi = psi[b ^ tm.x].y;
+        }
+        double wr = fma(qr, pr, qi * pi), wi = fma(qr, pi, -qi * pr);
+        double v = (tm.y & 1) ? wi : wr;
+        int neg = ((tm.y == 1) || (tm.y == 2)) ^ (__popc(b & tm.z) & 1);
+        acc += neg ? -v : v;
+      }
+      acc = block_sum(acc, red);
+      if (threadIdx.x == 0) vals[t] = acc / nrm;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.ne; e += blockDim.x) {
+      double s = 0;
+      for (int t = 0; t < a.nt; t++) s = fma(a.coeffs[e * a.nt + t], vals[t], s);
+      a.out[(size_t)job * a.ne + e] = s;
+    }
+    __syncthreads();
+  }
+}
+
+size_t traj_smem_bytes(bool f64, int n, int ng, int nt) {
+  size_t c = f64 ? 16 : 8;
+  size_t gm = f64 ? sizeof(GateMat<double>) : sizeof(GateMat<float>);
+  return (c << n) + gm * (size_t)(ng > 0 ? ng : 1) + 8 * (32 + (size_t)nt + 1);
+}
+
+template <class R>
+static cudaError_t launch_traj_t(const TrajArgs& a, size_t smem, int sm_count, cudaStream_t s) {
+  static int attr_dev = -1;
+  static std::mutex attr_mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaError_t e = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (attr_dev != dev) {
+      e = cudaFuncSetAttribute(traj_kernel<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
+      if (e == cudaSuccess) attr_dev = dev;
+    }
+  }
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_kernel<R, 256>, 256, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = sm_count * per_sm;
+  if (grid > a.ntraj) grid = a.ntraj;
+  e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  traj_kernel<R, 256><<<grid, 256, smem, s>>>(a);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_traj(bool f64, const TrajArgs& a, int sm_count, cudaStream_t s) {
+  const size_t smem = traj_smem_bytes(f64, a.n, a.ng, a.nt);
+  if (smem > (size_t)kBatchMaxSmem || a.ntraj < 1) return cudaErrorInvalidValue;
+  return f64 ? launch_traj_t<double>(a, smem, sm_count, s) : launch_traj_t<float>(a, smem, sm_count, s);
+}
+
 size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
   size_t c = f64 ? 16 : 8;
   size_t gm = f64 ? sizeof(GateMat<double>) : sizeof(GateMat<float>);

@@ -295,3 +295,36 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def trajectory_draws(n, gates, noise):
+    """Uniform draws one quantum trajectory of ``gates`` under ``noise`` consumes."""
+    arr, keep = encode_gates(gates)
+    nm, keep2 = encode_noise(noise, n)
+    d = ctypes.c_size_t()
+    check(L.lib().nwq_traj_draws(arr, len(gates), n, ctypes.byref(nm) if nm is not None else None, ctypes.byref(d)))
+    return d.value
+
+
+def trajectories(n, gates, noise, terms, coeffs, ntraj, dtype=F64, seed=0, uniforms=None, stream=None):
+    """Noisy energies by quantum trajectories (nwq_traj_run): returns an
+    (ntraj, ne) array, row t = sum_k coeffs[e, k] <P_k> of trajectory t.  The
+    draws are ``uniforms`` (ntraj x draws, in [0, 1)) or, by default, numpy's
+    default_rng(seed)."""
+    import torch
+    arr, keep = encode_gates(gates)
+    nm, keep2 = encode_noise(noise, n)
+    d = trajectory_draws(n, gates, noise)
+    if uniforms is None:
+        uniforms = np.random.default_rng(seed).random((ntraj, d))
+    u = torch.from_numpy(np.ascontiguousarray(uniforms, np.float64).reshape(ntraj, d)).cuda()
+    c = np.ascontiguousarray(np.asarray(coeffs, np.float64).reshape(-1, len(terms)))
+    ne = c.shape[0]
+    out = torch.empty(ntraj, ne, dtype=torch.float64, device="cuda")
+    tr = encode_terms(terms)
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    check(L.lib().nwq_traj_run(n, dtype, arr, len(gates), ctypes.byref(nm) if nm is not None else None, tr, len(terms),
+                               c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ne,
+                               ctypes.c_void_p(u.data_ptr() if d else 0), ntraj, ctypes.c_void_p(out.data_ptr()),
+                               ctypes.c_void_p(s)))
+    return out.cpu().numpy()
