@@ -411,6 +411,45 @@ def run_vqe_cobyla(args):
         ef.close()
 
 
+def run_traj(args):
+    """Noisy TFIM n = 12 (20 Trotter steps, device noise model) two ways: the
+    density matrix (4^12 FP64 Pauli coefficients) and 4096 quantum
+    trajectories (state vectors in shared memory); <H> and time of each."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, inputs, sim
+    build.build()
+    n, steps, ntraj = 12, 20, 4096
+    gates, noise = inputs.dm_noisy_tfim(n, steps)
+    terms = inputs.tfim_terms(n)
+    coeffs = [[t[2] for t in terms]]
+    with sim.State(L.DM, n, L.F64) as st, sim.Plan(L.DM, n, gates, L.F64, noise) as plan:
+        st.run(plan)
+        st.sync()
+        t0 = time.perf_counter()
+        st.reset()
+        st.run(plan)
+        e_dm = st.expect(terms, sum=True)
+        dm_s = time.perf_counter() - t0
+    for dtype, name in ((L.F64, "f64"), (L.F32, "f32")):
+        sim.trajectories(n, gates, noise, terms, coeffs, 64, dtype, seed=1)  # warm-up
+        d = sim.trajectory_draws(n, gates, noise)
+        u = np.random.default_rng(2).random((ntraj, d))
+        t0 = time.perf_counter()
+        e = sim.trajectories(n, gates, noise, terms, coeffs, ntraj, dtype, uniforms=u)[:, 0]
+        sec = time.perf_counter() - t0
+        line = {"workload": f"noisy_tfim_n{n}_{steps}steps_trajectories", "path": f"trajectories_{name}",
+                "metric": "trajectories/s", "value": ntraj / sec, "unit": "trajectories/s", "trajectories": ntraj,
+                "draws_per_trajectory": d, "wall_s": sec, "energy_mean": float(e.mean()),
+                "energy_stderr": float(e.std() / np.sqrt(ntraj)), "energy_density_matrix": e_dm,
+                "density_matrix_s": dm_s,
+                "note": "host wall clock incl. the host->device copy of the draws; the density matrix value is one "
+                        "FP64 run of the same circuit"}
+        print(json.dumps(line), flush=True)
+
+
 def serve_oracle_check(reqs, res, budget_s=20.0, every=100):
     """cpu_baseline leg of the serving line: the CPU oracle on a sample of the
     served requests (every 100th completed request with SV n <= 16 or DM n <= 9,
@@ -497,7 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "vqe-cobyla", "serve"])
+    ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "vqe-cobyla", "serve", "traj"])
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
@@ -517,6 +556,8 @@ def main():
         return run_sv(args)
     if args.workload == "vqe-cobyla":
         return run_vqe_cobyla(args)
+    if args.workload == "traj":
+        return run_traj(args)
     if args.workload == "vqe":
         return run_vqe(args)
     if args.workload == "serve":

@@ -445,3 +445,26 @@ def test_sv_n28_fp32_vs_fp64_tfim():
     print(f"n=28 fp32 vs fp64: rel energy {rerr:.3e}, <Z> {maxerr(res[L.F32][1], res[L.F64][1]):.3e}")
     assert rerr <= 1e-6
     assert maxerr(res[L.F32][1], res[L.F64][1]) <= 1e-5
+
+
+def test_qasm_program_on_the_gpu():
+    from paper_2401_06861_gb300 import qasm
+    prog = """OPENQASM 2.0;
+    include "qelib1.inc";
+    qreg q[5];
+    gate layer(a) x, y { ry(a) x; rz(-a/2) y; cx x, y; }
+    h q;
+    layer(0.3) q[0], q[1];
+    layer(1.1) q[3], q[4];
+    cp(pi/5) q[1], q[2];
+    crz(0.9) q[2], q[3];
+    ch q[4], q[0];
+    u3(0.2, 0.4, -0.6) q[2];
+    rzz(0.25) q[0], q[4];
+    """
+    r = qasm.parse(prog)
+    ref = oracle.sv_run(r["n"], r["gates"])
+    for dtype in DTYPES:
+        with State(L.SV, r["n"], dtype) as st:
+            st.apply(r["gates"])
+            assert maxerr(st.copy(), ref) <= TOL[dtype]
