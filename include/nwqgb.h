@@ -231,6 +231,13 @@ int nwq_plan_autotune(nwq_state* scratch, const nwq_gate* gates, size_t ng, cons
                       uint32_t flags, int reps, nwq_plan_tuning* best, double* best_ms,
                       nwq_plan_tuning* tried, double* tried_ms, int max_tried, int* ntried);
 
+/* Test hook: verify the plan's device tables against the bounds the kernels
+ * assume (tile geometry, masks, operator and entry offsets, register phases,
+ * coefficient ranges); NWQ_EINVAL with the first violation in
+ * nwq_last_error().  With the environment variable NWQ_CHECKS=1 every plan
+ * is verified when it is created.  Host only. */
+int nwq_plan_verify(const nwq_plan* plan);
+
 /* Test hook: generate and compile (host only; nothing is loaded on a device)
  * the run-time specialised kernel of every eligible sweep of a complex plan.
  * Complex sweeps of states with at least NWQ_JIT_MIN_BITS qubits (default 18)

@@ -100,6 +100,7 @@ def lib():
         "nwq_plan_autotune": (i32, [vp, P(Gate), sz, P(NoiseModel), u32, i32, P(PlanTuning), P(dbl),
                                     P(PlanTuning), P(dbl), i32, P(i32)]),
         "nwq_plan_jit_check": (i32, [vp, P(i32), P(i32)]),
+        "nwq_plan_verify": (i32, [vp]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),

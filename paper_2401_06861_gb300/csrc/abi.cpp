@@ -344,6 +344,14 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
   if (kind == NWQ_DM && !(flags & NWQ_PLAN_NO_RESCALE)) o.rescale_qubits = n;
   build_plan(ops, o, pl->p);
   pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
+  static const bool checks = [] {
+    const char* e = std::getenv("NWQ_CHECKS");
+    return e && e[0] == '1';
+  }();
+  if (checks) {
+    std::string cerr;
+    if (!verify_plan(pl->p, cerr)) return fail(NWQ_EINVAL, cerr);
+  }
   *out = pl.release();
   return NWQ_OK;
 }
@@ -432,6 +440,12 @@ extern "C" int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_ga
     if (op_ngates) op_ngates[k] = plan->p.op_ngates[k];
   }
   return NWQ_OK;
+}
+
+extern "C" int nwq_plan_verify(const nwq_plan* plan) {
+  if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
+  std::string err;
+  return verify_plan(plan->p, err) ? NWQ_OK : fail(NWQ_EINVAL, err);
 }
 
 extern "C" int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* built) {

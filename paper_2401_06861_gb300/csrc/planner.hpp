@@ -76,6 +76,10 @@ bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, st
 // Merge + sweep grouping + device table layout.
 void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan);
 
+// Verify the device tables of a built plan against the kernels' bounds
+// (plan_check.cpp); false with a message on the first violation.
+bool verify_plan(const Plan& p, std::string& err);
+
 // Cost model: floating-point operations (multiply or add) per state element.
 double op_cost(const BitOp& op, bool is_complex);
 

@@ -204,6 +204,10 @@ class Plan:
     def __exit__(self, *a):
         self.close()
 
+    def verify(self):
+        """Check the plan's device tables against the kernels' bounds (raises NwqError)."""
+        check(L.lib().nwq_plan_verify(self.h))
+
     def jit_check(self):
         """Compile (host only) the specialised kernels of this plan's sweeps:
         returns (eligible sweeps, compiled sweeps)."""

@@ -182,3 +182,38 @@ def test_plan_tuning_shapes_and_validation():
         p = sim.Plan(L.SV, 20, g, L.F64, tuning=dict(register_bits=rb, tile_bits=12))
         e, b = p.jit_check()
         assert e == b and e > 0
+
+
+def test_every_plan_passes_the_table_check():
+    # the host-side check of the device tables, over many random plans and shapes
+    rng = np.random.default_rng(5)
+    count = 0
+    for kind in (L.SV, L.DM):
+        for dtype in (L.F64, L.F32):
+            for n in ((3, 9, 14, 20) if kind == L.SV else (2, 5, 8, 10)):
+                for flags in (0, L.PLAN_PLAIN, L.PLAN_NO_MERGE):
+                    for tuning in (None, dict(tile_bits=10, fusion_bits=3, register_bits=3),
+                                   dict(tile_bits=13, fusion_bits=2, register_bits=4)):
+                        if tuning and (2 * (8 if dtype == L.F32 else 16) << tuning["tile_bits"]) > 200 * 1024:
+                            continue
+                        g = inputs.random_circuit(n, 120, int(rng.integers(1 << 30)))
+                        noise = inputs.noise_params(n, seed=int(rng.integers(1 << 30))) if kind == L.DM else None
+                        p = sim.Plan(kind, n, g, dtype, noise, flags, tuning=tuning)
+                        p.verify()
+                        p.close()
+                        count += 1
+    assert count >= 100
+
+
+def test_table_check_is_on_with_the_environment_variable():
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2401_06861_gb300 import _lib as L, inputs, sim\n"
+            "g, noise = inputs.dm_noisy_tfim(6, 3)\n"
+            "sim.Plan(L.DM, 6, g, L.F64, noise)\n"
+            "sim.Plan(L.SV, 12, inputs.random_circuit(12, 200, 1), L.F32)\n"
+            "print('ok')\n" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, NWQ_CHECKS="1"))
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
