@@ -152,6 +152,13 @@ int nwq_state_copy(nwq_state* st, void* dst, size_t bytes, int dst_on_device);
 /* DM only: copy the raw Pauli-basis coefficients (4^n reals). */
 int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst_on_device);
 
+/* DM only: load raw Pauli-basis coefficients (4^n reals in the state's
+ * precision, as nwq_dm_copy_pauli writes them): with nwq_dm_copy_pauli /
+ * nwq_state_copy and nwq_state_load for state vectors, a bit-exact checkpoint
+ * of a run between two circuits (a long run resumes from host memory).
+ * Synchronises the stream. */
+int nwq_dm_load_pauli(nwq_state* st, const void* src, size_t bytes, int src_on_device);
+
 /* Free the handle.  Library-owned device memory is released stream-ordered
  * on the state's stream (work queued there completes first; no device-wide
  * synchronisation).  A caller-owned buffer is left alone. */

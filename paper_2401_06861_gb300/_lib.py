@@ -88,6 +88,7 @@ def lib():
         "nwq_state_load": (i32, [vp, vp, sz, i32]),
         "nwq_state_copy": (i32, [vp, vp, sz, i32]),
         "nwq_dm_copy_pauli": (i32, [vp, vp, sz, i32]),
+        "nwq_dm_load_pauli": (i32, [vp, vp, sz, i32]),
         "nwq_destroy": (i32, [vp]),
         "nwq_sv_apply_circuit": (i32, [vp, P(Gate), sz, u32]),
         "nwq_dm_apply_circuit_noisy": (i32, [vp, P(Gate), sz, P(NoiseModel), u32]),

@@ -1,5 +1,6 @@
 // C ABI of the simulator: state handles, plans, measurement.  Every device
-// step runs in the kernels of sweep_kernels.cu / batch_kernels.cu; this file
+// step runs in the library's kernels (sweep_kernels.cu, expect_kernels.cu,
+// batch_kernels.cu and the run-time specialised sweeps of jit.cpp); this file
 // validates arguments, lowers circuits (planner.cpp), uploads operator tables
 // and launches.
 #include <cuda_runtime.h>
@@ -16,6 +17,7 @@
 #include "../../include/nwqgb.h"
 #include "expect_host.hpp"
 #include "jit.hpp"
+#include "nvtx_range.hpp"
 #include "kernels.hpp"
 #include "planner.hpp"
 #include "state.hpp"
@@ -118,6 +120,7 @@ static int plan_upload(Plan& p, cudaStream_t s) {
 }
 
 static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
+  NvtxRange range("nwq plan run");
   int rc = plan_upload(p, s);
   if (rc) return rc;
   const DevOp* ops = (const DevOp*)p.dev;
@@ -127,6 +130,7 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
   for (size_t i = 0; i < p.sweeps.size(); i++) {
     const SweepDesc& sd = p.sweeps[i];
     if (sd.nops == 0) continue;
+    NvtxRange sweep_range("nwq sweep");
     cudaError_t e = cudaSuccess;
     if (!((!p.is_complex || sd.nph > 0) && jit_launch_sweep(p, i, pt, data, sm_count, s, &e)))
       e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents, p.phases.empty() ? nullptr : &pt,
@@ -271,6 +275,17 @@ extern "C" int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst
   return NWQ_OK;
 }
 
+extern "C" int nwq_dm_load_pauli(nwq_state* st, const void* src, size_t bytes, int src_on_device) {
+  if (!st || !src) return fail(NWQ_EINVAL, "NULL argument");
+  if (st->kind != NWQ_DM) return fail(NWQ_EINVAL, "not a density matrix");
+  if (bytes != st->bytes) return fail(NWQ_EINVAL, "size mismatch");
+  CK(cudaMemcpyAsync(st->buf, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     st->stream),
+     "state load");
+  CK(cudaStreamSynchronize(st->stream), "state load");
+  return NWQ_OK;
+}
+
 extern "C" int nwq_state_load(nwq_state* st, const void* src, size_t bytes, int src_on_device) {
   if (!st || !src) return fail(NWQ_EINVAL, "NULL argument");
   cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -308,6 +323,7 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
                                      const nwq_noise_model* nm, uint32_t flags, const nwq_plan_tuning* tuning,
                                      void* stream, nwq_plan** out) {
   (void)stream;
+  NvtxRange range("nwq plan create");
   if (!out) return fail(NWQ_EINVAL, "out is NULL");
   *out = nullptr;
   if (!nwq_state_bytes(kind, n, dtype)) return fail(NWQ_EINVAL, "unsupported qubit count or dtype");
@@ -502,6 +518,7 @@ extern "C" int nwq_dm_apply_circuit_noisy(nwq_state* st, const nwq_gate* gates, 
 // ------------------------------------------------------------------ measurement
 extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, size_t nt, double* out_host,
                                     uint32_t flags) {
+  NvtxRange range("nwq expect");
   if (!st || !out_host || (nt && !terms)) return fail(NWQ_EINVAL, "NULL argument");
   if (nt == 0) {
     if (flags & NWQ_EXPECT_SUM) out_host[0] = 0.0;
@@ -590,6 +607,7 @@ static nwq_plan* probs_plan(nwq_state* st, double e, bool wht) {
 }
 
 extern "C" int nwq_probs(nwq_state* st, double readout_e, double* out_host) {
+  NvtxRange range("nwq probs");
   if (!st || !out_host) return fail(NWQ_EINVAL, "NULL argument");
   if (st->n > 30) return fail(NWQ_EUNSUPPORTED, "probabilities limited to n <= 30");
   if (!(readout_e >= 0.0 && readout_e <= 0.5)) return fail(NWQ_EINVAL, "readout error outside [0, 0.5]");

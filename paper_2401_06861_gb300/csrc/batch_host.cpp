@@ -13,6 +13,7 @@
 #include "../../include/nwqgb.h"
 #include "batch.hpp"
 #include "kernels.hpp"
+#include "nvtx_range.hpp"
 #include "planner.hpp"
 #include "state.hpp"
 
@@ -238,6 +239,7 @@ extern "C" int nwq_batch_create(int dtype, const nwq_batch_template* t, int ntem
 
 extern "C" int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* job_template, int njobs,
                              double* out, int out_stride, double* norms, void* stream, uint32_t flags) {
+  NvtxRange range("nwq batch run");
   if (!b || (njobs > 0 && (!out || (b->nparams > 0 && !params)))) return set_error(NWQ_EINVAL, "NULL argument");
   if (njobs < 0) return set_error(NWQ_EINVAL, "negative job count");
   if (njobs == 0) return NWQ_OK;
@@ -410,6 +412,7 @@ extern "C" int nwq_traj_draws(const nwq_gate* gates, size_t ng, int n, const nwq
 extern "C" int nwq_traj_run(int n, int dtype, const nwq_gate* gates, size_t ng, const nwq_noise_model* noise,
                             const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne,
                             const double* uniforms, int ntraj, double* out, void* stream) {
+  NvtxRange range("nwq trajectories");
   if ((ng && !gates) || (nt && !terms) || ne < 1 || !coeffs || ntraj < 1 || !out) return set_error(NWQ_EINVAL, "bad trajectory arguments");
   if (dtype != NWQ_F32 && dtype != NWQ_F64) return set_error(NWQ_EINVAL, "unsupported dtype");
   if (n < 1 || n > (dtype == NWQ_F64 ? 13 : 14)) return set_error(NWQ_EINVAL, "trajectory qubit count outside [1, 13] (F64) / [1, 14] (F32)");

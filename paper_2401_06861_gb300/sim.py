@@ -131,6 +131,11 @@ class State:
         check(L.lib().nwq_dm_copy_pauli(self.h, _ptr(out), out.nbytes, 0))
         return out
 
+    def load_pauli(self, coeffs):
+        """DM: load raw Pauli-basis coefficients (as ``pauli()`` returns them)."""
+        a = np.ascontiguousarray(coeffs, np.float64 if self.dtype == F64 else np.float32)
+        check(L.lib().nwq_dm_load_pauli(self.h, _ptr(a), a.nbytes, 0))
+
     def load(self, data):
         """SV: amplitude vector.  DM: row-major rho matrix."""
         if self.kind == SV:
