@@ -311,13 +311,18 @@ def run_sv(args):
         st.close()
         plan.close()
         gb = info["bytes"] / sec / 1e9
+        if dtype == L.F32:  # complex64: HBM bound
+            roof = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak,
+                    "fp_ops_per_amp": info["fma_per_elem"]}
+        else:  # complex128: FP64 pipe bound (2 FP64 instructions / clock / SM); the plan counts them per amplitude
+            fp64 = info["fma_per_elem"] * 2.0 ** n / sec
+            fpk = 152 * 2 * 2.07e9
+            roof = {"bound": "alu", "achieved": fp64, "peak": fpk, "unit": "FP64 instructions/s", "frac": fp64 / fpk,
+                    "fp_ops_per_amp": info["fma_per_elem"], "hbm_gbs": gb, "hbm_frac": gb / peak}
         line = {"workload": f"sv_tfim_n{n}_depth{args.sv_depth}", "plan": "plain" if flags else "fused",
                 "dtype": "c64" if dtype == L.F32 else "c128", "metric": "gate-updates/s",
                 "value": len(gates) * 2.0 ** n / sec, "unit": "gate-updates/s", "s_per_circuit": sec,
-                "sweeps": info["sweeps"], "operators": info["ops"],
-                "roofline": {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak,
-                             "fp_ops_per_amp": info["fma_per_elem"]},
-                "energy": e, "norm": nrm}
+                "sweeps": info["sweeps"], "operators": info["ops"], "roofline": roof, "energy": e, "norm": nrm}
         print(json.dumps(line), flush=True)
         torch.cuda.empty_cache()
 
