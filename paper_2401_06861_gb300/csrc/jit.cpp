@@ -101,12 +101,26 @@ int jit_min_bits() {
 }
 
 // ------------------------------------------------------------------ compiled kernels
+// One packed parameter range: cnt > 0: coefficients [pc0 + rel, + cnt) of the
+// complex table; cnt == 0: the coefficient of entry ent0 + rel of a real plan.
+struct RecipeItem {
+  uint32_t rel, cnt;
+};
+
+// A specialised kernel, cached by the structure of the sweeps it serves.  The
+// first sweep of a structure writes its description (source, the packing
+// recipe of its parameters, shared memory); later sweeps only pack their own
+// coefficients by the recipe.
 struct JitKernel {
   std::mutex mu;
-  std::atomic<bool> done{false}, ok{false}, queued{false};
+  std::atomic<bool> done{false}, ok{false}, queued{false}, described{false};
   cudaLibrary_t lib = nullptr;
   cudaKernel_t k = nullptr;
   std::atomic<int> attr_dev{-1};
+  std::string src;
+  std::vector<RecipeItem> recipe;
+  size_t smem = 0;
+  bool usable = false;  // the generator accepted the structure
 };
 
 std::mutex g_cache_mu;
@@ -157,10 +171,10 @@ bool compile(const std::string& src, JitKernel& jk) {
   return true;
 }
 
-void build_kernel(const std::string& src, JitKernel& jk) {
+void build_kernel(JitKernel& jk) {
   std::lock_guard<std::mutex> lk(jk.mu);
   if (jk.done) return;
-  jk.ok = compile(src, jk);
+  jk.ok = compile(jk.src, jk);
   jk.done = true;
   (jk.ok ? g_compiled : g_failed) += 1;
 }
@@ -170,16 +184,16 @@ void build_kernel(const std::string& src, JitKernel& jk) {
 struct AsyncCompiler {
   std::mutex mu;
   std::condition_variable cv;
-  std::deque<std::pair<std::string, std::shared_ptr<JitKernel>>> q;
+  std::deque<std::shared_ptr<JitKernel>> q;
   bool stop = false;
   std::thread th;
   AsyncCompiler() : th([this] { run(); }) {}
   ~AsyncCompiler() { shutdown(); }
-  void push(const std::string& src, std::shared_ptr<JitKernel> jk) {
+  void push(std::shared_ptr<JitKernel> jk) {
     {
       std::lock_guard<std::mutex> lk(mu);
       if (stop) return;  // after shutdown: the kernel stays interpreted
-      q.emplace_back(src, std::move(jk));
+      q.push_back(std::move(jk));
     }
     cv.notify_one();
   }
@@ -194,7 +208,7 @@ struct AsyncCompiler {
   }
   void run() {
     for (;;) {
-      std::pair<std::string, std::shared_ptr<JitKernel>> job;
+      std::shared_ptr<JitKernel> job;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv.wait(lk, [this] { return stop || !q.empty(); });
@@ -202,7 +216,7 @@ struct AsyncCompiler {
         job = std::move(q.front());
         q.pop_front();
       }
-      build_kernel(job.first, *job.second);
+      build_kernel(*job);
     }
   }
 };
@@ -221,25 +235,25 @@ AsyncCompiler& async_compiler() {
 }
 std::atomic<bool> g_async_started{false};
 
-// Cached kernel for src.  Synchronous: compiled before returning.
-// Asynchronous: queued for the background compiler on first request; until
-// it is ready the caller runs the interpreted kernel.
-std::shared_ptr<JitKernel> kernel_for(const std::string& src, bool async) {
-  std::shared_ptr<JitKernel> jk;
-  {
-    std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto& slot = g_cache[src];
-    if (!slot) slot = std::make_shared<JitKernel>();
-    jk = slot;
-  }
-  if (jk->done) return jk;
+// Cache entry of a structure key (created empty on first request).
+std::shared_ptr<JitKernel> entry_for(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto& slot = g_cache[key];
+  if (!slot) slot = std::make_shared<JitKernel>();
+  return slot;
+}
+
+// Compile a described entry.  Synchronous: before returning.  Asynchronous:
+// queued for the background compiler on first request; until it is ready the
+// caller runs the interpreted kernel.
+void request_compile(const std::shared_ptr<JitKernel>& jk, bool async) {
+  if (jk->done) return;
   if (!async) {
-    build_kernel(src, *jk);
+    build_kernel(*jk);
   } else if (!jk->queued.exchange(true)) {
     g_async_started = true;
-    async_compiler().push(src, jk);
+    async_compiler().push(jk);
   }
-  return jk;
 }
 
 // ------------------------------------------------------------------ source generation
@@ -271,6 +285,7 @@ struct Gen {
   bool c128;
   size_t cs;                        // bytes per coefficient
   std::vector<unsigned char> param; // packed coefficients
+  std::vector<RecipeItem> recipe;   // where they came from (relative to the sweep)
   struct Tab {
     uint32_t src, cnt, dst;  // sweep-relative source index, count, shared-memory index
   };
@@ -285,10 +300,11 @@ struct Gen {
   Gen(const Plan& p_, const SweepDesc& sd_)
       : p(p_), sd(sd_), c128(p_.is_complex && p_.dtype == NWQ_F64), cs(c128 ? 16 : 8), real(!p_.is_complex) {}
 
-  uint32_t pack_real(double v) {  // one FP64 coefficient
+  uint32_t pack_real(size_t entry, double v) {  // one FP64 coefficient (entry index of the plan)
     uint32_t at = (uint32_t)(param.size() / cs);
     const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
     param.insert(param.end(), b, b + 8);
+    recipe.push_back({(uint32_t)(entry - sd.ent0), 0});
     return at;
   }
 
@@ -344,7 +360,8 @@ struct Gen {
             uint32_t off;
             std::memcpy(&c, &p.ents[at], 8);
             std::memcpy(&off, &p.ents[at + 8], 4);
-            ex = "fma(" + K(pack_real(c)) + ", t" + std::to_string(ob | reg(off)) + ", " + ex + ")";
+            ex = "fma(" + K(pack_real((size_t)d.ent + rm.beg + e, c)) + ", t" + std::to_string(ob | reg(off)) + ", " +
+                 ex + ")";
           }
         }
         o << "      " << r(ob | reg(rm.out)) << " = " << ex << ";\n";
@@ -390,6 +407,7 @@ struct Gen {
     }
     uint32_t at = (uint32_t)(param.size() / cs);
     param.insert(param.end(), p.pcoef.begin() + (size_t)a * cs, p.pcoef.begin() + (size_t)(a + cnt) * cs);
+    recipe.push_back({a - sd.pc0, cnt});
     return at;
   }
   uint32_t table(uint32_t a, uint32_t cnt) {
@@ -653,6 +671,87 @@ struct Gen {
   size_t smem = 0;
 };
 
+// Structure key of a sweep: everything the generator reads except coefficient
+// values (tile geometry, register bits, operator codes, masks, forms, index
+// bits and permutations, coefficient positions relative to the sweep; for
+// real plans the operator rows and entry offsets).  Sweeps with equal keys
+// get identical kernel source.
+std::string struct_key(const Plan& p, const SweepDesc& sd) {
+  std::string key;
+  auto put = [&](const void* d, size_t n) { key.append(reinterpret_cast<const char*>(d), n); };
+  const int32_t hdr[8] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h, sd.prb, jit_min_blocks()};
+  put(hdr, sizeof(hdr));
+  if (p.is_complex) {
+    for (uint32_t ph = 0; ph < sd.nph; ph++) {
+      const PhaseDesc& P = p.phases[sd.ph0 + ph];
+      put(P.u, sizeof(P.u));
+      put(&P.nops, sizeof(P.nops));
+      for (uint32_t q = 0; q < P.nops; q++) {
+        const PhaseOp& o = p.pops[P.op0 + q];
+        const uint8_t f[6] = {o.cls, o.k, o.mask, o.form, o.code, o.dnu};
+        put(f, sizeof(f));
+        put(o.dpos, sizeof(o.dpos));
+        put(o.perm, sizeof(o.perm));
+        const uint32_t rel = o.coef - sd.pc0;
+        put(&rel, sizeof(rel));
+      }
+    }
+  } else {
+    for (int oi = 0; oi < sd.nops; oi++) {
+      const DevOp& d = p.ops[sd.op0 + oi];
+      put(&d.k, 1);
+      put(d.lb, sizeof(d.lb));
+      for (int i = 0; i < (1 << d.k) && i < 16; i++) {
+        const RowMeta& rm = d.row[i];
+        put(&rm, sizeof(RowMeta));
+        if (rm.kind != ROW_GEN) continue;
+        for (int e = 0; e < rm.cnt[0]; e++) {
+          const size_t at = ((size_t)d.ent + rm.beg + e) * p.ent_bytes + 8;
+          if (at + 4 <= p.ents.size()) key.append(reinterpret_cast<const char*>(&p.ents[at]), 4);  // entry offset
+        }
+      }
+    }
+  }
+  return key;
+}
+
+// Write the entry's description from this sweep (once per structure).
+bool describe(JitKernel& jk, const Plan& p, const SweepDesc& sd) {
+  if (jk.described) return jk.usable;
+  std::lock_guard<std::mutex> lk(jk.mu);  // never held by a compile here: compiles need a description
+  if (!jk.described) {
+    Gen g(p, sd);
+    std::string src;
+    jk.usable = g.run(src);
+    if (jk.usable) {
+      jk.src = std::move(src);
+      jk.recipe = std::move(g.recipe);
+      jk.smem = g.smem;
+    }
+    jk.described = true;
+  }
+  return jk.usable;
+}
+
+// This sweep's parameter bytes by the structure's recipe (empty on a range error).
+std::vector<unsigned char> pack_params(const Plan& p, const SweepDesc& sd, const std::vector<RecipeItem>& recipe) {
+  const size_t cs = (p.is_complex && p.dtype == NWQ_F64) ? 16 : 8;
+  std::vector<unsigned char> out;
+  for (const RecipeItem& it : recipe) {
+    if (it.cnt) {
+      const size_t a = (size_t)sd.pc0 + it.rel;
+      if ((a + it.cnt) * cs > p.pcoef.size()) return {};
+      out.insert(out.end(), p.pcoef.begin() + a * cs, p.pcoef.begin() + (a + it.cnt) * cs);
+    } else {
+      const size_t at = ((size_t)sd.ent0 + it.rel) * p.ent_bytes;
+      if (at + 8 > p.ents.size()) return {};
+      out.insert(out.end(), p.ents.begin() + at, p.ents.begin() + at + 8);
+    }
+  }
+  if (out.empty()) out.resize(cs, 0);
+  return out;
+}
+
 // Per-plan state: one entry per sweep, built on the plan's first launch.
 struct JitSweep {
   std::shared_ptr<JitKernel> k;  // null: run the interpreted kernel
@@ -708,9 +807,12 @@ int jit_prefetch(const Plan& p) {
   if (!jit_enabled()) return 0;
   int queued = 0;
   for (size_t i = 0; i < p.sweeps.size(); i++) {
-    std::string src;
-    if (!jit_source(p, i, src, nullptr, nullptr)) continue;
-    if (!kernel_for(src, true)->done) queued++;
+    const SweepDesc& sd = p.sweeps[i];
+    if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
+    std::shared_ptr<JitKernel> k = entry_for(struct_key(p, sd));
+    if (!describe(*k, p, sd)) continue;
+    request_compile(k, true);
+    if (!k->done) queued++;
   }
   return queued;
 }
@@ -732,18 +834,18 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
       for (size_t i = 0; i < p.sweeps.size(); i++) {
         const SweepDesc& sd = p.sweeps[i];
         if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
-        Gen g(p, sd);
-        std::string src;
-        if (!g.run(src)) continue;
+        std::shared_ptr<JitKernel> k = entry_for(struct_key(p, sd));
+        if (!describe(*k, p, sd)) continue;
         // one-shot plans never wait for a compile: their sweeps run interpreted
         // until the kernel of that structure is ready
-        std::shared_ptr<JitKernel> k = kernel_for(src, p.stream_ordered && !jit_sync_all());
+        request_compile(k, p.stream_ordered && !jit_sync_all());
         if (k->done && !k->ok) continue;
+        std::vector<unsigned char> param = pack_params(p, sd, k->recipe);
+        if (param.empty()) continue;
         JitSweep& js = jp.sw[i];
         js.k = k;
-        js.param = std::move(g.param);
-        if (js.param.empty()) js.param.resize(g.cs, 0);
-        js.smem = g.smem;
+        js.param = std::move(param);
+        js.smem = k->smem;
       }
       jp.built = true;
     }
