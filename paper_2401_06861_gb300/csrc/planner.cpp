@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <array>
+#include <map>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -207,6 +208,11 @@ bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, st
     return false;
   }
   std::vector<cd> R, D, Rl;
+  // A noisy circuit repeats the same gate on the same qubits (every Trotter
+  // step): the transfer matrix of gate plus noise is built once per distinct
+  // (kind, angles, qubits) in this call and reused.  Explicit-matrix gates are
+  // not memoised (their key would be the matrix itself).
+  std::map<std::array<double, 6>, std::vector<cd>> memo;
   for (size_t i = 0; i < ng; i++) {
     cd U[16];
     int k = gate_matrix(g[i], g[i].theta[0], U);
@@ -215,6 +221,24 @@ bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, st
       return false;
     }
     if (!check_gate(g[i], n, k, err)) return false;
+    const bool memo_ok = g[i].kind != NWQ_GATE_MAT1 && g[i].kind != NWQ_GATE_MAT2;
+    const std::array<double, 6> key{(double)g[i].kind, g[i].theta[0], g[i].theta[1], g[i].theta[2],
+                                    (double)g[i].q[0], (double)(k == 2 ? g[i].q[1] : -1)};
+    if (memo_ok) {
+      auto hit = memo.find(key);
+      if (hit != memo.end()) {
+        BitOp op;
+        op.k = 2 * k;
+        for (int j = 0; j < k; j++) {
+          op.bits[j] = g[i].q[j];
+          op.bits[k + j] = g[i].q[j] + n;
+        }
+        op.m = hit->second;
+        op.gate0 = (int)i;
+        out.push_back(std::move(op));
+        continue;
+      }
+    }
     unitary_ptm(k, U, R);
     snap_all(R);
     int np = 1 << (2 * k);
@@ -255,6 +279,7 @@ bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, st
     }
     op.m = R;
     op.gate0 = (int)i;
+    if (memo_ok) memo.emplace(key, R);
     out.push_back(std::move(op));
   }
   return true;
