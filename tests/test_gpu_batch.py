@@ -204,3 +204,40 @@ def test_batch_shapes_agree_and_autotune(dtype):
         with pytest.raises(L.NwqError):
             b.set_shape(*bad)
     b.close()
+
+
+def test_batch_full_size_bench_configuration():
+    # the benchmark's batched VQE at full size (n = 12, 4 layers, 4096 sets,
+    # 3 energies, graph replay, autotuned kernel shape): a sample of sets
+    # against the oracle and every energy above the exact ground energy
+    import torch
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.linalg import eigsh
+    n, layers, nsets = 12, 4, 4096
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    params = inputs.hea_params(n, layers, nsets, seed=4096)
+    e0 = []
+    N = 1 << n
+    idx = np.arange(N)
+    for h in H_LIST:  # H = -sum Z_i Z_{i+1} - h sum X_i as a sparse matrix
+        diag = -sum(1.0 - 2.0 * (((idx >> i) ^ (idx >> (i + 1))) & 1) for i in range(n - 1))
+        rows = np.concatenate([idx] + [idx for _ in range(n)])
+        cols = np.concatenate([idx] + [idx ^ (1 << i) for i in range(n)])
+        vals = np.concatenate([diag] + [np.full(N, -h) for _ in range(n)])
+        e0.append(eigsh(csr_matrix((vals, (rows, cols)), shape=(N, N)), k=1, which="SA")[0][0])
+    e0 = np.array(e0)
+    s = torch.cuda.current_stream().cuda_stream
+    p = torch.from_numpy(params).cuda()
+    sample = np.random.default_rng(4097).choice(nsets, 24, replace=False)
+    ref = np.array([oracle_energies(n, gates, pidx, params[i]) for i in sample])
+    for dtype, tol in ((L.F64, 1e-12), (L.F32, 1e-6)):
+        b = Batch([tfim_energy_template(n, gates, pidx)], layers * 2 * n, dtype, stream=s)
+        out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+        b.autotune(p.data_ptr(), nsets, out.data_ptr(), reps=1, stream=s)
+        for _ in range(2):
+            b.run(p.data_ptr(), nsets, out.data_ptr(), stream=s, graph=True)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert rel(got[sample], ref, n, np.array(H_LIST)[None, :]).max() <= tol
+        assert np.all(got >= e0[None, :] - 1e-6)
+        b.close()

@@ -492,3 +492,41 @@ def test_checkpoint_and_resume_is_bit_exact(kind, dtype):
             st.run(pb)
             straight = st.copy() if kind == L.SV else st.pauli()
     assert np.array_equal(resumed, straight)
+
+
+def test_dm_maximum_size_n16_product_state():
+    # the largest density matrix (4^16 FP64 Pauli coefficients, 32 GiB): a
+    # product-state circuit with the full noise model against one-qubit oracles
+    n = 16
+    noise = inputs.noise_params(n, seed=4300)
+    rng = np.random.default_rng(4301)
+    gates = []
+    for q in range(n):
+        for name in ("RX", "RY", "RZ"):
+            gates.append(inputs.gate(name, (q,), (float(rng.uniform(-np.pi, np.pi)),)))
+    z1 = []
+    for q in range(n):
+        nq = dict(noise, T1_us=noise["T1_us"][q:q + 1], T2_us=noise["T2_us"][q:q + 1])
+        r1 = oracle.dm_run(1, [(g[0], (0,), g[2]) for g in gates if g[1][0] == q], nq)
+        z1.append(oracle.dm_expect(r1, 1, [(0, 1, 1.0)])[0])
+    with State(L.DM, n, L.F64) as st:
+        st.apply(gates, noise)
+        z = st.expect(inputs.z_terms(n))
+        tr = st.expect([(0, 0, 1.0)])[0]
+    assert maxerr(z, z1) <= 1e-12
+    assert abs(tr - 1.0) <= 1e-14
+
+
+@pytest.mark.parametrize("kind,dtype", [(L.SV, L.F64), (L.SV, L.F32), (L.DM, L.F64), (L.DM, L.F32)])
+def test_empty_circuits_and_term_lists(kind, dtype):
+    # degenerate inputs: no gates (one-shot and planned), no terms
+    n = 20 if kind == L.SV else 10
+    with State(kind, n, dtype) as st, Plan(kind, n, [], dtype) as p:
+        st.apply([])
+        st.run(p)
+        assert p.info()["sweeps"] == 0
+        assert len(st.expect([])) == 0 and st.expect([], sum=True) == 0.0
+        z = st.expect(inputs.z_terms(n), normalize=True)
+        assert maxerr(z, np.ones(n)) <= 1e-6
+        probs = st.probs()
+        assert probs[0] == pytest.approx(1.0, abs=1e-6) and abs(probs.sum() - 1.0) <= 1e-6
