@@ -50,6 +50,24 @@ def workload():
     return gates, noise, inputs.z_terms(N), inputs.tfim_terms(N)
 
 
+def reduce_max(x, ws):
+    """Max over ranks of a host float (the slowest rank sets the job's time)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput: every rank processed units_per_rank in `seconds`
+    (the max over ranks)."""
+    return units_per_rank * ws / seconds
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -201,12 +219,8 @@ def run_ours(args, ws, rank, local):
     ck = clocks.stop()
     ms = t_start.elapsed_time(t_end) / args.steps
     sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = gate_updates * ws / (ms / 1e3)
+    ms = reduce_max(ms, ws)
+    value = job_rate(gate_updates, ws, ms / 1e3)
 
     # end to end through the public ABI with host buffers: host circuit in,
     # plan built and uploaded, run, results copied back, every step
@@ -220,11 +234,7 @@ def run_ours(args, ws, rank, local):
         p2 = st.probs(ro)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(e2e_s, ws)
     assert abs(e2 - e) <= 1e-12 and np.max(np.abs(p2 - p)) <= 1e-15, "e2e result differs from device-timed run"
     h2d = info["table_bytes"] + 24 * (len(zt) + len(ht))
     d2h = 8 * (len(zt) + 1 + (1 << N))
@@ -255,7 +265,7 @@ def run_ours(args, ws, rank, local):
                            "state_bytes": 8 << (2 * N), "l2": "inputs larger than L2 (512 MiB state)",
                            "plan": {"sweeps": info["sweeps"], "operators": info["ops"]},
                            "parallelism": f"replicas x{ws}"},
-                "e2e": {"value": gate_updates * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "e2e": {"value": job_rate(gate_updates, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
                 "results": {"energy": e, "z0": float(z[0]), "prob_sum": float(p.sum())}}
