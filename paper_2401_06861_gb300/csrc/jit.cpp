@@ -276,7 +276,15 @@ int pext4(int v, int mask) {  // gather v's bits at mask positions
     }
   return out;
 }
-uint32_t swz(bool c128, uint32_t l) { return c128 ? l + (l >> 3) : l + ((l >> 4) << 1); }
+// Padded tile layout for es-byte elements: 16 bytes of pad after every 128
+// bytes (additive over disjoint index bits; 16-byte vectors stay aligned).
+uint32_t swz(int es, uint32_t l) {
+  return es == 16 ? l + (l >> 3) : (es == 8 ? l + ((l >> 4) << 1) : l + ((l >> 5) << 2));
+}
+std::string swz_expr(int es, const std::string& v) {
+  return es == 16 ? "(" + v + " + (" + v + " >> 3))"
+                  : (es == 8 ? "(" + v + " + ((" + v + " >> 4) << 1))" : "(" + v + " + ((" + v + " >> 5) << 2))");
+}
 size_t padded_elems(int T) { return ((size_t)1 << T) + ((size_t)1 << T) / 8; }
 
 struct Gen {
@@ -298,12 +306,24 @@ struct Gen {
   // plans: FP64 elements.  8-byte elements share the complex64 tile layout.
   bool real;
   Gen(const Plan& p_, const SweepDesc& sd_)
-      : p(p_), sd(sd_), c128(p_.is_complex && p_.dtype == NWQ_F64), cs(c128 ? 16 : 8), real(!p_.is_complex) {}
+      : p(p_),
+        sd(sd_),
+        c128(p_.is_complex && p_.dtype == NWQ_F64),
+        cs(p_.is_complex ? (c128 ? 16 : 8) : (p_.dtype == NWQ_F64 ? 8 : 4)),
+        real(!p_.is_complex),
+        es((int)cs) {}
+  int es;  // bytes per state element (= per coefficient)
 
-  uint32_t pack_real(size_t entry, double v) {  // one FP64 coefficient (entry index of the plan)
+  uint32_t pack_real(size_t entry, double v) {  // one real coefficient (entry index of the plan)
     uint32_t at = (uint32_t)(param.size() / cs);
-    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
-    param.insert(param.end(), b, b + 8);
+    if (es == 8) {
+      const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+      param.insert(param.end(), b, b + 8);
+    } else {
+      const float f = (float)v;  // exact: the entry holds a float
+      const unsigned char* b = reinterpret_cast<const unsigned char*>(&f);
+      param.insert(param.end(), b, b + 4);
+    }
     recipe.push_back({(uint32_t)(entry - sd.ent0), 0});
     return at;
   }
@@ -358,8 +378,14 @@ struct Gen {
             }
             double c;
             uint32_t off;
-            std::memcpy(&c, &p.ents[at], 8);
-            std::memcpy(&off, &p.ents[at + 8], 4);
+            if (es == 8) {
+              std::memcpy(&c, &p.ents[at], 8);
+            } else {
+              float f;
+              std::memcpy(&f, &p.ents[at], 4);
+              c = f;
+            }
+            std::memcpy(&off, &p.ents[at + es], 4);
             ex = "fma(" + K(pack_real((size_t)d.ent + rm.beg + e, c)) + ", t" + std::to_string(ob | reg(off)) + ", " +
                  ex + ")";
           }
@@ -526,9 +552,9 @@ struct Gen {
 
   bool run(std::string& src) {
     const int T = sd.T, m = sd.m, h = sd.h, RB = real ? 4 : sd.prb, NR = 1 << RB;
-    const int lvpe = c128 ? 0 : 1;
+    const int lvpe = es == 16 ? 0 : (es == 8 ? 1 : 2);
     if (RB < 1 || RB > 4 || T < RB || T > 13 || m < lvpe || m + h != T || p.B - T > 24) return false;
-    if (real && (p.dtype != NWQ_F64 || p.ent_bytes != 16)) return false;
+    if (real && p.ent_bytes != (p.dtype == NWQ_F64 ? 16u : 8u)) return false;
     const size_t PE = padded_elems(T);
     const uint32_t NG = 1u << (T - RB);
     std::vector<std::pair<std::array<uint8_t, 4>, std::vector<int>>> rph;
@@ -550,13 +576,13 @@ struct Gen {
         const uint32_t lowm = (1u << P.u[t]) - 1u;
         o << "    gb = ((gb & " << (~lowm) << "u) << 1) | (gb & " << lowm << "u);\n";
       }
-      o << "    C* gt = tile + " << (c128 ? "(gb + (gb >> 3))" : "(gb + ((gb >> 4) << 1))") << ";\n";
+      o << "    C* gt = tile + " << swz_expr(es, "gb") << ";\n";
       uint32_t roff[16];
       for (int i = 0; i < NR; i++) {
         uint32_t l = 0;
         for (int b = 0; b < RB; b++)
           if ((i >> b) & 1) l |= 1u << P.u[b];
-        roff[i] = swz(c128, l);
+        roff[i] = swz(es, l);
         o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
       }
       if (real) {
@@ -577,8 +603,8 @@ struct Gen {
     const uint32_t nb = 1u << pb;
     smem = btab_byte + 4 * (size_t)nb * 8;
     if (smem > (size_t)kMaxDynSmem) return false;
-    const char* RT = (c128 || real) ? "double" : "float";
-    const char* CT = real ? "double" : (c128 ? "double2" : "float2");
+    const char* RT = (c128 || (real && es == 8)) ? "double" : "float";
+    const char* CT = real ? RT : (c128 ? "double2" : "float2");
     o << "typedef " << RT << " R;\ntypedef " << CT << " C;\n"
       << "struct Coef { C c[" << npk << "]; };\n"
       << "__device__ __forceinline__ unsigned long long dep(unsigned long long v, unsigned long long mask) {\n"
@@ -604,15 +630,14 @@ struct Gen {
     for (const Tab& t : tabs)
       o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << kJitThreads << "u) dtab[" << t.dst
         << " + j] = pcs[" << t.src << " + j];\n";
-    const int VPE = c128 ? 1 : 2, lvpc = m - lvpe;
+    const int VPE = 16 / es, lvpc = m - lvpe;
     const uint32_t nvec = (1u << T) / VPE;
     const uint32_t NVT = (nvec + kJitThreads - 1) / kJitThreads;  // vectors per thread
     const bool ragged = nvec % kJitThreads != 0;
     // per-thread vector offsets inside a tile (global, registers) and shared-memory slots
     // (swz is additive over the disjoint bits of threadIdx.x * VPE and 256 * i * VPE)
     o << "  __syncthreads();\n"
-      << "  const unsigned s0 = " << (c128 ? "threadIdx.x + (threadIdx.x >> 3)" : "threadIdx.x * 2u + ((threadIdx.x >> 3) << 1)")
-      << ";\n";
+      << "  const unsigned s0 = " << swz_expr(es, "(threadIdx.x * " + std::to_string(VPE) + "u)") << ";\n";
     for (uint32_t i = 0; i < NVT; i++) {
       const std::string v = "(threadIdx.x + " + std::to_string(i * kJitThreads) + "u)";
       const std::string off = "hoff[" + v + " >> " + std::to_string(lvpc) + "] + (unsigned long long)(" + v + " & " +
@@ -622,7 +647,7 @@ struct Gen {
       else
         o << "  const unsigned long long o" << i << " = " << off << ";\n";
     }
-    auto sidx = [&](uint32_t i) { return std::to_string(swz(c128, i * kJitThreads * VPE)); };
+    auto sidx = [&](uint32_t i) { return std::to_string(swz(es, i * kJitThreads * VPE)); };
     auto guard = [&](uint32_t i) -> std::string {
       return (ragged && i == NVT - 1) ? "if (threadIdx.x + " + std::to_string(i * kJitThreads) + "u < " +
                                             std::to_string(nvec) + "u) "
@@ -706,7 +731,7 @@ std::string struct_key(const Plan& p, const SweepDesc& sd) {
         put(&rm, sizeof(RowMeta));
         if (rm.kind != ROW_GEN) continue;
         for (int e = 0; e < rm.cnt[0]; e++) {
-          const size_t at = ((size_t)d.ent + rm.beg + e) * p.ent_bytes + 8;
+          const size_t at = ((size_t)d.ent + rm.beg + e) * p.ent_bytes + (p.dtype == NWQ_F64 ? 8 : 4);
           if (at + 4 <= p.ents.size()) key.append(reinterpret_cast<const char*>(&p.ents[at]), 4);  // entry offset
         }
       }
@@ -735,7 +760,7 @@ bool describe(JitKernel& jk, const Plan& p, const SweepDesc& sd) {
 
 // This sweep's parameter bytes by the structure's recipe (empty on a range error).
 std::vector<unsigned char> pack_params(const Plan& p, const SweepDesc& sd, const std::vector<RecipeItem>& recipe) {
-  const size_t cs = (p.is_complex && p.dtype == NWQ_F64) ? 16 : 8;
+  const size_t cs = p.is_complex ? (p.dtype == NWQ_F64 ? 16 : 8) : (p.dtype == NWQ_F64 ? 8 : 4);
   std::vector<unsigned char> out;
   for (const RecipeItem& it : recipe) {
     if (it.cnt) {
@@ -744,8 +769,8 @@ std::vector<unsigned char> pack_params(const Plan& p, const SweepDesc& sd, const
       out.insert(out.end(), p.pcoef.begin() + a * cs, p.pcoef.begin() + (a + it.cnt) * cs);
     } else {
       const size_t at = ((size_t)sd.ent0 + it.rel) * p.ent_bytes;
-      if (at + 8 > p.ents.size()) return {};
-      out.insert(out.end(), p.ents.begin() + at, p.ents.begin() + at + 8);
+      if (at + cs > p.ents.size()) return {};
+      out.insert(out.end(), p.ents.begin() + at, p.ents.begin() + at + cs);
     }
   }
   if (out.empty()) out.resize(cs, 0);

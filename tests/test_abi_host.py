@@ -141,6 +141,13 @@ def test_specialised_sweep_kernels_compile(dtype):
         assert built == eligible, L.lib().nwq_last_error()
         total += eligible
         p.close()
+    for n in (9, 12):  # density matrices: real operators in register phases
+        g, noise = inputs.dm_noisy_tfim(n, 3)
+        p = sim.Plan(L.DM, n, g, dtype, noise)
+        eligible, built = p.jit_check()
+        assert built == eligible, L.lib().nwq_last_error()
+        total += eligible
+        p.close()
     assert total >= 10
 
 
