@@ -402,6 +402,48 @@ def run_vqe(args):
                       "sample": f"{sample} sets, host wall clock", "rel_energy_err_vs_batched_f64": err}), flush=True)
 
 
+def run_dm32(args):
+    """The headline noisy DM TFIM (n = 13, 20 steps) in FP32 storage and
+    arithmetic (FP64 reductions): gate-updates/s, HBM roofline, and the energy
+    against the FP64 path."""
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build
+    from paper_2401_06861_gb300.sim import Plan, State
+    build.build()
+    stream = torch.cuda.current_stream()
+    gates, noise, zt, ht = workload()
+    e = {}
+    for dtype in (L.F64, L.F32):
+        with Plan(L.DM, N, gates, dtype, noise) as plan, State(L.DM, N, dtype, stream=stream.cuda_stream) as st:
+            info = plan.info()
+            for _ in range(3):
+                st.reset()
+                st.run(plan)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                st.reset()
+                st.run(plan)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sec = a.elapsed_time(b) / args.steps / 1e3
+            e[dtype] = (st.expect(ht, sum=True), sec, info)
+    e64 = e[L.F64][0]
+    en, sec, info = e[L.F32]
+    gb = info["bytes"] / sec / 1e9
+    peak = _peaks()["hbm_gbs"]
+    norm1 = sum(abs(t[2]) for t in ht)
+    line = {"workload": WORKLOAD, "path": "dm_f32", "metric": METRIC, "value": len(gates) * 4.0 ** N / sec,
+            "unit": UNIT, "ms_per_step": sec * 1e3, "dtype": "f32", "sweeps": info["sweeps"],
+            "roofline": {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak},
+            "energy": en, "energy_f64": e64, "rel_energy_err_vs_f64": abs(en - e64) / max(abs(e64), norm1),
+            "f64_ms_per_step": e[L.F64][1] * 1e3}
+    print(json.dumps(line), flush=True)
+
+
 def run_vqe_cobyla(args):
     """VQE outer loop (COBYLA) on the Ising chain: noise-free n = 12 (4 layers,
     96 parameters; 256 batched starts, then COBYLA with one launch per energy)
@@ -551,7 +593,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dm", choices=["dm", "sv", "vqe", "vqe-cobyla", "serve", "traj"])
+    ap.add_argument("--workload", default="dm", choices=["dm", "dm32", "sv", "vqe", "vqe-cobyla", "serve", "traj"])
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
@@ -573,6 +615,8 @@ def main():
         return run_vqe_cobyla(args)
     if args.workload == "traj":
         return run_traj(args)
+    if args.workload == "dm32":
+        return run_dm32(args)
     if args.workload == "vqe":
         return run_vqe(args)
     if args.workload == "serve":
