@@ -105,7 +105,7 @@ enum nwq_plan_flags {
   NWQ_PLAN_PLAIN = 1u,      /* one gate (plus its noise) per pass over the state */
   NWQ_PLAN_NO_MERGE = 2u,   /* fused sweeps, but no algebraic merging of operators */
   NWQ_PLAN_NO_RESCALE = 4u, /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
-  NWQ_PLAN_INTERPRETED = 8u /* complex sweeps: never the run-time specialised kernels (see nwq_plan_jit_check) */
+  NWQ_PLAN_INTERPRETED = 8u /* never the run-time specialised sweep kernels (see nwq_plan_jit_check) */
 };
 
 /* Expectation flags.  NWQ_EXPECT_NORMALIZE divides every value by the FP64
@@ -246,11 +246,12 @@ int nwq_plan_autotune(nwq_state* scratch, const nwq_gate* gates, size_t ng, cons
 int nwq_plan_verify(const nwq_plan* plan);
 
 /* Test hook: generate and compile (host only; nothing is loaded on a device)
- * the run-time specialised kernel of every eligible sweep of a complex plan.
- * Complex sweeps of states with at least NWQ_JIT_MIN_BITS qubits (default 18)
- * run such kernels: one per distinct sweep structure, compiled by NVRTC for
- * sm_103a on first use and cached for the process; set NWQ_JIT=0 to run the
- * interpreted kernel instead.  *eligible: sweeps whose structure and tables
+ * the run-time specialised kernel of every eligible sweep of a plan.  Sweeps
+ * over at least NWQ_JIT_MIN_BITS index bits (default 18: state vectors of
+ * >= 18 qubits, density matrices of >= 9) run such kernels: one per distinct
+ * sweep structure, compiled by NVRTC for sm_103a on first use and cached for
+ * the process (reusable plans compile before their first run, one-shot plans
+ * in the background); set NWQ_JIT=0 to run the interpreted kernels instead.  *eligible: sweeps whose structure and tables
  * fit the specialised kernel; *built: those compiled.  NWQ_EUNSUPPORTED when
  * NVRTC cannot be loaded, with the reason (or the first compiler message) in
  * nwq_last_error(). */
@@ -273,9 +274,14 @@ int nwq_plan_destroy(nwq_plan* plan);
 
 /* ---------------------------------------------------------------- measurement */
 
-/* Expectation values of Pauli strings (SV: <psi|P|psi>; DM: Tr(rho P)),
- * accumulated in FP64.  flags NWQ_EXPECT_TERMS: out_host[t] = <P_t> (the
- * coefficients are ignored); NWQ_EXPECT_SUM: out_host[0] = sum_t coeff_t <P_t>.
+/* Expectation values of Pauli strings (SV: <psi|P|psi>; DM: Tr(rho P)).
+ * Sums are FP64; for complex64 state vectors the products and each warp's
+ * partial sum (at most 1024 products) are FP32, everything above FP64.
+ * State vectors: one read of the state per group of terms whose X support
+ * fits a shared-memory tile (all Z-type strings and the low X supports share
+ * the first pass).  flags NWQ_EXPECT_TERMS: out_host[t] = <P_t> (the
+ * coefficients are ignored); NWQ_EXPECT_SUM: out_host[0] = sum_t coeff_t <P_t>;
+ * NWQ_EXPECT_NORMALIZE: divided by <psi|psi> (Tr rho) of the same pass.
  * Synchronises the stream. */
 int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, size_t nt, double* out_host,
                          uint32_t flags);

@@ -13,7 +13,7 @@ namespace nwq {
 extern std::atomic<unsigned long long> g_launches;
 
 constexpr int kSweepThreads = 256;
-constexpr int kExpectChunk = 16;         // terms per expectation launch
+constexpr int kExpectChunk = 16;         // terms per launch of the general (per-x) expectation kernel
 constexpr int kMaxDynSmem = 200 * 1024;      // dynamic shared memory cap of the sweep kernel
 constexpr int kTableSmemLimit = 112 * 1024;  // stage a sweep's tables in shared memory up to this total
 
@@ -41,8 +41,9 @@ struct PhaseTables {
   const void* pc;
 };
 
-// Complex sweeps with register phases run the phase kernel; everything else
-// (real DM sweeps, tiny tiles) the row kernel.
+// Interpreted sweeps (the run-time specialised kernels of jit.cpp take the
+// sweeps of large states): complex sweeps with register phases run the phase
+// kernel; everything else (real DM sweeps, tiny tiles) the row kernel.
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
                          const void* ents, const PhaseTables* pt, int sm_count, cudaStream_t s);
 cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s);
