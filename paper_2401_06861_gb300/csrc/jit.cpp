@@ -462,6 +462,11 @@ struct Gen {
           << ".x, i0.y, " << K(pb + 1) << ".y * i1.x)};\n";
         o << "      " << r(ob | M) << " = C{fma(" << K(pb + 3) << ".x, i1.x, -" << K(pb + 2) << ".y * i0.y), fma("
           << K(pb + 3) << ".x, i1.y, " << K(pb + 2) << ".y * i0.x)};\n";
+      } else if (f == PD_XROTU) {  // unit diagonal: 4 FMA per pair
+        o << "      " << r(ob) << " = C{fma(-" << K(pb + 1) << ".y, i1.y, i0.x), fma(" << K(pb + 1)
+          << ".y, i1.x, i0.y)};\n";
+        o << "      " << r(ob | M) << " = C{fma(-" << K(pb + 2) << ".y, i0.y, i1.x), fma(" << K(pb + 2)
+          << ".y, i0.x, i1.y)};\n";
       } else {
         for (int i = 0; i < D; i++) {
           o << "      { C a{R(0), R(0)};";

@@ -98,7 +98,9 @@ namespace nwq {
 enum : uint8_t { PO_DIAG = 0, PO_PERM = 1, PO_DENSE = 2, PO_KRON = 3 };
 
 // DENSE structure classes (select the arithmetic at compile time).
-enum : uint8_t { PD_GEN = 0, PD_REAL = 1, PD_XROT = 2 };
+// PD_XROTU: X-rotation with a unit diagonal [[1, i y01], [i y10, 1]] (its cos
+// factor deferred by the planner into a later diagonal): 2 FMA per entry pair.
+enum : uint8_t { PD_GEN = 0, PD_REAL = 1, PD_XROT = 2, PD_XROTU = 3 };
 
 // Dispatch code of a phase operator (one switch in the kernel):
 //   0..15   DIAG, register-bit mask SU       16 + m  PERM on register mask m

@@ -116,7 +116,7 @@ bool verify_plan(const Plan& p, std::string& err) {
           for (int b = 0; b < 4; b++)
             if ((po.mask >> b) & 1) {
               need = 4 * (size_t)(b + 1);
-              if (((po.form >> (2 * b)) & 3) > PD_XROT) return fail_at(err, "KRON form", s, ph);
+              if (((po.form >> (2 * b)) & 3) > PD_XROTU) return fail_at(err, "KRON form", s, ph);
             }
         } else {
           const int M = code & 15, cls = code >> 4;

@@ -608,6 +608,35 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
     if (k == 1 && m[0].imag() == 0.0 && m[3].imag() == 0.0 && m[1].real() == 0.0 && m[2].real() == 0.0) return PD_XROT;
     return PD_GEN;
   };
+  // FP64 plans whose sweeps all run in register phases defer the cos factor of
+  // X-rotations (|tan| <= 1) into a global scalar: the rotation keeps a unit
+  // diagonal (2 FP64 instructions per element instead of 4) and the scalar is
+  // folded into the next diagonal operator (free), or applied as a
+  // one-coefficient diagonal when its binary exponent leaves [-200, 200] and
+  // at the end of the plan.
+  bool defer = f64;
+  for (const SweepDesc& sd : plan.sweeps) {
+    if (sd.nops == 0) continue;
+    bool ok = sd.T >= RB;
+    for (int s = 0; s < sd.nops && ok; s++) {
+      const BitOp& op = ops[order[sd.op0 + s]];
+      ok = is_diagonal(op) || op.k <= 2;
+    }
+    defer &= ok;
+  }
+  cd gscale = 1.0;
+  double saved = 0.0;  // FP instructions per element removed by the deferral
+  auto push_scalar = [&]() {  // one-coefficient diagonal: every element times gscale
+    PhaseOp po;
+    std::memset(&po, 0, sizeof(po));
+    po.cls = PO_DIAG;
+    po.coef = (uint32_t)ncoef;
+    po.code = 0;
+    push_coef(gscale);
+    plan.pops.push_back(po);
+    gscale = 1.0;
+    saved -= 4.0;
+  };
   for (SweepDesc& sd : plan.sweeps) {
     sd.prb = (uint8_t)RB;
     sd.ph0 = (uint32_t)plan.phases.size();
@@ -690,6 +719,10 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
         po.dnu = (uint8_t)nout;
         po.code = SU;
         int dim = 1 << dg.k;
+        if (gscale != cd(1.0)) {  // the deferred scalar rides on this diagonal
+          for (cd& f : dg.f) f *= gscale;
+          gscale = 1.0;
+        }
         for (int nidx = 0; nidx < dim; nidx++) {
           int uval = nidx & ((1 << kU) - 1), oval = nidx >> kU, old = 0, c = 0;
           for (int q = 0; q < RB; q++)
@@ -716,12 +749,26 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
         po.mask = kron_mask;
         po.code = PCODE_KRON;
         for (int p = 0; p < RB; p++) {
-          po.form |= (uint8_t)(form_of(kron[p], 1) << (2 * p));
-          for (int e = 0; e < 4; e++) push_coef(kron[p][e]);
+          uint8_t f = form_of(kron[p], 1);
+          const cd c0 = kron[p][0];
+          if (defer && ((kron_mask >> p) & 1) && f == PD_XROT && c0 == kron[p][3] && c0.real() != 0.0 &&
+              std::abs(kron[p][1]) <= std::abs(c0) && std::abs(kron[p][2]) <= std::abs(c0)) {
+            f = PD_XROTU;
+            push_coef(1.0);
+            push_coef(kron[p][1] / c0);
+            push_coef(kron[p][2] / c0);
+            push_coef(1.0);
+            gscale *= c0;
+            saved += 2.0;
+          } else {
+            for (int e = 0; e < 4; e++) push_coef(kron[p][e]);
+          }
+          po.form |= (uint8_t)(f << (2 * p));
         }
         plan.pops.push_back(po);
         kron_any = false;
         kron_mask = 0;
+        if (std::fabs(std::log2(std::abs(gscale))) > 200.0) push_scalar();  // keep the state's scale in range
       };
       auto kron_reset = [&]() {
         for (int p = 0; p < 4; p++) {
@@ -838,6 +885,18 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
     sd.npop = (uint32_t)plan.pops.size() - sd.pop0;
     sd.npc = (uint32_t)ncoef - sd.pc0;
   }
+  if (defer && gscale != cd(1.0)) {  // what no diagonal absorbed: onto the last phase of the plan
+    for (size_t s = plan.sweeps.size(); s-- > 0;) {
+      SweepDesc& sd = plan.sweeps[s];
+      if (sd.nph == 0) continue;
+      push_scalar();
+      plan.phases.back().nops++;
+      sd.npop++;
+      sd.npc++;
+      break;
+    }
+  }
+  plan.fma_per_elem -= saved;
 }
 
 // ------------------------------------------------------------------ sweeps

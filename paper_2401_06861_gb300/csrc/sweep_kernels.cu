@@ -343,6 +343,10 @@ __device__ __forceinline__ void phase_dense(typename Cplx<R>::T (&r)[NR], const 
       const C a = in[0], b = in[1];
       r[o] = C{fma(m[0].x, a.x, -m[1].y * b.y), fma(m[0].x, a.y, m[1].y * b.x)};
       r[o | MASK] = C{fma(m[3].x, b.x, -m[2].y * a.y), fma(m[3].x, b.y, m[2].y * a.x)};
+    } else if constexpr (FORM == PD_XROTU) {  // K == 1, unit diagonal
+      const C a = in[0], b = in[1];
+      r[o] = C{fma(-m[1].y, b.y, a.x), fma(m[1].y, b.x, a.y)};
+      r[o | MASK] = C{fma(-m[2].y, a.y, b.x), fma(m[2].y, a.x, b.y)};
     } else {
 #pragma unroll
       for (int i = 0; i < D; i++) {
@@ -372,6 +376,7 @@ __device__ __forceinline__ void kron_bit(typename Cplx<R>::T (&r)[NR], const typ
       const typename Cplx<R>::T* m = cf + 4 * P;
       const int f = (form >> (2 * P)) & 3;
       if (f == PD_XROT) phase_dense<NR, 1 << P, PD_XROT, R>(r, m);
+      else if (f == PD_XROTU) phase_dense<NR, 1 << P, PD_XROTU, R>(r, m);
       else if (f == PD_REAL) phase_dense<NR, 1 << P, PD_REAL, R>(r, m);
       else phase_dense<NR, 1 << P, PD_GEN, R>(r, m);
     }

@@ -224,3 +224,28 @@ def test_table_check_is_on_with_the_environment_variable():
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
                        env=dict(os.environ, NWQ_CHECKS="1"))
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
+
+
+def test_complex128_x_rotations_keep_a_unit_diagonal():
+    # FP64 complex plans carry the cos factor of X-rotations as a deferred
+    # scalar (2 FP64 instructions per element instead of 4); long chains push
+    # the scalar back into the state before its exponent leaves range
+    rng = np.random.default_rng(3)
+    for n in (10, 18):  # 18 qubits: large enough for the specialised kernels
+        gates = []
+        for i in range(900 if n == 10 else 240):
+            q = int(rng.integers(n))
+            gates.append(inputs.gate("RX", (q,), (float(rng.uniform(-1.5, 1.5)),)))
+            if i % 3 == 2:
+                gates.append(inputs.gate("CX", (q, (q + 1) % n)))
+        for flags in (L.PLAN_FUSED, L.PLAN_NO_MERGE):
+            f64 = sim.Plan(L.SV, n, gates, L.F64, flags=flags)
+            f32 = sim.Plan(L.SV, n, gates, L.F32, flags=flags)
+            f64.verify()
+            e, b = f64.jit_check()
+            assert e == b and (e > 0) == (n == 18), L.lib().nwq_last_error()
+            assert f64.info()["fma_per_elem"] < f32.info()["fma_per_elem"]
+            f64.close()
+            f32.close()
+    g, _ = inputs.large_sv_tfim(20, 4)
+    assert sim.Plan(L.SV, 20, g, L.F64).info()["fma_per_elem"] < sim.Plan(L.SV, 20, g, L.F32).info()["fma_per_elem"]

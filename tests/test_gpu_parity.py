@@ -411,6 +411,29 @@ def _closed_form_rabi(n, h, dt, steps, idx):
     return amp
 
 
+@pytest.mark.parametrize("flags", [L.PLAN_FUSED, L.PLAN_NO_MERGE])
+def test_sv_long_x_rotation_chains(flags):
+    # 900 X-rotations with |tan| <= 1 between permutations and no diagonal:
+    # complex128 plans carry their cos factors as one deferred scalar, which
+    # must be re-applied whenever its exponent leaves range and at the end
+    n = 10
+    rng = np.random.default_rng(41)
+    gates = []
+    for i in range(900):
+        q = int(rng.integers(n))
+        gates.append(inputs.gate("RX", (q,), (float(rng.uniform(-1.5, 1.5)),)))
+        if i % 3 == 2:
+            gates.append(inputs.gate("CX", (q, (q + 1 + int(rng.integers(n - 1))) % n)))
+    psi0 = inputs.random_state(n, 43)
+    ref = oracle.sv_run(n, gates, psi0)
+    for dtype in DTYPES:
+        with State(L.SV, n, dtype) as st, Plan(L.SV, n, gates, dtype, flags=flags) as p:
+            st.load(psi0)
+            st.run(p)
+            assert maxerr(st.copy(), ref) <= 10 * TOL[dtype]
+            assert abs(st.norm() - np.sum(np.abs(ref) ** 2)) <= 10 * TOL[dtype]
+
+
 @pytest.mark.parametrize("n,dtype", [(33, L.F64), (34, L.F32)])
 def test_large_sv_rabi_closed_form(n, dtype):
     import torch
