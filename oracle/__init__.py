@@ -13,6 +13,10 @@ here to something other than itself: dense unitaries built from matrix
 exponentials of Pauli generators, closed forms (Rabi oscillation, global
 phase, depolarising and relaxation decay laws), exact diagonalisation and
 the invariants of density matrices.
+
+``tfim_fermion`` (numpy) gives exact expectation values of the Trotterised
+Ising chain at any size through free fermions; it is pinned to this
+package's state-vector oracle on small chains.
 """
 from __future__ import annotations
 

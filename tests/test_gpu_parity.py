@@ -455,6 +455,29 @@ def test_large_sv_rabi_closed_form(n, dtype):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("n,dtype", [(33, L.F64), (34, L.F32)])
+def test_large_sv_tfim_matches_free_fermions(n, dtype):
+    # the full-size depth-10 TFIM chains, run as the benchmark runs them (one
+    # reusable fused plan), against exact free-fermion expectation values
+    from oracle import tfim_fermion
+    gates, h = inputs.large_sv_tfim(n, 10)
+    ref = tfim_fermion.tfim_observables(n, gates)
+    terms = inputs.tfim_terms(n, 1.0, h)
+    eref = -float(np.sum(ref["zz"])) - float(np.dot(h, ref["x"]))
+    norm = dtype == L.F32  # FP32: values of the renormalised state (the flagged option)
+    with Plan(L.SV, n, gates, dtype) as p, State(L.SV, n, dtype) as st:
+        st.run(p)
+        zz = np.real(st.expect(inputs.zz_terms(n), normalize=norm))
+        x = np.real(st.expect(inputs.x_terms(n), normalize=norm))
+        z0 = float(np.real(st.expect([(0, 1, 1.0)], normalize=norm)[0]))
+        e = st.expect(terms, sum=True, normalize=norm)
+        nrm = st.norm()
+    err = max(maxerr(zz, ref["zz"]), maxerr(x, ref["x"]), abs(z0 - ref["z0"]))
+    print(f"n={n} dtype={dtype}: max term error {err:.3e}, E {e:.12f} vs {eref:.12f}, norm-1 {nrm - 1:.2e}")
+    assert err <= TOL[dtype]
+    assert rel_energy(e, eref, terms) <= (1e-12 if dtype == L.F64 else 1e-6)
+
+
 def test_sv_n28_fp32_vs_fp64_tfim():
     n = 28
     gates, h = inputs.large_sv_tfim(n, steps=3)
