@@ -211,7 +211,7 @@ int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op
 
 /* Plan shape, chosen by nwq_plan_autotune or by hand (0 = the default):
  *   tile_bits      shared-memory tile of a sweep = 2^tile_bits state elements
- *                  (default 11 for 16-byte, 12 for 8-byte, 13 for 4-byte elements);
+ *                  (default 10 for 16-byte, 12 for 8-byte, 13 for 4-byte elements);
  *   fusion_bits    widest operator the planner merges gates into, in state-index
  *                  bits, 2..4 (default 4; a density-matrix qubit spans 2 bits);
  *   register_bits  complex sweeps: state elements per thread group = 2^register_bits,

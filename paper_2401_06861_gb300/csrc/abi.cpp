@@ -59,8 +59,9 @@ extern "C" size_t nwq_state_bytes(int kind, int n, int dtype) {
 static void plan_options(int kind, int dtype, uint32_t flags, PlanOptions& o) {
   bool cplx = kind == NWQ_SV;
   size_t esz = (cplx ? 2 : 1) * (dtype == NWQ_F64 ? 8 : 4);
-  // two 32 KiB ping-pong tiles per CTA (several resident CTAs per SM), >= 128 contiguous bytes
-  o.tile_bits = esz == 16 ? 11 : esz == 8 ? 12 : 13;
+  // ping-pong tiles of 32 KiB (16 KiB for complex128: its FP64-bound phases
+  // run faster with 4 resident CTAs per SM than with 2), >= 128 contiguous bytes
+  o.tile_bits = esz == 16 ? 10 : esz == 8 ? 12 : 13;
   o.min_low = esz == 16 ? 3 : esz == 8 ? 4 : 5;
   if (const char* tb = std::getenv("NWQ_TILE_BITS")) {
     int v = std::atoi(tb);

@@ -21,6 +21,7 @@
 #include <array>
 #include <atomic>
 #include <condition_variable>
+#include <cstdio>
 #include <cstdlib>
 #include <deque>
 #include <thread>
@@ -639,18 +640,17 @@ struct Gen {
     const uint32_t nvec = (1u << T) / VPE;
     const uint32_t NVT = (nvec + kJitThreads - 1) / kJitThreads;  // vectors per thread
     const bool ragged = nvec % kJitThreads != 0;
-    // per-thread vector offsets inside a tile (global, registers) and shared-memory slots
-    // (swz is additive over the disjoint bits of threadIdx.x * VPE and 256 * i * VPE)
+    // per-thread vector offsets inside a tile (global) and shared-memory slots
+    // (swz is additive over the disjoint bits of threadIdx.x * VPE and 256 * i * VPE).
+    // The global offsets are read from the shared table where used, once per
+    // tile copy, rather than held in 64-bit registers across the tile loop (the
+    // registers go to the phases); the copy guard covers threads past the last vector.
     o << "  __syncthreads();\n"
       << "  const unsigned s0 = " << swz_expr(es, "(threadIdx.x * " + std::to_string(VPE) + "u)") << ";\n";
     for (uint32_t i = 0; i < NVT; i++) {
       const std::string v = "(threadIdx.x + " + std::to_string(i * kJitThreads) + "u)";
-      const std::string off = "hoff[" + v + " >> " + std::to_string(lvpc) + "] + (unsigned long long)(" + v + " & " +
-                              std::to_string((1u << lvpc) - 1u) + "u) * " + std::to_string(VPE);
-      if (ragged && i == NVT - 1)  // threads past the last vector read no table entry
-        o << "  const unsigned long long o" << i << " = " << v << " < " << nvec << "u ? " << off << " : 0ull;\n";
-      else
-        o << "  const unsigned long long o" << i << " = " << off << ";\n";
+      o << "#define o" << i << " (hoff[" << v << " >> " << lvpc << "] + (unsigned long long)(" << v << " & "
+        << ((1u << lvpc) - 1u) << "u) * " << VPE << ")\n";
     }
     auto sidx = [&](uint32_t i) { return std::to_string(swz(es, i * kJitThreads * VPE)); };
     auto guard = [&](uint32_t i) -> std::string {
@@ -902,6 +902,12 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
       return true;
     }
     js.per_sm = per_sm < 1 ? 1 : per_sm;
+    if (const char* v = std::getenv("NWQ_JIT_VERBOSE"); v && v[0] == '1') {  // resources of each sweep's kernel
+      cudaFuncAttributes fa{};
+      cudaFuncGetAttributes(&fa, fn);
+      std::fprintf(stderr, "jit sweep %zu: T %d, %d registers, %d local bytes, smem %zu, %d CTAs per SM\n", sweep,
+                   p.sweeps[sweep].T, fa.numRegs, (int)fa.localSizeBytes, js.smem, js.per_sm);
+    }
   }
   const SweepDesc& sd = p.sweeps[sweep];
   unsigned long long ntiles = 1ull << (p.B - sd.T);
