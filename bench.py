@@ -299,8 +299,11 @@ def run_sv(args):
     build.build()
     stream = torch.cuda.current_stream()
     peak = _peaks()["hbm_gbs"]
-    cases = [(args.sv_n, L.F32, 0, args.steps), (args.sv_n - 1, L.F64, 0, max(1, args.steps // 3)),
-             (args.sv_n, L.F32, L.PLAN_PLAIN, 1)]
+    all_cases = {"fused32": (args.sv_n, L.F32, 0, args.steps),
+                 "fused64": (args.sv_n - 1, L.F64, 0, max(1, args.steps // 3)),
+                 "plain32": (args.sv_n, L.F32, L.PLAN_PLAIN, 1),
+                 "tc32": (args.sv_n, L.F32, L.PLAN_TC, max(1, args.steps // 3))}
+    cases = [all_cases[c] for c in args.sv_cases.split(",")]
     for n, dtype, flags, steps in cases:
         gates, h = inputs.large_sv_tfim(n, steps=args.sv_depth)
         plan = Plan(L.SV, n, gates, dtype, None, flags)
@@ -321,7 +324,12 @@ def run_sv(args):
         st.close()
         plan.close()
         gb = info["bytes"] / sec / 1e9
-        if dtype == L.F32:  # complex64: HBM bound
+        if flags & L.PLAN_TC:  # dense blocks on the tensor cores: HBM bound, TF32 pipe reported beside it
+            tf = 2.0 * info["fma_per_elem"] * 2.0 ** n / sec / 1e12
+            tf_peak = _peaks().get("bf16_tflops", 1900.0) * 1.1 / 2.25  # TF32 = measured bf16 x nominal TF32/bf16 ratio
+            roof = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak,
+                    "tf32_tflops": tf, "tf32_peak": tf_peak, "tf32_frac": tf / tf_peak}
+        elif dtype == L.F32:  # complex64: HBM bound
             roof = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak,
                     "fp_ops_per_amp": info["fma_per_elem"]}
         else:  # complex128: FP64 pipe bound (2 FP64 instructions / clock / SM); the plan counts them per amplitude
@@ -329,7 +337,8 @@ def run_sv(args):
             fpk = 152 * 2 * 2.07e9
             roof = {"bound": "alu", "achieved": fp64, "peak": fpk, "unit": "FP64 instructions/s", "frac": fp64 / fpk,
                     "fp_ops_per_amp": info["fma_per_elem"], "hbm_gbs": gb, "hbm_frac": gb / peak}
-        line = {"workload": f"sv_tfim_n{n}_depth{args.sv_depth}", "plan": "plain" if flags else "fused",
+        pname = "tc" if flags & L.PLAN_TC else "plain" if flags else "fused"
+        line = {"workload": f"sv_tfim_n{n}_depth{args.sv_depth}", "plan": pname,
                 "dtype": "c64" if dtype == L.F32 else "c128", "metric": "gate-updates/s",
                 "value": len(gates) * 2.0 ** n / sec, "unit": "gate-updates/s", "s_per_circuit": sec,
                 "sweeps": info["sweeps"], "operators": info["ops"], "roofline": roof, "energy": e, "norm": nrm}
@@ -597,6 +606,8 @@ def main():
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
+    ap.add_argument("--sv-cases", default="fused32,fused64,plain32,tc32",
+                    help="comma list of fused32, fused64, plain32, tc32 (tensor-core blocks)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serial-seconds", type=float, default=5.0)
     ap.add_argument("--serve-slots", type=int, default=8)

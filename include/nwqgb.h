@@ -105,8 +105,21 @@ enum nwq_plan_flags {
   NWQ_PLAN_PLAIN = 1u,      /* one gate (plus its noise) per pass over the state */
   NWQ_PLAN_NO_MERGE = 2u,   /* fused sweeps, but no algebraic merging of operators */
   NWQ_PLAN_NO_RESCALE = 4u, /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
-  NWQ_PLAN_INTERPRETED = 8u /* never the run-time specialised sweep kernels (see nwq_plan_jit_check) */
+  NWQ_PLAN_INTERPRETED = 8u, /* never the run-time specialised sweep kernels (see nwq_plan_jit_check) */
+  NWQ_PLAN_TC = 16u          /* dense five-qubit blocks on the tensor cores (see below) */
 };
+
+/* Tensor-core plans (NWQ_PLAN_TC; complex64 state vectors of >= 12 qubits,
+ * else NWQ_EUNSUPPORTED).  The gate stream is fused into dense blocks of 5
+ * qubits (paper Sec. III, "we optimize the quantum circuit", read as gate
+ * fusion): a gate joins the block, at or after the latest block touching its
+ * qubits, that stays within 5 qubits and grows least (earliest on a tie),
+ * else opens a new block; each block's 32 x 32 matrix is multiplied out in
+ * FP64 (blocks under 5 qubits are padded with idle qubits).  One pass over
+ * the state per block applies it as a dense contraction on the tensor cores
+ * (tcgen05, TF32 inputs split as hi + lo with the three products
+ * hi*hi + hi*lo + lo*hi, FP32 accumulation).  nwq_plan_info: sweeps = ops =
+ * blocks; fma_per_elem = 384 TF32 multiply-adds per amplitude per block. */
 
 /* Expectation flags.  NWQ_EXPECT_NORMALIZE divides every value by the FP64
  * norm <psi|psi> (SV) or trace (DM) measured in the same call: the physical
@@ -244,6 +257,19 @@ int nwq_plan_autotune(nwq_state* scratch, const nwq_gate* gates, size_t ng, cons
  * nwq_last_error().  With the environment variable NWQ_CHECKS=1 every plan
  * is verified when it is created.  Host only. */
 int nwq_plan_verify(const nwq_plan* plan);
+
+/* Test hook: the blocks of a tensor-core plan (count = sweeps of
+ * nwq_plan_info): qubits[5 b + i] = qubit of local index bit i of block b
+ * (ascending), mats[2048 b + 2 (32 r + c) + {0, 1}] = re / im of its FP64
+ * matrix entry (r, c), applied in block order.  Either pointer may be NULL.
+ * NWQ_EINVAL if the plan is not a tensor-core plan.  Host only. */
+int nwq_plan_tc_blocks(const nwq_plan* plan, int* qubits, double* mats);
+
+/* Test hook: number of bounded waits (MMA completion) that ran out in the
+ * tensor-core kernel on the current device since the library was loaded;
+ * 0 in a healthy run.  A wait that runs out leaves its tile unwritten.
+ * Synchronises the device. */
+int nwq_tc_timeouts(int* count);
 
 /* Test hook: generate and compile (host only; nothing is loaded on a device)
  * the run-time specialised kernel of every eligible sweep of a plan.  Sweeps

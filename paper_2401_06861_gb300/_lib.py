@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libnwqgb.so")
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 F32, F64 = 1, 2
 SV, DM = 1, 2
-PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED = 0, 1, 2, 4, 8
+PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED, PLAN_TC = 0, 1, 2, 4, 8, 16
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
 NOALLOC_MAX_TERMS = 256
@@ -102,6 +102,8 @@ def lib():
                                     P(PlanTuning), P(dbl), i32, P(i32)]),
         "nwq_plan_jit_check": (i32, [vp, P(i32), P(i32)]),
         "nwq_plan_verify": (i32, [vp]),
+        "nwq_plan_tc_blocks": (i32, [vp, P(i32), P(dbl)]),
+        "nwq_tc_timeouts": (i32, [P(i32)]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),

@@ -92,7 +92,8 @@ static int plan_upload(Plan& p, cudaStream_t s) {
   size_t o_ph = al(ob + p.ents.size());
   size_t o_po = al(o_ph + p.phases.size() * sizeof(PhaseDesc));
   size_t o_pc = al(o_po + p.pops.size() * sizeof(PhaseOp));
-  size_t total = al(o_pc + p.pcoef.size()) + 16;
+  size_t o_tc = al(o_pc + p.pcoef.size());
+  size_t total = o_tc + p.tctab.size() * sizeof(float) + 16;
   void* d = nullptr;
   if (p.stream_ordered) {
     CK(cudaMallocAsync(&d, total, s), "plan table allocation");
@@ -111,6 +112,10 @@ static int plan_upload(Plan& p, cudaStream_t s) {
        "plan upload");
   if (!p.pcoef.empty())
     CK(cudaMemcpyAsync((char*)d + o_pc, p.pcoef.data(), p.pcoef.size(), cudaMemcpyHostToDevice, s), "plan upload");
+  if (!p.tctab.empty())
+    CK(cudaMemcpyAsync((char*)d + o_tc, p.tctab.data(), p.tctab.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+       "plan upload");
+  p.tc_off = o_tc;
   p.pt_off[0] = o_ph;
   p.pt_off[1] = o_po;
   p.pt_off[2] = o_pc;
@@ -124,6 +129,15 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
   NvtxRange range("nwq plan run");
   int rc = plan_upload(p, s);
   if (rc) return rc;
+  if (p.tc) {  // dense five-qubit blocks on the tensor cores, one pass each
+    const float* tab = (const float*)((const char*)p.dev + p.tc_off);
+    for (size_t i = 0; i < p.tcg.size(); i++) {
+      NvtxRange sweep_range("nwq tc block");
+      cudaError_t e = launch_tc_block(data, p.tcg[i], tab + i * kTcMatFloats, sm_count, s);
+      if (e != cudaSuccess) return cuda_fail(e, "tensor-core block launch");
+    }
+    return NWQ_OK;
+  }
   const DevOp* ops = (const DevOp*)p.dev;
   const void* ents = (const char*)p.dev + p.ops.size() * sizeof(DevOp);
   PhaseTables pt{(const PhaseDesc*)((const char*)p.dev + p.pt_off[0]), (const PhaseOp*)((const char*)p.dev + p.pt_off[1]),
@@ -338,6 +352,21 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
   std::string err;
   bool ok = kind == NWQ_SV ? lower_sv(gates, ng, n, ops, err) : lower_dm(gates, ng, n, nm, ops, err);
   if (!ok) return fail(NWQ_EINVAL, err);
+  if (flags & NWQ_PLAN_TC) {
+    if (kind != NWQ_SV || dtype != NWQ_F32 || n < kTcMinQubits)
+      return fail(NWQ_EUNSUPPORTED, "tensor-core plans take complex64 state vectors of at least 12 qubits");
+    if (!build_tc_plan(ops, pl->p, err)) return fail(NWQ_EINVAL, err);
+    static const bool tc_checks = [] {
+      const char* e = std::getenv("NWQ_CHECKS");
+      return e && e[0] == '1';
+    }();
+    if (tc_checks) {
+      std::string cerr;
+      if (!verify_plan(pl->p, cerr)) return fail(NWQ_EINVAL, cerr);
+    }
+    *out = pl.release();
+    return NWQ_OK;
+  }
   PlanOptions o;
   plan_options(kind, dtype, flags, o);
   if (tuning) {
@@ -439,11 +468,13 @@ extern "C" int nwq_plan_info(const nwq_plan* plan, int* sweeps, int* ops, double
   if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
   int ns = 0;
   for (auto& s : plan->p.sweeps) ns += s.nops > 0;
+  if (plan->p.tc) ns = (int)plan->p.tcb.size();
   if (sweeps) *sweeps = ns;
-  if (ops) *ops = (int)plan->p.ops.size();
+  if (ops) *ops = plan->p.tc ? ns : (int)plan->p.ops.size();
   if (bytes) *bytes = plan->p.bytes;
   if (fma_per_elem) *fma_per_elem = plan->p.fma_per_elem;
-  if (table_bytes) *table_bytes = plan->p.ops.size() * sizeof(DevOp) + plan->p.ents.size();
+  if (table_bytes)
+    *table_bytes = plan->p.ops.size() * sizeof(DevOp) + plan->p.ents.size() + plan->p.tctab.size() * sizeof(float);
   return NWQ_OK;
 }
 
@@ -452,10 +483,35 @@ extern "C" int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_ga
   int s = 0;
   for (auto& sd : plan->p.sweeps)
     if (sd.nops > 0 && sweep_nops) sweep_nops[s++] = sd.nops;
-  for (size_t k = 0; k < plan->p.ops.size(); k++) {
+  if (plan->p.tc && sweep_nops)
+    for (size_t k = 0; k < plan->p.tcb.size(); k++) sweep_nops[k] = 1;
+  for (size_t k = 0; k < plan->p.op_gate0.size(); k++) {
     if (op_gate) op_gate[k] = plan->p.op_gate0[k];
     if (op_ngates) op_ngates[k] = plan->p.op_ngates[k];
   }
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_tc_blocks(const nwq_plan* plan, int* qubits, double* mats) {
+  if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
+  if (!plan->p.tc) return fail(NWQ_EINVAL, "not a tensor-core plan");
+  for (size_t b = 0; b < plan->p.tcb.size(); b++) {
+    const TcBlock& blk = plan->p.tcb[b];
+    if (qubits)
+      for (int i = 0; i < kTcBits; i++) qubits[b * kTcBits + i] = blk.q[i];
+    if (mats)
+      for (size_t e = 0; e < blk.U.size(); e++) {
+        mats[(b * 1024 + e) * 2] = blk.U[e].real();
+        mats[(b * 1024 + e) * 2 + 1] = blk.U[e].imag();
+      }
+  }
+  return NWQ_OK;
+}
+
+extern "C" int nwq_tc_timeouts(int* count) {
+  if (!count) return fail(NWQ_EINVAL, "count is NULL");
+  CK(cudaDeviceSynchronize(), "device synchronize");
+  CK(tc_timeouts(count), "tensor-core status read");
   return NWQ_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "planner.hpp"
 
@@ -26,9 +27,94 @@ uint32_t outside(uint32_t v, uint32_t span) { return v & ~span; }
 
 int popc(uint32_t v) { return __builtin_popcount(v); }
 
+// Tensor-core plans: each block's tile geometry must place every amplitude
+// of the state in exactly one tile position (global offsets are distinct
+// single bits covering the n qubits, qubit 0 first so pairs are 16-byte
+// vectors) and every tile position in a distinct operand slot (the operand
+// weights are exactly the 12 weights of the shared-memory layout).
+bool verify_tc(const Plan& p, std::string& err) {
+  const size_t nb = p.tcb.size();
+  if (p.n < kTcMinQubits || p.n > 34 || p.tcg.size() != nb || p.tctab.size() != nb * kTcMatFloats ||
+      p.op_gate0.size() != nb || p.op_ngates.size() != nb)
+    return fail_at(err, "tensor-core plan tables", 0, -1);
+  static const uint32_t want[kTcTileBits] = {8, 16, 32, 64, 16384, 128 ^ 16, 256 ^ 32, 512 ^ 64, 1024, 2048, 4096, 8192};
+  const uint64_t full = (1ull << p.n) - 1;
+  for (size_t b = 0; b < nb; b++) {
+    const TcBlock& blk = p.tcb[b];
+    const TcGeom& g = p.tcg[b];
+    for (int i = 0; i < kTcBits; i++)
+      if (blk.q[i] < 0 || blk.q[i] >= p.n || (i && blk.q[i] <= blk.q[i - 1]))
+        return fail_at(err, "tensor-core block qubits", b, i);
+    if (blk.U.size() != 1024) return fail_at(err, "tensor-core block matrix", b, -1);
+    uint64_t seen = 0;
+    uint32_t wseen = 0;
+    for (int t = 0; t < kTcTileBits; t++) {
+      const uint64_t w = g.gw[t];
+      if (!w || (w & (w - 1)) || (w & seen) || (w & ~full) || (t && w <= g.gw[t - 1]))
+        return fail_at(err, "tensor-core tile offsets", b, t);
+      seen |= w;
+      int k = 0;
+      while (k < kTcTileBits && want[k] != g.sw[t]) k++;
+      if (k == kTcTileBits || ((wseen >> k) & 1)) return fail_at(err, "tensor-core operand offsets", b, t);
+      wseen |= 1u << k;
+    }
+    if (g.gw[0] != 1) return fail_at(err, "tensor-core tile without qubit 0", b, 0);
+    for (int i = 0; i < kTcBits; i++)
+      if (!((seen >> blk.q[i]) & 1)) return fail_at(err, "tensor-core block qubit outside its tile", b, i);
+    for (int f = 0; f < kTcMaxFree; f++) {
+      const uint64_t w = g.fw[f];
+      if (f < p.n - kTcTileBits) {
+        if (!w || (w & (w - 1)) || (w & seen) || (w & ~full)) return fail_at(err, "tensor-core tile index", b, f);
+        seen |= w;
+      } else if (w) {
+        return fail_at(err, "tensor-core tile index", b, f);
+      }
+    }
+    if (seen != full || g.ntiles != (1u << (p.n - kTcTileBits))) return fail_at(err, "tensor-core tile cover", b, -1);
+    // Emulate the kernel's addressing of one tile (thread tid, step i, pair
+    // element e): each amplitude must land in the operand slot of its column
+    // m (the 7 lowest qubits outside the block) and block index j, 8-byte
+    // aligned (16-byte for the first of a contiguous pair), each slot once.
+    int rows[kTcRowBits], nr = 0;
+    uint64_t bmask = 0;
+    for (int i = 0; i < kTcBits; i++) bmask |= 1ull << blk.q[i];
+    for (int q = 0; nr < kTcRowBits; q++)
+      if (!((bmask >> q) & 1)) rows[nr++] = q;
+    std::vector<char> slot(4096, 0);
+    for (int tid = 0; tid < 128; tid++)
+      for (int i = 0; i < 16; i++) {
+        uint64_t goff = 0;
+        uint32_t soff = 0;
+        for (int k = 1; k < 8; k++)
+          if ((tid >> (k - 1)) & 1) {
+            goff += g.gw[k];
+            soff ^= g.sw[k];
+          }
+        for (int k = 0; k < 4; k++)
+          if ((i >> k) & 1) {
+            goff += g.gw[8 + k];
+            soff ^= g.sw[8 + k];
+          }
+        if (g.sw[0] == 8 && (soff & 15)) return fail_at(err, "tensor-core pair alignment", b, tid);
+        for (int e = 0; e < 2; e++) {
+          const uint64_t amp = goff + (e ? g.gw[0] : 0);
+          const uint32_t s = soff ^ (e ? g.sw[0] : 0);
+          uint32_t j = 0, m = 0;
+          for (int k = 0; k < kTcBits; k++) j |= (uint32_t)((amp >> blk.q[k]) & 1) << k;
+          for (int r = 0; r < kTcRowBits; r++) m |= (uint32_t)((amp >> rows[r]) & 1) << r;
+          const uint32_t want_s = (j >> 4) * 16384u + m * 128u + ((((j >> 1) & 7u) ^ (m & 7u)) << 4) + (j & 1u) * 8u;
+          if (s != want_s || s >= 32768u || (s & 7u) || slot[s >> 3]++)
+            return fail_at(err, "tensor-core operand addressing", b, tid);
+        }
+      }
+  }
+  return true;
+}
+
 }  // namespace
 
 bool verify_plan(const Plan& p, std::string& err) {
+  if (p.tc) return verify_tc(p, err);
   const uint64_t full = p.B >= 64 ? ~0ull : ((1ull << p.B) - 1);
   const size_t nent = p.ent_bytes ? p.ents.size() / p.ent_bytes : 0;
   const size_t cbytes = p.dtype == NWQ_F64 ? 16 : 8;

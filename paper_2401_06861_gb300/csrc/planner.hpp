@@ -9,6 +9,7 @@
 
 #include "../../include/nwqgb.h"
 #include "nwq_internal.h"
+#include "tc.hpp"
 
 #include <cuda_runtime.h>
 
@@ -61,6 +62,12 @@ struct Plan {
   // run-time specialised kernels of this plan's sweeps (built on first launch)
   std::shared_ptr<void> jit;
   bool interpreted = false;  // never use them
+  // tensor-core plans (NWQ_PLAN_TC): dense five-qubit blocks, one pass each
+  bool tc = false;
+  std::vector<TcBlock> tcb;
+  std::vector<TcGeom> tcg;
+  std::vector<float> tctab;  // kTcMatFloats per block (TF32 hi, then lo)
+  size_t tc_off = 0;         // device offset of tctab
   ~Plan();
 };
 
@@ -72,6 +79,11 @@ int gate_matrix(const nwq_gate& g, double theta0, cd* U);
 bool lower_sv(const nwq_gate* g, size_t ng, int n, std::vector<BitOp>& out, std::string& err);
 bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, std::vector<BitOp>& out,
               std::string& err);
+
+// Tensor-core plans (tc_plan.cpp): fuse one- and two-qubit operators into
+// dense five-qubit blocks; fill the plan's block tables.
+bool tc_fuse(const std::vector<BitOp>& ops, int n, std::vector<TcBlock>& out, std::string& err);
+bool build_tc_plan(const std::vector<BitOp>& ops, Plan& plan, std::string& err);
 
 // Merge + sweep grouping + device table layout.
 void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan);

@@ -1,0 +1,341 @@
+// Tensor-core pass of one dense five-qubit block over a complex64 state
+// vector: tcgen05 MMAs of kind TF32 with the accumulator in tensor memory.
+//
+// A tile is 2^12 amplitudes: the block's 5 qubits and the 7 lowest other
+// qubits (so qubits 0..6 are always in the tile and every global access runs
+// over >= 1 KiB contiguous).  Its 128 columns (one per setting of the 7 row
+// qubits) are the rows of the MMA operand A (128 x 64 reals, interleaved
+// re/im of the 32 block amplitudes); B is the 64 x 64 real form of the block
+// matrix.  D = A B^T (128 x 64 FP32) is the updated tile.  FP32 accuracy from
+// TF32 inputs uses the three-term split x = hi + lo, D = lo*hi + hi*lo + hi*hi
+// (the lo*lo term is below FP32 rounding).
+//
+// Operands sit in shared memory in the 128-byte-swizzled K-major layout
+// (rows of 128 bytes, 16-byte chunk c of row r stored at chunk c ^ (r & 7),
+// 8-row groups 1024 bytes apart), in two K halves of 32 reals.  Each CTA
+// (128 threads, one elected thread issuing the MMAs) walks its tiles:
+// loads the next tile into registers while the MMAs of the current one run,
+// waits on an mbarrier the MMA commit arrives on (bounded), moves the
+// accumulator rows from tensor memory to shared memory, and writes the tile
+// back with the same coalesced pattern it was read with.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "kernels.hpp"
+#include "tc.hpp"
+
+namespace nwq {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr uint32_t kSmA = 32768;  // one A operand: 128 rows x 64 FP32, two K halves of 16 KiB
+constexpr uint32_t kSmB = 16384;  // one B operand: 64 rows x 64 FP32, two K halves of 8 KiB
+constexpr uint32_t kOffAhi = 0, kOffAlo = kSmA, kOffBhi = 2 * kSmA, kOffBlo = 2 * kSmA + kSmB;
+constexpr uint32_t kOffGi = 2 * kSmA + 2 * kSmB;  // 16 x u64: amplitude offsets of tile bits 8..11
+constexpr uint32_t kOffSi = kOffGi + 16 * 8;      // 16 x u32: operand offsets of tile bits 8..11
+constexpr uint32_t kOffFw = kOffSi + 16 * 4;      // kTcMaxFree x u64: tile-index bit weights
+constexpr uint32_t kOffBar = kOffFw + 8 * kTcMaxFree;
+constexpr uint32_t kOffTmem = kOffBar + 8;
+constexpr uint32_t kSmUsed = kOffTmem + 8;
+constexpr size_t kTcSmem = kSmUsed + 1024;  // + room to align the operands to 1024 bytes
+constexpr uint32_t kTmemCols = 64;          // accumulator: 128 lanes x 64 FP32 columns
+constexpr uint32_t kWaitPolls = 1u << 20;   // bound on polls of the MMA-completion barrier
+static_assert(kOffBar % 8 == 0, "mbarrier alignment");
+
+// Instruction descriptor: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 = 2),
+// both K-major, N = 64 (bits 17-22 = N/8), M = 128 (bits 24-28 = M/16).
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ int g_tc_timeouts;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, 128-byte swizzle, K-major: start address,
+// leading offset 16 bytes (unused for this layout), 8-row groups 1024 bytes
+// apart, descriptor version 1 (bit 46), swizzle mode 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split4(const float4 v, float4& h, float4& l) {
+  h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+  l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+}
+
+__device__ __forceinline__ void st16(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st8(uint32_t a, float x, float y) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ float4 ld16(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ float2 ld8(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitPolls; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's accumulator lane (load and wait in one statement).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+    tc_block_kernel(float4* __restrict__ psi, const float4* __restrict__ mats, const __grid_constant__ TcGeom g) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sb = (raw + 1023u) & ~1023u;
+  unsigned char* sm = smem_raw + (sb - raw);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  uint64_t* gi_tab = (uint64_t*)(sm + kOffGi);
+  uint32_t* si_tab = (uint32_t*)(sm + kOffSi);
+  uint64_t* fw = (uint64_t*)(sm + kOffFw);
+  const uint32_t bar = sb + kOffBar;
+  const uint32_t sAhi = sb + kOffAhi, sAlo = sb + kOffAlo;
+
+  if (tid < 16) {
+    uint64_t go = 0;
+    uint32_t so = 0;
+    for (int b = 0; b < 4; b++)
+      if ((tid >> b) & 1) {
+        go += g.gw[8 + b];
+        so ^= g.sw[8 + b];
+      }
+    gi_tab[tid] = go;
+    si_tab[tid] = so;
+  }
+  if (tid < kTcMaxFree) fw[tid] = g.fw[tid];
+  // B operands: TF32 hi and lo parts of the block's real 64 x 64 matrix (row n, reals k)
+  for (int idx = tid; idx < 1024; idx += kTcThreads) {
+    const int n = idx >> 4, c = idx & 15;
+    const uint32_t off = (uint32_t)(c >> 3) * 8192u + (uint32_t)n * 128u + ((uint32_t)((c & 7) ^ (n & 7)) << 4);
+    st16(sb + kOffBhi + off, mats[idx]);
+    st16(sb + kOffBlo + off, mats[1024 + idx]);
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sb + kOffTmem),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *(volatile uint32_t*)(sm + kOffTmem);
+  const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 accumulator lanes
+
+  // This thread's amplitude pairs in a tile: tile index t = 2 tid + 256 i
+  // (tile bits 1..7 from tid, 8..11 from i); the pair partner is tile bit 0 = qubit 0.
+  uint64_t goff = 0;
+  uint32_t soff = 0;
+  for (int b = 1; b < 8; b++)
+    if ((tid >> (b - 1)) & 1) {
+      goff += g.gw[b];
+      soff ^= g.sw[b];
+    }
+  const uint32_t w0 = g.sw[0];
+  const bool pair16 = w0 == 8u;  // qubit 0 is block bit 0: the pair is 16 contiguous operand bytes
+
+  float4 r[16];
+  uint32_t tile = blockIdx.x;
+  uint64_t base = 0;
+  if (tile < g.ntiles) {
+    uint32_t x = tile;
+    while (x) {
+      base += fw[__ffs(x) - 1];
+      x &= x - 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; i++) r[i] = __ldcs(psi + ((base + goff + gi_tab[i]) >> 1));
+  }
+  uint32_t phase = 0;
+  bool timed_out = false;
+  for (; tile < g.ntiles; tile += gridDim.x) {
+    // 1. TF32 split into the A operands
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const uint32_t s = soff ^ si_tab[i];
+      float4 h, l;
+      split4(r[i], h, l);
+      if (pair16) {
+        st16(sAhi + s, h);
+        st16(sAlo + s, l);
+      } else {
+        st8(sAhi + s, h.x, h.y);
+        st8(sAhi + (s ^ w0), h.z, h.w);
+        st8(sAlo + s, l.x, l.y);
+        st8(sAlo + (s ^ w0), l.z, l.w);
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+    // 2. one thread issues the 24 MMAs (3 products x 8 K steps of 8 reals) and commits them to the barrier
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int p = 0; p < 3; p++) {
+        const uint32_t a0 = p == 0 ? sAlo : sAhi;
+        const uint32_t b0 = sb + (p == 1 ? kOffBlo : kOffBhi);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const uint32_t ka = (uint32_t)(k >> 2) * 16384u + (uint32_t)(k & 3) * 32u;
+          const uint32_t kb = (uint32_t)(k >> 2) * 8192u + (uint32_t)(k & 3) * 32u;
+          mma_tf32(tmem, sw128_desc(a0 + ka), sw128_desc(b0 + kb), (p | k) != 0);
+        }
+      }
+      mma_commit(bar);
+    }
+    // 3. the next tile's loads are in flight while the MMAs run
+    const uint64_t cur = base;
+    const uint32_t next = tile + gridDim.x;
+    if (next < g.ntiles) {
+      uint32_t x = next;
+      base = 0;
+      while (x) {
+        base += fw[__ffs(x) - 1];
+        x &= x - 1;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; i++) r[i] = __ldcs(psi + ((base + goff + gi_tab[i]) >> 1));
+    }
+    const bool ok = mbar_wait_bounded(bar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    tc_fence_after();
+    // 4. accumulator lane tid (one state column) -> shared memory, in the A layout
+    {
+      float d[64];
+      tmem_ld32(tmem_row, d);
+      tmem_ld32(tmem_row + 32u, d + 32);
+#pragma unroll
+      for (int c = 0; c < 16; c++) {
+        const uint32_t off =
+            (uint32_t)(c >> 3) * 16384u + (uint32_t)tid * 128u + ((uint32_t)((c & 7) ^ (tid & 7)) << 4);
+        st16(sAhi + off, make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]));
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // 5. write the tile back with the load pattern
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const uint32_t s = soff ^ si_tab[i];
+      float4 v;
+      if (pair16) {
+        v = ld16(sAhi + s);
+      } else {
+        const float2 a = ld8(sAhi + s), b = ld8(sAhi + (s ^ w0));
+        v = make_float4(a.x, a.y, b.x, b.y);
+      }
+      __stcs(psi + ((cur + goff + gi_tab[i]) >> 1), v);
+    }
+    __syncthreads();
+  }
+  if (timed_out) {
+    if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
+    mbar_wait_bounded(bar, phase ^ 1u);  // one more bounded wait for the MMAs in flight
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, int sm_count, cudaStream_t s) {
+  static std::atomic<int> attr_dev{-1};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev.load() != dev) {
+    cudaError_t e = cudaFuncSetAttribute(tc_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_block_kernel, kTcThreads, kTcSmem);
+  if (e != cudaSuccess) return e;
+  // at most 2 resident CTAs x 64 tensor-memory columns: allocation never waits
+  per_sm = per_sm < 1 ? 1 : per_sm > 2 ? 2 : per_sm;
+  uint64_t grid = (uint64_t)sm_count * per_sm;
+  if (grid > g.ntiles) grid = g.ntiles;
+  tc_block_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>((float4*)psi, (const float4*)mats_dev, g);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t tc_timeouts(int* count) { return cudaMemcpyFromSymbol(count, g_tc_timeouts, sizeof(int)); }
+
+}  // namespace nwq

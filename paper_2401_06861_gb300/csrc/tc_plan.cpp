@@ -1,0 +1,225 @@
+// Host planner of tensor-core plans: the gate stream fused into dense
+// five-qubit blocks (each one 32 x 32 complex matrix, multiplied out in FP64),
+// the blocks' tile geometry, and the TF32 hi / lo tables of their real form.
+//
+// Fusion (this build's reading of "we optimize the quantum circuit",
+// paper Sec. III, in the form that feeds tensor cores): gates are taken in
+// order; a gate on qubits Q may join any block at or after the latest block
+// that touches Q (it commutes with every block it passes, since none of
+// them touches Q) whose qubit set stays within 5 qubits with Q added; among
+// those the one that grows least, the earliest on a tie; otherwise it opens
+// a new block at the end.  Blocks with fewer than 5 qubits are padded with
+// idle qubits (identity).
+#include <algorithm>
+#include <cstring>
+
+#include "planner.hpp"
+#include "tc.hpp"
+
+namespace nwq {
+
+namespace {
+
+struct Building {
+  std::vector<int> qs;  // local bit i <-> qubit qs[i] (insertion order)
+  std::vector<cd> M;    // 2^|qs| square, row-major
+  int gate0 = 0, ngates = 0;
+};
+
+int local_pos(const Building& b, int q) {
+  for (size_t i = 0; i < b.qs.size(); i++)
+    if (b.qs[i] == q) return (int)i;
+  return -1;
+}
+
+// Add qubit q as the next local bit: M <- I (x) M.
+void add_qubit(Building& b, int q) {
+  const int nq = (int)b.qs.size(), d = 1 << nq, d2 = 2 * d;
+  std::vector<cd> E((size_t)d2 * d2, 0.0);
+  for (int i = 0; i < d2; i++)
+    for (int j = 0; j < d2; j++)
+      if ((i >> nq) == (j >> nq)) E[(size_t)i * d2 + j] = b.M[(size_t)(i & (d - 1)) * d + (j & (d - 1))];
+  b.qs.push_back(q);
+  b.M.swap(E);
+}
+
+// M <- G M for a gate G on qubits already in the block.
+void apply_gate(Building& b, const BitOp& op) {
+  const int d = 1 << b.qs.size(), dk = 1 << op.k;
+  int pos[4];
+  int opmask = 0;
+  for (int t = 0; t < op.k; t++) {
+    pos[t] = local_pos(b, op.bits[t]);
+    opmask |= 1 << pos[t];
+  }
+  std::vector<cd> R(b.M.size());
+  for (int base = 0; base < d; base++) {
+    if (base & opmask) continue;
+    int idx[16];
+    for (int a = 0; a < dk; a++) {
+      int r = base;
+      for (int t = 0; t < op.k; t++)
+        if ((a >> t) & 1) r |= 1 << pos[t];
+      idx[a] = r;
+    }
+    for (int col = 0; col < d; col++)
+      for (int a = 0; a < dk; a++) {
+        cd s = 0.0;
+        for (int c = 0; c < dk; c++) s += op.m[(size_t)a * dk + c] * b.M[(size_t)idx[c] * d + col];
+        R[(size_t)idx[a] * d + col] = s;
+      }
+  }
+  b.M.swap(R);
+}
+
+// Pad to 5 qubits with the lowest idle qubits and order the local bits by qubit.
+void finish(Building& b, TcBlock& out) {
+  for (int q = 0; (int)b.qs.size() < kTcBits; q++)
+    if (local_pos(b, q) < 0) add_qubit(b, q);
+  int order[kTcBits];
+  for (int i = 0; i < kTcBits; i++) order[i] = i;
+  std::sort(order, order + kTcBits, [&](int x, int y) { return b.qs[x] < b.qs[y]; });
+  for (int i = 0; i < kTcBits; i++) out.q[i] = b.qs[order[i]];
+  // new local index bit i = old local bit order[i]
+  auto old_index = [&](int j) {
+    int o = 0;
+    for (int i = 0; i < kTcBits; i++)
+      if ((j >> i) & 1) o |= 1 << order[i];
+    return o;
+  };
+  out.U.assign(32 * 32, 0.0);
+  for (int i = 0; i < 32; i++)
+    for (int j = 0; j < 32; j++) out.U[(size_t)i * 32 + j] = b.M[(size_t)old_index(i) * 32 + old_index(j)];
+  out.gate0 = b.gate0;
+  out.ngates = b.ngates;
+}
+
+// Round to TF32 (10 explicit mantissa bits), to nearest with ties away from
+// zero, on the FP32 bit pattern (finite inputs).
+float tf32_host(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+}  // namespace
+
+bool tc_fuse(const std::vector<BitOp>& ops, int n, std::vector<TcBlock>& out, std::string& err) {
+  if (n < kTcMinQubits) {
+    err = "tensor-core plans need at least 12 qubits";
+    return false;
+  }
+  std::vector<Building> blocks;
+  std::vector<int> last(n, -1);
+  for (const BitOp& op : ops) {
+    if (op.k < 1 || op.k > 2) {
+      err = "tensor-core fusion takes one- and two-qubit gates";
+      return false;
+    }
+    int bmin = 0;
+    for (int t = 0; t < op.k; t++) bmin = std::max(bmin, last[op.bits[t]]);
+    int best = -1, best_growth = kTcBits + 1;
+    for (int b = bmin; b < (int)blocks.size(); b++) {
+      int growth = 0;
+      for (int t = 0; t < op.k; t++) growth += local_pos(blocks[b], op.bits[t]) < 0;
+      if ((int)blocks[b].qs.size() + growth > kTcBits || growth >= best_growth) continue;
+      best = b;
+      best_growth = growth;
+      if (growth == 0) break;
+    }
+    if (best < 0) {
+      blocks.emplace_back();
+      blocks.back().M.assign(1, 1.0);
+      blocks.back().gate0 = op.gate0;
+      best = (int)blocks.size() - 1;
+    }
+    Building& b = blocks[best];
+    for (int t = 0; t < op.k; t++)
+      if (local_pos(b, op.bits[t]) < 0) add_qubit(b, op.bits[t]);
+    apply_gate(b, op);
+    b.ngates += op.ngates;
+    for (int t = 0; t < op.k; t++) last[op.bits[t]] = best;
+  }
+  out.resize(blocks.size());
+  for (size_t i = 0; i < blocks.size(); i++) finish(blocks[i], out[i]);
+  return true;
+}
+
+void tc_geometry(const int* q, int n, TcGeom& g) {
+  std::memset(&g, 0, sizeof(g));
+  uint64_t smask = 0;
+  for (int i = 0; i < kTcBits; i++) smask |= 1ull << q[i];
+  int rows[kTcRowBits], nr = 0;
+  for (int b = 0; nr < kTcRowBits; b++)
+    if (!((smask >> b) & 1)) rows[nr++] = b;
+  uint64_t tmask = smask;
+  for (int r = 0; r < kTcRowBits; r++) tmask |= 1ull << rows[r];
+  // Operand byte offset of block bit i (reals 2j, 2j+1 of column m) and of row bit r:
+  // offset = (j >> 4) * 16384 + m * 128 + (((j >> 1) & 7) ^ (m & 7)) * 16 + (j & 1) * 8,
+  // the XOR of one weight per set bit.
+  static const uint32_t jw[kTcBits] = {8, 16, 32, 64, 16384};
+  static const uint32_t mw[kTcRowBits] = {128 ^ 16, 256 ^ 32, 512 ^ 64, 1024, 2048, 4096, 8192};
+  int p = 0, f = 0;
+  for (int b = 0; b < n; b++) {
+    if ((tmask >> b) & 1) {
+      g.gw[p] = 1ull << b;
+      int i = 0;
+      while (i < kTcBits && q[i] != b) i++;
+      if (i < kTcBits) {
+        g.sw[p] = jw[i];
+      } else {
+        int r = 0;
+        while (rows[r] != b) r++;
+        g.sw[p] = mw[r];
+      }
+      p++;
+    } else {
+      g.fw[f++] = 1ull << b;
+    }
+  }
+  g.ntiles = 1u << (n - kTcTileBits);
+}
+
+void tc_matrix_tables(const TcBlock& b, float* out) {
+  // real form over interleaved (re, im): row 2a / 2a+1 = re / im of output a
+  for (int a = 0; a < 32; a++)
+    for (int c = 0; c < 32; c++) {
+      const cd u = b.U[(size_t)a * 32 + c];
+      const double v[2][2] = {{u.real(), -u.imag()}, {u.imag(), u.real()}};
+      for (int ra = 0; ra < 2; ra++)
+        for (int rc = 0; rc < 2; rc++) {
+          const size_t idx = (size_t)(2 * a + ra) * 64 + (2 * c + rc);
+          const double x = v[ra][rc];
+          const float hi = tf32_host((float)x);
+          out[idx] = hi;
+          out[4096 + idx] = tf32_host((float)(x - (double)hi));
+        }
+    }
+}
+
+bool build_tc_plan(const std::vector<BitOp>& ops, Plan& plan, std::string& err) {
+  std::vector<TcBlock> blocks;
+  if (!tc_fuse(ops, plan.n, blocks, err)) return false;
+  plan.tc = true;
+  plan.tcb = std::move(blocks);
+  const size_t nb = plan.tcb.size();
+  plan.tcg.resize(nb);
+  plan.tctab.assign(nb * kTcMatFloats, 0.f);
+  plan.op_gate0.clear();
+  plan.op_ngates.clear();
+  for (size_t i = 0; i < nb; i++) {
+    tc_geometry(plan.tcb[i].q, plan.n, plan.tcg[i]);
+    tc_matrix_tables(plan.tcb[i], plan.tctab.data() + i * kTcMatFloats);
+    plan.op_gate0.push_back(plan.tcb[i].gate0);
+    plan.op_ngates.push_back(plan.tcb[i].ngates);
+  }
+  const double state_bytes = (double)plan.elem_bytes * (double)(1ull << plan.n);
+  plan.bytes = 2.0 * state_bytes * (double)nb;
+  plan.fma_per_elem = 384.0 * (double)nb;  // TF32 multiply-adds: 3 products x 64 per real x 2 reals
+  return true;
+}
+
+}  // namespace nwq

@@ -153,6 +153,13 @@ def _tuning(t):
     return L.PlanTuning(int(t.get("tile_bits", 0)), int(t.get("fusion_bits", 0)), int(t.get("register_bits", 0)))
 
 
+def tc_timeouts():
+    """Bounded waits of the tensor-core kernel that ran out on the current device (0 when healthy)."""
+    c = ctypes.c_int()
+    check(L.lib().nwq_tc_timeouts(ctypes.byref(c)))
+    return c.value
+
+
 def autotune(state, gates, noise=None, flags=0, reps=3):
     """Time the circuit's plan for each candidate shape on ``state`` (a State
     of the circuit's kind, size and dtype; overwritten) and return
@@ -212,6 +219,16 @@ class Plan:
     def verify(self):
         """Check the plan's device tables against the kernels' bounds (raises NwqError)."""
         check(L.lib().nwq_plan_verify(self.h))
+
+    def tc_blocks(self):
+        """Blocks of a tensor-core plan (flags=PLAN_TC): list of (qubits, 32x32 complex matrix)."""
+        nb = self.info()["sweeps"]
+        qs = np.zeros(max(nb, 1) * 5, np.int32)
+        ms = np.zeros(max(nb, 1) * 2048, np.float64)
+        check(L.lib().nwq_plan_tc_blocks(self.h, qs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                         ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        mats = ms.view(np.complex128).reshape(-1, 32, 32)
+        return [(tuple(int(q) for q in qs[5 * b:5 * b + 5]), mats[b].copy()) for b in range(nb)]
 
     def jit_check(self):
         """Compile (host only) the specialised kernels of this plan's sweeps:

@@ -1,0 +1,116 @@
+"""Tensor-core plans on the host (no GPU): the dense five-qubit blocks the
+planner fuses, applied in order as plain matrices, reproduce the oracle's
+gate-by-gate state; every block is unitary and accounts for its gates; the
+tile geometry passes the plan checker; unsupported requests are refused."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_06861_gb300 import _lib as L
+from paper_2401_06861_gb300 import inputs, sim
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2401_06861_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def apply_block(psi, n, qs, U):
+    """psi <- U on qubits qs (local index bit i <-> qubit qs[i]), by index gathering."""
+    others = [q for q in range(n) if q not in qs]
+    r = np.arange(1 << (n - len(qs)))
+    base = np.zeros_like(r)
+    for i, q in enumerate(others):
+        base |= ((r >> i) & 1) << q
+    j = np.arange(1 << len(qs))
+    off = np.zeros_like(j)
+    for i, q in enumerate(qs):
+        off |= ((j >> i) & 1) << q
+    idx = base[:, None] | off[None, :]
+    out = psi.copy()
+    out[idx] = psi[idx] @ U.T
+    return out
+
+
+def run_blocks(n, blocks, psi0):
+    psi = psi0.copy()
+    for qs, U in blocks:
+        psi = apply_block(psi, n, qs, U)
+    return psi
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (12, 2), (13, 3), (14, 4)])
+def test_blocks_reproduce_oracle_random_circuits(n, seed):
+    gates = inputs.random_circuit(n, 80, seed)
+    psi0 = inputs.random_state(n, seed + 100)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        blocks = pl.tc_blocks()
+        pl.verify()
+        sweeps, og, on = pl.layout()
+    assert sum(on) == len(gates)
+    assert sweeps == [1] * len(blocks)
+    ref = oracle.sv_run(n, gates, psi0)
+    got = run_blocks(n, blocks, psi0)
+    assert np.max(np.abs(got - ref)) <= 1e-12
+
+
+def test_blocks_reproduce_oracle_tfim_chain():
+    n = 16
+    gates, _ = inputs.large_sv_tfim(n, 3)
+    psi0 = inputs.random_state(n, 7)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        blocks = pl.tc_blocks()
+        info = pl.info()
+        pl.verify()
+    assert info["sweeps"] == len(blocks) and info["ops"] == len(blocks)
+    state_bytes = 8 * (1 << n)
+    assert info["bytes"] == pytest.approx(2 * state_bytes * len(blocks))
+    assert info["fma_per_elem"] == pytest.approx(384 * len(blocks))
+    # fusion packs the 3 x (15 x 3 + 16) = 183 gates into far fewer passes
+    assert len(blocks) <= 25
+    ref = oracle.sv_run(n, gates, psi0)
+    assert np.max(np.abs(run_blocks(n, blocks, psi0) - ref)) <= 1e-12
+
+
+def test_blocks_are_unitary_on_valid_qubits():
+    n = 13
+    gates = inputs.random_circuit(n, 120, 11)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        blocks = pl.tc_blocks()
+    for qs, U in blocks:
+        assert len(qs) == 5 and list(qs) == sorted(set(qs)) and 0 <= qs[0] and qs[-1] < n
+        assert np.max(np.abs(U @ U.conj().T - np.eye(32))) <= 1e-12
+
+
+def test_edge_qubits_and_padding():
+    # gates only on the top qubits and on qubit 0: padded blocks, tiles whose
+    # block bits sit far above the row bits, and a block holding qubit 0
+    n = 14
+    gates = [("H", (13,), ()), ("CX", (13, 12), ()), ("RX", (11,), (0.3,)), ("CX", (0, 13), ()),
+             ("MAT1", (9,), inputs.random_unitary(2, np.random.default_rng(5))), ("T", (0,), ())]
+    psi0 = inputs.random_state(n, 9)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        blocks = pl.tc_blocks()
+        pl.verify()
+    assert np.max(np.abs(run_blocks(n, blocks, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+def test_empty_circuit_has_no_blocks():
+    with sim.Plan(L.SV, 12, [], dtype=L.F32, flags=L.PLAN_TC) as pl:
+        assert pl.info()["sweeps"] == 0
+        assert pl.tc_blocks() == []
+
+
+@pytest.mark.parametrize("kind,n,dtype", [(L.SV, 11, L.F32), (L.SV, 12, L.F64), (L.DM, 8, L.F32)])
+def test_unsupported_requests(kind, n, dtype):
+    with pytest.raises(L.NwqError) as e:
+        sim.Plan(kind, n, [("H", (0,), ())], dtype=dtype, flags=L.PLAN_TC)
+    assert e.value.code == L.EUNSUPPORTED
+
+
+def test_not_a_tc_plan():
+    with sim.Plan(L.SV, 12, [("H", (0,), ())], dtype=L.F32) as pl:
+        with pytest.raises(L.NwqError):
+            pl.tc_blocks()
