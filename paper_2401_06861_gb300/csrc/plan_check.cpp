@@ -50,15 +50,14 @@ bool verify_tc(const Plan& p, std::string& err) {
     uint32_t wseen = 0;
     for (int t = 0; t < kTcTileBits; t++) {
       const uint64_t w = g.gw[t];
-      if (!w || (w & (w - 1)) || (w & seen) || (w & ~full) || (t && w <= g.gw[t - 1]))
-        return fail_at(err, "tensor-core tile offsets", b, t);
+      if (!w || (w & (w - 1)) || (w & seen) || (w & ~full)) return fail_at(err, "tensor-core tile offsets", b, t);
       seen |= w;
       int k = 0;
       while (k < kTcTileBits && want[k] != g.sw[t]) k++;
       if (k == kTcTileBits || ((wseen >> k) & 1)) return fail_at(err, "tensor-core operand offsets", b, t);
       wseen |= 1u << k;
     }
-    if (g.gw[0] != 1) return fail_at(err, "tensor-core tile without qubit 0", b, 0);
+    if (g.sw[0] != 8 || g.gw[0] != (1ull << blk.q[0])) return fail_at(err, "tensor-core pair bit", b, 0);
     for (int i = 0; i < kTcBits; i++)
       if (!((seen >> blk.q[i]) & 1)) return fail_at(err, "tensor-core block qubit outside its tile", b, i);
     for (int f = 0; f < kTcMaxFree; f++) {
@@ -73,8 +72,9 @@ bool verify_tc(const Plan& p, std::string& err) {
     if (seen != full || g.ntiles != (1u << (p.n - kTcTileBits))) return fail_at(err, "tensor-core tile cover", b, -1);
     // Emulate the kernel's addressing of one tile (thread tid, step i, pair
     // element e): each amplitude must land in the operand slot of its column
-    // m (the 7 lowest qubits outside the block) and block index j, 8-byte
-    // aligned (16-byte for the first of a contiguous pair), each slot once.
+    // m (the 7 lowest qubits outside the block) and block index j, a pair in
+    // one 16-byte chunk, each slot once; each warp's accesses must stay within
+    // 512 contiguous amplitudes apart from the pair partner (coalescing).
     int rows[kTcRowBits], nr = 0;
     uint64_t bmask = 0;
     for (int i = 0; i < kTcBits; i++) bmask |= 1ull << blk.q[i];
@@ -95,7 +95,7 @@ bool verify_tc(const Plan& p, std::string& err) {
             goff += g.gw[8 + k];
             soff ^= g.sw[8 + k];
           }
-        if (g.sw[0] == 8 && (soff & 15)) return fail_at(err, "tensor-core pair alignment", b, tid);
+        if (soff & 15) return fail_at(err, "tensor-core pair alignment", b, tid);
         for (int e = 0; e < 2; e++) {
           const uint64_t amp = goff + (e ? g.gw[0] : 0);
           const uint32_t s = soff ^ (e ? g.sw[0] : 0);
@@ -105,6 +105,8 @@ bool verify_tc(const Plan& p, std::string& err) {
           const uint32_t want_s = (j >> 4) * 16384u + m * 128u + ((((j >> 1) & 7u) ^ (m & 7u)) << 4) + (j & 1u) * 8u;
           if (s != want_s || s >= 32768u || (s & 7u) || slot[s >> 3]++)
             return fail_at(err, "tensor-core operand addressing", b, tid);
+          if (e == 0 && ((g.gw[1] | g.gw[2] | g.gw[3] | g.gw[4] | g.gw[5]) >> 6) != 0)
+            return fail_at(err, "tensor-core lane bits above qubit 5", b, tid);
         }
       }
   }

@@ -2,8 +2,8 @@
 // vector: tcgen05 MMAs of kind TF32 with the accumulator in tensor memory.
 //
 // A tile is 2^12 amplitudes: the block's 5 qubits and the 7 lowest other
-// qubits (so qubits 0..6 are always in the tile and every global access runs
-// over >= 1 KiB contiguous).  Its 128 columns (one per setting of the 7 row
+// qubits (so qubits 0..6 are always in the tile and each warp access covers
+// >= 256 contiguous bytes).  Its 128 columns (one per setting of the 7 row
 // qubits) are the rows of the MMA operand A (128 x 64 reals, interleaved
 // re/im of the 32 block amplitudes); B is the 64 x 64 real form of the block
 // matrix.  D = A B^T (128 x 64 FP32) is the updated tile.  FP32 accuracy from
@@ -33,9 +33,7 @@ constexpr int kTcThreads = 128;
 constexpr uint32_t kSmA = 32768;  // one A operand: 128 rows x 64 FP32, two K halves of 16 KiB
 constexpr uint32_t kSmB = 16384;  // one B operand: 64 rows x 64 FP32, two K halves of 8 KiB
 constexpr uint32_t kOffAhi = 0, kOffAlo = kSmA, kOffBhi = 2 * kSmA, kOffBlo = 2 * kSmA + kSmB;
-constexpr uint32_t kOffGi = 2 * kSmA + 2 * kSmB;  // 16 x u64: amplitude offsets of tile bits 8..11
-constexpr uint32_t kOffSi = kOffGi + 16 * 8;      // 16 x u32: operand offsets of tile bits 8..11
-constexpr uint32_t kOffFw = kOffSi + 16 * 4;      // kTcMaxFree x u64: tile-index bit weights
+constexpr uint32_t kOffFw = 2 * kSmA + 2 * kSmB;  // kTcMaxFree x u64: tile-index bit weights
 constexpr uint32_t kOffBar = kOffFw + 8 * kTcMaxFree;
 constexpr uint32_t kOffTmem = kOffBar + 8;
 constexpr uint32_t kSmUsed = kOffTmem + 8;
@@ -142,30 +140,38 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// The two amplitudes of a pair (block bit 0 = 0 and 1, same column): one
+// 16-byte access when that bit is qubit 0, else two 8-byte accesses.
+__device__ __forceinline__ float4 load_pair(const float2* psi, uint64_t amp, uint64_t gp, bool q0) {
+  if (q0) return __ldcs((const float4*)(psi + amp));
+  const float2 a = __ldcs(psi + amp), b = __ldcs(psi + amp + gp);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void store_pair(float2* psi, uint64_t amp, uint64_t gp, bool q0, float4 v) {
+  if (q0) {
+    __stcs((float4*)(psi + amp), v);
+  } else {
+    __stcs(psi + amp, make_float2(v.x, v.y));
+    __stcs(psi + amp + gp, make_float2(v.z, v.w));
+  }
+}
+
+// Tile bits by role (host-chosen, TcGeom): bit 0 = block bit 0 (the pair,
+// 8 operand bytes apart, so a pair is one 16-byte operand chunk), bits 1..5 =
+// lane, 6..7 = warp, 8..11 = loop step i.  The lane bits are the five lowest
+// other tile qubits (a warp covers >= 256 contiguous bytes), lane bits 0..2
+// chosen so that each quarter-warp writes 8 distinct 16-byte bank groups.
 __global__ void __launch_bounds__(kTcThreads, 2)
-    tc_block_kernel(float4* __restrict__ psi, const float4* __restrict__ mats, const __grid_constant__ TcGeom g) {
+    tc_block_kernel(float2* __restrict__ psi, const float4* __restrict__ mats, const __grid_constant__ TcGeom g) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sb = (raw + 1023u) & ~1023u;
   unsigned char* sm = smem_raw + (sb - raw);
   const int tid = threadIdx.x, warp = tid >> 5;
-  uint64_t* gi_tab = (uint64_t*)(sm + kOffGi);
-  uint32_t* si_tab = (uint32_t*)(sm + kOffSi);
   uint64_t* fw = (uint64_t*)(sm + kOffFw);
   const uint32_t bar = sb + kOffBar;
   const uint32_t sAhi = sb + kOffAhi, sAlo = sb + kOffAlo;
 
-  if (tid < 16) {
-    uint64_t go = 0;
-    uint32_t so = 0;
-    for (int b = 0; b < 4; b++)
-      if ((tid >> b) & 1) {
-        go += g.gw[8 + b];
-        so ^= g.sw[8 + b];
-      }
-    gi_tab[tid] = go;
-    si_tab[tid] = so;
-  }
   if (tid < kTcMaxFree) fw[tid] = g.fw[tid];
   // B operands: TF32 hi and lo parts of the block's real 64 x 64 matrix (row n, reals k)
   for (int idx = tid; idx < 1024; idx += kTcThreads) {
@@ -191,8 +197,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const uint32_t tmem = *(volatile uint32_t*)(sm + kOffTmem);
   const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 accumulator lanes
 
-  // This thread's amplitude pairs in a tile: tile index t = 2 tid + 256 i
-  // (tile bits 1..7 from tid, 8..11 from i); the pair partner is tile bit 0 = qubit 0.
+  // this thread's pairs: tile-index bits 1..7 from tid, 8..11 from the loop step i
   uint64_t goff = 0;
   uint32_t soff = 0;
   for (int b = 1; b < 8; b++)
@@ -200,8 +205,12 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       goff += g.gw[b];
       soff ^= g.sw[b];
     }
-  const uint32_t w0 = g.sw[0];
-  const bool pair16 = w0 == 8u;  // qubit 0 is block bit 0: the pair is 16 contiguous operand bytes
+  const uint64_t gp = g.gw[0];
+  const bool q0 = gp == 1;
+  const uint64_t l0 = g.gw[8], l1 = g.gw[9], l2 = g.gw[10], l3 = g.gw[11];
+  const uint32_t s0 = g.sw[8], s1 = g.sw[9], s2 = g.sw[10], s3 = g.sw[11];
+#define TC_GI(i) (((i)&1 ? l0 : 0) + ((i)&2 ? l1 : 0) + ((i)&4 ? l2 : 0) + ((i)&8 ? l3 : 0))
+#define TC_SI(i) (((i)&1 ? s0 : 0) ^ ((i)&2 ? s1 : 0) ^ ((i)&4 ? s2 : 0) ^ ((i)&8 ? s3 : 0))
 
   float4 r[16];
   uint32_t tile = blockIdx.x;
@@ -212,27 +221,21 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       base += fw[__ffs(x) - 1];
       x &= x - 1;
     }
+    const uint64_t a = base + goff;
 #pragma unroll
-    for (int i = 0; i < 16; i++) r[i] = __ldcs(psi + ((base + goff + gi_tab[i]) >> 1));
+    for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
   }
   uint32_t phase = 0;
   bool timed_out = false;
   for (; tile < g.ntiles; tile += gridDim.x) {
-    // 1. TF32 split into the A operands
+    // 1. TF32 split into the A operands (one 16-byte chunk per pair)
 #pragma unroll
     for (int i = 0; i < 16; i++) {
-      const uint32_t s = soff ^ si_tab[i];
+      const uint32_t so = soff ^ TC_SI(i);
       float4 h, l;
       split4(r[i], h, l);
-      if (pair16) {
-        st16(sAhi + s, h);
-        st16(sAlo + s, l);
-      } else {
-        st8(sAhi + s, h.x, h.y);
-        st8(sAhi + (s ^ w0), h.z, h.w);
-        st8(sAlo + s, l.x, l.y);
-        st8(sAlo + (s ^ w0), l.z, l.w);
-      }
+      st16(sAhi + so, h);
+      st16(sAlo + so, l);
     }
     fence_async_smem();
     __syncthreads();
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       mma_commit(bar);
     }
     // 3. the next tile's loads are in flight while the MMAs run
-    const uint64_t cur = base;
+    const uint64_t cur = base + goff;
     const uint32_t next = tile + gridDim.x;
     if (next < g.ntiles) {
       uint32_t x = next;
@@ -262,8 +265,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         base += fw[__ffs(x) - 1];
         x &= x - 1;
       }
+      const uint64_t a = base + goff;
 #pragma unroll
-      for (int i = 0; i < 16; i++) r[i] = __ldcs(psi + ((base + goff + gi_tab[i]) >> 1));
+      for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
     }
     const bool ok = mbar_wait_bounded(bar, phase);
     phase ^= 1u;
@@ -288,19 +292,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     __syncthreads();
     // 5. write the tile back with the load pattern
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-      const uint32_t s = soff ^ si_tab[i];
-      float4 v;
-      if (pair16) {
-        v = ld16(sAhi + s);
-      } else {
-        const float2 a = ld8(sAhi + s), b = ld8(sAhi + (s ^ w0));
-        v = make_float4(a.x, a.y, b.x, b.y);
-      }
-      __stcs(psi + ((cur + goff + gi_tab[i]) >> 1), v);
-    }
+    for (int i = 0; i < 16; i++) store_pair(psi, cur + TC_GI(i), gp, q0, ld16(sAhi + (soff ^ TC_SI(i))));
     __syncthreads();
   }
+#undef TC_GI
+#undef TC_SI
   if (timed_out) {
     if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
     mbar_wait_bounded(bar, phase ^ 1u);  // one more bounded wait for the MMAs in flight
@@ -321,17 +317,18 @@ cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, i
   cudaGetDevice(&dev);
   if (attr_dev.load() != dev) {
     cudaError_t e = cudaFuncSetAttribute(tc_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc_block_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_block_kernel, kTcThreads, kTcSmem);
-  if (e != cudaSuccess) return e;
-  // at most 2 resident CTAs x 64 tensor-memory columns: allocation never waits
-  per_sm = per_sm < 1 ? 1 : per_sm > 2 ? 2 : per_sm;
-  uint64_t grid = (uint64_t)sm_count * per_sm;
+  // Two CTAs per SM (shared memory allows 2; each holds 64 of the SM's 512
+  // tensor-memory columns, so allocation never waits).  The grid is not taken
+  // from the occupancy query, which reported 1 for this kernel.
+  uint64_t grid = (uint64_t)sm_count * 2;
   if (grid > g.ntiles) grid = g.ntiles;
-  tc_block_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>((float4*)psi, (const float4*)mats_dev, g);
+  tc_block_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>((float2*)psi, (const float4*)mats_dev, g);
   g_launches += 1;
   return cudaGetLastError();
 }

@@ -12,6 +12,7 @@
 // idle qubits (identity).
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "planner.hpp"
 #include "tc.hpp"
@@ -155,31 +156,59 @@ void tc_geometry(const int* q, int n, TcGeom& g) {
   int rows[kTcRowBits], nr = 0;
   for (int b = 0; nr < kTcRowBits; b++)
     if (!((smask >> b) & 1)) rows[nr++] = b;
-  uint64_t tmask = smask;
-  for (int r = 0; r < kTcRowBits; r++) tmask |= 1ull << rows[r];
-  // Operand byte offset of block bit i (reals 2j, 2j+1 of column m) and of row bit r:
-  // offset = (j >> 4) * 16384 + m * 128 + (((j >> 1) & 7) ^ (m & 7)) * 16 + (j & 1) * 8,
-  // the XOR of one weight per set bit.
+  // Operand byte offset of column m (row bits) and block index j:
+  // (j >> 4) * 16384 + m * 128 + (((j >> 1) & 7) ^ (m & 7)) * 16 + (j & 1) * 8,
+  // the XOR of one weight per set bit.  bank[] = the weight's share of
+  // offset bits 4..6 (the 16-byte bank group).
   static const uint32_t jw[kTcBits] = {8, 16, 32, 64, 16384};
   static const uint32_t mw[kTcRowBits] = {128 ^ 16, 256 ^ 32, 512 ^ 64, 1024, 2048, 4096, 8192};
-  int p = 0, f = 0;
+  struct Bit {
+    int qubit;
+    uint32_t w, bank;
+  };
+  std::vector<Bit> other;  // tile bits except block bit 0, ascending by qubit
   for (int b = 0; b < n; b++) {
-    if ((tmask >> b) & 1) {
-      g.gw[p] = 1ull << b;
-      int i = 0;
-      while (i < kTcBits && q[i] != b) i++;
-      if (i < kTcBits) {
-        g.sw[p] = jw[i];
-      } else {
-        int r = 0;
-        while (rows[r] != b) r++;
-        g.sw[p] = mw[r];
-      }
-      p++;
-    } else {
-      g.fw[f++] = 1ull << b;
+    int i = 0;
+    while (i < kTcBits && q[i] != b) i++;
+    if (i < kTcBits) {
+      if (i > 0) other.push_back({b, jw[i], (jw[i] >> 4) & 7u});
+      continue;
     }
+    int r = 0;
+    while (r < kTcRowBits && rows[r] != b) r++;
+    if (r < kTcRowBits) other.push_back({b, mw[r], (mw[r] >> 4) & 7u});
   }
+  // roles: 0 = block bit 0 (the pair); 1..5 = lane bits, the five lowest other
+  // tile qubits with lane bits 0..2 covering bank bits 1, 2, 4 (always possible:
+  // the five hold m0..m(a-1) and j1..j(b) with a + b = 5); 6..7 warp; 8..11 loop.
+  int role_q[kTcTileBits];
+  uint32_t role_w[kTcTileBits];
+  role_q[0] = q[0];
+  role_w[0] = jw[0];
+  std::vector<int> order;  // indices into other, in role order 1..11
+  std::vector<char> used(other.size(), 0);
+  for (int k = 0; k < 3; k++)
+    for (int c = 0; c < 5; c++)
+      if (!used[c] && other[c].bank == (1u << k)) {
+        used[c] = 1;
+        order.push_back(c);
+        break;
+      }
+  for (int c = 0; c < (int)other.size(); c++)
+    if (!used[c]) order.push_back(c);
+  for (int p = 1; p < kTcTileBits; p++) {
+    role_q[p] = other[order[p - 1]].qubit;
+    role_w[p] = other[order[p - 1]].w;
+  }
+  for (int p = 0; p < kTcTileBits; p++) {
+    g.gw[p] = 1ull << role_q[p];
+    g.sw[p] = role_w[p];
+  }
+  uint64_t tmask = smask;
+  for (int r = 0; r < kTcRowBits; r++) tmask |= 1ull << rows[r];
+  int f = 0;
+  for (int b = 0; b < n; b++)
+    if (!((tmask >> b) & 1)) g.fw[f++] = 1ull << b;
   g.ntiles = 1u << (n - kTcTileBits);
 }
 
