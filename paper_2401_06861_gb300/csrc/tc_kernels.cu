@@ -13,11 +13,13 @@
 // Operands sit in shared memory in the 128-byte-swizzled K-major layout
 // (rows of 128 bytes, 16-byte chunk c of row r stored at chunk c ^ (r & 7),
 // 8-row groups 1024 bytes apart), in two K halves of 32 reals.  Each CTA
-// (128 threads, one elected thread issuing the MMAs) walks its tiles:
-// loads the next tile into registers while the MMAs of the current one run,
-// waits on an mbarrier the MMA commit arrives on (bounded), moves the
-// accumulator rows from tensor memory to shared memory, and writes the tile
-// back with the same coalesced pattern it was read with.
+// (128 threads, one thread issuing the MMAs; 3 CTAs per SM) walks its
+// tiles with one A buffer: the TF32 lo parts go in and the lo * B_hi MMAs
+// run, then the hi parts replace them for hi * B_lo + hi * B_hi while the
+// next tile's loads go out (small products first in the FP32 accumulator); every MMA group is committed to an mbarrier
+// and waited on (bounded); the accumulator rows then move from tensor memory
+// to shared memory and the tile is written back with the pattern it was read
+// with.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,10 +32,11 @@ namespace nwq {
 namespace {
 
 constexpr int kTcThreads = 128;
-constexpr uint32_t kSmA = 32768;  // one A operand: 128 rows x 64 FP32, two K halves of 16 KiB
+constexpr int kTcCtasPerSm = 3;
+constexpr uint32_t kSmA = 32768;  // the A operand: 128 rows x 64 FP32, two K halves of 16 KiB
 constexpr uint32_t kSmB = 16384;  // one B operand: 64 rows x 64 FP32, two K halves of 8 KiB
-constexpr uint32_t kOffAhi = 0, kOffAlo = kSmA, kOffBhi = 2 * kSmA, kOffBlo = 2 * kSmA + kSmB;
-constexpr uint32_t kOffFw = 2 * kSmA + 2 * kSmB;  // kTcMaxFree x u64: tile-index bit weights
+constexpr uint32_t kOffA = 0, kOffBhi = kSmA, kOffBlo = kSmA + kSmB;
+constexpr uint32_t kOffFw = kSmA + 2 * kSmB;  // kTcMaxFree x u64: tile-index bit weights
 constexpr uint32_t kOffBar = kOffFw + 8 * kTcMaxFree;
 constexpr uint32_t kOffTmem = kOffBar + 8;
 constexpr uint32_t kSmUsed = kOffTmem + 8;
@@ -63,17 +66,9 @@ __device__ __forceinline__ float tf32_rna(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
-__device__ __forceinline__ void split4(const float4 v, float4& h, float4& l) {
-  h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-  l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
-}
-
 __device__ __forceinline__ void st16(uint32_t a, float4 v) {
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
                : "memory");
-}
-__device__ __forceinline__ void st8(uint32_t a, float x, float y) {
-  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
 }
 __device__ __forceinline__ float4 ld16(uint32_t a) {
   float4 v;
@@ -81,12 +76,6 @@ __device__ __forceinline__ float4 ld16(uint32_t a) {
                : "memory");
   return v;
 }
-__device__ __forceinline__ float2 ld8(uint32_t a) {
-  float2 v;
-  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -161,7 +150,7 @@ __device__ __forceinline__ void store_pair(float2* psi, uint64_t amp, uint64_t g
 // lane, 6..7 = warp, 8..11 = loop step i.  The lane bits are the five lowest
 // other tile qubits (a warp covers >= 256 contiguous bytes), lane bits 0..2
 // chosen so that each quarter-warp writes 8 distinct 16-byte bank groups.
-__global__ void __launch_bounds__(kTcThreads, 2)
+__global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     tc_block_kernel(float2* __restrict__ psi, const float4* __restrict__ mats, const __grid_constant__ TcGeom g) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -170,7 +159,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const int tid = threadIdx.x, warp = tid >> 5;
   uint64_t* fw = (uint64_t*)(sm + kOffFw);
   const uint32_t bar = sb + kOffBar;
-  const uint32_t sAhi = sb + kOffAhi, sAlo = sb + kOffAlo;
+  const uint32_t sA = sb + kOffA;
 
   if (tid < kTcMaxFree) fw[tid] = g.fw[tid];
   // B operands: TF32 hi and lo parts of the block's real 64 x 64 matrix (row n, reals k)
@@ -211,95 +200,105 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const uint32_t s0 = g.sw[8], s1 = g.sw[9], s2 = g.sw[10], s3 = g.sw[11];
 #define TC_GI(i) (((i)&1 ? l0 : 0) + ((i)&2 ? l1 : 0) + ((i)&4 ? l2 : 0) + ((i)&8 ? l3 : 0))
 #define TC_SI(i) (((i)&1 ? s0 : 0) ^ ((i)&2 ? s1 : 0) ^ ((i)&4 ? s2 : 0) ^ ((i)&8 ? s3 : 0))
-
-  float4 r[16];
-  uint32_t tile = blockIdx.x;
-  uint64_t base = 0;
-  if (tile < g.ntiles) {
-    uint32_t x = tile;
+  auto tile_base = [&](uint32_t x) {
+    uint64_t b = 0;
     while (x) {
-      base += fw[__ffs(x) - 1];
+      b += fw[__ffs(x) - 1];
       x &= x - 1;
     }
-    const uint64_t a = base + goff;
-#pragma unroll
-    for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
-  }
+    return b;
+  };
   uint32_t phase = 0;
   bool timed_out = false;
-  for (; tile < g.ntiles; tile += gridDim.x) {
-    // 1. TF32 split into the A operands (one 16-byte chunk per pair)
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-      const uint32_t so = soff ^ TC_SI(i);
-      float4 h, l;
-      split4(r[i], h, l);
-      st16(sAhi + so, h);
-      st16(sAlo + so, l);
-    }
+  // Issue one product group (lo or hi A parts already in shared memory) and commit it.
+  auto mma_group = [&](bool lo_pass) {
     fence_async_smem();
     __syncthreads();
-    // 2. one thread issues the 24 MMAs (3 products x 8 K steps of 8 reals) and commits them to the barrier
     if (tid == 0) {
       tc_fence_after();
 #pragma unroll
-      for (int p = 0; p < 3; p++) {
-        const uint32_t a0 = p == 0 ? sAlo : sAhi;
-        const uint32_t b0 = sb + (p == 1 ? kOffBlo : kOffBhi);
+      for (int p = 0; p < 2; p++) {
+        if (lo_pass && p == 1) break;  // lo pass: lo * B_hi only
+        const uint32_t b0 = sb + (!lo_pass && p == 0 ? kOffBlo : kOffBhi);
 #pragma unroll
         for (int k = 0; k < 8; k++) {
           const uint32_t ka = (uint32_t)(k >> 2) * 16384u + (uint32_t)(k & 3) * 32u;
           const uint32_t kb = (uint32_t)(k >> 2) * 8192u + (uint32_t)(k & 3) * 32u;
-          mma_tf32(tmem, sw128_desc(a0 + ka), sw128_desc(b0 + kb), (p | k) != 0);
+          mma_tf32(tmem, sw128_desc(sA + ka), sw128_desc(b0 + kb), (!lo_pass || p || k) ? 1u : 0u);
         }
       }
       mma_commit(bar);
     }
-    // 3. the next tile's loads are in flight while the MMAs run
-    const uint64_t cur = base + goff;
-    const uint32_t next = tile + gridDim.x;
-    if (next < g.ntiles) {
-      uint32_t x = next;
-      base = 0;
-      while (x) {
-        base += fw[__ffs(x) - 1];
-        x &= x - 1;
-      }
-      const uint64_t a = base + goff;
-#pragma unroll
-      for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
-    }
+  };
+  auto mma_wait = [&]() -> bool {
     const bool ok = mbar_wait_bounded(bar, phase);
+    if (__syncthreads_or(!ok)) return false;
     phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
+    tc_fence_after();
+    return true;
+  };
+
+  float4 r[16];
+  uint32_t tile = blockIdx.x;
+  if (tile < g.ntiles) {
+    const uint64_t a = tile_base(tile) + goff;
+#pragma unroll
+    for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
+  }
+  for (; tile < g.ntiles; tile += gridDim.x) {
+    // 1. A <- TF32 lo parts, MMAs lo * B_hi (the small products accumulate first)
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      const float4 v = r[i];
+      const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+      st16(sA + (soff ^ TC_SI(i)),
+           make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w)));
+      r[i] = h;  // keep the hi parts
+    }
+    mma_group(true);
+    if (!mma_wait()) {
       timed_out = true;
       break;
     }
-    tc_fence_after();
-    // 4. accumulator lane tid (one state column) -> shared memory, in the A layout
-    {
-      float d[64];
-      tmem_ld32(tmem_row, d);
-      tmem_ld32(tmem_row + 32u, d + 32);
+    // 2. A <- TF32 hi parts (A is free: the lo MMAs completed); MMAs hi * B_lo + hi * B_hi
 #pragma unroll
-      for (int c = 0; c < 16; c++) {
-        const uint32_t off =
-            (uint32_t)(c >> 3) * 16384u + (uint32_t)tid * 128u + ((uint32_t)((c & 7) ^ (tid & 7)) << 4);
-        st16(sAhi + off, make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]));
+    for (int i = 0; i < 16; i++) st16(sA + (soff ^ TC_SI(i)), r[i]);
+    mma_group(false);
+    // 3. the next tile's loads are in flight while these MMAs and the write-back run
+    const uint64_t cur = tile_base(tile) + goff;
+    const uint32_t next = tile + gridDim.x;
+    if (next < g.ntiles) {
+      const uint64_t a = tile_base(next) + goff;
+#pragma unroll
+      for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
+    }
+    if (!mma_wait()) {
+      timed_out = true;
+      break;
+    }
+    // 4. accumulator lane tid (one state column) -> shared memory (the A layout), 32 columns at a time
+#pragma unroll
+    for (int hh = 0; hh < 2; hh++) {
+      float d[32];
+      tmem_ld32(tmem_row + 32u * (uint32_t)hh, d);
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const uint32_t off = (uint32_t)hh * 16384u + (uint32_t)tid * 128u + ((uint32_t)(c ^ (tid & 7)) << 4);
+        st16(sA + off, make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]));
       }
     }
     tc_fence_before();
     __syncthreads();
     // 5. write the tile back with the load pattern
 #pragma unroll
-    for (int i = 0; i < 16; i++) store_pair(psi, cur + TC_GI(i), gp, q0, ld16(sAhi + (soff ^ TC_SI(i))));
+    for (int i = 0; i < 16; i++) store_pair(psi, cur + TC_GI(i), gp, q0, ld16(sA + (soff ^ TC_SI(i))));
     __syncthreads();
   }
 #undef TC_GI
 #undef TC_SI
   if (timed_out) {
     if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
-    mbar_wait_bounded(bar, phase ^ 1u);  // one more bounded wait for the MMAs in flight
+    mbar_wait_bounded(bar, phase);  // one more bounded wait for the MMAs in flight
   }
   tc_fence_before();
   __syncthreads();
@@ -323,10 +322,10 @@ cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, i
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
-  // Two CTAs per SM (shared memory allows 2; each holds 64 of the SM's 512
-  // tensor-memory columns, so allocation never waits).  The grid is not taken
-  // from the occupancy query, which reported 1 for this kernel.
-  uint64_t grid = (uint64_t)sm_count * 2;
+  // Three CTAs per SM (65 KB of shared memory and 64 of the SM's 512
+  // tensor-memory columns each, so allocation never waits).  The grid is not
+  // taken from the occupancy query, which under-reports this kernel.
+  uint64_t grid = (uint64_t)sm_count * kTcCtasPerSm;
   if (grid > g.ntiles) grid = g.ntiles;
   tc_block_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>((float2*)psi, (const float4*)mats_dev, g);
   g_launches += 1;
