@@ -291,6 +291,7 @@ def _peaks():
 def run_sv(args):
     """Large state vector: TFIM depth 10 with random h_i, fused sweeps vs one
     gate per pass, FP32 and FP64; gate-updates/s and HBM GB/s."""
+    import numpy as np
     import torch
 
     from paper_2401_06861_gb300 import _lib as L
@@ -305,7 +306,14 @@ def run_sv(args):
                  "tc32": (args.sv_n, L.F32, L.PLAN_TC, max(1, args.steps // 3))}
     cases = [all_cases[c] for c in args.sv_cases.split(",")]
     for n, dtype, flags, steps in cases:
-        gates, h = inputs.large_sv_tfim(n, steps=args.sv_depth)
+        if args.sv_circuit == "tfim":
+            gates, h = inputs.large_sv_tfim(n, steps=args.sv_depth)
+            wname = f"sv_tfim_n{n}_depth{args.sv_depth}"
+        else:  # generic dense one- and two-qubit gates on random qubits (half two-qubit)
+            ng = 10 * n
+            gates = inputs.random_circuit(n, ng, 2401 + n, names=["MAT1", "MAT2"], two_qubit_frac=0.5)
+            h = np.ones(n)
+            wname = f"sv_random2q_n{n}_{ng}gates"
         plan = Plan(L.SV, n, gates, dtype, None, flags)
         info = plan.info()
         st = State(L.SV, n, dtype, stream=stream.cuda_stream)
@@ -338,7 +346,7 @@ def run_sv(args):
             roof = {"bound": "alu", "achieved": fp64, "peak": fpk, "unit": "FP64 instructions/s", "frac": fp64 / fpk,
                     "fp_ops_per_amp": info["fma_per_elem"], "hbm_gbs": gb, "hbm_frac": gb / peak}
         pname = "tc" if flags & L.PLAN_TC else "plain" if flags else "fused"
-        line = {"workload": f"sv_tfim_n{n}_depth{args.sv_depth}", "plan": pname,
+        line = {"workload": wname, "plan": pname,
                 "dtype": "c64" if dtype == L.F32 else "c128", "metric": "gate-updates/s",
                 "value": len(gates) * 2.0 ** n / sec, "unit": "gate-updates/s", "s_per_circuit": sec,
                 "sweeps": info["sweeps"], "operators": info["ops"], "roofline": roof, "energy": e, "norm": nrm}
@@ -606,6 +614,8 @@ def main():
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
+    ap.add_argument("--sv-circuit", default="tfim", choices=["tfim", "random2q"],
+                    help="large-SV circuit: TFIM Trotter chain, or random dense one/two-qubit gates")
     ap.add_argument("--sv-cases", default="fused32,fused64,plain32,tc32",
                     help="comma list of fused32, fused64, plain32, tc32 (tensor-core blocks)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)

@@ -227,6 +227,9 @@ int nwq_plan_layout(const nwq_plan* plan, int* sweep_nops, int* op_gate, int* op
  *                  (default 10 for 16-byte, 12 for 8-byte, 13 for 4-byte elements);
  *   fusion_bits    widest operator the planner merges gates into, in state-index
  *                  bits, 2..4 (default 4; a density-matrix qubit spans 2 bits);
+ *                  5 = dense five-qubit blocks on the tensor cores (NWQ_PLAN_TC:
+ *                  complex64 state vectors of >= 12 qubits; the other fields
+ *                  are then unused);
  *   register_bits  complex sweeps: state elements per thread group = 2^register_bits,
  *                  3 or 4 (default 3 for complex128, 4 for complex64). */
 typedef struct {
@@ -240,7 +243,8 @@ int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate* gates, siz
 
 /* Autotuner: build the circuit's plan for each candidate shape (tile bits of
  * the default -1, +0, +1; fusion bits 3 and 4 (density matrix: 2 and 4);
- * register bits 3 and 4 for state vectors), run each on `scratch` (a state of
+ * register bits 3 and 4 for state vectors; for complex64 state vectors of >= 12
+ * qubits also the tensor-core plan, fusion bits 5), run each on `scratch` (a state of
  * the circuit's kind, size and dtype; its contents are overwritten) once to
  * warm up and `reps` times under CUDA events on the state's stream, and return
  * the fastest shape in *best with its mean time in *best_ms.  When `tried` is

@@ -352,6 +352,7 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
   std::string err;
   bool ok = kind == NWQ_SV ? lower_sv(gates, ng, n, ops, err) : lower_dm(gates, ng, n, nm, ops, err);
   if (!ok) return fail(NWQ_EINVAL, err);
+  if (tuning && tuning->fusion_bits == kTcBits) flags |= NWQ_PLAN_TC;  // shape "5 fused qubits" = tensor-core blocks
   if (flags & NWQ_PLAN_TC) {
     if (kind != NWQ_SV || dtype != NWQ_F32 || n < kTcMinQubits)
       return fail(NWQ_EUNSUPPORTED, "tensor-core plans take complex64 state vectors of at least 12 qubits");
@@ -378,7 +379,7 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
       o.tile_bits = tuning->tile_bits;
     }
     if (tuning->fusion_bits) {
-      if (tuning->fusion_bits < 2 || tuning->fusion_bits > 4) return fail(NWQ_EINVAL, "fusion_bits must be 2..4");
+      if (tuning->fusion_bits < 2 || tuning->fusion_bits > 4) return fail(NWQ_EINVAL, "fusion_bits must be 2..4 (5: tensor-core blocks, complex64 state vectors)");
       o.max_merge_bits = tuning->fusion_bits;
     }
     if (tuning->register_bits) {
@@ -423,6 +424,9 @@ extern "C" int nwq_plan_autotune(nwq_state* st, const nwq_gate* gates, size_t ng
     for (int fb : (st->kind == NWQ_DM ? std::vector<int>{2, 4} : std::vector<int>{3, 4}))
       for (int rb : (st->kind == NWQ_SV ? std::vector<int>{3, 4} : std::vector<int>{0})) cand.push_back({tb, fb, rb});
   }
+  // complex64 state vectors: also the dense five-qubit blocks on the tensor cores
+  if (st->kind == NWQ_SV && st->dtype == NWQ_F32 && st->n >= kTcMinQubits && !(flags & NWQ_PLAN_PLAIN))
+    cand.push_back({0, kTcBits, 0});
   cudaEvent_t a = nullptr, b = nullptr;
   CK(cudaEventCreate(&a), "event");
   CK(cudaEventCreate(&b), "event");

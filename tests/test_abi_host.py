@@ -181,7 +181,7 @@ def test_plan_tuning_shapes_and_validation():
     d4 = sim.Plan(L.DM, 8, gd, L.F64, noise).info()
     assert d2["ops"] > d4["ops"]  # two-qubit noisy blocks are only merged at 4 bits
     for bad, msg in [(dict(tile_bits=3), b"tile_bits"), (dict(tile_bits=16), b"tile_bits"),
-                     (dict(fusion_bits=5), b"fusion_bits"), (dict(register_bits=2), b"register_bits")]:
+                     (dict(fusion_bits=6), b"fusion_bits"), (dict(register_bits=2), b"register_bits")]:
         with pytest.raises(L.NwqError):
             sim.Plan(L.SV, 20, g, L.F32, tuning=bad)
         assert msg in L.lib().nwq_last_error()

@@ -114,3 +114,17 @@ def test_not_a_tc_plan():
     with sim.Plan(L.SV, 12, [("H", (0,), ())], dtype=L.F32) as pl:
         with pytest.raises(L.NwqError):
             pl.tc_blocks()
+
+
+def test_fusion_bits_5_is_the_tensor_core_plan():
+    # the autotuner's shape for tensor-core plans: fusion_bits = 5
+    n = 13
+    gates = inputs.random_circuit(n, 60, 21)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as a, \
+            sim.Plan(L.SV, n, gates, dtype=L.F32, tuning={"fusion_bits": 5}) as b:
+        ba, bb = a.tc_blocks(), b.tc_blocks()
+    assert [q for q, _ in ba] == [q for q, _ in bb]
+    assert all(np.array_equal(x, y) for (_, x), (_, y) in zip(ba, bb))
+    with pytest.raises(L.NwqError) as e:
+        sim.Plan(L.SV, n, gates, dtype=L.F64, tuning={"fusion_bits": 5})
+    assert e.value.code == L.EUNSUPPORTED
