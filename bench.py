@@ -354,6 +354,50 @@ def run_sv(args):
         torch.cuda.empty_cache()
 
 
+def run_sv_errors(args):
+    """Large state vector, errors measured against the FP64 path: the depth-10
+    TFIM chain at n = sv_n - 1 (33: a 128 GiB complex128 state and a 64 GiB
+    complex64 state fit together) run in complex128 (fused), then in complex64
+    with each plan (fused sweeps, one gate per pass, tensor-core blocks); per
+    plan the max absolute amplitude error over all 2^n amplitudes and the
+    relative energy error against the complex128 state."""
+    import numpy as np  # noqa: F401
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, inputs
+    from paper_2401_06861_gb300.sim import Plan, State
+    build.build()
+    n = args.sv_n - 1
+    gates, h = inputs.large_sv_tfim(n, steps=args.sv_depth)
+    terms = inputs.tfim_terms(n, 1.0, h)
+    hnorm = float(sum(abs(t[2]) for t in terms))
+    ref = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    with State(L.SV, n, L.F64, buf=ref.data_ptr(), buf_bytes=ref.numel() * 16) as st, Plan(L.SV, n, gates, L.F64) as p:
+        st.run(p)
+        e_ref = st.expect(terms, sum=True)
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    chunk = 1 << 27
+    for name, flags in (("fused", 0), ("plain", L.PLAN_PLAIN), ("tc", L.PLAN_TC)):
+        with State(L.SV, n, L.F32, buf=psi.data_ptr(), buf_bytes=psi.numel() * 8) as st, \
+                Plan(L.SV, n, gates, L.F32, flags=flags) as p:
+            st.run(p)
+            e = st.expect(terms, sum=True, normalize=True)
+            nrm = st.norm()
+        torch.cuda.synchronize()
+        err = 0.0
+        for a in range(0, 1 << n, chunk):
+            d = (psi[a:a + chunk].to(torch.complex128) - ref[a:a + chunk]).abs().max().item()
+            err = max(err, d)
+        line = {"workload": f"sv_tfim_n{n}_depth{args.sv_depth}_errors_vs_fp64", "plan": name, "dtype": "c64",
+                "reference": "the same circuit in complex128 (fused plan)", "max_abs_amplitude_error": err,
+                "rel_energy_error": abs(e - e_ref) / max(abs(e_ref), hnorm), "energy": e, "energy_fp64": e_ref,
+                "norm": nrm, "tolerance": {"amplitude": 1e-5, "rel_energy": 1e-6}}
+        print(json.dumps(line), flush=True)
+    del ref, psi
+    torch.cuda.empty_cache()
+
+
 def run_vqe(args):
     """Batched VQE energies: n = 12 hardware-efficient ansatz (4 layers, 96
     parameters), 4096 sets, energies for h in {0.5, 1, 2}; batched FP32 and
@@ -610,7 +654,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dm", choices=["dm", "dm32", "sv", "vqe", "vqe-cobyla", "serve", "traj"])
+    ap.add_argument("--workload", default="dm",
+                    choices=["dm", "dm32", "sv", "sv-errors", "vqe", "vqe-cobyla", "serve", "traj"])
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
@@ -632,6 +677,8 @@ def main():
         return rc
     if args.workload == "sv":
         return run_sv(args)
+    if args.workload == "sv-errors":
+        return run_sv_errors(args)
     if args.workload == "vqe-cobyla":
         return run_vqe_cobyla(args)
     if args.workload == "traj":

@@ -16,10 +16,10 @@
 // (128 threads, one thread issuing the MMAs; 3 CTAs per SM) walks its
 // tiles with one A buffer: the TF32 lo parts go in and the lo * B_hi MMAs
 // run, then the hi parts replace them for hi * B_lo + hi * B_hi while the
-// next tile's loads go out (small products first in the FP32 accumulator); every MMA group is committed to an mbarrier
-// and waited on (bounded); the accumulator rows then move from tensor memory
-// to shared memory and the tile is written back with the pattern it was read
-// with.
+// next tile's loads go out (small products first in the FP32 accumulator).
+// Every MMA group is committed to an mbarrier and waited on (bounded); the
+// accumulator rows then move from tensor memory to shared memory and the
+// tile is written back with the pattern it was read with.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -493,6 +493,33 @@ def test_sv_n28_fp32_vs_fp64_tfim():
     assert maxerr(res[L.F32][1], res[L.F64][1]) <= 1e-5
 
 
+def test_sv_n33_complex64_amplitudes_vs_complex128():
+    # amplitude-level FP32 error at full size: the depth-10 chain at n = 33 in
+    # complex128 (128 GiB) and in complex64 (64 GiB), fused and tensor-core plans
+    import torch
+    n = 33
+    gates, h = inputs.large_sv_tfim(n, 10)
+    terms = inputs.tfim_terms(n, 1.0, h)
+    ref = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    with State(L.SV, n, L.F64, buf=ref.data_ptr(), buf_bytes=ref.numel() * 16) as st, Plan(L.SV, n, gates, L.F64) as p:
+        st.run(p)
+        e_ref = st.expect(terms, sum=True)
+    psi = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    for flags in (L.PLAN_FUSED, L.PLAN_TC):
+        with State(L.SV, n, L.F32, buf=psi.data_ptr(), buf_bytes=psi.numel() * 8) as st, \
+                Plan(L.SV, n, gates, L.F32, flags=flags) as p:
+            st.run(p)
+            e = st.expect(terms, sum=True, normalize=True)
+        torch.cuda.synchronize()
+        err = max((psi[a:a + (1 << 27)].to(torch.complex128) - ref[a:a + (1 << 27)]).abs().max().item()
+                  for a in range(0, 1 << n, 1 << 27))
+        print(f"n=33 complex64 flags={flags}: max amplitude error {err:.3e}, rel energy {rel_energy(e, e_ref, terms):.3e}")
+        assert err <= TOL[L.F32]
+        assert rel_energy(e, e_ref, terms) <= 1e-6
+    del ref, psi
+    torch.cuda.empty_cache()
+
+
 def test_qasm_program_on_the_gpu():
     from paper_2401_06861_gb300 import qasm
     prog = """OPENQASM 2.0;
