@@ -12,6 +12,9 @@ torch tensor (``buf=tensor.data_ptr(), buf_bytes=...``).
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
+import os
 
 import numpy as np
 
@@ -160,18 +163,59 @@ def tc_timeouts():
     return c.value
 
 
-def autotune(state, gates, noise=None, flags=0, reps=3):
+def _device_name():
+    try:
+        import torch
+        return torch.cuda.get_device_name() if torch.cuda.is_available() else "no-device"
+    except Exception:  # torch is optional plumbing
+        return "unknown-device"
+
+
+def autotune_key(kind, n, dtype, gates, noise=None, flags=0, device=None):
+    """Cache key of an autotuning result: the device name and the circuit's
+    structure (kind, qubits, precision, flags, noise or not, each gate's kind
+    and qubits); angles and matrices are left out, as they do not change
+    which plan shape runs fastest."""
+    desc = [device if device is not None else _device_name(), int(kind), int(n), int(dtype), int(flags),
+            noise is not None, [(g[0], [int(q) for q in g[1]]) for g in gates]]
+    return hashlib.sha256(json.dumps(desc, separators=(",", ":")).encode()).hexdigest()
+
+
+def autotune(state, gates, noise=None, flags=0, reps=3, cache=None):
     """Time the circuit's plan for each candidate shape on ``state`` (a State
     of the circuit's kind, size and dtype; overwritten) and return
-    dict(best=tuning dict, best_ms, tried=[(tuning dict, ms)])."""
+    dict(best=tuning dict, best_ms, tried=[(tuning dict, ms)]).
+
+    ``cache``: a JSON file of earlier results (default: the file named by the
+    environment variable NWQ_AUTOTUNE_CACHE, none if unset), keyed by
+    ``autotune_key``.  A hit returns the stored result (with cached=True)
+    without running anything; a miss runs the tuner and adds its result."""
+    path = cache if cache is not None else os.environ.get("NWQ_AUTOTUNE_CACHE")
+    key = data = None
+    if path:
+        key = autotune_key(state.kind, state.n, state.dtype, gates, noise, flags)
+        try:
+            with open(path) as f:
+                data = json.load(f)
+        except (OSError, ValueError):
+            data = {}
+        if key in data:
+            return dict(data[key], cached=True)
     arr, keep = encode_gates(gates)
     nm, keep2 = encode_noise(noise, state.n)
     best, bms = L.PlanTuning(), ctypes.c_double()
     tried, tms, nt = (L.PlanTuning * 32)(), (ctypes.c_double * 32)(), ctypes.c_int()
     check(L.lib().nwq_plan_autotune(state.h, arr, len(gates), ctypes.byref(nm) if nm is not None else None, flags,
                                     reps, ctypes.byref(best), ctypes.byref(bms), tried, tms, 32, ctypes.byref(nt)))
-    return dict(best=best.as_dict(), best_ms=bms.value,
-                tried=[(tried[i].as_dict(), tms[i]) for i in range(nt.value)])
+    res = dict(best=best.as_dict(), best_ms=bms.value,
+               tried=[(tried[i].as_dict(), tms[i]) for i in range(nt.value)])
+    if path:
+        data[key] = res
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f)
+        os.replace(tmp, path)
+    return dict(res, cached=False)
 
 
 class Plan:
