@@ -128,3 +128,32 @@ def test_fusion_bits_5_is_the_tensor_core_plan():
     with pytest.raises(L.NwqError) as e:
         sim.Plan(L.SV, n, gates, dtype=L.F64, tuning={"fusion_bits": 5})
     assert e.value.code == L.EUNSUPPORTED
+
+
+def _tf32_rna(x):
+    """Round float32 values to TF32 (10 explicit mantissa bits), to nearest with ties away from zero."""
+    u = np.asarray(x, np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def test_three_term_tf32_split_reaches_fp32_accuracy():
+    # the tensor-core arithmetic, emulated: inputs split x = hi + lo with both
+    # parts TF32, products lo*hi + hi*lo + hi*hi accumulated in FP32, against
+    # the exact (FP64) 64-term real contraction of a random unitary's real form
+    rng = np.random.default_rng(3)
+    U = inputs.random_unitary(32, rng)
+    M = np.block([[U.real, -U.imag], [U.imag, U.real]])  # acts on (re, im) halves
+    X = (rng.standard_normal((64, 128)) * 1e-3).astype(np.float32)
+    Mf = M.astype(np.float32)
+    mh = _tf32_rna(Mf)
+    ml = _tf32_rna(M - mh.astype(np.float64))
+    xh = _tf32_rna(X)
+    xl = _tf32_rna(X - xh)
+    f32 = lambda a, b: (a.astype(np.float32) @ b.astype(np.float32)).astype(np.float64)
+    D = f32(ml, xh) + f32(mh, xl) + f32(mh, xh)
+    exact = M @ X.astype(np.float64)
+    scale = np.abs(M) @ np.abs(X.astype(np.float64))
+    rel = np.max(np.abs(D - exact) / scale)
+    one_term = np.max(np.abs(f32(mh, xh) - exact) / scale)
+    assert rel < 2.0 ** -19, rel          # FP32-level (a 64-term FP32 sum of exact products ~ 2^-20)
+    assert one_term > 2.0 ** -14          # a single TF32 product is far coarser
