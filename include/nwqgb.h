@@ -112,10 +112,14 @@ enum nwq_plan_flags {
 /* Tensor-core plans (NWQ_PLAN_TC; complex64 state vectors of >= 12 qubits,
  * else NWQ_EUNSUPPORTED).  The gate stream is fused into dense blocks of 5
  * qubits (paper Sec. III, "we optimize the quantum circuit", read as gate
- * fusion): a gate joins the block, at or after the latest block touching its
- * qubits, that stays within 5 qubits and grows least (earliest on a tie),
- * else opens a new block; each block's 32 x 32 matrix is multiplied out in
- * FP64 (blocks under 5 qubits are padded with idle qubits).  One pass over
+ * fusion): a gate on a subset of the qubits of the latest gate on each of them
+ * is first multiplied into it (CX RZ CX becomes one diagonal gate) unless a
+ * diagonal gate would stop being diagonal; then blocks are built one at a
+ * time from the gates not yet placed, in order, taking each gate that fits in
+ * 5 qubits and may move ahead of the gates skipped so far (it shares no qubit
+ * with them, or it and they are diagonal, so they commute); each block's
+ * 32 x 32 matrix is multiplied out in FP64 (blocks under 5 qubits are padded
+ * with idle qubits).  One pass over
  * the state per block applies it as a dense contraction on the tensor cores
  * (tcgen05, TF32 inputs split as hi + lo with the three products
  * hi*hi + hi*lo + lo*hi, FP32 accumulation).  nwq_plan_info: sweeps = ops =

@@ -3,13 +3,18 @@
 // the blocks' tile geometry, and the TF32 hi / lo tables of their real form.
 //
 // Fusion (this build's reading of "we optimize the quantum circuit",
-// paper Sec. III, in the form that feeds tensor cores): gates are taken in
-// order; a gate on qubits Q may join any block at or after the latest block
-// that touches Q (it commutes with every block it passes, since none of
-// them touches Q) whose qubit set stays within 5 qubits with Q added; among
-// those the one that grows least, the earliest on a tie; otherwise it opens
-// a new block at the end.  Blocks with fewer than 5 qubits are padded with
-// idle qubits (identity).
+// paper Sec. III, in the form that feeds tensor cores), in two steps:
+//   1. fold: a gate whose qubits are a subset of those of the latest gate on
+//      each of them is multiplied into that gate (CX * RZ * CX becomes one
+//      diagonal two-qubit gate), unless that would turn a diagonal gate into
+//      a non-diagonal one;
+//   2. blocks, one at a time: scan the gates not yet placed, in order, and
+//      place each that fits the block's 5 qubits and may move ahead of every
+//      gate skipped so far on its qubits (a gate may pass a skipped gate it
+//      shares no qubit with, and a diagonal gate may pass a skipped diagonal
+//      gate, since diagonal matrices commute); a skipped gate keeps its
+//      qubits from later gates that may not pass it.  Blocks with fewer than
+//      5 qubits are padded with idle qubits (identity).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -108,44 +113,100 @@ float tf32_host(float x) {
 
 }  // namespace
 
+namespace {
+
+bool diagonal(const std::vector<cd>& m, int k) {
+  const int d = 1 << k;
+  for (int i = 0; i < d; i++)
+    for (int j = 0; j < d; j++)
+      if (i != j && m[(size_t)i * d + j] != cd(0.0)) return false;
+  return true;
+}
+
+constexpr size_t kTcLookahead = 1u << 16;  // gates scanned per block
+
+}  // namespace
+
 bool tc_fuse(const std::vector<BitOp>& ops, int n, std::vector<TcBlock>& out, std::string& err) {
   if (n < kTcMinQubits) {
     err = "tensor-core plans need at least 12 qubits";
     return false;
   }
-  std::vector<Building> blocks;
+  // 1. fold gates into the latest gate on their qubits (matrices on that gate's qubit order)
+  std::vector<Building> g;
+  std::vector<char> diag;
   std::vector<int> last(n, -1);
   for (const BitOp& op : ops) {
     if (op.k < 1 || op.k > 2) {
       err = "tensor-core fusion takes one- and two-qubit gates";
       return false;
     }
-    int bmin = 0;
-    for (int t = 0; t < op.k; t++) bmin = std::max(bmin, last[op.bits[t]]);
-    int best = -1, best_growth = kTcBits + 1;
-    for (int b = bmin; b < (int)blocks.size(); b++) {
-      int growth = 0;
-      for (int t = 0; t < op.k; t++) growth += local_pos(blocks[b], op.bits[t]) < 0;
-      if ((int)blocks[b].qs.size() + growth > kTcBits || growth >= best_growth) continue;
-      best = b;
-      best_growth = growth;
-      if (growth == 0) break;
+    const int a = last[op.bits[0]];
+    bool fold = a >= 0;
+    for (int t = 1; t < op.k; t++) fold = fold && last[op.bits[t]] == a;
+    for (int t = 0; fold && t < op.k; t++) fold = local_pos(g[a], op.bits[t]) >= 0;
+    if (fold) {
+      Building c = g[a];
+      apply_gate(c, op);
+      const bool dg = diagonal(c.M, (int)c.qs.size());
+      if (!diag[a] || dg) {
+        c.ngates += op.ngates;
+        g[a] = std::move(c);
+        diag[a] = dg;
+        continue;
+      }
     }
-    if (best < 0) {
-      blocks.emplace_back();
-      blocks.back().M.assign(1, 1.0);
-      blocks.back().gate0 = op.gate0;
-      best = (int)blocks.size() - 1;
-    }
-    Building& b = blocks[best];
-    for (int t = 0; t < op.k; t++)
-      if (local_pos(b, op.bits[t]) < 0) add_qubit(b, op.bits[t]);
+    Building b;
+    b.M.assign(1, 1.0);
+    b.gate0 = op.gate0;
+    for (int t = 0; t < op.k; t++) add_qubit(b, op.bits[t]);
     apply_gate(b, op);
-    b.ngates += op.ngates;
-    for (int t = 0; t < op.k; t++) last[op.bits[t]] = best;
+    b.ngates = op.ngates;
+    diag.push_back(diagonal(b.M, op.k));
+    g.push_back(std::move(b));
+    for (int t = 0; t < op.k; t++) last[op.bits[t]] = (int)g.size() - 1;
   }
-  out.resize(blocks.size());
-  for (size_t i = 0; i < blocks.size(); i++) finish(blocks[i], out[i]);
+  // 2. blocks, one at a time, over the gates not yet placed
+  const size_t m = g.size();
+  const uint64_t full = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+  std::vector<char> placed(m, 0);
+  out.clear();
+  size_t pos = 0;
+  while (pos < m) {
+    Building b;
+    b.M.assign(1, 1.0);
+    b.gate0 = g[pos].gate0;
+    uint64_t S = 0, blk_all = 0, blk_nd = 0;
+    size_t scanned = 0;
+    for (size_t i = pos; i < m && scanned < kTcLookahead; i++) {
+      if (placed[i]) continue;
+      scanned++;
+      uint64_t Q = 0;
+      for (int q : g[i].qs) Q |= 1ull << q;
+      const bool ok = !(Q & blk_all) && (diag[i] || !(Q & blk_nd)) && __builtin_popcountll(S | Q) <= kTcBits;
+      if (ok) {
+        S |= Q;
+        placed[i] = 1;
+        BitOp op;  // the folded gate on its own qubits
+        op.k = (int)g[i].qs.size();
+        for (int t = 0; t < op.k; t++) op.bits[t] = g[i].qs[t];
+        op.m = g[i].M;
+        for (int q : g[i].qs)
+          if (local_pos(b, q) < 0) add_qubit(b, q);
+        apply_gate(b, op);
+        b.ngates += g[i].ngates;
+        b.gate0 = std::min(b.gate0, g[i].gate0);
+      } else if (diag[i]) {
+        blk_nd |= Q;
+      } else {
+        blk_all |= Q;
+        if (blk_all == full) break;
+      }
+    }
+    out.emplace_back();
+    finish(b, out.back());
+    while (pos < m && placed[pos]) pos++;
+  }
   return true;
 }
 

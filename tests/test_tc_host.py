@@ -68,8 +68,9 @@ def test_blocks_reproduce_oracle_tfim_chain():
     state_bytes = 8 * (1 << n)
     assert info["bytes"] == pytest.approx(2 * state_bytes * len(blocks))
     assert info["fma_per_elem"] == pytest.approx(384 * len(blocks))
-    # fusion packs the 3 x (15 x 3 + 16) = 183 gates into far fewer passes
-    assert len(blocks) <= 25
+    # fusion packs the 3 x (15 x 3 + 16) = 183 gates into far fewer passes: the
+    # CX RZ CX bonds fold into diagonal gates, which pass one another
+    assert len(blocks) <= 8
     ref = oracle.sv_run(n, gates, psi0)
     assert np.max(np.abs(run_blocks(n, blocks, psi0) - ref)) <= 1e-12
 
@@ -157,3 +158,38 @@ def test_three_term_tf32_split_reaches_fp32_accuracy():
     one_term = np.max(np.abs(f32(mh, xh) - exact) / scale)
     assert rel < 2.0 ** -19, rel          # FP32-level (a 64-term FP32 sum of exact products ~ 2^-20)
     assert one_term > 2.0 ** -14          # a single TF32 product is far coarser
+
+
+def test_fusion_lets_diagonal_gates_pass_each_other():
+    # the depth-10 chains of the large-state workloads: diagonal bond gates
+    # commute, so blocks follow the light cone instead of one Trotter step each
+    for n, most in [(26, 40), (34, 50)]:
+        gates, _ = inputs.large_sv_tfim(n, 10)
+        with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+            nb = pl.info()["sweeps"]
+            _, _, on = pl.layout()
+        assert nb <= most and sum(on) == len(gates)
+    # a diagonal gate may not pass a non-diagonal one: H(0) . RZ(0) . H(0) keeps its order
+    n = 12
+    gates = [("H", (0,), ()), ("RZ", (0,), (0.7,)), ("H", (0,), ()), ("CZ", (0, 1), ()), ("RX", (1,), (0.3,)),
+             ("CZ", (1, 2), ()), ("H", (2,), ()), ("CZ", (0, 2), ())]
+    psi0 = inputs.random_state(n, 4)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        blocks = pl.tc_blocks()
+    assert np.max(np.abs(run_blocks(n, blocks, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+@pytest.mark.parametrize("seed", [31, 32, 33, 34])
+def test_fusion_with_many_diagonal_gates_reproduces_oracle(seed):
+    # mostly diagonal gates on random qubits (so blocks split and diagonal
+    # gates pass skipped ones), with non-diagonal gates in between
+    n = 13
+    names = ["RZ", "CZ", "RZZ", "T", "P", "S", "RX", "H", "CX"]
+    gates = inputs.random_circuit(n, 240, seed, names=names, two_qubit_frac=0.5)
+    psi0 = inputs.random_state(n, seed)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        blocks = pl.tc_blocks()
+        pl.verify()
+        _, _, on = pl.layout()
+    assert sum(on) == len(gates) and len(blocks) > 3
+    assert np.max(np.abs(run_blocks(n, blocks, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
