@@ -103,6 +103,7 @@ def lib():
         "nwq_plan_jit_check": (i32, [vp, P(i32), P(i32)]),
         "nwq_plan_verify": (i32, [vp]),
         "nwq_plan_tc_blocks": (i32, [vp, P(i32), P(dbl)]),
+        "nwq_plan_ops": (i32, [vp, P(i32), P(i32), P(dbl)]),
         "nwq_tc_timeouts": (i32, [P(i32)]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),

@@ -525,6 +525,28 @@ extern "C" int nwq_plan_tc_blocks(const nwq_plan* plan, int* qubits, double* mat
   return NWQ_OK;
 }
 
+extern "C" int nwq_plan_ops(const nwq_plan* plan, int* k, int* bits, double* mats) {
+  if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
+  const Plan& p = plan->p;
+  if (!p.is_complex || p.tc || p.exec_ops.size() != p.ops.size())
+    return fail(NWQ_EINVAL, "operators are recorded for state-vector sweep plans only");
+  for (size_t o = 0; o < p.exec_ops.size(); o++) {
+    const BitOp& op = p.exec_ops[o];
+    const int d = 1 << op.k;
+    if (k) k[o] = op.k;
+    if (bits)
+      for (int t = 0; t < 4; t++) bits[4 * o + t] = t < op.k ? op.bits[t] : -1;
+    if (mats)
+      for (int r = 0; r < 16; r++)
+        for (int c = 0; c < 16; c++) {
+          const cd v = (r < d && c < d) ? op.m[(size_t)r * d + c] : cd(0.0);
+          mats[(o * 256 + (size_t)r * 16 + c) * 2] = v.real();
+          mats[(o * 256 + (size_t)r * 16 + c) * 2 + 1] = v.imag();
+        }
+  }
+  return NWQ_OK;
+}
+
 extern "C" int nwq_tc_timeouts(int* count) {
   if (!count) return fail(NWQ_EINVAL, "count is NULL");
   CK(cudaDeviceSynchronize(), "device synchronize");

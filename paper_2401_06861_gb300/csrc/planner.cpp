@@ -961,6 +961,10 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
     plan.sweeps.push_back(sd);
   }
 
+  plan.exec_ops.clear();
+  if (cplx)
+    for (int i : order) plan.exec_ops.push_back(ops[i]);
+
   // device tables
   plan.ops.clear();
   plan.ents.clear();

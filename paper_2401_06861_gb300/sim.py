@@ -264,6 +264,23 @@ class Plan:
         """Check the plan's device tables against the kernels' bounds (raises NwqError)."""
         check(L.lib().nwq_plan_verify(self.h))
 
+    def ops(self):
+        """Merged operators of a state-vector sweep plan in execution order:
+        list of (qubits, 2^k x 2^k complex matrix), local index bit t <-> qubits[t]."""
+        no = self.info()["ops"]
+        k = np.zeros(max(no, 1), np.int32)
+        bits = np.zeros(max(no, 1) * 4, np.int32)
+        ms = np.zeros(max(no, 1) * 512, np.float64)
+        check(L.lib().nwq_plan_ops(self.h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   bits.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                   ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        mats = ms.view(np.complex128).reshape(-1, 16, 16)
+        out = []
+        for o in range(no):
+            d = 1 << int(k[o])
+            out.append((tuple(int(b) for b in bits[4 * o:4 * o + int(k[o])]), mats[o, :d, :d].copy()))
+        return out
+
     def tc_blocks(self):
         """Blocks of a tensor-core plan (flags=PLAN_TC): list of (qubits, 32x32 complex matrix)."""
         nb = self.info()["sweeps"]

@@ -145,3 +145,20 @@ def partial_trace_replace(rho, n, qubits):
                 acc += rho[(r & ~mask) | bits, (c & ~mask) | bits]
             out[r, c] = acc / (1 << k)
     return out
+
+
+def apply_local(psi, n, qs, U):
+    """psi <- U acting on qubits qs (local index bit t <-> qubit qs[t]), by index gathering."""
+    others = [q for q in range(n) if q not in qs]
+    r = np.arange(1 << (n - len(qs)))
+    base = np.zeros_like(r)
+    for i, q in enumerate(others):
+        base |= ((r >> i) & 1) << q
+    j = np.arange(1 << len(qs))
+    off = np.zeros_like(j)
+    for i, q in enumerate(qs):
+        off |= ((j >> i) & 1) << q
+    idx = base[:, None] | off[None, :]
+    out = psi.copy()
+    out[idx] = psi[idx] @ np.asarray(U).T
+    return out

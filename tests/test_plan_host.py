@@ -1,0 +1,73 @@
+"""Host-side pin of the sweep planner of state vectors (no GPU): the merged
+operators of a plan, applied in the plan's execution order as plain matrices,
+reproduce the oracle's gate-by-gate state, for every plan form and shape."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_06861_gb300 import _lib as L
+from paper_2401_06861_gb300 import inputs, sim
+from tests.dense import apply_local
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2401_06861_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def run_ops(n, ops, psi0):
+    psi = psi0.copy()
+    for qs, U in ops:
+        psi = apply_local(psi, n, qs, U)
+    return psi
+
+
+@pytest.mark.parametrize("flags", [L.PLAN_FUSED, L.PLAN_NO_MERGE, L.PLAN_PLAIN])
+@pytest.mark.parametrize("dtype", [L.F64, L.F32])
+@pytest.mark.parametrize("n", [3, 8, 13])
+def test_plan_operators_reproduce_oracle(n, dtype, flags):
+    gates = inputs.random_circuit(n, 150, 7000 + n)
+    psi0 = inputs.random_state(n, 7100 + n)
+    with sim.Plan(L.SV, n, gates, dtype, flags=flags) as pl:
+        ops = pl.ops()
+        info = pl.info()
+        _, og, on = pl.layout()
+    assert len(ops) == info["ops"] and sum(on) == len(gates)
+    if flags == L.PLAN_PLAIN:
+        assert len(ops) == len(gates)
+    assert np.max(np.abs(run_ops(n, ops, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+@pytest.mark.parametrize("tuning", [dict(tile_bits=10, fusion_bits=3, register_bits=3),
+                                    dict(tile_bits=13, fusion_bits=4, register_bits=4), dict(fusion_bits=2)])
+def test_tuned_plan_shapes_reproduce_oracle(tuning):
+    n = 14
+    gates, _ = inputs.large_sv_tfim(n, 4)
+    gates = gates + inputs.random_circuit(n, 60, 7200)
+    psi0 = inputs.random_state(n, 7300)
+    with sim.Plan(L.SV, n, gates, L.F32, tuning=tuning) as pl:
+        ops = pl.ops()
+    assert np.max(np.abs(run_ops(n, ops, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+def test_tfim_bonds_merge_into_diagonal_operators():
+    n = 12
+    gates, _ = inputs.large_sv_tfim(n, 2)
+    with sim.Plan(L.SV, n, gates, L.F64) as pl:
+        ops = pl.ops()
+    diag = [np.count_nonzero(U - np.diag(np.diag(U))) == 0 for _, U in ops]
+    assert len(ops) < len(gates) and any(diag)
+    psi0 = inputs.random_state(n, 3)
+    assert np.max(np.abs(run_ops(n, ops, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+def test_ops_hook_refuses_other_plans():
+    with sim.Plan(L.SV, 12, [("H", (0,), ())], L.F32, flags=L.PLAN_TC) as pl:
+        with pytest.raises(L.NwqError):
+            pl.ops()
+    gates, noise = inputs.dm_noisy_tfim(3, 1)
+    with sim.Plan(L.DM, 3, gates, L.F64, noise) as pl:
+        with pytest.raises(L.NwqError):
+            pl.ops()
