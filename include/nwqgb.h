@@ -106,7 +106,10 @@ enum nwq_plan_flags {
   NWQ_PLAN_NO_MERGE = 2u,   /* fused sweeps, but no algebraic merging of operators */
   NWQ_PLAN_NO_RESCALE = 4u, /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
   NWQ_PLAN_INTERPRETED = 8u, /* never the run-time specialised sweep kernels (see nwq_plan_jit_check) */
-  NWQ_PLAN_TC = 16u          /* dense five-qubit blocks on the tensor cores (see below) */
+  NWQ_PLAN_TC = 16u,         /* dense five-qubit blocks on the tensor cores (see below) */
+  NWQ_PLAN_COMMUTE = 32u     /* state vectors: when grouping sweeps, a diagonal operator may move ahead of
+                                skipped diagonal operators (they commute): fewer passes for circuits
+                                of diagonal gates (opt-in) */
 };
 
 /* Tensor-core plans (NWQ_PLAN_TC; complex64 state vectors of >= 12 qubits,

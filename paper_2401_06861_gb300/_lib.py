@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libnwqgb.so")
 OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 F32, F64 = 1, 2
 SV, DM = 1, 2
-PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED, PLAN_TC = 0, 1, 2, 4, 8, 16
+PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED, PLAN_TC, PLAN_COMMUTE = 0, 1, 2, 4, 8, 16, 32
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
 NOALLOC_MAX_TERMS = 256

@@ -68,6 +68,7 @@ static void plan_options(int kind, int dtype, uint32_t flags, PlanOptions& o) {
     if (v >= 4 && v <= kMaxTileBits && (2 * esz << v) <= (size_t)kMaxDynSmem) o.tile_bits = v;
   }
   o.plain = (flags & NWQ_PLAN_PLAIN) != 0;
+  o.commute = kind == NWQ_SV && (flags & NWQ_PLAN_COMMUTE) != 0 && !o.plain;
   o.merge = !(flags & (NWQ_PLAN_PLAIN | NWQ_PLAN_NO_MERGE));
 }
 

@@ -921,23 +921,30 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
   plan.sweeps.clear();
   std::vector<uint64_t> sweep_tiles;
   size_t pos = 0;
+  // With opt.commute (complex plans), a diagonal operator may move ahead of a
+  // skipped diagonal operator (diagonal matrices commute): skipped diagonal
+  // operators block only non-diagonal ones (blocked_nd), every other skipped
+  // operator blocks everything on its bits (blocked).
+  std::vector<char> diag(nops, 0);
+  if (opt.commute && cplx)
+    for (size_t i = 0; i < nops; i++) diag[i] = is_diagonal(ops[i]);
   while (pos < nops) {
-    uint64_t R = low, blocked = 0;
+    uint64_t R = low, blocked = 0, blocked_nd = 0;
     int first = (int)order.size();
     int scanned = 0;
     for (size_t i = pos; i < nops && scanned < opt.lookahead; i++) {
       if (done[i]) continue;
       scanned++;
       uint64_t m = op_mask(ops[i]);
-      if (m & blocked) {
-        blocked |= m;
+      if ((m & blocked) || (!diag[i] && (m & blocked_nd))) {
+        (diag[i] ? blocked_nd : blocked) |= m;
       } else if (__builtin_popcountll(R | m) <= T) {
         R |= m;
         done[i] = 1;
         order.push_back((int)i);
         if (opt.plain) break;
       } else {
-        blocked |= m;
+        (diag[i] ? blocked_nd : blocked) |= m;
       }
       if ((full & ~blocked) == 0) break;
     }

@@ -30,6 +30,7 @@ struct PlanOptions {
   int min_low = 3;        // coalescing: low contiguous bits always in the tile
   bool merge = true;      // algebraic merging of adjacent operators
   bool plain = false;     // one operator per sweep
+  bool commute = false;   // complex plans: diagonal operators may pass one another when grouping
   int max_merge_bits = 4;
   int lookahead = 4096;   // operators scanned when filling a sweep
   int rescale_qubits = 0; // DM: deferred per-qubit scaling over this many qubits (0 = off)

@@ -71,3 +71,33 @@ def test_ops_hook_refuses_other_plans():
     with sim.Plan(L.DM, 3, gates, L.F64, noise) as pl:
         with pytest.raises(L.NwqError):
             pl.ops()
+
+
+@pytest.mark.parametrize("dtype", [L.F64, L.F32])
+@pytest.mark.parametrize("n,family", [(8, "diag"), (13, "diag"), (16, "tfim"), (13, "mixed")])
+def test_commuting_plans_reproduce_oracle(n, family, dtype):
+    # NWQ_PLAN_COMMUTE: diagonal operators pass skipped diagonal operators
+    if family == "diag":
+        gates = inputs.random_circuit(n, 200, 7400 + n, names=["RZ", "CZ", "RZZ", "T", "P", "S", "RX", "H", "CX"],
+                                      two_qubit_frac=0.5)
+    elif family == "tfim":
+        gates = inputs.large_sv_tfim(n, 6)[0]
+    else:
+        gates = inputs.random_circuit(n, 150, 7500 + n)
+    psi0 = inputs.random_state(n, 7600 + n)
+    with sim.Plan(L.SV, n, gates, dtype, flags=L.PLAN_COMMUTE) as pl:
+        ops = pl.ops()
+        _, _, on = pl.layout()
+        pl.verify()
+    assert sum(on) == len(gates)
+    assert np.max(np.abs(run_ops(n, ops, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+def test_commuting_plans_need_fewer_sweeps_for_diagonal_bonds():
+    # the depth-10 chain at n = 34: CX RZ CX bonds merge into diagonal
+    # operators, which now share sweeps across Trotter steps
+    gates, _ = inputs.large_sv_tfim(34, 10)
+    with sim.Plan(L.SV, 34, gates, L.F32) as a, sim.Plan(L.SV, 34, gates, L.F32, flags=L.PLAN_COMMUTE) as b:
+        ia, ib = a.info(), b.info()
+    assert ib["ops"] == ia["ops"] and ib["fma_per_elem"] == ia["fma_per_elem"]
+    assert ib["sweeps"] <= 0.6 * ia["sweeps"]
