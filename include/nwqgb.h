@@ -282,11 +282,14 @@ int nwq_plan_verify(const nwq_plan* plan);
  * NWQ_EINVAL if the plan is not a tensor-core plan.  Host only. */
 int nwq_plan_tc_blocks(const nwq_plan* plan, int* qubits, double* mats);
 
-/* Test hook: the merged operators of a state-vector sweep plan (not a
- * tensor-core plan), in the order the sweeps apply them (count = ops of
- * nwq_plan_info): k[o] qubits, bits[4 o + t] = qubit of local index bit t
- * (-1 past k), mats[2 (256 o + 16 r + c) + {0, 1}] = re / im of entry (r, c)
- * of its 2^k x 2^k matrix (zero outside).  Any pointer may be NULL.  Host only. */
+/* Test hook: the merged operators of a sweep plan (not a tensor-core plan),
+ * in the order the sweeps apply them (count = ops of nwq_plan_info): k[o]
+ * index bits, bits[4 o + t] = state-index bit of local bit t (-1 past k),
+ * mats[2 (256 o + 16 r + c) + {0, 1}] = re / im of entry (r, c) of its
+ * 2^k x 2^k matrix (zero outside).  State vectors: bits are qubits.
+ * Density matrices: real Pauli-transfer operators on the 2n-bit index of the
+ * coefficients r[x + 2^n z] (qubit q owns bits q and q + n), deferred
+ * per-qubit scales included.  Any pointer may be NULL.  Host only. */
 int nwq_plan_ops(const nwq_plan* plan, int* k, int* bits, double* mats);
 
 /* Test hook: number of bounded waits (MMA completion) that ran out in the

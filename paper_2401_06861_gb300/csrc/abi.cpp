@@ -529,8 +529,7 @@ extern "C" int nwq_plan_tc_blocks(const nwq_plan* plan, int* qubits, double* mat
 extern "C" int nwq_plan_ops(const nwq_plan* plan, int* k, int* bits, double* mats) {
   if (!plan) return fail(NWQ_EINVAL, "plan is NULL");
   const Plan& p = plan->p;
-  if (!p.is_complex || p.tc || p.exec_ops.size() != p.ops.size())
-    return fail(NWQ_EINVAL, "operators are recorded for state-vector sweep plans only");
+  if (p.tc || p.exec_ops.size() != p.ops.size()) return fail(NWQ_EINVAL, "operators are recorded for sweep plans only");
   for (size_t o = 0; o < p.exec_ops.size(); o++) {
     const BitOp& op = p.exec_ops[o];
     const int d = 1 << op.k;

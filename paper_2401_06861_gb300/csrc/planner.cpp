@@ -969,8 +969,7 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
   }
 
   plan.exec_ops.clear();
-  if (cplx)
-    for (int i : order) plan.exec_ops.push_back(ops[i]);
+  for (int i : order) plan.exec_ops.push_back(ops[i]);
 
   // device tables
   plan.ops.clear();

@@ -63,7 +63,7 @@ struct Plan {
   // run-time specialised kernels of this plan's sweeps (built on first launch)
   std::shared_ptr<void> jit;
   bool interpreted = false;  // never use them
-  // complex plans: the merged operators in execution order (nwq_plan_ops)
+  // the merged operators in execution order (nwq_plan_ops)
   std::vector<BitOp> exec_ops;
   // tensor-core plans (NWQ_PLAN_TC): dense five-qubit blocks, one pass each
   bool tc = false;

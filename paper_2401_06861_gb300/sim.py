@@ -265,8 +265,10 @@ class Plan:
         check(L.lib().nwq_plan_verify(self.h))
 
     def ops(self):
-        """Merged operators of a state-vector sweep plan in execution order:
-        list of (qubits, 2^k x 2^k complex matrix), local index bit t <-> qubits[t]."""
+        """Merged operators of a sweep plan in execution order: list of
+        (index bits, 2^k x 2^k complex matrix), local index bit t <-> bits[t]
+        (qubits for state vectors; Pauli-coefficient index bits, real
+        matrices, for density matrices)."""
         no = self.info()["ops"]
         k = np.zeros(max(no, 1), np.int32)
         bits = np.zeros(max(no, 1) * 4, np.int32)

@@ -67,10 +67,6 @@ def test_ops_hook_refuses_other_plans():
     with sim.Plan(L.SV, 12, [("H", (0,), ())], L.F32, flags=L.PLAN_TC) as pl:
         with pytest.raises(L.NwqError):
             pl.ops()
-    gates, noise = inputs.dm_noisy_tfim(3, 1)
-    with sim.Plan(L.DM, 3, gates, L.F64, noise) as pl:
-        with pytest.raises(L.NwqError):
-            pl.ops()
 
 
 @pytest.mark.parametrize("dtype", [L.F64, L.F32])
@@ -101,3 +97,42 @@ def test_commuting_plans_need_fewer_sweeps_for_diagonal_bonds():
         ia, ib = a.info(), b.info()
     assert ib["ops"] == ia["ops"] and ib["fma_per_elem"] == ia["fma_per_elem"]
     assert ib["sweeps"] <= 0.6 * ia["sweeps"]
+
+
+def pauli_coefficients(rho, n):
+    """r[x + 2^n z] = Tr(rho P(x, z)), P(x, z) = i^{|x & z|} X^x Z^z (from the definition)."""
+    N = 1 << n
+    b = np.arange(N)
+    popc = np.vectorize(lambda v: bin(int(v)).count("1"))
+    r = np.zeros(N * N)
+    for z in range(N):
+        sign = (-1.0) ** popc(b & z)
+        for x in range(N):
+            v = (1j ** bin(x & z).count("1")) * np.sum(rho[b, b ^ x] * sign)
+            r[x + N * z] = v.real
+    return r
+
+
+@pytest.mark.parametrize("flags", [L.PLAN_FUSED, L.PLAN_NO_MERGE, L.PLAN_PLAIN, L.PLAN_NO_RESCALE])
+@pytest.mark.parametrize("dtype", [L.F64, L.F32])
+@pytest.mark.parametrize("n", [2, 4])
+def test_dm_plan_operators_reproduce_kraus_oracle(n, dtype, flags):
+    # the density-matrix planner (gate + depolarising + relaxation lowered to
+    # Pauli-transfer operators, merged, rescaled, grouped): its operators,
+    # applied to the coefficients of |0..0><0..0|, give the Pauli coefficients
+    # of the Kraus-form oracle's density matrix
+    gates = inputs.random_circuit(n, 40, 7700 + n)
+    noise = inputs.noise_params(n, seed=7800 + n)
+    with sim.Plan(L.DM, n, gates, dtype, noise, flags=flags) as pl:
+        ops = pl.ops()
+        _, _, on = pl.layout()
+    assert sum(on) == len(gates)
+    N = 1 << n
+    r = np.zeros(N * N, complex)
+    r[N * np.arange(N)] = 1.0  # Tr(|0><0| X^x Z^z) = [x = 0]
+    for bits, M in ops:
+        assert np.max(np.abs(M.imag)) == 0.0
+        r = apply_local(r, 2 * n, bits, M)
+    ref = pauli_coefficients(oracle.dm_run(n, gates, noise), n)
+    assert np.max(np.abs(r.imag)) == 0.0
+    assert np.max(np.abs(r.real - ref)) <= 1e-12
