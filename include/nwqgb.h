@@ -213,10 +213,11 @@ int nwq_plan_create(int kind, int n, int dtype, const nwq_gate* gates, size_t ng
                     const nwq_noise_model* nm, uint32_t flags, void* stream, nwq_plan** out);
 
 /* Plan form by environment: NWQ_PLAN=plain (one gate per pass), fused (the
- * default) or tc (tensor-core blocks where supported: complex64 state vectors
- * of >= 12 qubits) applies to nwq_plan_create, nwq_sv_apply_circuit and
- * nwq_dm_apply_circuit_noisy calls whose flags name neither NWQ_PLAN_PLAIN nor
- * NWQ_PLAN_TC and that give no tuning; read once per process. */
+ * default), tc (tensor-core blocks where supported: complex64 state vectors
+ * of >= 12 qubits) or commute (NWQ_PLAN_COMMUTE) applies to nwq_plan_create,
+ * nwq_sv_apply_circuit and nwq_dm_apply_circuit_noisy calls whose flags name
+ * none of NWQ_PLAN_PLAIN, NWQ_PLAN_TC, NWQ_PLAN_COMMUTE and that give no
+ * tuning; read once per process. */
 
 /* Run a plan on a state of matching kind, n and dtype.  Asynchronous. */
 int nwq_plan_run(nwq_state* st, const nwq_plan* plan);
