@@ -968,9 +968,6 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
     plan.sweeps.push_back(sd);
   }
 
-  plan.exec_ops.clear();
-  for (int i : order) plan.exec_ops.push_back(ops[i]);
-
   // device tables
   plan.ops.clear();
   plan.ents.clear();
@@ -1071,6 +1068,10 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
   if (cplx) build_phases(ops, order, plan, opt.register_bits);
   double state_bytes = (double)plan.elem_bytes * (double)(1ull << B);
   plan.bytes = 2.0 * state_bytes * (double)plan.sweeps.size();
+  // the operators in execution order, moved (not copied): the caller's list is spent
+  plan.exec_ops.clear();
+  plan.exec_ops.reserve(order.size());
+  for (int i : order) plan.exec_ops.push_back(std::move(ops[i]));
 }
 
 }  // namespace nwq

@@ -88,7 +88,8 @@ bool lower_dm(const nwq_gate* g, size_t ng, int n, const nwq_noise_model* nm, st
 bool tc_fuse(const std::vector<BitOp>& ops, int n, std::vector<TcBlock>& out, std::string& err);
 bool build_tc_plan(const std::vector<BitOp>& ops, Plan& plan, std::string& err);
 
-// Merge + sweep grouping + device table layout.
+// Merge + sweep grouping + device table layout.  The operators end up moved
+// into plan.exec_ops (execution order); `ops` is left spent.
 void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan);
 
 // Verify the device tables of a built plan against the kernels' bounds
