@@ -293,6 +293,18 @@ int nwq_plan_tc_blocks(const nwq_plan* plan, int* qubits, double* mats);
  * per-qubit scales included.  Any pointer may be NULL.  Host only. */
 int nwq_plan_ops(const nwq_plan* plan, int* k, int* bits, double* mats);
 
+/* Test hook: the pass plan nwq_expect_pauli_sum makes for nt terms on an
+ * n-qubit state vector (host only).  *npass tiled passes; pass p reads the
+ * index bits tile_masks[p] of each tile (its low bits contiguous) and
+ * evaluates term records term_range[2p] .. term_range[2p] + term_range[2p+1]
+ * - 1; record r: xl[r], zl[r] = the term's x and z bits inside the tile
+ * (tile-local positions), zh[r] = its z bits outside, y[r] = |x & z| mod 4,
+ * out[r] = its term index (nt: the identity string, for NWQ_EXPECT_NORMALIZE).
+ * *nfb terms fb[0 ..] whose X support fits no tile go to the general kernel.
+ * Arrays hold nt + 1 entries; any pointer may be NULL. */
+int nwq_expect_plan(int n, const nwq_pauli_term* terms, size_t nt, int normalize, int* npass, uint64_t* tile_masks,
+                    int* term_range, uint32_t* xl, uint32_t* zl, uint64_t* zh, int* y, int* out, int* nfb, int* fb);
+
 /* Test hook: number of bounded waits (MMA completion) that ran out in the
  * tensor-core kernel on the current device since the library was loaded;
  * 0 in a healthy run.  A wait that runs out leaves its tile unwritten.

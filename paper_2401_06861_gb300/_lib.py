@@ -104,6 +104,9 @@ def lib():
         "nwq_plan_verify": (i32, [vp]),
         "nwq_plan_tc_blocks": (i32, [vp, P(i32), P(dbl)]),
         "nwq_plan_ops": (i32, [vp, P(i32), P(i32), P(dbl)]),
+        "nwq_expect_plan": (i32, [i32, P(PauliTerm), sz, i32, P(i32), P(ctypes.c_uint64), P(i32),
+                                  P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint64), P(i32), P(i32),
+                                  P(i32), P(i32)]),
         "nwq_tc_timeouts": (i32, [P(i32)]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),

@@ -550,6 +550,43 @@ extern "C" int nwq_plan_ops(const nwq_plan* plan, int* k, int* bits, double* mat
   return NWQ_OK;
 }
 
+extern "C" int nwq_expect_plan(int n, const nwq_pauli_term* terms, size_t nt, int normalize, int* npass,
+                               uint64_t* tile_masks, int* term_range, uint32_t* xl, uint32_t* zl, uint64_t* zh,
+                               int* y, int* out, int* nfb, int* fb) {
+  if (n < 1 || n > 34) return fail(NWQ_EINVAL, "n must be 1..34");
+  if (nt && !terms) return fail(NWQ_EINVAL, "terms is NULL");
+  const uint64_t qmask = (1ull << n) - 1;
+  for (size_t t = 0; t < nt; t++)
+    if ((terms[t].x_mask & ~qmask) || (terms[t].z_mask & ~qmask)) return fail(NWQ_EINVAL, "Pauli mask out of range");
+  std::vector<ExpPass> passes(nt + 1);
+  std::vector<ExpTerm> eterms(nt + 1);
+  std::vector<int> fbv(nt + 1), work(2 * nt + 2);
+  std::vector<SvChunk> chunks(nt + 1);
+  SvExpectHost h{passes.data(), eterms.data(), fbv.data(), chunks.data(), work.data()};
+  SvExpectCounts c{};
+  plan_sv_expect(n, terms, nt, normalize != 0, h, c);
+  if (npass) *npass = c.npass;
+  if (nfb) *nfb = c.nfb;
+  for (int p = 0; p < c.npass; p++) {
+    const ExpPass& P = passes[p];
+    if (tile_masks) tile_masks[p] = ((1ull << P.m) - 1) | P.hmask;
+    if (term_range) {
+      term_range[2 * p] = P.k0;
+      term_range[2 * p + 1] = P.nk;
+    }
+  }
+  for (int r = 0; r < c.nterms; r++) {
+    if (xl) xl[r] = eterms[r].xl;
+    if (zl) zl[r] = eterms[r].zl;
+    if (zh) zh[r] = eterms[r].zh;
+    if (y) y[r] = eterms[r].y;
+    if (out) out[r] = eterms[r].out;
+  }
+  if (fb)
+    for (int i = 0; i < c.nfb; i++) fb[i] = fbv[i];
+  return NWQ_OK;
+}
+
 extern "C" int nwq_tc_timeouts(int* count) {
   if (!count) return fail(NWQ_EINVAL, "count is NULL");
   CK(cudaDeviceSynchronize(), "device synchronize");

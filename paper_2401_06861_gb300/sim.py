@@ -156,6 +156,32 @@ def _tuning(t):
     return L.PlanTuning(int(t.get("tile_bits", 0)), int(t.get("fusion_bits", 0)), int(t.get("register_bits", 0)))
 
 
+def expect_plan(n, terms, normalize=False):
+    """The pass plan of nwq_expect_pauli_sum (host only): dict(passes=[(tile mask,
+    [(out, xl, zl, zh, y), ...]), ...], general=[term index, ...])."""
+    nt = len(terms)
+    arr = encode_terms(terms)
+    m = nt + 1
+    P32, P64 = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)
+    npass, nfb = ctypes.c_int(), ctypes.c_int()
+    tiles = np.zeros(m, np.uint64)
+    rng = np.zeros(2 * m, np.int32)
+    xl, zl = np.zeros(m, np.uint32), np.zeros(m, np.uint32)
+    zh = np.zeros(m, np.uint64)
+    y, out, fb = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m, np.int32)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    check(L.lib().nwq_expect_plan(n, arr, nt, int(normalize), ctypes.byref(npass), tiles.ctypes.data_as(P64),
+                                  rng.ctypes.data_as(P32), xl.ctypes.data_as(u32), zl.ctypes.data_as(u32),
+                                  zh.ctypes.data_as(P64), y.ctypes.data_as(P32), out.ctypes.data_as(P32),
+                                  ctypes.byref(nfb), fb.ctypes.data_as(P32)))
+    passes = []
+    for p in range(npass.value):
+        k0, nk = int(rng[2 * p]), int(rng[2 * p + 1])
+        passes.append((int(tiles[p]), [(int(out[r]), int(xl[r]), int(zl[r]), int(zh[r]), int(y[r]))
+                                       for r in range(k0, k0 + nk)]))
+    return dict(passes=passes, general=[int(v) for v in fb[:nfb.value]])
+
+
 def tc_timeouts():
     """Bounded waits of the tensor-core kernel that ran out on the current device (0 when healthy)."""
     c = ctypes.c_int()

@@ -136,3 +136,64 @@ def test_dm_plan_operators_reproduce_kraus_oracle(n, dtype, flags):
     ref = pauli_coefficients(oracle.dm_run(n, gates, noise), n)
     assert np.max(np.abs(r.imag)) == 0.0
     assert np.max(np.abs(r.real - ref)) <= 1e-12
+
+
+def _deposit(v, S):
+    out, i = 0, 0
+    for b in range(64):
+        if (S >> b) & 1:
+            if (v >> i) & 1:
+                out |= 1 << b
+            i += 1
+    return out
+
+
+def _expect_terms(n, nt, seed):
+    # Z strings, X/Y on low qubits, on high qubits, and wide X supports
+    rng = np.random.default_rng(seed)
+    terms = []
+    for t in range(nt):
+        kind = t % 4
+        if kind == 0:
+            x = 0
+        elif kind == 1:
+            x = int(rng.integers(1, 1 << min(n, 12)))
+        elif kind == 2:
+            qs = rng.choice(n, size=min(n, 3), replace=False)
+            x = int(sum(1 << int(q) for q in qs))
+        else:
+            qs = rng.choice(n, size=min(n, 14), replace=False)
+            x = int(sum(1 << int(q) for q in qs))
+        z = int(rng.integers(0, 1 << n))
+        terms.append((x, z, float(rng.normal())))
+    return terms
+
+
+@pytest.mark.parametrize("n", [3, 12, 20, 30])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_expectation_pass_plan_invariants(n, normalize):
+    terms = _expect_terms(n, 300, 900 + n)
+    plan = sim.expect_plan(n, terms, normalize)
+    T = min(n, 12)
+    seen = {}
+    for p, (tile, recs) in enumerate(plan["passes"]):
+        assert bin(tile).count("1") == T and tile < (1 << n) and 0 < len(recs) <= 256
+        m = 0
+        while (tile >> m) & 1:
+            m += 1
+        assert m >= min(T, 4)  # contiguous low bits
+        for out, xl, zl, zh, y in recs:
+            seen[out] = seen.get(out, 0) + 1
+            x, z = (0, 0) if out == len(terms) else (terms[out][0], terms[out][1])
+            assert _deposit(xl, tile) == x and x & ~tile == 0  # X support inside the tile
+            assert _deposit(zl, tile) | zh == z and zh & tile == 0
+            assert y == bin(x & z).count("1") % 4
+            if out == len(terms):  # the identity string rides with the low-tile terms
+                assert normalize and tile == (1 << T) - 1
+    for t in plan["general"]:
+        seen[t] = seen.get(t, 0) + 1
+        assert bin(terms[t][0] & ~0xF).count("1") > T - 4  # no tile can hold its X support
+    want = set(range(len(terms))) | ({len(terms)} if normalize else set())
+    assert set(seen) == want and all(v == 1 for v in seen.values())
+    if n >= 20:
+        assert plan["general"]  # the wide X supports take the general kernel
