@@ -301,7 +301,8 @@ int nwq_plan_ops(const nwq_plan* plan, int* k, int* bits, double* mats);
  * (tile-local positions), zh[r] = its z bits outside, y[r] = |x & z| mod 4,
  * out[r] = its term index (nt: the identity string, for NWQ_EXPECT_NORMALIZE).
  * *nfb terms fb[0 ..] whose X support fits no tile go to the general kernel.
- * Arrays hold nt + 1 entries; any pointer may be NULL. */
+ * Sizes: tile_masks nt + 1 entries, term_range 2 (nt + 1) ints, xl, zl, zh,
+ * y and out nt + 1 entries, fb nt entries; any pointer may be NULL. */
 int nwq_expect_plan(int n, const nwq_pauli_term* terms, size_t nt, int normalize, int* npass, uint64_t* tile_masks,
                     int* term_range, uint32_t* xl, uint32_t* zl, uint64_t* zh, int* y, int* out, int* nfb, int* fb);
 
@@ -369,13 +370,26 @@ int nwq_probs(nwq_state* st, double readout_e, double* out_host);
  * process exits.
  *   - nt <= NWQ_NOALLOC_MAX_TERMS, else NWQ_EINVAL (nothing is computed);
  *   - the first call on a device looks up the scratch array's device address
- *     on that device; make that first call before any stream capture;
+ *     on that device, making that device current for the lookup and then
+ *     restoring the caller's device (host threads that change the current
+ *     device at the same moment race with it); make that first call before
+ *     any stream capture;
  *   - all calls share the scratch array (it keeps the last call's contents),
  *     so calls that overlap on the GPU race: serialise them;
- *   - arguments, flags, results and synchronisation as nwq_expect_pauli_sum. */
+ *   - state vectors: at most 256 blocks for strings whose X support fits no
+ *     tile, and the tiled grid reduced until its partial sums fit the array;
+ *     the results differ from nwq_expect_pauli_sum only in FP64 summation order;
+ *   - arguments, flags and results as nwq_expect_pauli_sum; every call
+ *     synchronises the state's stream before it returns. */
 #define NWQ_NOALLOC_MAX_TERMS 256
 int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term* terms, size_t nt, double* out_host,
                                  uint32_t flags);
+
+/* Test hook: the launch shape of the state-vector expectation passes for nt
+ * terms: *grid tiled-kernel blocks and *fblocks general-kernel blocks, of
+ * nwq_expect_pauli_sum (noalloc = 0) or nwq_expect_pauli_sum_noalloc
+ * (noalloc = 1).  NWQ_EINVAL for density matrices.  Host only. */
+int nwq_expect_launch_shape(const nwq_state* st, size_t nt, int noalloc, int* grid, int* fblocks);
 
 /* ---------------------------------------------------------------- batched VQE */
 
@@ -487,6 +501,16 @@ int nwq_device_sync(nwq_state* st);
 /* Number of device kernels this library has launched in this process
  * (monotonic; for accounting in benchmarks). */
 uint64_t nwq_launch_count(void);
+
+/* Measurement helper (the paper has no counterpart): the arithmetic rate of
+ * one pipe of the current device, for roofline denominators.  A grid of
+ * several CTAs per SM runs independent FMA chains per thread (8 FP64 or 16
+ * FP32 chains, enough to cover the pipe latency) for about 60 ms after a
+ * warm-up launch, timed with CUDA events on a private stream; *fma_per_second
+ * = thread-level FMA instructions retired per second (2 flops each).  Uses
+ * and frees a small device buffer; synchronises its own stream only. */
+enum nwq_probe { NWQ_PROBE_FP64_FMA = 0, NWQ_PROBE_FP32_FMA = 1 };
+int nwq_peak_probe(int what, double* fma_per_second);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, 
 F32, F64 = 1, 2
 SV, DM = 1, 2
 PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED, PLAN_TC, PLAN_COMMUTE = 0, 1, 2, 4, 8, 16, 32
+PROBE_FP64_FMA, PROBE_FP32_FMA = 0, 1
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
 NOALLOC_MAX_TERMS = 256
@@ -112,6 +113,7 @@ def lib():
         "nwq_jit_shutdown": (i32, []),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
+        "nwq_expect_launch_shape": (i32, [vp, sz, i32, P(i32), P(i32)]),
         "nwq_probs": (i32, [vp, dbl, P(dbl)]),
         "nwq_batch_energy": (i32, [i32, i32, P(Gate), sz, vp, i32, i32, P(PauliTerm), sz, P(dbl), i32, vp, vp]),
         "nwq_batch_create": (i32, [i32, P(BatchTemplate), i32, i32, vp, pp]),
@@ -124,6 +126,7 @@ def lib():
         "nwq_last_error": (ctypes.c_char_p, []),
         "nwq_device_sync": (i32, [vp]),
         "nwq_launch_count": (ctypes.c_uint64, []),
+        "nwq_peak_probe": (i32, [i32, P(dbl)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnwqgb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["sweep_kernels.cu", "expect_kernels.cu", "batch_kernels.cu", "noalloc.cu", "tc_kernels.cu", "planner.cpp", "tc_plan.cpp", "plan_check.cpp", "jit.cpp", "expect_host.cpp", "abi.cpp", "batch_host.cpp"]
+SOURCES = ["sweep_kernels.cu", "expect_kernels.cu", "batch_kernels.cu", "noalloc.cu", "tc_kernels.cu", "probe.cu", "planner.cpp", "tc_plan.cpp", "plan_check.cpp", "jit.cpp", "expect_host.cpp", "abi.cpp", "batch_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -700,10 +700,8 @@ extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, 
   SvExpectHost h{passes.data(), eterms.data(), fb.data(), chunks.data(), work.data()};
   SvExpectCounts c{};
   plan_sv_expect(st->n, terms, nt, norm, h, c);
-  int grid = (int)std::min<uint64_t>(1ull << (st->n - std::min(st->n, kExpTileBits)),
-                                     (uint64_t)st->sm_count * (f64 ? 2 : 4));
-  const uint64_t N = 1ull << st->n;
-  const int fblocks = (int)std::min<uint64_t>((N + 255) / 256, (uint64_t)st->sm_count * 4);
+  int grid = 0, fblocks = 0;
+  sv_expect_shape(st, nt, 0, &grid, &fblocks);
   std::vector<unsigned char> stage(sv_expect_stage_bytes(nt));
   void* d = nullptr;
   CK(cudaMallocAsync(&d, sv_expect_scratch_bytes(nt, grid, fblocks), s), "scratch allocation");

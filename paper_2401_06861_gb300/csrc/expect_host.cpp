@@ -117,6 +117,21 @@ void plan_sv_expect(int n, const nwq_pauli_term* terms, size_t nt, bool norm, Sv
   }
 }
 
+void sv_expect_shape(const nwq_state* st, size_t nt, size_t scratch_limit, int* grid, int* fblocks) {
+  const bool f64 = st->dtype == NWQ_F64;
+  const uint64_t N = 1ull << st->n;
+  uint64_t fb = (N + 255) / 256;
+  if (fb > (uint64_t)st->sm_count * 4) fb = (uint64_t)st->sm_count * 4;
+  uint64_t g = 1ull << (st->n - (st->n < kExpTileBits ? st->n : kExpTileBits));
+  if (g > (uint64_t)st->sm_count * (f64 ? 2 : 4)) g = (uint64_t)st->sm_count * (f64 ? 2 : 4);
+  if (scratch_limit) {
+    if (fb > (uint64_t)kNoallocMaxGeneralBlocks) fb = kNoallocMaxGeneralBlocks;
+    while (g > 1 && sv_expect_scratch_bytes(nt, (int)g, (int)fb) > scratch_limit) g--;
+  }
+  *grid = (int)g;
+  *fblocks = (int)fb;
+}
+
 cudaError_t sv_expect_enqueue(const nwq_state* st, const nwq_pauli_term* terms, size_t nt, uint32_t flags,
                               double* out_host, const SvExpectHost& h, const SvExpectCounts& c, int grid,
                               int fblocks, unsigned char* stage, unsigned char* dev) {

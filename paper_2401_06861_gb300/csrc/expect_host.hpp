@@ -41,6 +41,16 @@ constexpr size_t sv_expect_scratch_bytes(size_t nt, int grid, int fblocks) {
          sv_expect_up16((size_t)fblocks * kExpectChunk * 8);
 }
 
+// Launch shape of the state-vector passes: tiled-kernel grid and general-
+// kernel blocks.  The allocating entry point uses one tiled block per tile up
+// to 2 (FP64) / 4 (FP32) per SM and one general block per 256 amplitudes up to
+// 4 per SM.  The allocation-free entry point (scratch_limit > 0) caps the
+// general blocks at kNoallocMaxGeneralBlocks and shrinks the tiled grid until
+// sv_expect_scratch_bytes fits scratch_limit; both change only how the FP64
+// partial sums are partitioned, not which products are summed.
+constexpr int kNoallocMaxGeneralBlocks = 256;
+void sv_expect_shape(const nwq_state* st, size_t nt, size_t scratch_limit, int* grid, int* fblocks);
+
 // Stage the tables (stage: sv_expect_stage_bytes(nt) host bytes), copy them
 // to dev (sv_expect_scratch_bytes(nt, grid, fblocks) device bytes) and enqueue
 // every launch on st's stream, ending with the copy of the result to out_host.

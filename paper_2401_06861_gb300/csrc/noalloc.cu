@@ -11,9 +11,11 @@
 // library holds that array until the process exits.  All calls share it and
 // it keeps the last call's contents; each call clears or writes every slot
 // before reading it.  State vectors take the same passes and kernels as
-// nwq_expect_pauli_sum (host tables on the stack), with the tiled grid
-// reduced until its per-block partial sums fit the array.  Calls that overlap on the GPU
-// (two host threads, or two streams) race on the array and must be
+// nwq_expect_pauli_sum (host tables on the stack) with two launch-shape
+// reductions: the general (wide-X) kernel uses at most 256 blocks, and the
+// tiled grid is reduced until its per-block partial sums fit the array.  Both
+// change only the partition of the FP64 partial sums.  Calls that overlap on
+// the GPU (two host threads, or two streams) race on the array and must be
 // serialised by the caller.
 #include <cuda_runtime.h>
 
@@ -30,13 +32,12 @@ namespace {
 
 constexpr int kMaxTerms = NWQ_NOALLOC_MAX_TERMS;
 constexpr size_t kScratchBytes = 192 * 1024;
-constexpr int kMaxGeneralBlocks = 256;  // partial sums per general-kernel pass
 // DM: term table (x, z, coefficient per term) then the values
 constexpr size_t kDmTable = 3 * kMaxTerms * sizeof(uint64_t);
 static_assert(kDmTable + (kMaxTerms + 2) * sizeof(double) <= kScratchBytes, "DM scratch");
 // SV: the tables and general partials for kMaxTerms terms leave room for the
 // tiled partials of at least 32 blocks
-static_assert(sv_expect_scratch_bytes(kMaxTerms, 32, kMaxGeneralBlocks) <= kScratchBytes, "SV scratch");
+static_assert(sv_expect_scratch_bytes(kMaxTerms, 32, kNoallocMaxGeneralBlocks) <= kScratchBytes, "SV scratch");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -119,16 +120,18 @@ extern "C" int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term*
   SvExpectHost h{passes, eterms, fb, chunks, work};
   SvExpectCounts c{};
   plan_sv_expect(st->n, terms, nt, norm, h, c);
-  const uint64_t N = 1ull << st->n;
-  uint64_t fblocks = (N + 255) / 256;
-  if (fblocks > (uint64_t)st->sm_count * 4) fblocks = (uint64_t)st->sm_count * 4;
-  if (fblocks > (uint64_t)kMaxGeneralBlocks) fblocks = kMaxGeneralBlocks;
-  uint64_t grid = 1ull << (st->n - (st->n < kExpTileBits ? st->n : kExpTileBits));
-  if (grid > (uint64_t)st->sm_count * (f64 ? 2 : 4)) grid = (uint64_t)st->sm_count * (f64 ? 2 : 4);
-  while (grid > 1 && sv_expect_scratch_bytes(nt, (int)grid, (int)fblocks) > kScratchBytes) grid--;
-  e = sv_expect_enqueue(st, terms, nt, flags, out_host, h, c, (int)grid, (int)fblocks, stage, base);
+  int grid = 0, fblocks = 0;
+  sv_expect_shape(st, nt, kScratchBytes, &grid, &fblocks);
+  e = sv_expect_enqueue(st, terms, nt, flags, out_host, h, c, grid, fblocks, stage, base);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return set_error(NWQ_ECUDA, cudaGetErrorString(e));
+  return NWQ_OK;
+}
+
+extern "C" int nwq_expect_launch_shape(const nwq_state* st, size_t nt, int noalloc, int* grid, int* fblocks) {
+  if (!st || !grid || !fblocks) return set_error(NWQ_EINVAL, "NULL argument");
+  if (st->kind != NWQ_SV) return set_error(NWQ_EINVAL, "launch shape: state vectors only");
+  sv_expect_shape(st, nt, noalloc ? kScratchBytes : 0, grid, fblocks);
   return NWQ_OK;
 }

@@ -68,3 +68,93 @@ def test_noalloc_rejects_too_many_terms():
         assert b"NWQ_NOALLOC_MAX_TERMS" in lib.nwq_last_error()
         rc, out = call(lib.nwq_expect_pauli_sum_noalloc, st, terms[:L.NOALLOC_MAX_TERMS], L.EXPECT_SUM)
         assert rc == L.OK and np.isfinite(out[0])
+
+
+def launch_shape(st, nt, noalloc):
+    g, fb = ctypes.c_int(0), ctypes.c_int(0)
+    assert L.lib().nwq_expect_launch_shape(st.h, nt, noalloc, ctypes.byref(g), ctypes.byref(fb)) == L.OK
+    return g.value, fb.value
+
+
+def wide_terms(n, count, seed):
+    """Strings over every tile pass and the general kernel: Z-type and
+    low-X strings, X supports on high bits, and X supports wider than any
+    tile (more than 8 bits above bit 3)."""
+    rng = np.random.default_rng(seed)
+    t = inputs.tfim_terms(n) + inputs.z_terms(n)
+    for k in range(count - len(t)):
+        w = (2, 6, 11, 16)[k % 4]
+        bits = rng.choice(n, size=w, replace=False)
+        x = int(sum(1 << int(b) for b in bits))
+        t.append((x, int(rng.integers(0, 1 << n)), float(rng.uniform(-1, 1))))
+    return t
+
+
+@pytest.mark.parametrize("dtype", [L.F32, L.F64])
+def test_noalloc_reduced_launch_shape_matches_twice(dtype):
+    # 256 terms on 2^22 amplitudes: the allocation-free call caps the general
+    # kernel's blocks at 256 and shrinks the tiled grid until its partial sums
+    # fit the static array; only the FP64 summation order may change
+    lib = L.lib()
+    n, nt = 22, L.NOALLOC_MAX_TERMS
+    with State(L.SV, n, dtype) as st:
+        g_a, fb_a = launch_shape(st, nt, 0)
+        g_n, fb_n = launch_shape(st, nt, 1)
+        assert g_n < g_a and fb_n == 256 < fb_a, (g_a, fb_a, g_n, fb_n)
+        for call_no, seed in enumerate((21, 22)):
+            st.load(inputs.random_state(n, seed))
+            terms = wide_terms(n, nt - call_no, seed)
+            for flags in (L.EXPECT_TERMS, L.EXPECT_SUM | L.EXPECT_NORMALIZE):
+                rc_a, ref = call(lib.nwq_expect_pauli_sum, st, terms, flags)
+                rc_b, got = call(lib.nwq_expect_pauli_sum_noalloc, st, terms, flags)
+                assert rc_a == L.OK and rc_b == L.OK, lib.nwq_last_error()
+                err = float(np.max(np.abs(got - ref)))
+                assert err <= 1e-12, (call_no, flags, err)
+
+
+class DefaultPool:
+    """Used-memory figures of the device's default stream-ordered memory pool
+    (driver API through ctypes); the allocating entry point takes its scratch
+    from that pool."""
+    USED_CURRENT, USED_HIGH = 7, 8  # CUmemPool_attribute
+
+    def __init__(self, ordinal):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        assert self.cu.cuInit(0) == 0
+        dev = ctypes.c_int(0)
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), ordinal) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def get(self, attr):
+        v = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolGetAttribute(self.pool, attr, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):  # the high watermark restarts from the current use
+        v = ctypes.c_uint64(0)
+        assert self.cu.cuMemPoolSetAttribute(self.pool, self.USED_HIGH, ctypes.byref(v)) == 0
+
+
+def test_noalloc_allocates_no_device_memory():
+    import torch
+    lib = L.lib()
+    n = 22
+    pool = DefaultPool(torch.cuda.current_device())
+    with State(L.SV, n, L.F32) as st:
+        st.load(inputs.random_state(n, 31))
+        terms = wide_terms(n, L.NOALLOC_MAX_TERMS, 31)
+        for fn in (lib.nwq_expect_pauli_sum_noalloc, lib.nwq_expect_pauli_sum):  # load every kernel once
+            assert call(fn, st, terms, L.EXPECT_TERMS)[0] == L.OK
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        pool.reset_high()
+        used0 = pool.get(pool.USED_CURRENT)
+        for flags in (L.EXPECT_TERMS, L.EXPECT_SUM):
+            assert call(lib.nwq_expect_pauli_sum_noalloc, st, terms, flags)[0] == L.OK
+        assert pool.get(pool.USED_HIGH) == used0 == pool.get(pool.USED_CURRENT)
+        assert torch.cuda.mem_get_info()[0] == free0
+        # the same probe sees the allocating entry point's scratch
+        pool.reset_high()
+        assert call(lib.nwq_expect_pauli_sum, st, terms, L.EXPECT_TERMS)[0] == L.OK
+        assert pool.get(pool.USED_HIGH) > used0
