@@ -71,7 +71,9 @@ def lib():
         _lib.oracle_sv_probs.argtypes = [D, c_int, c_dbl, D]
         _lib.oracle_dm_probs.argtypes = [D, c_int, c_dbl, D]
         _lib.oracle_traj_run.argtypes = [D, c_int, c_int, Ip, Ip, D, D, c_int, D, D, c_dbl, c_dbl, c_dbl, c_dbl,
-                                         ctypes.c_uint, D, c_int]
+                                         ctypes.c_uint, D, c_int, D, Ip]
+        _lib.oracle_set_threads.argtypes = [c_int]
+        _lib.oracle_max_threads.restype = c_int
         _lib.oracle_traj_draws.argtypes = [c_int, Ip, c_int, c_dbl, c_dbl, c_dbl, c_dbl, ctypes.c_uint]
     return _lib
 
@@ -123,6 +125,27 @@ def sv_run(n, gates, psi0=None):
     return psi
 
 
+def sv_run_inplace(psi, n, gates):
+    """Apply ``gates`` to the complex128 array ``psi`` in place (no copy of the
+    state; for timing large states)."""
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous and psi.size == 1 << n
+    ng, kinds, qs, th, mats = _encode(gates)
+    rc = lib().oracle_sv_run(_p(psi.view(np.float64)), n, ng, _p(kinds, ctypes.c_int),
+                             _p(qs, ctypes.c_int), _p(th), _p(mats))
+    if rc:
+        raise ValueError("oracle_sv_run failed")
+    return psi
+
+
+def set_threads(t):
+    """OpenMP threads of the oracle's parallel loops."""
+    lib().oracle_set_threads(int(t))
+
+
+def max_threads():
+    return int(lib().oracle_max_threads())
+
+
 def dm_zero(n):
     N = 1 << n
     rho = np.zeros((N, N), np.complex128)
@@ -169,18 +192,25 @@ def traj_draws(gates, noise):
                                        ctypes.c_double(p1), ctypes.c_double(p2), flags))
 
 
-def traj_run(n, gates, noise, uniforms):
-    """One quantum trajectory (final normalised state) driven by ``uniforms``."""
+def traj_run(n, gates, noise, uniforms, margins=False):
+    """One quantum trajectory (final normalised state) driven by ``uniforms``.
+
+    With ``margins``, returns (psi, margin, kind): per draw consumed, its
+    relative distance to the nearest outcome boundary and its kind (0
+    depolarising, 1 amplitude damping, 2 phase damping)."""
     psi = np.array(zero_state(n), dtype=np.complex128, copy=True)
     ng, kinds, qs, th, mats = _encode(gates)
     noisy, T1, T2, t1, t2, p1, p2, flags = _noise_args(n, noise)
     u = np.ascontiguousarray(uniforms, np.float64)
+    mg = np.full(max(len(u), 1), np.inf)
+    kd = np.full(max(len(u), 1), -1, np.int32)
     rc = lib().oracle_traj_run(_p(psi.view(np.float64)), n, ng, _p(kinds, ctypes.c_int), _p(qs, ctypes.c_int),
                                _p(th), _p(mats), noisy, _p(T1), _p(T2), ctypes.c_double(t1), ctypes.c_double(t2),
-                               ctypes.c_double(p1), ctypes.c_double(p2), flags, _p(u), len(u))
+                               ctypes.c_double(p1), ctypes.c_double(p2), flags, _p(u), len(u),
+                               _p(mg) if margins else None, _p(kd, ctypes.c_int) if margins else None)
     if rc < 0:
         raise ValueError(f"oracle_traj_run failed ({rc})")
-    return psi
+    return (psi, mg[:rc], kd[:rc]) if margins else psi
 
 
 def dm_depolarize(rho, n, qubits, p):

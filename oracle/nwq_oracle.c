@@ -25,6 +25,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -152,6 +153,36 @@ static void apply_vec(cx *v, int n, size_t stride, int k, const int *q, const cx
   }
 }
 
+/* The same action on a state vector (stride 1), amplitude groups split over
+ * OpenMP threads (independent: each group's indices are disjoint). */
+static void apply_vec_par(cx *v, int n, int k, const int *q, const cx *U) {
+  size_t N = (size_t)1 << n;
+  size_t m0 = (size_t)1 << q[0];
+  size_t m1 = k == 2 ? ((size_t)1 << q[1]) : 0;
+  int d = 1 << k;
+#pragma omp parallel for schedule(static) if (n >= 16)
+  for (long bb = 0; bb < (long)N; bb++) {
+    size_t b = (size_t)bb;
+    if (b & (m0 | m1)) continue;
+    size_t idx[4];
+    cx in[4], out[4];
+    for (int j = 0; j < d; j++) {
+      idx[j] = b | ((j & 1) ? m0 : 0) | ((j & 2) ? m1 : 0);
+      in[j] = v[idx[j]];
+    }
+    for (int r = 0; r < d; r++) {
+      cx acc = 0;
+      for (int j = 0; j < d; j++) acc += U[r * d + j] * in[j];
+      out[r] = acc;
+    }
+    for (int j = 0; j < d; j++) v[idx[j]] = out[j];
+  }
+}
+
+/* Thread count of the OpenMP loops (benchmark baselines time 1 and all). */
+void oracle_set_threads(int t) { omp_set_num_threads(t > 0 ? t : 1); }
+int oracle_max_threads(void) { return omp_get_max_threads(); }
+
 /* psi <- U psi */
 void oracle_sv_apply(double *psi_reim, int n, int k, const int *q, const double *U_reim) {
   cx U[16];
@@ -168,7 +199,7 @@ int oracle_sv_run(double *psi_reim, int n, int ng, const int *kinds, const int *
     cx U[16];
     int k = gate_matrix(kinds[g], th + 3 * g, mats + 32 * g, U);
     if (!k) return -1;
-    apply_vec(psi, n, 1, k, qs + 2 * g, U);
+    apply_vec_par(psi, n, k, qs + 2 * g, U);
   }
   return 0;
 }
@@ -343,7 +374,12 @@ int oracle_dm_run(double *rho_reim, int n, int ng, const int *kinds, const int *
  *     sqrt(1 - lambda)); the state is then renormalised (its norm after the
  *     Kraus operator is the probability of the branch taken).
  * Returns the number of draws consumed, -1 for an unknown gate, -2 when T2 >
- * 2 T1, -3 when more than nu draws would be needed. */
+ * 2 T1, -3 when more than nu draws would be needed.
+ * margin and kind (may be NULL) receive, per draw consumed, how far the draw
+ * lay from the nearest value at which its outcome changes, relative to the
+ * branch width: depolarising (kind 0): min_j |u - j p/4^k| / (p/4^k) over the
+ * sub-interval ends j = 1 .. 4^k - 1; amplitude damping (kind 1) and phase
+ * damping (kind 2): |u - rate P1| / (rate P1) (+inf when rate P1 = 0). */
 static double prob_one(const cx *psi, int n, int q) {
   size_t N = (size_t)1 << n, m = (size_t)1 << q;
   double s = 0.0;
@@ -359,7 +395,8 @@ static void scale_vec(cx *psi, int n, double f) {
 
 int oracle_traj_run(double *psi_reim, int n, int ng, const int *kinds, const int *qs, const double *th,
                     const double *mats, int noisy, const double *T1_us, const double *T2_us, double t1q_ns,
-                    double t2q_ns, double p1, double p2, unsigned flags, const double *u, int nu) {
+                    double t2q_ns, double p1, double p2, unsigned flags, const double *u, int nu,
+                    double *margin, int *kind) {
   const cx *P1[4] = {PI_, PX_, PY_, PZ_};
   cx *psi = (cx *)psi_reim;
   int used = 0;
@@ -376,7 +413,14 @@ int oracle_traj_run(double *psi_reim, int n, int ng, const int *kinds, const int
     if (flags & 2u) p = p * np / (np - 1.0);
     if (p > 0) {
       if (used >= nu) return -3;
-      double x = u[used++];
+      double x = u[used];
+      if (margin) {
+        double w = p / np, best = INFINITY;
+        for (int j = 1; j < np; j++) best = fmin(best, fabs(x - j * w) / w);
+        margin[used] = best;
+      }
+      if (kind) kind[used] = 0;
+      used++;
       if (x < (np - 1) * p / np) {
         int s = 1 + (int)floor(x * np / p);
         if (s > np - 1) s = np - 1;
@@ -398,8 +442,14 @@ int oracle_traj_run(double *psi_reim, int n, int ng, const int *kinds, const int
         double rate[2] = {gamma, 1.0 - oml};
         for (int step = 0; step < 2; step++) {  /* amplitude damping, then phase damping */
           if (used >= nu) return -3;
-          double x = u[used++];
+          double x = u[used];
           double pr1 = prob_one(psi, n, qq);
+          if (margin) {
+            double thr = rate[step] * pr1;
+            margin[used] = thr > 0 ? fabs(x - thr) / thr : INFINITY;
+          }
+          if (kind) kind[used] = 1 + step;
+          used++;
           size_t N = (size_t)1 << n, m = (size_t)1 << qq;
           if (x < rate[step] * pr1) {
             for (size_t b = 0; b < N; b++) {

@@ -41,12 +41,24 @@ def test_each_trajectory_matches_the_oracle(n, dtype):
     assert d == oracle.traj_draws(g, noise) and d > 0
     u = np.random.default_rng(62 + n).random((ntraj, d))
     got = sim.trajectories(n, g, noise, terms, coeffs, ntraj, dtype, uniforms=u)
-    ref = np.array([oracle.sv_expect(oracle.traj_run(n, g, noise, u[t]), n, terms) for t in range(ntraj)])
+    ref, near = [], []
+    for t in range(ntraj):
+        psi, margin, kind = oracle.traj_run(n, g, noise, u[t], margins=True)
+        ref.append(oracle.sv_expect(psi, n, terms))
+        # A jump is taken when the draw is below rate * P1, with P1 summed
+        # from the stored state.  FP32 storage puts a relative error of at
+        # most a few 2^-24 per gate on P1 (these circuits have 60 gates, so
+        # below 1e-5); a relaxation draw within 1e-4 (relative) of its
+        # threshold may therefore take the other branch in FP32.  The
+        # depolarising draws are compared with FP64 parameters on both sides.
+        near.append(bool(np.any((kind > 0) & (margin <= 1e-4))))
+    ref, near = np.array(ref), np.array(near)
     err = np.abs(got - ref).max(axis=1)
     if dtype == L.F64:
         assert err.max() <= 1e-12
-    else:  # an FP32 rounding can flip a draw sitting on a jump threshold: that trajectory diverges
-        assert np.mean(err > 1e-5) <= 0.05, err
+    else:  # every trajectory with no draw near a threshold matches at the FP32 tolerance
+        assert err[~near].max() <= 1e-5, (err, near)
+        assert near.mean() <= 0.1, near
 
 
 def test_average_converges_to_the_density_matrix():

@@ -76,3 +76,25 @@ def test_depolarising_draw_selects_the_pauli_string():
         got = oracle.traj_run(2, g2, noise2, [(s - 0.5) * p2 / 16])
         want = dense.embed1(2, 1, P[b]) @ dense.embed1(2, 0, P[a]) @ base
         np.testing.assert_allclose(got, want, atol=1e-15)
+
+
+def test_draw_margins_measure_the_distance_to_the_outcome_boundary():
+    # amplitude damping from |1>: P1 = 1, the boundary is gamma itself; the
+    # phase-damping draw of T2 = 2 T1 has rate 0 (no boundary: +inf)
+    T1 = 100.0
+    noise = dict(T1_us=np.array([T1]), T2_us=np.array([2 * T1]), t1q_ns=5000.0, t2q_ns=0.0, p1=0.0, p2=0.0,
+                 readout_e=0.0)
+    gamma = 1.0 - np.exp(-5000.0 / (T1 * 1e3))
+    _, mg, kd = oracle.traj_run(1, [inputs.gate("X", (0,))], noise, [gamma * (1 - 1e-9), 0.5], margins=True)
+    assert list(kd) == [1, 2]
+    assert abs(mg[0] - 1e-9) <= 1e-15 and np.isinf(mg[1])
+    # |+>: P1 = 1/2, the boundary is gamma / 2
+    _, mg, _ = oracle.traj_run(1, [inputs.gate("H", (0,))], noise, [0.75 * gamma, 0.5], margins=True)
+    assert abs(mg[0] - 0.5) <= 1e-12
+    # depolarising: the draw's distance to the nearest of the sub-interval ends p/4, 2p/4, 3p/4, in units of p/4
+    p = 0.3
+    noise1 = dict(T1_us=np.array([1.0]), T2_us=np.array([1.0]), t1q_ns=0.0, t2q_ns=0.0, p1=p, p2=0.0,
+                  readout_e=0.0)
+    for x, want in ((0.5 * p / 4, 0.5), (1.9 * p / 4, 0.1), (3.2 * p / 4, 0.2), (0.9, 0.9 * 4 / p - 3)):
+        _, mg, kd = oracle.traj_run(1, [inputs.gate("H", (0,))], noise1, [x], margins=True)
+        assert list(kd) == [0] and abs(mg[0] - want) <= 1e-12, (x, mg, want)
