@@ -1,12 +1,22 @@
-"""Benchmark: noisy density-matrix TFIM evolution (n = 13, 20 Trotter steps, FP64).
+"""Benchmark of the hot path of NWQ-Sim's simulators (paper Sec. II-III) on one GB300.
 
-One step = one pass of the whole hot path over one synthetic input:
-  reset rho to |0..0><0..0|  ->  run the lowered noisy circuit (980 gates, each
-  followed by depolarising + thermal-relaxation noise; 60 shared-memory sweeps)
-  ->  <Z_i> and <H>  ->  outcome distribution with 2% readout error.
-Metric: gate-updates/s = (gates x 4^n density-matrix elements updated) / s.
+Default line: the largest single-GPU state-vector workload.  Transverse-field
+Ising chain, n = 33 qubits in complex128 (a 128 GiB state), 10 first-order
+Trotter steps (J = 1, dt = 0.05, per-qubit fields h_i ~ U(0.5, 2) from seed
+3334; per step CX RZ(2 J dt) CX on the 32 bonds, then RX(2 h_i dt) on every
+qubit: 1290 gates), run as one reusable fused plan.  One step = reset to
+|0..0>  ->  the whole circuit  ->  <Z_i> for every qubit and <H> (FP64 sums).
+Metric: gate-updates/s = sum over the original (unfused) gates of the
+amplitudes each logically updates (2^n per one-qubit or diagonal gate,
+2^(n-1) per CX), per second.
+
+--workload dm: the noisy density-matrix TFIM (n = 13, 20 Trotter steps,
+FP64): reset rho -> 980 gates, each followed by depolarising and thermal
+relaxation -> <Z_i>, <H> -> the outcome distribution with 2% readout error;
+gate-updates = gates x 4^n.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload sv|dm|...]
 Under torchrun each rank runs its own replica (independent problems, weak
 scaling, no data-path collective); rank 0 prints one JSON line.
 """
@@ -24,30 +34,63 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N = 13
-TROTTER_STEPS = 20
 METRIC = "gate-updates/s"
 UNIT = "gate-updates/s"
+_CSRC = os.path.join(ROOT, "paper_2401_06861_gb300", "csrc")
+
+# ---- the large state-vector workload (default)
+SV_N, SV_DEPTH = 33, 10
+SV_WORKLOAD = f"sv_tfim_n{SV_N}_c128_depth{SV_DEPTH}"
+SV_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sv_jit_sweep_c128_n33_traffic.json")
+SV_KERNEL = "nwq_jit_sweep (run-time specialised complex128 sweep)"
+
+# ---- the noisy density-matrix workload (--workload dm)
+N = 13
+TROTTER_STEPS = 20
 WORKLOAD = f"dm_noisy_tfim_n{N}_{TROTTER_STEPS}steps"
 # The DM sweeps run the run-time specialised kernel (generated by jit.cpp from
 # the plan of planner.cpp) unless NWQ_JIT=0 selects the interpreted one.
 JIT = os.environ.get("NWQ_JIT", "1") != "0"
-_CSRC = os.path.join(ROOT, "paper_2401_06861_gb300", "csrc")
+JIT_SRCS = [os.path.join(_CSRC, f) for f in ("jit.cpp", "planner.cpp")]
 if JIT:
-    KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("jit.cpp", "planner.cpp")]
+    KERNEL_SRCS = JIT_SRCS
     TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_jit_sweep_f64_n13_traffic.json")
     KERNEL_NAME = "nwq_jit_sweep (run-time specialised FP64 Pauli-basis DM sweep)"
 else:
     KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("sweep_kernels.cu", "device_util.cuh")]
     TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_sweep_f64_n13_traffic.json")
     KERNEL_NAME = "sweep_kernel<double,real> (FP64 Pauli-basis DM sweep, interpreted)"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flop x max clock
 
 
 def workload():
     from paper_2401_06861_gb300 import inputs
     gates, noise = inputs.dm_noisy_tfim(N, TROTTER_STEPS)
     return gates, noise, inputs.z_terms(N), inputs.tfim_terms(N)
+
+
+def sv_workload(n=SV_N, depth=SV_DEPTH):
+    from paper_2401_06861_gb300 import inputs
+    gates, h = inputs.large_sv_tfim(n, depth)
+    return gates, h, inputs.z_terms(n), inputs.tfim_terms(n, 1.0, h)
+
+
+def sv_gate_updates(gates, n):
+    """Amplitudes the original gates logically update: 2^(n-1) per CX (the
+    control = 1 half moves), 2^n per other gate."""
+    return sum(2.0 ** (n - 1) if g[0] == "CX" else 2.0 ** n for g in gates)
+
+
+def config_of(workload_name, ws):
+    """The workload description printed by both arms."""
+    if workload_name == "sv":
+        return {"workload": SV_WORKLOAD, "n": SV_N, "state": "complex128 (16 B/amplitude, 128 GiB)",
+                "gates": SV_DEPTH * (3 * (SV_N - 1) + SV_N), "trotter_steps": SV_DEPTH, "J": 1.0, "dt": 0.05,
+                "h": "U(0.5, 2), seed 3334", "l2": "inputs larger than L2 (128 GiB state)",
+                "parallelism": f"replicas x{ws}"}
+    return {"workload": WORKLOAD, "n": N, "gates": TROTTER_STEPS * (3 * (N - 1) + N), "trotter_steps": TROTTER_STEPS,
+            "state_bytes": 8 << (2 * N), "l2": "inputs larger than L2 (512 MiB state)",
+            "noise": "depolarising p1=1e-3 / p2=1e-2, relaxation 35 / 300 ns, T1/T2 seed 2401, readout 2%",
+            "parallelism": f"replicas x{ws}"}
 
 
 def reduce_max(x, ws):
@@ -114,20 +157,37 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_per_launch():
-    """DRAM bytes per sweep launch from the committed ncu summary, or None if the
-    kernel source changed since the counters were taken."""
+def traffic_per_launch(path, srcs):
+    """DRAM bytes per sweep launch from a committed ncu summary, or None if the
+    kernel sources changed since the counters were taken."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
-        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in KERNEL_SRCS)).hexdigest()[:16]
+        rec = json.load(open(path))
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         return rec["traffic_bytes_per_launch"] if rec.get("kernel_sha") == h else None
     except (OSError, ValueError, KeyError):
         return None
 
 
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def probe_rate(what):
+    """FMA instructions per second of one pipe, measured now (nwq_peak_probe)."""
+    import ctypes
+
+    from paper_2401_06861_gb300 import _lib as L
+    v = ctypes.c_double(0.0)
+    L.check(L.lib().nwq_peak_probe(what, ctypes.byref(v)))
+    return v.value
+
+
 # ---------------------------------------------------------------- CPU oracle
 def oracle_sample(gates, noise, ngates):
-    """Time the CPU oracle on the first ``ngates`` noisy gates of the workload."""
+    """Time the CPU oracle on the first ``ngates`` noisy gates of the DM workload."""
     import oracle
     oracle.lib()
     t0 = time.perf_counter()
@@ -144,28 +204,229 @@ def cpu_cores():
     return int(os.environ.get("OMP_NUM_THREADS", aff))
 
 
+def oracle_sv_rate(n, gates, threads):
+    """Gate-updates/s of the oracle on ``gates`` from |0..0> at n qubits with
+    ``threads`` OpenMP threads, and the seconds it took."""
+    import oracle
+    oracle.set_threads(threads)
+    psi = oracle.zero_state(n)
+    t0 = time.perf_counter()
+    oracle.sv_run_inplace(psi, n, gates)
+    dt = time.perf_counter() - t0
+    del psi
+    return sv_gate_updates(gates, n) / dt, dt
+
+
+def sv_cpu_baseline():
+    """The oracle (plain FP64 C, OpenMP over amplitude groups) on the same
+    circuit family: one Trotter step at n = 26 on all host cores and at n = 22
+    on one core.  The per-amplitude work of a gate does not depend on n once
+    the state is far larger than the CPU caches, so the rate stands for the
+    n = 33 workload (whose 10 steps would take that time x 2^(33-26) x 10)."""
+    cores = cpu_cores()
+    g26 = sv_workload(26, 1)[0]
+    g22 = sv_workload(22, 1)[0]
+    v_all, t_all = oracle_sv_rate(26, g26, cores)
+    v_one, t_one = oracle_sv_rate(22, g22, 1)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one Trotter step of the same chain ({len(g26)} gates) at n=26 (1 GiB complex128) on "
+                      f"{cores} threads, {t_all:.1f} s; same at n=22 on 1 thread: {v_one:.3e} {UNIT} "
+                      f"({t_one:.1f} s); n=33 x 10 steps would take {t_all * 2 ** 7 * 10:.0f} s at this rate",
+            "single_thread_value": v_one}
+
+
+def sv_oracle_check(gates, h, z, zz, x, e):
+    """The GPU results against the exact free-fermion values of the same
+    circuit (oracle/tfim_fermion.py): max term error and relative energy error."""
+    import numpy as np
+
+    from oracle import tfim_fermion
+    ref = tfim_fermion.tfim_observables(SV_N, gates)
+    eref = -float(np.sum(ref["zz"])) - float(np.dot(h, ref["x"]))
+    norm1 = (SV_N - 1) + float(np.sum(np.abs(h)))
+    return {"max_term_err": float(max(np.max(np.abs(zz - ref["zz"])), np.max(np.abs(x - ref["x"])),
+                                      abs(z[0] - ref["z0"]))),
+            "rel_energy_err": abs(e - eref) / max(abs(eref), norm1), "energy_exact": eref,
+            "reference": "free-fermion values of <Z_i Z_i+1>, <X_i>, <Z_0> (oracle/tfim_fermion.py)"}
+
+
 def run_reference(args, ws, rank):
+    """The oracle as the reference arm, on host cores, bounded samples per step."""
     if rank != 0:
         return 0
-    gates, noise, _, _ = workload()
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, _ = oracle_sample(gates, noise, 1)
-        if i >= args.warmup:
-            vals.append(v)
-    value = statistics.mean(vals)
-    sample = f"first noisy gate (CX(0,1) + 2q depolarising + relaxation) of the n={N} circuit, per step"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 4.0 ** N / value * 1e3, "higher_is_better": True,
+    cores = cpu_cores()
+    if args.workload == "dm":
+        gates, noise, _, _ = workload()
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, _ = oracle_sample(gates, noise, 1)
+            if i >= args.warmup:
+                vals.append(v)
+        value = statistics.mean(vals)
+        sample = f"first noisy gate (CX(0,1) + 2q depolarising + relaxation) of the n={N} circuit, per step"
+        ms = 4.0 ** N / value * 1e3
+    else:
+        import oracle
+        oracle.set_threads(cores)
+        n, per = 26, 12
+        g = sv_workload(n, 1)[0]
+        psi = oracle.zero_state(n)
+        upd = tm = 0.0
+        for i in range(args.warmup + args.steps):
+            sl = [g[(i * per + j) % len(g)] for j in range(per)]
+            t0 = time.perf_counter()
+            oracle.sv_run_inplace(psi, n, sl)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                upd += sv_gate_updates(sl, n)
+                tm += dt
+        value = upd / tm
+        sample = (f"per step {per} consecutive gates of one Trotter step of the same chain at n=26 (1 GiB "
+                  f"complex128), {cores} threads")
+        ms = tm / args.steps * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "config": config_of(args.workload, ws),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-# ---------------------------------------------------------------- GPU arm
+# ---------------------------------------------------------------- GPU arm, state vector (default)
+def run_ours_sv(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build
+    from paper_2401_06861_gb300.sim import Plan, State, launch_count
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    n = SV_N
+    gates, h, zt, ht = sv_workload()
+    zzt = [t for t in ht if t[0] == 0]
+    xt = [t for t in ht if t[0] != 0]
+    updates = sv_gate_updates(gates, n)
+    t0 = time.perf_counter()
+    plan = Plan(L.SV, n, gates, L.F64)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    st = State(L.SV, n, L.F64, stream=stream.cuda_stream)
+    # cold first run: builds and compiles the plan's specialised kernels
+    t0 = time.perf_counter()
+    st.run(plan)
+    st.sync()
+    cold_s = time.perf_counter() - t0
+
+    def step(ev=None):
+        st.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        st.run(plan)
+        if ev is not None:
+            ev[1].record(stream)
+        z = st.expect(zt)
+        e = st.expect(ht, sum=True)
+        return z, e
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t0 = time.perf_counter()
+    step()
+    st.sync()
+    warm_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup, 3) - 1):
+        step()
+    barrier()
+    clocks = Clocks(dev)
+    n0 = launch_count()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sweep_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start.record(stream)
+    for k in range(args.steps):
+        z, e = step(sweep_ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = launch_count() - n0
+    ck = clocks.stop()
+    ms = t_start.elapsed_time(t_end) / args.steps
+    sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_ev) / args.steps
+    ms = reduce_max(ms, ws)
+    value = job_rate(updates, ws, ms / 1e3)
+    zz = st.expect(zzt)
+    x = st.expect(xt)
+
+    # end to end through the public ABI from host buffers: the host gate list
+    # in (one-shot call: lowering, table upload, run), results copied back
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st.reset()
+        st.apply(gates)
+        z2 = st.expect(zt)
+        e2 = st.expect(ht, sum=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = reduce_max(e2e_s, ws)
+    assert abs(e2 - e) <= 1e-12 and np.max(np.abs(z2 - z)) <= 1e-12, "e2e result differs from device-timed run"
+    h2d = 56 * len(gates) + 24 * (len(zt) + len(ht))
+    d2h = 8 * (len(zt) + 1)
+
+    # roofline of the dominant kernel: FP64-pipe bound (the plan counts its
+    # FP64 instructions per amplitude), HBM beside it
+    nlaunch = info["sweeps"]
+    launch_s = sweep_ms / 1e3 / nlaunch
+    fp64_peak = probe_rate(L.PROBE_FP64_FMA)
+    achieved = info["fma_per_elem"] * 2.0 ** n / (sweep_ms / 1e3)
+    hbm = info["bytes"] / (sweep_ms / 1e3) / 1e9
+    traffic = traffic_per_launch(SV_TRAFFIC_FILE, JIT_SRCS)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": fp64_peak / 1e9,
+                "unit": "FP64 Ginstr/s", "frac": achieved / fp64_peak, "traffic": traffic,
+                "peak_source": "measured in this run (nwq_peak_probe: FP64 FMA chains on every SM)",
+                "kernel": SV_KERNEL, "fp64_instr_per_amplitude": info["fma_per_elem"],
+                "launches_per_step": nlaunch, "ms_per_launch": launch_s * 1e3,
+                "algorithmic_bytes_per_launch": info["bytes"] / nlaunch, "hbm_gbs": hbm,
+                "hbm_frac": hbm / _peaks()["hbm_gbs"]}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = sv_cpu_baseline()
+        cpu["oracle_check"] = sv_oracle_check(gates, h, z, zz, x, e)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of("sv", ws),
+                "plan": {"form": "fused (reusable)", "sweeps": info["sweeps"], "operators": info["ops"],
+                         "create_s": plan_s},
+                "gates_per_s": job_rate(len(gates), ws, ms / 1e3),
+                "e2e": {"value": job_rate(updates, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                        "path": "nwq_sv_apply_circuit from the host gate list, then nwq_expect_pauli_sum",
+                        "cold_compile_s": max(cold_s - warm_s, 0.0),
+                        "note": "the one-shot calls find the specialised kernels compiled by the timed plan; "
+                                "cold_compile_s is the first run's extra time (NVRTC compiles)"},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "results": {"energy": e, "z0": float(z[0]), "norm": st.norm()}}
+        print(json.dumps(line), flush=True)
+    st.close()
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm, density matrix
 def run_ours(args, ws, rank, local):
     import numpy as np
     import torch
@@ -244,8 +505,10 @@ def run_ours(args, ws, rank, local):
     flops_per_launch = 2.0 * info["fma_per_elem"] * 4.0 ** N / nlaunch
     launch_s = sweep_ms / 1e3 / nlaunch
     achieved = flops_per_launch / launch_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic_per_launch(),
+    peak = 2.0 * probe_rate(L.PROBE_FP64_FMA) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_per_launch(TRAFFIC_FILE, KERNEL_SRCS),
+                "peak_source": "measured in this run (nwq_peak_probe: FP64 FMA chains on every SM, 2 flops each)",
                 "kernel": KERNEL_NAME,
                 "launches_per_step": nlaunch, "ms_per_launch": launch_s * 1e3,
                 "algorithmic_bytes_per_launch": info["bytes"] / nlaunch,
@@ -260,11 +523,8 @@ def run_ours(args, ws, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": N, "gates": len(gates), "trotter_steps": TROTTER_STEPS,
-                           "state_bytes": 8 << (2 * N), "l2": "inputs larger than L2 (512 MiB state)",
-                           "plan": {"sweeps": info["sweeps"], "operators": info["ops"]},
-                           "parallelism": f"replicas x{ws}"},
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of("dm", ws),
+                "plan": {"sweeps": info["sweeps"], "operators": info["ops"]},
                 "e2e": {"value": job_rate(gate_updates, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
@@ -281,14 +541,9 @@ def run_ours(args, ws, rank, local):
 # ---------------------------------------------------------------- other workloads
 # These print one JSON line each for the design notes; the default run above
 # is the headline measurement.
-def _peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        return {"hbm_gbs": 6800.0, "fallback": True}
 
 
-def run_sv(args):
+def run_sv_cases(args):
     """Large state vector: TFIM depth 10 with random h_i, fused sweeps vs one
     gate per pass, FP32 and FP64; gate-updates/s and HBM GB/s."""
     import numpy as np
@@ -656,8 +911,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dm",
-                    choices=["dm", "dm32", "sv", "sv-errors", "vqe", "vqe-cobyla", "serve", "traj"])
+    ap.add_argument("--workload", default="sv",
+                    choices=["sv", "dm", "dm32", "sv-cases", "sv-errors", "vqe", "vqe-cobyla", "serve", "traj"],
+                    help="sv: the default line (n=33 complex128 TFIM, depth 10); dm: noisy DM TFIM n=13; "
+                         "the others print design-note lines")
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
     ap.add_argument("--sv-n", type=int, default=34)
     ap.add_argument("--sv-depth", type=int, default=10)
@@ -679,7 +936,9 @@ def main():
             dist.destroy_process_group()
         return rc
     if args.workload == "sv":
-        return run_sv(args)
+        return run_ours_sv(args, ws, rank, local)
+    if args.workload == "sv-cases":
+        return run_sv_cases(args)
     if args.workload == "sv-errors":
         return run_sv_errors(args)
     if args.workload == "vqe-cobyla":
