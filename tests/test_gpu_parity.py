@@ -136,7 +136,7 @@ def test_sv_every_gate_on_every_qubit_position(dtype):
             st.apply(gates, flags=flags)
             err = maxerr(st.copy(), ref)
         print(f"all-gates n={n} flags={flags} dtype={dtype} ({len(gates)} gates) max_abs_err={err:.3e}")
-        assert err <= TOL[dtype] * (4 if dtype == L.F32 else 1)
+        assert err <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -349,6 +349,53 @@ def test_dm_n13_noiseless_matches_sv_oracle_outer_product():
     assert maxerr(rho[r, c], psi[r] * psi[c].conj()) <= 1e-12
 
 
+def _golden_n13():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "dm_noisy_tfim_n13.npz")
+    return np.load(path)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_dm_n13_noisy_tfim_steps_match_the_kraus_oracle(dtype):
+    # The density-matrix benchmark's noisy entangling circuit at its full
+    # size (paper Sec. III: TFIM chain with depolarising and relaxation after
+    # every gate), against the Kraus-form oracle (tests/golden/
+    # make_dm_n13_golden.py): one Trotter step through the one-shot call, two
+    # steps through a reusable plan (the specialised kernels the benchmark
+    # runs); every <Z_i>, all 25 TFIM terms, 10^4 sampled rho entries and
+    # the readout-noisy outcome distribution.
+    n = 13
+    gold = _golden_n13()
+    r, c = gold["r"], gold["c"]
+    tfim = inputs.tfim_terms(n)
+    ro = inputs.noise_params(n)["readout_e"]
+    tol = TOL[dtype]
+
+    def check(st, k):
+        z = st.expect(inputs.z_terms(n))
+        t = st.expect(tfim)
+        e = st.expect(tfim, sum=True)
+        p = st.probs(ro)
+        rho = st.copy()
+        eref = oracle.energy(gold[f"tfim{k}"], tfim)
+        errs = dict(z=maxerr(z, gold[f"z{k}"]), terms=maxerr(t, gold[f"tfim{k}"]),
+                    rho=maxerr(rho[r, c], gold[f"rho{k}"]), probs=maxerr(p, gold[f"probs{k}"]),
+                    rel_energy=rel_energy(e, eref, tfim))
+        print(f"dm n=13 noisy TFIM, {k} step(s), dtype={dtype}: {errs}")
+        assert errs["z"] <= tol and errs["terms"] <= tol and errs["rho"] <= tol
+        assert errs["probs"] <= (1e-12 if dtype == L.F64 else 1e-6)
+        assert errs["rel_energy"] <= (1e-12 if dtype == L.F64 else 1e-6)
+
+    gates1, noise = inputs.dm_noisy_tfim(n, 1)
+    gates2, _ = inputs.dm_noisy_tfim(n, 2)
+    with State(L.DM, n, dtype) as st:
+        st.apply(gates1, noise)
+        check(st, 1)
+    with State(L.DM, n, dtype) as st, Plan(L.DM, n, gates2, dtype, noise) as plan:
+        st.run(plan)
+        check(st, 2)
+
+
 def test_dm_n13_noisy_product_state_matches_single_qubit_oracle():
     # J = 0: no entangling gates, so rho is a product of one-qubit states,
     # each given by the oracle on one qubit with that qubit's T1/T2.
@@ -430,8 +477,8 @@ def test_sv_long_x_rotation_chains(flags):
         with State(L.SV, n, dtype) as st, Plan(L.SV, n, gates, dtype, flags=flags) as p:
             st.load(psi0)
             st.run(p)
-            assert maxerr(st.copy(), ref) <= 10 * TOL[dtype]
-            assert abs(st.norm() - np.sum(np.abs(ref) ** 2)) <= 10 * TOL[dtype]
+            assert maxerr(st.copy(), ref) <= TOL[dtype]
+            assert abs(st.norm() - np.sum(np.abs(ref) ** 2)) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("n,dtype", [(33, L.F64), (34, L.F32)])
