@@ -107,10 +107,26 @@ enum nwq_plan_flags {
   NWQ_PLAN_NO_RESCALE = 4u, /* DM: no deferred per-qubit scale factors (see nwq_plan_create) */
   NWQ_PLAN_INTERPRETED = 8u, /* never the run-time specialised sweep kernels (see nwq_plan_jit_check) */
   NWQ_PLAN_TC = 16u,         /* dense five-qubit blocks on the tensor cores (see below) */
-  NWQ_PLAN_COMMUTE = 32u     /* state vectors: when grouping sweeps, a diagonal operator may move ahead of
+  NWQ_PLAN_COMMUTE = 32u,    /* state vectors: when grouping sweeps, a diagonal operator may move ahead of
                                 skipped diagonal operators (they commute): fewer passes for circuits
                                 of diagonal gates (opt-in) */
+  NWQ_PLAN_DW = 64u          /* FP64 plans: double-word sweeps (see below) */
 };
+
+/* Double-word sweeps (NWQ_PLAN_DW, or NWQ_DW=1 in the environment for every
+ * FP64 plan; NWQ_DW=0 turns them off).  GB300 issues FP32 FMAs at 64 times
+ * its FP64 rate, so an FP64 plan may run its sweeps with every FP64 value
+ * held as an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2,
+ * about 48 significant bits) and every FP64 FMA done as a double-word
+ * multiply-add on the FP32 pipe (error-free product and sum transformations,
+ * relative error a few 2^-48 of the operands; Dekker, and Joldes, Muller and
+ * Popescu, "Tight and rigorous error bounds for basic building blocks of
+ * double-word arithmetic", 2017).  The state stays complex128 / FP64 between
+ * calls: a plan run converts it to the double-word layout (same bytes) before
+ * its first sweep and back after its last.  It applies when every sweep of
+ * the plan runs a specialised kernel (states of >= NWQ_JIT_MIN_BITS index
+ * bits, the kernels compiled); otherwise the plan runs its FP64 kernels.
+ * Such plans keep deferred scale factors within the float exponent range. */
 
 /* Tensor-core plans (NWQ_PLAN_TC; complex64 state vectors of >= 12 qubits,
  * else NWQ_EUNSUPPORTED).  The gate stream is fused into dense blocks of 5
@@ -323,6 +339,19 @@ int nwq_tc_timeouts(int* count);
  * NVRTC cannot be loaded, with the reason (or the first compiler message) in
  * nwq_last_error(). */
 int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* built);
+
+/* *dw = 1 when the plan's latest nwq_plan_run took the double-word path
+ * (NWQ_PLAN_DW with every sweep's double-word kernel ready), else 0. */
+int nwq_plan_last_run_dw(const nwq_plan* plan, int* dw);
+
+/* Arithmetic of the plan's run-time specialised sweep kernels, for roofline
+ * accounting (host only): per state element, summed over the sweeps that
+ * have such a kernel (*sweeps of them, may be NULL), the multiply-adds and
+ * multiplies of the kernels' value type as generated.  dw = 0: the kernels of
+ * the plan's own precision (one FP64 / FP32 instruction each); dw = 1: the
+ * double-word kernels of an FP64 plan (a multiply-add is 15 FP32
+ * instructions, a multiply 7). */
+int nwq_plan_kernel_arith(const nwq_plan* plan, int dw, double* fma_per_elem, double* mul_per_elem, int* sweeps);
 
 /* Queue background compilation of the plan's specialised sweep kernels that
  * are not compiled yet (one compiler thread per process) and return at once;

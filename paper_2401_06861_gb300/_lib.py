@@ -20,6 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, 
 F32, F64 = 1, 2
 SV, DM = 1, 2
 PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED, PLAN_TC, PLAN_COMMUTE = 0, 1, 2, 4, 8, 16, 32
+PLAN_DW = 64
 PROBE_FP64_FMA, PROBE_FP32_FMA = 0, 1
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
@@ -110,6 +111,8 @@ def lib():
                                   P(i32), P(i32)]),
         "nwq_tc_timeouts": (i32, [P(i32)]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
+        "nwq_plan_kernel_arith": (i32, [vp, i32, P(dbl), P(dbl), P(i32)]),
+        "nwq_plan_last_run_dw": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),
         "nwq_expect_pauli_sum_noalloc": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),

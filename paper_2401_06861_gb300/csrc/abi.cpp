@@ -143,15 +143,31 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
   const void* ents = (const char*)p.dev + p.ops.size() * sizeof(DevOp);
   PhaseTables pt{(const PhaseDesc*)((const char*)p.dev + p.pt_off[0]), (const PhaseOp*)((const char*)p.dev + p.pt_off[1]),
                  (const char*)p.dev + p.pt_off[2]};
+  // double-word plans: the state goes to the double-word layout for the
+  // sweeps when every sweep has its double-word kernel, and back after them
+  const bool dw = p.dw && jit_dw_ready(p);
+  p.last_run_dw = dw;
+  const uint64_t ndouble = (p.is_complex ? 2ull : 1ull) << p.B;
+  if (dw) {
+    cudaError_t e = launch_dw_convert(data, ndouble, true, sm_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "double-word conversion");
+  }
   for (size_t i = 0; i < p.sweeps.size(); i++) {
     const SweepDesc& sd = p.sweeps[i];
     if (sd.nops == 0) continue;
     NvtxRange sweep_range("nwq sweep");
     cudaError_t e = cudaSuccess;
-    if (!((!p.is_complex || sd.nph > 0) && jit_launch_sweep(p, i, pt, data, sm_count, s, &e)))
+    if (dw) {
+      if (!jit_launch_sweep(p, i, pt, data, sm_count, s, &e, true)) e = cudaErrorInvalidValue;  // ready: never
+    } else if (!((!p.is_complex || sd.nph > 0) && jit_launch_sweep(p, i, pt, data, sm_count, s, &e))) {
       e = launch_sweep(p.is_complex, p.dtype == NWQ_F64, data, p.B, sd, ops, ents, p.phases.empty() ? nullptr : &pt,
                        sm_count, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+  }
+  if (dw) {
+    cudaError_t e = launch_dw_convert(data, ndouble, false, sm_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "double-word conversion");
   }
   return NWQ_OK;
 }
@@ -406,6 +422,12 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
     }
   }
   if (kind == NWQ_DM && !(flags & NWQ_PLAN_NO_RESCALE)) o.rescale_qubits = n;
+  // double-word sweeps: NWQ_PLAN_DW, or NWQ_DW=1 / 0 to force them on / off
+  static const int env_dw = [] {
+    const char* e = std::getenv("NWQ_DW");
+    return !e ? -1 : (e[0] == '1' ? 1 : 0);
+  }();
+  pl->p.dw = dtype == NWQ_F64 && (env_dw == 1 || (env_dw == -1 && (flags & NWQ_PLAN_DW)));
   build_plan(ops, o, pl->p);
   pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
   static const bool checks = [] {
@@ -605,6 +627,20 @@ extern "C" int nwq_plan_jit_check(const nwq_plan* plan, int* eligible, int* buil
   std::string log;
   jit_build_check(plan->p, eligible, built, &log);
   if (*built < *eligible) return fail(NWQ_EUNSUPPORTED, log.empty() ? "specialised kernel compilation failed" : log);
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_last_run_dw(const nwq_plan* plan, int* dw) {
+  if (!plan || !dw) return fail(NWQ_EINVAL, "NULL argument");
+  *dw = plan->p.last_run_dw ? 1 : 0;
+  return NWQ_OK;
+}
+
+extern "C" int nwq_plan_kernel_arith(const nwq_plan* plan, int dw, double* fma_per_elem, double* mul_per_elem,
+                                     int* sweeps) {
+  if (!plan || !fma_per_elem || !mul_per_elem) return fail(NWQ_EINVAL, "NULL argument");
+  const int e = jit_plan_arith(plan->p, dw != 0, fma_per_elem, mul_per_elem);
+  if (sweeps) *sweeps = e;
   return NWQ_OK;
 }
 

@@ -137,8 +137,21 @@ bool compile_cubin(const std::string& src, std::vector<char>& bin, std::string* 
   }
   nvrtcProgram prog;
   if (N.create(&prog, src.c_str(), "nwq_jit_sweep.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return false;
-  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device"};
-  bool ok = N.compile(prog, 3, opts) == NVRTC_SUCCESS;
+  // NWQ_JIT_PTXAS=1: the assembler's resource report of every kernel on stderr
+  static const bool ptxas_v = [] {
+    const char* e = std::getenv("NWQ_JIT_PTXAS");
+    return e && e[0] == '1';
+  }();
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device", "--ptxas-options=-v"};
+  bool ok = N.compile(prog, ptxas_v ? 4 : 3, opts) == NVRTC_SUCCESS;
+  if (ok && ptxas_v) {
+    size_t ls = 0;
+    if (N.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
+      std::string l(ls, '\0');
+      N.log(prog, &l[0]);
+      std::fprintf(stderr, "%s\n", l.c_str());
+    }
+  }
   if (!ok && log) {
     size_t ls = 0;
     if (N.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
@@ -288,6 +301,66 @@ std::string swz_expr(int es, const std::string& v) {
 }
 size_t padded_elems(int T) { return ((size_t)1 << T) + ((size_t)1 << T) / 8; }
 
+// Double words (NWQ_PLAN_DW): an FP64 value v as floats h + l, h = v rounded
+// to float, l = the rest rounded to float (about 48 significant bits).
+void append_dw(std::vector<unsigned char>& out, double v) {
+  const float w[2] = {(float)v, (float)(v - (double)(float)v)};
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(w);
+  out.insert(out.end(), b, b + 8);
+}
+// Append nbytes of FP64 coefficients, as double words when dw.
+void append_coefs(std::vector<unsigned char>& out, const unsigned char* src, size_t nbytes, bool dw) {
+  if (!dw) {
+    out.insert(out.end(), src, src + nbytes);
+    return;
+  }
+  for (size_t i = 0; i + 8 <= nbytes; i += 8) {
+    double v;
+    std::memcpy(&v, src + i, 8);
+    append_dw(out, v);
+  }
+}
+
+// Device arithmetic of double words, written into double-word kernels.  The
+// product takes the exact error of the high parts' product from an FMA and
+// adds the cross terms (Dekker's product with an FMA); the sum of the product
+// and c adds the high parts with Knuth's TwoSum (exact) and the low parts in
+// float, then renormalises with Fast2Sum (Joldes, Muller, Popescu 2017,
+// double-word building blocks).  Error: a few 2^-48 of |a b| + |c|.  The _rn
+// intrinsics keep the compiler from contracting or reordering these steps.
+const char* kDwPrelude = R"DW(struct __align__(8) dw {
+  float h, l;
+  dw() = default;
+  __device__ explicit dw(int z) : h((float)z), l(0.f) {}
+  __device__ dw(float a, float b) : h(a), l(b) {}
+};
+__device__ __forceinline__ dw d2w(double x) {
+  const float h = __double2float_rn(x);
+  return dw(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ dw operator-(dw a) { return dw(-a.h, -a.l); }
+__device__ __forceinline__ dw operator*(dw a, dw b) {
+  const float ph = __fmul_rn(a.h, b.h);
+  float pl = __fmaf_rn(a.h, b.h, -ph);
+  pl = __fmaf_rn(a.h, b.l, pl);
+  pl = __fmaf_rn(a.l, b.h, pl);
+  const float h = __fadd_rn(ph, pl);
+  return dw(h, __fsub_rn(pl, __fsub_rn(h, ph)));
+}
+__device__ __forceinline__ dw fma(dw a, dw b, dw c) {
+  const float ph = __fmul_rn(a.h, b.h);
+  float pl = __fmaf_rn(a.h, b.h, -ph);
+  pl = __fmaf_rn(a.h, b.l, pl);
+  pl = __fmaf_rn(a.l, b.h, pl);
+  const float s = __fadd_rn(ph, c.h);
+  const float v = __fsub_rn(s, ph);
+  float e = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, v)), __fsub_rn(c.h, v));
+  e = __fadd_rn(e, __fadd_rn(pl, c.l));
+  const float h = __fadd_rn(s, e);
+  return dw(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+)DW";
+
 struct Gen {
   const Plan& p;
   const SweepDesc& sd;
@@ -306,18 +379,22 @@ struct Gen {
   // complex plans: complex64 / complex128 elements; real (density-matrix)
   // plans: FP64 elements.  8-byte elements share the complex64 tile layout.
   bool real;
-  Gen(const Plan& p_, const SweepDesc& sd_)
+  Gen(const Plan& p_, const SweepDesc& sd_, bool dw_)
       : p(p_),
         sd(sd_),
         c128(p_.is_complex && p_.dtype == NWQ_F64),
         cs(p_.is_complex ? (c128 ? 16 : 8) : (p_.dtype == NWQ_F64 ? 8 : 4)),
         real(!p_.is_complex),
-        es((int)cs) {}
-  int es;  // bytes per state element (= per coefficient)
+        es((int)cs),
+        dw(dw_ && p_.dtype == NWQ_F64) {}
+  int es;   // bytes per state element (= per coefficient)
+  bool dw;  // FP64 values as double words (two floats), FP32-pipe arithmetic
 
   uint32_t pack_real(size_t entry, double v) {  // one real coefficient (entry index of the plan)
     uint32_t at = (uint32_t)(param.size() / cs);
-    if (es == 8) {
+    if (es == 8 && dw) {
+      append_dw(param, v);
+    } else if (es == 8) {
       const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
       param.insert(param.end(), b, b + 8);
     } else {
@@ -433,7 +510,7 @@ struct Gen {
       return 0;
     }
     uint32_t at = (uint32_t)(param.size() / cs);
-    param.insert(param.end(), p.pcoef.begin() + (size_t)a * cs, p.pcoef.begin() + (size_t)(a + cnt) * cs);
+    append_coefs(param, &p.pcoef[(size_t)a * cs], (size_t)cnt * cs, dw);
     recipe.push_back({a - sd.pc0, cnt});
     return at;
   }
@@ -591,10 +668,19 @@ struct Gen {
         roff[i] = swz(es, l);
         o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
       }
+      const std::string before = o.str();
       if (real) {
         for (int oi : rph[ph].second) op_real(p.ops[sd.op0 + oi], P.u);
       } else {
         for (uint32_t q = 0; q < P.nops && ok; q++) op(NR, p.pops[P.op0 + q]);
+      }
+      {  // arithmetic of one register group (NR elements): every fma( and every " * "
+        const std::string code = o.str().substr(before.size());
+        size_t nf = 0, nm = 0;
+        for (size_t at = code.find("fma("); at != std::string::npos; at = code.find("fma(", at + 4)) nf++;
+        for (size_t at = code.find(" * "); at != std::string::npos; at = code.find(" * ", at + 3)) nm++;
+        fma_per_elem += (double)nf / NR;
+        mul_per_elem += (double)nm / NR;
       }
       for (int i = 0; i < NR; i++) o << "    gt[" << roff[i] << "] = " << r(i) << ";\n";
       o << "    }\n    __syncthreads();\n";
@@ -609,10 +695,20 @@ struct Gen {
     const uint32_t nb = 1u << pb;
     smem = btab_byte + 4 * (size_t)nb * 8;
     if (smem > (size_t)kMaxDynSmem) return false;
-    const char* RT = (c128 || (real && es == 8)) ? "double" : "float";
-    const char* CT = real ? RT : (c128 ? "double2" : "float2");
-    o << "typedef " << RT << " R;\ntypedef " << CT << " C;\n"
-      << "struct Coef { C c[" << npk << "]; };\n"
+    if (dw) {
+      o << kDwPrelude << "typedef dw R;\n";
+      if (real) o << "typedef dw C;\n";
+      else o << "struct __align__(16) C { dw x, y; };\n";
+      o << "typedef " << (real ? "double" : "double2") << " CT;\n";  // FP64 diagonal tables in global memory
+      o << "__device__ __forceinline__ C from_table(CT v) { return " << (real ? "d2w(v)" : "C{d2w(v.x), d2w(v.y)}")
+        << "; }\n";
+    } else {
+      const char* RT = (c128 || (real && es == 8)) ? "double" : "float";
+      const char* CT = real ? RT : (c128 ? "double2" : "float2");
+      o << "typedef " << RT << " R;\ntypedef " << CT << " C;\ntypedef C CT;\n"
+        << "__device__ __forceinline__ C from_table(CT v) { return v; }\n";
+    }
+    o << "struct Coef { C c[" << npk << "]; };\n"
       << "__device__ __forceinline__ unsigned long long dep(unsigned long long v, unsigned long long mask) {\n"
       << "  unsigned long long out = 0;\n"
       << "  while (v && mask) { unsigned long long lb = mask & (~mask + 1ull); if (v & 1ull) out |= lb; v >>= 1; mask ^= lb; }\n"
@@ -622,7 +718,7 @@ struct Gen {
       << "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(a), \"l\"(g) : \"memory\");\n}\n"
       << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << jit_min_blocks()
       << ") nwq_jit_sweep(C* __restrict__ state, "
-      << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const C* __restrict__ pcs, "
+      << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const CT* __restrict__ pcs, "
       << "const Coef K) {\n"
       << "  extern __shared__ __align__(16) unsigned char sm[];\n"
       << "  C* tile = (C*)sm;\n  C* ntile = tile + " << PE << ";\n  C* dtab = tile + " << 2 * PE << ";\n"
@@ -635,7 +731,7 @@ struct Gen {
       << ")), fmask);\n";
     for (const Tab& t : tabs)
       o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << kJitThreads << "u) dtab[" << t.dst
-        << " + j] = pcs[" << t.src << " + j];\n";
+        << " + j] = from_table(pcs[" << t.src << " + j]);\n";
     const int VPE = 16 / es, lvpc = m - lvpe;
     const uint32_t nvec = (1u << T) / VPE;
     const uint32_t NVT = (nvec + kJitThreads - 1) / kJitThreads;  // vectors per thread
@@ -699,6 +795,10 @@ struct Gen {
     return true;
   }
   size_t smem = 0;
+  // arithmetic per state element of this sweep, counted on the emitted source:
+  // multiply-adds and multiplies of R values (one FP64 instruction each; a
+  // double-word multiply-add is 15 FP32 instructions, a multiply 7)
+  double fma_per_elem = 0.0, mul_per_elem = 0.0;
 };
 
 // Structure key of a sweep: everything the generator reads except coefficient
@@ -706,10 +806,11 @@ struct Gen {
 // bits and permutations, coefficient positions relative to the sweep; for
 // real plans the operator rows and entry offsets).  Sweeps with equal keys
 // get identical kernel source.
-std::string struct_key(const Plan& p, const SweepDesc& sd) {
+std::string struct_key(const Plan& p, const SweepDesc& sd, bool dw) {
   std::string key;
   auto put = [&](const void* d, size_t n) { key.append(reinterpret_cast<const char*>(d), n); };
-  const int32_t hdr[8] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h, sd.prb, jit_min_blocks()};
+  const int32_t hdr[9] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h, sd.prb, jit_min_blocks(),
+                          dw ? 1 : 0};
   put(hdr, sizeof(hdr));
   if (p.is_complex) {
     for (uint32_t ph = 0; ph < sd.nph; ph++) {
@@ -746,11 +847,11 @@ std::string struct_key(const Plan& p, const SweepDesc& sd) {
 }
 
 // Write the entry's description from this sweep (once per structure).
-bool describe(JitKernel& jk, const Plan& p, const SweepDesc& sd) {
+bool describe(JitKernel& jk, const Plan& p, const SweepDesc& sd, bool dw) {
   if (jk.described) return jk.usable;
   std::lock_guard<std::mutex> lk(jk.mu);  // never held by a compile here: compiles need a description
   if (!jk.described) {
-    Gen g(p, sd);
+    Gen g(p, sd, dw);
     std::string src;
     jk.usable = g.run(src);
     if (jk.usable) {
@@ -764,18 +865,20 @@ bool describe(JitKernel& jk, const Plan& p, const SweepDesc& sd) {
 }
 
 // This sweep's parameter bytes by the structure's recipe (empty on a range error).
-std::vector<unsigned char> pack_params(const Plan& p, const SweepDesc& sd, const std::vector<RecipeItem>& recipe) {
+std::vector<unsigned char> pack_params(const Plan& p, const SweepDesc& sd, const std::vector<RecipeItem>& recipe,
+                                       bool dw) {
   const size_t cs = p.is_complex ? (p.dtype == NWQ_F64 ? 16 : 8) : (p.dtype == NWQ_F64 ? 8 : 4);
+  dw = dw && p.dtype == NWQ_F64;
   std::vector<unsigned char> out;
   for (const RecipeItem& it : recipe) {
     if (it.cnt) {
       const size_t a = (size_t)sd.pc0 + it.rel;
       if ((a + it.cnt) * cs > p.pcoef.size()) return {};
-      out.insert(out.end(), p.pcoef.begin() + a * cs, p.pcoef.begin() + (a + it.cnt) * cs);
+      append_coefs(out, &p.pcoef[a * cs], it.cnt * cs, dw);
     } else {
       const size_t at = ((size_t)sd.ent0 + it.rel) * p.ent_bytes;
       if (at + cs > p.ents.size()) return {};
-      out.insert(out.end(), p.ents.begin() + at, p.ents.begin() + at + cs);
+      append_coefs(out, &p.ents[at], cs, dw);
     }
   }
   if (out.empty()) out.resize(cs, 0);
@@ -789,10 +892,10 @@ struct JitSweep {
   size_t smem = 0;
   int per_sm = 0;
 };
-struct JitPlan {
+struct JitPlan {  // [0]: kernels in the plan's own precision, [1]: double-word kernels
   std::mutex mu;
-  bool built = false;
-  std::vector<JitSweep> sw;
+  bool built[2] = {false, false};
+  std::vector<JitSweep> sw[2];
 };
 
 }  // namespace
@@ -801,7 +904,7 @@ bool jit_source(const Plan& p, size_t sweep, std::string& src, size_t* param_byt
   src.clear();
   if (sweep >= p.sweeps.size() || p.sweeps[sweep].nops == 0 || (p.is_complex && p.sweeps[sweep].nph == 0))
     return false;
-  Gen g(p, p.sweeps[sweep]);
+  Gen g(p, p.sweeps[sweep], p.dw);
   if (!g.run(src)) {
     src.clear();
     return false;
@@ -829,6 +932,22 @@ int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log) 
   return 0;
 }
 
+int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem) {
+  *fma_per_elem = *mul_per_elem = 0.0;
+  int eligible = 0;
+  for (size_t i = 0; i < p.sweeps.size(); i++) {
+    const SweepDesc& sd = p.sweeps[i];
+    if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
+    Gen g(p, sd, dw);
+    std::string src;
+    if (!g.run(src)) continue;
+    *fma_per_elem += g.fma_per_elem;
+    *mul_per_elem += g.mul_per_elem;
+    eligible++;
+  }
+  return eligible;
+}
+
 void jit_shutdown() {
   if (g_async_started) async_compiler().shutdown();
 }
@@ -839,8 +958,8 @@ int jit_prefetch(const Plan& p) {
   for (size_t i = 0; i < p.sweeps.size(); i++) {
     const SweepDesc& sd = p.sweeps[i];
     if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
-    std::shared_ptr<JitKernel> k = entry_for(struct_key(p, sd));
-    if (!describe(*k, p, sd)) continue;
+    std::shared_ptr<JitKernel> k = entry_for(struct_key(p, sd, p.dw));
+    if (!describe(*k, p, sd, p.dw)) continue;
     request_compile(k, true);
     if (!k->done) queued++;
   }
@@ -852,35 +971,56 @@ void jit_stats(int* compiled, int* failed) {
   if (failed) *failed = g_failed.load();
 }
 
-bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state, int sm_count, cudaStream_t s,
-                      cudaError_t* err) {
-  if (!jit_enabled() || p.interpreted || p.B < jit_min_bits() || sweep >= p.sweeps.size()) return false;
+// The plan's kernels of one mode (0: its own precision, 1: double words),
+// described and requested on first use; null when specialised kernels are off.
+static JitPlan* jit_plan_mode(Plan& p, int mode) {
+  if (!jit_enabled() || p.interpreted || p.B < jit_min_bits()) return nullptr;
   if (!p.jit) p.jit = std::make_shared<JitPlan>();
   JitPlan& jp = *std::static_pointer_cast<JitPlan>(p.jit);
-  {
-    std::lock_guard<std::mutex> lk(jp.mu);
-    if (!jp.built) {
-      jp.sw.resize(p.sweeps.size());
-      for (size_t i = 0; i < p.sweeps.size(); i++) {
-        const SweepDesc& sd = p.sweeps[i];
-        if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
-        std::shared_ptr<JitKernel> k = entry_for(struct_key(p, sd));
-        if (!describe(*k, p, sd)) continue;
-        // one-shot plans never wait for a compile: their sweeps run interpreted
-        // until the kernel of that structure is ready
-        request_compile(k, p.stream_ordered && !jit_sync_all());
-        if (k->done && !k->ok) continue;
-        std::vector<unsigned char> param = pack_params(p, sd, k->recipe);
-        if (param.empty()) continue;
-        JitSweep& js = jp.sw[i];
-        js.k = k;
-        js.param = std::move(param);
-        js.smem = k->smem;
-      }
-      jp.built = true;
+  std::lock_guard<std::mutex> lk(jp.mu);
+  if (!jp.built[mode]) {
+    jp.sw[mode].resize(p.sweeps.size());
+    for (size_t i = 0; i < p.sweeps.size(); i++) {
+      const SweepDesc& sd = p.sweeps[i];
+      if (sd.nops == 0 || (p.is_complex && sd.nph == 0)) continue;
+      std::shared_ptr<JitKernel> k = entry_for(struct_key(p, sd, mode == 1));
+      if (!describe(*k, p, sd, mode == 1)) continue;
+      // one-shot plans never wait for a compile: their sweeps run interpreted
+      // until the kernel of that structure is ready
+      request_compile(k, p.stream_ordered && !jit_sync_all());
+      if (k->done && !k->ok) continue;
+      std::vector<unsigned char> param = pack_params(p, sd, k->recipe, mode == 1);
+      if (param.empty()) continue;
+      JitSweep& js = jp.sw[mode][i];
+      js.k = k;
+      js.param = std::move(param);
+      js.smem = k->smem;
     }
+    jp.built[mode] = true;
   }
-  JitSweep& js = jp.sw[sweep];
+  return &jp;
+}
+
+bool jit_dw_ready(Plan& p) {
+  if (!p.dw) return false;
+  JitPlan* jp = jit_plan_mode(p, 1);
+  if (!jp) return false;
+  bool any = false;
+  for (size_t i = 0; i < p.sweeps.size(); i++) {
+    if (p.sweeps[i].nops == 0) continue;
+    const JitSweep& js = jp->sw[1][i];
+    if (!js.k || !js.k->done || !js.k->ok) return false;
+    any = true;
+  }
+  return any;
+}
+
+bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state, int sm_count, cudaStream_t s,
+                      cudaError_t* err, bool dw) {
+  if (sweep >= p.sweeps.size()) return false;
+  JitPlan* jpp = jit_plan_mode(p, dw ? 1 : 0);
+  if (!jpp) return false;
+  JitSweep& js = jpp->sw[dw ? 1 : 0][sweep];
   if (!js.k || !js.k->done || !js.k->ok) return false;
   const void* fn = (const void*)js.k->k;
   int dev = 0;

@@ -47,6 +47,8 @@ struct PhaseTables {
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
                          const void* ents, const PhaseTables* pt, int sm_count, cudaStream_t s);
 cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s);
+// FP64 array of ndouble values (even) to the double-word layout (to_dw) or back, in place.
+cudaError_t launch_dw_convert(void* data, uint64_t ndouble, bool to_dw, int sm_count, cudaStream_t s);
 cudaError_t launch_real_to_cplx(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_cplx_to_real(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_sv_abs2(bool f64, const void* psi, double* p, uint64_t count, int sm_count, cudaStream_t s);

@@ -612,9 +612,11 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
   // X-rotations (|tan| <= 1) into a global scalar: the rotation keeps a unit
   // diagonal (2 FP64 instructions per element instead of 4) and the scalar is
   // folded into the next diagonal operator (free), or applied as a
-  // one-coefficient diagonal when its binary exponent leaves [-200, 200] and
+  // one-coefficient diagonal when its binary exponent leaves [-200, 200]
+  // ([-60, 60] for double-word plans, whose values have float exponents) and
   // at the end of the plan.
   bool defer = f64;
+  const double scalar_range = plan.dw ? 60.0 : 200.0;
   for (const SweepDesc& sd : plan.sweeps) {
     if (sd.nops == 0) continue;
     bool ok = sd.T >= RB;
@@ -768,7 +770,7 @@ static void build_phases(const std::vector<BitOp>& ops, const std::vector<int>& 
         plan.pops.push_back(po);
         kron_any = false;
         kron_mask = 0;
-        if (std::fabs(std::log2(std::abs(gscale))) > 200.0) push_scalar();  // keep the state's scale in range
+        if (std::fabs(std::log2(std::abs(gscale))) > scalar_range) push_scalar();  // keep the state's scale in range
       };
       auto kron_reset = [&]() {
         for (int p = 0; p < 4; p++) {
@@ -907,7 +909,10 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
     // complex: a second pass joins diagonal operators that became adjacent
     if (cplx) merge_ops(ops, cplx, opt.max_merge_bits);
   }
-  if (!cplx && opt.rescale_qubits > 0) rescale_dm(ops, opt.rescale_qubits, plan.dtype == NWQ_F64 ? 0x1p-40 : 0x1p-6);
+  // per-qubit scale limit: FP64 storage 2^-40; FP32 storage and double-word
+  // plans (float exponents) 2^-6, so 16 qubits stay below 2^96
+  if (!cplx && opt.rescale_qubits > 0)
+    rescale_dm(ops, opt.rescale_qubits, plan.dtype == NWQ_F64 && !plan.dw ? 0x1p-40 : 0x1p-6);
 
   const int B = plan.B;
   const int T = std::min(opt.tile_bits, B);

@@ -63,6 +63,12 @@ struct Plan {
   // run-time specialised kernels of this plan's sweeps (built on first launch)
   std::shared_ptr<void> jit;
   bool interpreted = false;  // never use them
+  // FP64 plans: run the sweeps in double-word arithmetic (each FP64 value as
+  // an unevaluated sum of two floats, FP32 pipe) when every sweep has such a
+  // kernel; set before build_plan, which then keeps stored values within the
+  // float exponent range (deferred scales and scalars)
+  bool dw = false;
+  bool last_run_dw = false;  // the latest run took the double-word path
   // the merged operators in execution order (nwq_plan_ops)
   std::vector<BitOp> exec_ops;
   // tensor-core plans (NWQ_PLAN_TC): dense five-qubit blocks, one pass each

@@ -672,6 +672,33 @@ cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, c
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ double words
+// In place, pairs of doubles: to_dw turns each double v into the float pair
+// (h, l), h = v rounded to float and l = v - h rounded to float, in the same
+// 8 bytes; back, each pair becomes the double h + l.
+__global__ void dw_convert_kernel(void* __restrict__ data, uint64_t npairs, int to_dw) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < npairs; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (to_dw) {
+      const double2 d = reinterpret_cast<const double2*>(data)[i];
+      const float h0 = __double2float_rn(d.x), h1 = __double2float_rn(d.y);
+      const float l0 = __double2float_rn(d.x - (double)h0), l1 = __double2float_rn(d.y - (double)h1);
+      reinterpret_cast<float4*>(data)[i] = make_float4(h0, l0, h1, l1);
+    } else {
+      const float4 f = reinterpret_cast<const float4*>(data)[i];
+      reinterpret_cast<double2*>(data)[i] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+    }
+  }
+}
+
+cudaError_t launch_dw_convert(void* data, uint64_t ndouble, bool to_dw, int sm_count, cudaStream_t s) {
+  const uint64_t npairs = ndouble / 2;
+  unsigned grid = (unsigned)std::min<uint64_t>((npairs + 255) / 256, (uint64_t)sm_count * 8);
+  if (grid == 0) return cudaSuccess;
+  dw_convert_kernel<<<grid, 256, 0, s>>>(data, npairs, to_dw ? 1 : 0);
+  g_launches += 1;
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ conversions
 // Pauli reals -> complex (imag 0) and complex -> real parts.
 template <class R>

@@ -319,6 +319,21 @@ class Plan:
         mats = ms.view(np.complex128).reshape(-1, 32, 32)
         return [(tuple(int(q) for q in qs[5 * b:5 * b + 5]), mats[b].copy()) for b in range(nb)]
 
+    def kernel_arith(self, dw=False):
+        """Per state element, summed over the sweeps with specialised kernels:
+        (multiply-adds, multiplies, sweeps) as generated (dw: the double-word
+        kernels of an FP64 plan)."""
+        f, m, sw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        check(L.lib().nwq_plan_kernel_arith(self.h, 1 if dw else 0, ctypes.byref(f), ctypes.byref(m),
+                                            ctypes.byref(sw)))
+        return f.value, m.value, sw.value
+
+    def last_run_dw(self):
+        """True when the latest run took the double-word path."""
+        d = ctypes.c_int()
+        check(L.lib().nwq_plan_last_run_dw(self.h, ctypes.byref(d)))
+        return bool(d.value)
+
     def jit_check(self):
         """Compile (host only) the specialised kernels of this plan's sweeps:
         returns (eligible sweeps, compiled sweeps)."""
