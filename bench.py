@@ -43,6 +43,8 @@ SV_N, SV_DEPTH = 33, 10
 SV_WORKLOAD = f"sv_tfim_n{SV_N}_c128_depth{SV_DEPTH}"
 SV_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sv_jit_sweep_c128_n33_traffic.json")
 SV_KERNEL = "nwq_jit_sweep (run-time specialised complex128 sweep)"
+SV_KERNEL_DW = "nwq_jit_sweep (run-time specialised complex128 sweep, double-word arithmetic)"
+SV_TRAFFIC_FILE_DW = os.path.join(ROOT, "profiles", "sv_jit_sweep_dw_n33_traffic.json")
 
 # ---- the noisy density-matrix workload (--workload dm)
 N = 13
@@ -56,10 +58,13 @@ if JIT:
     KERNEL_SRCS = JIT_SRCS
     TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_jit_sweep_f64_n13_traffic.json")
     KERNEL_NAME = "nwq_jit_sweep (run-time specialised FP64 Pauli-basis DM sweep)"
+    KERNEL_NAME_DW = "nwq_jit_sweep (run-time specialised Pauli-basis DM sweep, double-word arithmetic)"
+    TRAFFIC_FILE_DW = os.path.join(ROOT, "profiles", "dm_jit_sweep_dw_n13_traffic.json")
 else:
     KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("sweep_kernels.cu", "device_util.cuh")]
     TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dm_sweep_f64_n13_traffic.json")
     KERNEL_NAME = "sweep_kernel<double,real> (FP64 Pauli-basis DM sweep, interpreted)"
+    KERNEL_NAME_DW, TRAFFIC_FILE_DW = KERNEL_NAME, TRAFFIC_FILE
 
 
 def workload():
@@ -382,21 +387,50 @@ def run_ours_sv(args, ws, rank, local):
     h2d = 56 * len(gates) + 24 * (len(zt) + len(ht))
     d2h = 8 * (len(zt) + 1)
 
-    # roofline of the dominant kernel: FP64-pipe bound (the plan counts its
-    # FP64 instructions per amplitude), HBM beside it
+    # roofline of the dominant kernel: arithmetic-pipe bound, HBM beside it.
+    # The instructions per amplitude are counted on the generated kernels
+    # (FP64 path: one FP64 instruction per multiply-add or multiply;
+    # double-word path: 15 FP32 instructions per multiply-add, 7 per multiply).
+    dw_ran = plan.last_run_dw()
+    fmas, muls, _ = plan.kernel_arith(dw=dw_ran)
     nlaunch = info["sweeps"]
     launch_s = sweep_ms / 1e3 / nlaunch
-    fp64_peak = probe_rate(L.PROBE_FP64_FMA)
-    achieved = info["fma_per_elem"] * 2.0 ** n / (sweep_ms / 1e3)
+    if dw_ran:
+        instr, pipe, kname = 15 * fmas + 7 * muls, "FP32", SV_KERNEL_DW
+        peak = probe_rate(L.PROBE_FP32_FMA)
+    else:
+        instr, pipe, kname = fmas + muls, "FP64", SV_KERNEL
+        peak = probe_rate(L.PROBE_FP64_FMA)
+    achieved = instr * 2.0 ** n / (sweep_ms / 1e3)
     hbm = info["bytes"] / (sweep_ms / 1e3) / 1e9
-    traffic = traffic_per_launch(SV_TRAFFIC_FILE, JIT_SRCS)
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": fp64_peak / 1e9,
-                "unit": "FP64 Ginstr/s", "frac": achieved / fp64_peak, "traffic": traffic,
-                "peak_source": "measured in this run (nwq_peak_probe: FP64 FMA chains on every SM)",
-                "kernel": SV_KERNEL, "fp64_instr_per_amplitude": info["fma_per_elem"],
+    traffic = traffic_per_launch(SV_TRAFFIC_FILE_DW if dw_ran else SV_TRAFFIC_FILE, JIT_SRCS)
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                "unit": f"{pipe} Ginstr/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"measured in this run (nwq_peak_probe: {pipe} FMA chains on every SM)",
+                "kernel": kname, f"{pipe.lower()}_instr_per_amplitude": instr,
                 "launches_per_step": nlaunch, "ms_per_launch": launch_s * 1e3,
                 "algorithmic_bytes_per_launch": info["bytes"] / nlaunch, "hbm_gbs": hbm,
-                "hbm_frac": hbm / _peaks()["hbm_gbs"]}
+                "hbm_frac": hbm / _peaks()["hbm_gbs"],
+                "note": "timed per plan run (the sweeps" + (" and the two double-word layout conversions" if dw_ran
+                                                            else "") + ")"}
+
+    # the same circuit on the FP64 pipe (one plan run), beside the default path
+    fp64_side = None
+    if dw_ran and not args.no_fp64_side:
+        with Plan(L.SV, n, gates, L.F64, flags=L.PLAN_FP64) as p64:
+            st.reset()
+            st.run(p64)  # compiles its kernels
+            st.reset()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            st.run(p64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            z64 = st.expect(zt)
+            e64 = st.expect(ht, sum=True)
+        t64 = a.elapsed_time(b) / 1e3
+        fp64_side = {"plan_run_s": t64, "double_word_plan_run_s": sweep_ms / 1e3, "speedup": t64 / (sweep_ms / 1e3),
+                     "max_z_diff": float(np.max(np.abs(z64 - z))), "energy_diff": abs(e64 - e)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -405,9 +439,13 @@ def run_ours_sv(args, ws, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of("sv", ws),
-                "plan": {"form": "fused (reusable)", "sweeps": info["sweeps"], "operators": info["ops"],
-                         "create_s": plan_s},
+                "vs_baseline": None, "dtype": "f32x2" if dw_ran else "f64", "data": "synthetic",
+                "config": config_of("sv", ws),
+                "arithmetic": ("double-word: each FP64 value as two floats (about 48 significant bits), FP32 pipe; "
+                               "complex128 storage between plan runs; FP64 parity tolerance 1e-12") if dw_ran
+                else "FP64",
+                "plan": {"form": "fused (reusable)" + (", double-word" if dw_ran else ""), "sweeps": info["sweeps"],
+                         "operators": info["ops"], "create_s": plan_s},
                 "gates_per_s": job_rate(len(gates), ws, ms / 1e3),
                 "e2e": {"value": job_rate(updates, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": e2e_steps,
@@ -416,6 +454,8 @@ def run_ours_sv(args, ws, rank, local):
                         "note": "the one-shot calls find the specialised kernels compiled by the timed plan; "
                                 "cold_compile_s is the first run's extra time (NVRTC compiles)"},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "step_split_ms": {"plan_run": sweep_ms, "reset_and_expectations": ms - sweep_ms},
+                "fp64_pipe_path": fp64_side,
                 "results": {"energy": e, "z0": float(z[0]), "norm": st.norm()}}
         print(json.dumps(line), flush=True)
     st.close()
@@ -500,19 +540,47 @@ def run_ours(args, ws, rank, local):
     h2d = info["table_bytes"] + 24 * (len(zt) + len(ht))
     d2h = 8 * (len(zt) + 1 + (1 << N))
 
-    # roofline of the dominant kernel (the FP64 DM sweep), from the live events
+    # roofline of the dominant kernel (the DM sweep), from the live events;
+    # multiply-adds per element counted on the generated kernels
+    dw_ran = plan.last_run_dw()
+    fmas, muls, _ = plan.kernel_arith(dw=dw_ran) if JIT else (info["fma_per_elem"], 0.0, 0)
     nlaunch = info["sweeps"]
-    flops_per_launch = 2.0 * info["fma_per_elem"] * 4.0 ** N / nlaunch
     launch_s = sweep_ms / 1e3 / nlaunch
-    achieved = flops_per_launch / launch_s / 1e12
-    peak = 2.0 * probe_rate(L.PROBE_FP64_FMA) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_per_launch(TRAFFIC_FILE, KERNEL_SRCS),
-                "peak_source": "measured in this run (nwq_peak_probe: FP64 FMA chains on every SM, 2 flops each)",
-                "kernel": KERNEL_NAME,
+    if dw_ran:  # FP32 instructions of the double-word kernels against the FP32 pipe
+        instr = (15 * fmas + 7 * muls) * 4.0 ** N / nlaunch
+        achieved = instr / launch_s / 1e9
+        peak = probe_rate(L.PROBE_FP32_FMA) / 1e9
+        unit, pipe, kname = "FP32 Ginstr/s", "FP32", KERNEL_NAME_DW
+    else:  # FP64 flops (2 per multiply-add) against the FP64 pipe
+        achieved = 2.0 * (fmas + muls) * 4.0 ** N / nlaunch / launch_s / 1e12
+        peak = 2.0 * probe_rate(L.PROBE_FP64_FMA) / 1e12
+        unit, pipe, kname = "TFLOP/s", "FP64", KERNEL_NAME
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak,
+                "traffic": traffic_per_launch(TRAFFIC_FILE_DW if dw_ran else TRAFFIC_FILE, KERNEL_SRCS),
+                "peak_source": f"measured in this run (nwq_peak_probe: {pipe} FMA chains on every SM)",
+                "kernel": kname, "fma_per_element": fmas,
                 "launches_per_step": nlaunch, "ms_per_launch": launch_s * 1e3,
                 "algorithmic_bytes_per_launch": info["bytes"] / nlaunch,
-                "hbm_gbs": info["bytes"] / nlaunch / launch_s / 1e9}
+                "hbm_gbs": info["bytes"] / nlaunch / launch_s / 1e9,
+                "hbm_frac": info["bytes"] / nlaunch / launch_s / 1e9 / _peaks()["hbm_gbs"]}
+
+    fp64_side = None
+    if dw_ran and not args.no_fp64_side:
+        with Plan(L.DM, N, gates, L.F64, noise, flags=L.PLAN_FP64) as p64:
+            st.reset()
+            st.run(p64)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                st.reset()
+                st.run(p64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            e64 = st.expect(ht, sum=True)
+        t64 = a.elapsed_time(b) / args.steps / 1e3
+        fp64_side = {"reset_and_plan_run_s": t64, "double_word_plan_run_s": sweep_ms / 1e3,
+                     "speedup": t64 / (sweep_ms / 1e3), "energy_diff": abs(e64 - e)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -523,11 +591,15 @@ def run_ours(args, ws, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of("dm", ws),
+                "vs_baseline": None, "dtype": "f32x2" if dw_ran else "f64", "data": "synthetic",
+                "config": config_of("dm", ws),
+                "arithmetic": ("double-word: each FP64 value as two floats (about 48 significant bits), FP32 pipe; "
+                               "FP64 storage between plan runs; FP64 parity tolerance 1e-12") if dw_ran else "FP64",
                 "plan": {"sweeps": info["sweeps"], "operators": info["ops"]},
                 "e2e": {"value": job_rate(gate_updates, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": ck,
+                "fp64_pipe_path": fp64_side,
                 "results": {"energy": e, "z0": float(z[0]), "prob_sum": float(p.sum())}}
         print(json.dumps(line), flush=True)
     st.close()
@@ -911,6 +983,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-side", action="store_true",
+                    help="skip the one FP64-pipe run beside a double-word headline")
     ap.add_argument("--workload", default="sv",
                     choices=["sv", "dm", "dm32", "sv-cases", "sv-errors", "vqe", "vqe-cobyla", "serve", "traj"],
                     help="sv: the default line (n=33 complex128 TFIM, depth 10); dm: noisy DM TFIM n=13; "

@@ -110,11 +110,13 @@ enum nwq_plan_flags {
   NWQ_PLAN_COMMUTE = 32u,    /* state vectors: when grouping sweeps, a diagonal operator may move ahead of
                                 skipped diagonal operators (they commute): fewer passes for circuits
                                 of diagonal gates (opt-in) */
-  NWQ_PLAN_DW = 64u          /* FP64 plans: double-word sweeps (see below) */
+  NWQ_PLAN_DW = 64u,         /* FP64 plans: double-word sweeps (the default; see below) */
+  NWQ_PLAN_FP64 = 128u       /* FP64 plans: FP64-pipe sweeps only, never double words */
 };
 
-/* Double-word sweeps (NWQ_PLAN_DW, or NWQ_DW=1 in the environment for every
- * FP64 plan; NWQ_DW=0 turns them off).  GB300 issues FP32 FMAs at 64 times
+/* Double-word sweeps (the default for FP64 plans; NWQ_PLAN_FP64 or NWQ_DW=0 in
+ * the environment selects the FP64-pipe kernels, NWQ_DW=1 forces double words
+ * even over NWQ_PLAN_FP64).  GB300 issues FP32 FMAs at 64 times
  * its FP64 rate, so an FP64 plan may run its sweeps with every FP64 value
  * held as an unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2,
  * about 48 significant bits) and every FP64 FMA done as a double-word

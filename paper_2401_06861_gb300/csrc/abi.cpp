@@ -422,12 +422,13 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
     }
   }
   if (kind == NWQ_DM && !(flags & NWQ_PLAN_NO_RESCALE)) o.rescale_qubits = n;
-  // double-word sweeps: NWQ_PLAN_DW, or NWQ_DW=1 / 0 to force them on / off
+  // double-word sweeps for FP64 plans unless NWQ_PLAN_FP64; NWQ_DW=1 / 0
+  // forces them on / off
   static const int env_dw = [] {
     const char* e = std::getenv("NWQ_DW");
     return !e ? -1 : (e[0] == '1' ? 1 : 0);
   }();
-  pl->p.dw = dtype == NWQ_F64 && (env_dw == 1 || (env_dw == -1 && (flags & NWQ_PLAN_DW)));
+  pl->p.dw = dtype == NWQ_F64 && (env_dw == 1 || (env_dw == -1 && !(flags & NWQ_PLAN_FP64)));
   build_plan(ops, o, pl->p);
   pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
   static const bool checks = [] {

@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cstdlib>
 
 #include "nwq_internal.h"
 #include "kernels.hpp"
@@ -131,6 +132,154 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled(const typename Cp
   }
 }
 
+// ------------------------------------------------------------------ double words
+// Complex128 passes with full tiles (2^12 amplitudes, 32 per thread): the
+// same passes, products and per-warp sums in double-word arithmetic on the
+// FP32 pipe (GB300 issues FP32 at 64 times its FP64 rate).  Each thread splits
+// its own 32 amplitudes in shared memory into float pairs by integer
+// operations (h = the top 24 significant bits, l = the next 23, rounded:
+// |x - h - l| <= 2^-47 |x|; magnitudes below 2^-103 become 0), forms each
+// product with an exact FMA-based product (Dekker) plus cross terms, and adds
+// the signed products into a compensated float pair (Knuth's TwoSum on the
+// running sum, the rounding errors and low parts collected separately).  The
+// warp's pairs are added the same way across lanes and lane 0 adds the pair,
+// converted to FP64, into the FP64 per-warp sums, as in sv_expect_tiled.
+struct Dw {
+  float h, l;
+};
+
+__device__ __forceinline__ Dw dw_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const unsigned e = (hi32 >> 20) & 0x7ffu;
+  // h: exponent rebiased 1023 -> 127, the top 23 fraction bits
+  const unsigned hb = (hi32 & 0x80000000u) | (__funnelshift_l(lo32, hi32 - (896u << 20), 3) & 0x7fffffffu);
+  // l: the other 29 fraction bits r (value r 2^(E-52)) as (2^(E-23) + q 2^(E-46)) - 2^(E-23),
+  // q = r / 64 rounded (at most 2^23); exact by Sterbenz's lemma
+  const unsigned mb = (hb & 0xff800000u) - (23u << 23);
+  const unsigned q = ((lo32 & 0x1fffffffu) + 32u) >> 6;
+  const float l = __fsub_rn(__int_as_float((int)(mb + q)), __int_as_float((int)mb));
+  if (e < 920u) return Dw{0.f, 0.f};                                        // |x| < 2^-103
+  if (e > 1150u) return Dw{__int_as_float((int)((hi32 & 0x80000000u) | 0x7f800000u)), 0.f};  // |x| >= 2^128
+  return Dw{__int_as_float((int)hb), l};
+}
+__device__ __forceinline__ Dw dw_mul(Dw a, Dw b) {
+  const float ph = __fmul_rn(a.h, b.h);
+  float pl = __fmaf_rn(a.h, b.h, -ph);
+  pl = __fmaf_rn(a.h, b.l, pl);
+  pl = __fmaf_rn(a.l, b.h, pl);
+  const float h = __fadd_rn(ph, pl);
+  return Dw{h, __fsub_rn(pl, __fsub_rn(h, ph))};
+}
+__device__ __forceinline__ Dw dw_fma(Dw a, Dw b, Dw c) {  // a b + c
+  const float ph = __fmul_rn(a.h, b.h);
+  float pl = __fmaf_rn(a.h, b.h, -ph);
+  pl = __fmaf_rn(a.h, b.l, pl);
+  pl = __fmaf_rn(a.l, b.h, pl);
+  const float s = __fadd_rn(ph, c.h);
+  const float v = __fsub_rn(s, ph);
+  float e = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, v)), __fsub_rn(c.h, v));
+  e = __fadd_rn(e, __fadd_rn(pl, c.l));
+  const float h = __fadd_rn(s, e);
+  return Dw{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// (s, c) += v, sign flipped when sg = 0x80000000
+__device__ __forceinline__ void dw_acc(float& s, float& c, Dw v, uint32_t sg) {
+  const float vh = __int_as_float(__float_as_int(v.h) ^ (int)sg), vl = __int_as_float(__float_as_int(v.l) ^ (int)sg);
+  const float t = __fadd_rn(s, vh);
+  const float z = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(vh, z));
+  c = __fadd_rn(c, __fadd_rn(e, vl));
+  s = t;
+}
+
+template <int E>
+__global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2* __restrict__ psi, uint64_t ntiles,
+                                                                  ExpPass P, const ExpTerm* __restrict__ terms,
+                                                                  double* __restrict__ part, int ncols) {
+  constexpr int kWarps = kExpThreads / 32;
+  static_assert(E == 32, "full 2^12 tiles");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t nel = 1u << P.T;
+  double2* tile = reinterpret_cast<double2*>(smem_raw);
+  float4* tw = reinterpret_cast<float4*>(smem_raw);  // the same tile as double words (re.h, re.l, im.h, im.l)
+  uint64_t* hoff = reinterpret_cast<uint64_t*>(smem_raw + sizeof(double2) * (size_t)nel);
+  ExpTerm* st = reinterpret_cast<ExpTerm*>(hoff + (1u << P.h));
+  double* red = reinterpret_cast<double*>(st + P.nk);  // [warp][term] FP64 sums
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int i = tid; i < P.nk; i += kExpThreads) st[i] = terms[P.k0 + i];
+  for (uint32_t j = tid; j < (1u << P.h); j += kExpThreads) hoff[j] = deposit(j, P.hmask);
+  for (int i = tid; i < kWarps * P.nk; i += kExpThreads) red[i] = 0.0;
+  const uint32_t lowmask = (1u << P.m) - 1u;
+
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = deposit(t, P.fmask);
+    __syncthreads();  // tables staged; previous tile consumed
+    // each thread copies, then splits, its own 32 amplitudes tid + 128 j
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+      const uint32_t l = tid + kExpThreads * j;
+      cp_async16(tile + l, psi + base + hoff[l >> P.m] + (l & lowmask));
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    Dw p[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+      const uint32_t l = tid + kExpThreads * j;
+      const double2 a = tile[l];
+      const Dw x = dw_split(a.x), y = dw_split(a.y);
+      tw[l] = make_float4(x.h, x.l, y.h, y.l);
+      p[j] = dw_fma(y, y, dw_mul(x, x));
+    }
+    __syncthreads();
+
+    for (int k = 0; k < P.nk; k++) {
+      const ExpTerm tm = st[k];
+      const uint32_t hi = (uint32_t)__popc((uint32_t)lane & (tm.zl >> 7)) & 1u;
+      uint32_t W = __ballot_sync(0xffffffffu, hi);
+      const uint32_t flip = ((uint32_t)__popc((uint32_t)tid & tm.zl & 127u) + (uint32_t)__popcll(base & tm.zh) +
+                             (uint32_t)(tm.y == 1 || tm.y == 2)) & 1u;
+      W ^= 0u - flip;
+      float as = 0.f, ac = 0.f;
+      if (tm.xl == 0) {
+#pragma unroll
+        for (int j = 0; j < E; j++) dw_acc(as, ac, p[j], (W << (31 - j)) & 0x80000000u);
+      } else if ((tm.y & 1) == 0) {  // Re(conj(q) s) = q.x s.x + q.y s.y
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+          const uint32_t l = tid + kExpThreads * j;
+          const float4 sv = tw[l], qv = tw[l ^ tm.xl];
+          const Dw w = dw_fma(Dw{qv.x, qv.y}, Dw{sv.x, sv.y}, dw_mul(Dw{qv.z, qv.w}, Dw{sv.z, sv.w}));
+          dw_acc(as, ac, w, (W << (31 - j)) & 0x80000000u);
+        }
+      } else {  // Im(conj(q) s) = q.x s.y - q.y s.x
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+          const uint32_t l = tid + kExpThreads * j;
+          const float4 sv = tw[l], qv = tw[l ^ tm.xl];
+          const Dw w = dw_fma(Dw{qv.x, qv.y}, Dw{sv.z, sv.w}, dw_mul(Dw{-qv.z, -qv.w}, Dw{sv.x, sv.y}));
+          dw_acc(as, ac, w, (W << (31 - j)) & 0x80000000u);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, as, o), oc = __shfl_xor_sync(0xffffffffu, ac, o);
+        dw_acc(as, ac, Dw{os, oc}, 0u);
+      }
+      if (lane == 0) red[warp * P.nk + k] += (double)as + (double)ac;
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < P.nk; k += kExpThreads) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) v += red[w * P.nk + k];
+    part[(size_t)blockIdx.x * ncols + st[k].out] = v;
+  }
+}
+
 // One group of terms sharing x; per-block partial sums to part[block * nt + t].
 template <class R>
 __global__ void __launch_bounds__(256) sv_expect_group(const typename Cplx<R>::T* __restrict__ psi, uint64_t N,
@@ -205,9 +354,35 @@ cudaError_t launch_tiled_e(const void* psi, uint64_t ntiles, const ExpPass& P, c
   return cudaGetLastError();
 }
 
+// NWQ_EXPECT_FP64=1: complex128 passes on the FP64 pipe only (no double words)
+bool expect_fp64_only() {
+  static const bool on = [] {
+    const char* e = std::getenv("NWQ_EXPECT_FP64");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+cudaError_t launch_tiled_dw(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
+                            int ncols, int grid, size_t smem, cudaStream_t s) {
+  static std::atomic<int> attr_dev{-1};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev.load() != dev) {
+    cudaError_t e = cudaFuncSetAttribute(sv_expect_tiled_dw<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  sv_expect_tiled_dw<32><<<grid, kExpThreads, smem, s>>>((const double2*)psi, ntiles, P, terms, part, ncols);
+  return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_tiled_r(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
                            int ncols, int grid, size_t smem, cudaStream_t s) {
+  if (sizeof(R) == 8 && P.T == 12 && !expect_fp64_only())
+    return launch_tiled_dw(psi, ntiles, P, terms, part, ncols, grid, smem, s);
   switch (P.T <= 7 ? 0 : P.T - 7) {
     case 0: return launch_tiled_e<R, 1>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
     case 1: return launch_tiled_e<R, 2>(psi, ntiles, P, terms, part, ncols, grid, smem, s);

@@ -1,4 +1,4 @@
-"""Double-word sweeps (NWQ_PLAN_DW): FP64 plans whose specialised kernels hold
+"""Double-word sweeps (the default of FP64 plans): specialised kernels that hold
 every value as two floats and run on the FP32 pipe, against the FP64 oracle
 at the FP64 tolerance (1e-12).
 
@@ -32,13 +32,14 @@ def maxerr(a, b):
 
 def run_both(kind, n, gates, noise=None, psi0=None, flags=0):
     out = {}
-    for extra in (0, L.PLAN_DW):
+    for extra in (L.PLAN_FP64, L.PLAN_DW):
         with State(kind, n, L.F64) as st, Plan(kind, n, gates, L.F64, noise, flags=flags | extra) as p:
             if psi0 is not None:
                 st.load(psi0)
             st.run(p)
+            assert p.last_run_dw() == (extra == L.PLAN_DW)
             out[extra] = st.copy()
-    return out[0], out[L.PLAN_DW]
+    return out[L.PLAN_FP64], out[L.PLAN_DW]
 
 
 @pytest.mark.parametrize("n,family", [(18, "random"), (19, "random_mat"), (20, "tfim"), (18, "hea"), (21, "plain")])
@@ -69,16 +70,17 @@ def test_dw_noisy_density_matrices_match_the_oracle(n, seed):
     noise = inputs.noise_params(n, seed=5500 + seed)
     rho0 = inputs.random_density(n, 5600 + seed)
     out = {}
-    for extra in (0, L.PLAN_DW):
+    for extra in (L.PLAN_FP64, L.PLAN_DW):
         with State(L.DM, n, L.F64) as st, Plan(L.DM, n, gates, L.F64, noise, flags=extra) as p:
             st.load(rho0)
             st.run(p)
+            assert p.last_run_dw() == (extra == L.PLAN_DW)
             out[extra] = st.copy()
     ref = oracle.dm_run(n, gates, noise, rho0)
     err = maxerr(out[L.PLAN_DW], ref)
-    print(f"dw dm n={n}: double-word err {err:.3e}, FP64 err {maxerr(out[0], ref):.3e}")
+    print(f"dw dm n={n}: double-word err {err:.3e}, FP64 err {maxerr(out[L.PLAN_FP64], ref):.3e}")
     assert err <= 1e-12
-    assert not np.array_equal(out[0], out[L.PLAN_DW])
+    assert not np.array_equal(out[L.PLAN_FP64], out[L.PLAN_DW])
 
 
 def test_dw_noisy_tfim_n13_two_steps_match_the_kraus_oracle():

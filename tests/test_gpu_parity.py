@@ -74,8 +74,10 @@ def test_sv_specialised_kernels(n, family, dtype):
     psi0 = inputs.random_state(n, 2100 + n)
     out = {}
     for extra in (0, L.PLAN_INTERPRETED):
-        # a reusable plan compiles its kernels before its first run
-        with State(L.SV, n, dtype) as st, Plan(L.SV, n, gates, dtype, flags=flags | extra) as plan:
+        # a reusable plan compiles its kernels before its first run; FP64
+        # plans take the FP64-pipe kernels here (the double-word ones round
+        # differently; tests/test_gpu_dw.py checks them against the oracle)
+        with State(L.SV, n, dtype) as st, Plan(L.SV, n, gates, dtype, flags=flags | extra | L.PLAN_FP64) as plan:
             st.load(psi0)
             st.run(plan)
             out[extra] = st.copy()
