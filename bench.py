@@ -834,6 +834,90 @@ def run_dm32(args):
     print(json.dumps(line), flush=True)
 
 
+def run_vqe_sharded(args, ws, rank, local):
+    """Batched VQE over several GPUs (torchrun): the 4096 sets split into one
+    share per rank (paper_2401_06861_gb300/dispatch.py), each share one
+    batched FP32 launch on that rank's GPU, energies gathered on rank 0.
+    Whole-job energies/s = 3 x 4096 / the slowest rank's time (strong scaling:
+    the total is fixed)."""
+    import numpy as np
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, dispatch, inputs
+    from paper_2401_06861_gb300.sim import Batch
+    build.build()
+    torch.cuda.set_device(local)
+    n, layers, nsets = 12, 4, 4096
+    hs = (0.5, 1.0, 2.0)
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    params = inputs.hea_params(n, layers, nsets, seed=4096)
+    terms = inputs.zz_terms(n) + inputs.x_terms(n)
+    coeffs = np.array([[-1.0] * (n - 1) + [-h] * n for h in hs])
+    stream = torch.cuda.current_stream()
+    timing = {}
+
+    def run_share(lo, hi, share):
+        p = torch.from_numpy(np.ascontiguousarray(share)).cuda()
+        out = torch.zeros(max(hi - lo, 1), 3, dtype=torch.float64, device="cuda")
+        b = Batch([dict(n=n, gates=gates, param_index=pidx, terms=terms, coeffs=coeffs)], layers * 2 * n, L.F32,
+                  stream=stream.cuda_stream)
+        for _ in range(max(args.warmup, 3)):
+            b.run(p.data_ptr(), hi - lo, out.data_ptr(), stream=stream.cuda_stream, graph=True)
+        torch.cuda.synchronize()
+        import torch.distributed as dist
+        dist.barrier()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            b.run(p.data_ptr(), hi - lo, out.data_ptr(), stream=stream.cuda_stream, graph=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        timing["s"] = t0.elapsed_time(t1) / args.steps / 1e3
+        b.close()
+        return out[:hi - lo].cpu().numpy()
+
+    energies = dispatch.run_batched(run_share, params, ws, rank)
+    sec = reduce_max(timing["s"], ws)
+    if rank == 0:
+        print(json.dumps({"workload": "vqe_hea_n12_4layers_4096sets", "path": "batched_f32_sharded",
+                          "metric": "energies/s", "value": 3 * nsets / sec, "unit": "energies/s", "n_gpus": ws,
+                          "scaling": "strong", "ms_per_batch": sec * 1e3, "sets_per_rank": nsets // ws,
+                          "energies_shape": list(energies.shape)}), flush=True)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+    return 0
+
+
+def run_serve_sharded(args, ws, rank, local):
+    """Serving over several GPUs (torchrun): the request stream dealt
+    round-robin to the ranks (paper_2401_06861_gb300/dispatch.py), each rank
+    serving its share with its own executor, streams and 150 GB budget;
+    results gathered on rank 0."""
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build, dispatch, inputs
+    from paper_2401_06861_gb300.serve import GpuExecutor, Server, summarize
+    build.build()
+    torch.cuda.set_device(local)
+    reqs = inputs.serve_requests(rate=200.0, duration=args.serve_seconds, seed=200)
+    warm = inputs.serve_requests(rate=200.0, duration=1.0, seed=7, sv_n=(8, 20), dm_n=(6, 9))
+    Server(GpuExecutor(L.F32), slots=8, dtype=L.F32).serve(warm)
+    import torch.distributed as dist
+    dist.barrier()
+    res, stats = dispatch.serve_sharded(
+        lambda: Server(GpuExecutor(L.F32), slots=args.serve_slots, dtype=L.F32, budget_bytes=150e9), reqs, ws, rank)
+    if rank == 0:
+        wall = max(st["wall"] for st in stats)
+        s = summarize(res, wall)
+        s.update(workload=f"serve_poisson200_{args.serve_seconds:g}s", path="served_f32_sharded", n_gpus=ws,
+                 metric="circuits/s", value=s["circuits_per_s"], unit="circuits/s", per_rank=stats)
+        print(json.dumps(s), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def run_vqe_cobyla(args):
     """VQE outer loop (COBYLA) on the Ising chain: noise-free n = 12 (4 layers,
     96 parameters; 256 batched starts, then COBYLA with one launch per energy)
@@ -1022,9 +1106,9 @@ def main():
     if args.workload == "dm32":
         return run_dm32(args)
     if args.workload == "vqe":
-        return run_vqe(args)
+        return run_vqe_sharded(args, ws, rank, local) if ws > 1 else run_vqe(args)
     if args.workload == "serve":
-        return run_serve(args)
+        return run_serve_sharded(args, ws, rank, local) if ws > 1 else run_serve(args)
     return run_ours(args, ws, rank, local)
 
 
