@@ -390,16 +390,16 @@ def run_ours_sv(args, ws, rank, local):
     # roofline of the dominant kernel: arithmetic-pipe bound, HBM beside it.
     # The instructions per amplitude are counted on the generated kernels
     # (FP64 path: one FP64 instruction per multiply-add or multiply;
-    # double-word path: 15 FP32 instructions per multiply-add, 7 per multiply).
+    # double-word path: the FP32 instructions of its operations).
     dw_ran = plan.last_run_dw()
-    fmas, muls, _ = plan.kernel_arith(dw=dw_ran)
+    fmas, muls, instr, _ = plan.kernel_arith(dw=dw_ran)
     nlaunch = info["sweeps"]
     launch_s = sweep_ms / 1e3 / nlaunch
     if dw_ran:
-        instr, pipe, kname = 15 * fmas + 7 * muls, "FP32", SV_KERNEL_DW
+        pipe, kname = "FP32", SV_KERNEL_DW
         peak = probe_rate(L.PROBE_FP32_FMA)
     else:
-        instr, pipe, kname = fmas + muls, "FP64", SV_KERNEL
+        pipe, kname = "FP64", SV_KERNEL
         peak = probe_rate(L.PROBE_FP64_FMA)
     achieved = instr * 2.0 ** n / (sweep_ms / 1e3)
     hbm = info["bytes"] / (sweep_ms / 1e3) / 1e9
@@ -543,11 +543,12 @@ def run_ours(args, ws, rank, local):
     # roofline of the dominant kernel (the DM sweep), from the live events;
     # multiply-adds per element counted on the generated kernels
     dw_ran = plan.last_run_dw()
-    fmas, muls, _ = plan.kernel_arith(dw=dw_ran) if JIT else (info["fma_per_elem"], 0.0, 0)
+    fmas, muls, per_elem, _ = (plan.kernel_arith(dw=dw_ran) if JIT
+                               else (info["fma_per_elem"], 0.0, info["fma_per_elem"], 0))
     nlaunch = info["sweeps"]
     launch_s = sweep_ms / 1e3 / nlaunch
     if dw_ran:  # FP32 instructions of the double-word kernels against the FP32 pipe
-        instr = (15 * fmas + 7 * muls) * 4.0 ** N / nlaunch
+        instr = per_elem * 4.0 ** N / nlaunch
         achieved = instr / launch_s / 1e9
         peak = probe_rate(L.PROBE_FP32_FMA) / 1e9
         unit, pipe, kname = "FP32 Ginstr/s", "FP32", KERNEL_NAME_DW

@@ -330,6 +330,15 @@ int nwq_expect_plan(int n, const nwq_pauli_term* terms, size_t nt, int normalize
  * Synchronises the device. */
 int nwq_tc_timeouts(int* count);
 
+/* Test hook of the bounded waits: runs the first block of a tensor-core plan
+ * on the state with its MMAs withheld and each MMA-completion wait bounded at
+ * 4096 polls, so every wait runs out with nothing in flight; each CTA counts
+ * its timeout, frees its tensor memory and returns, leaving its tiles
+ * unwritten (the state is unchanged).  *timeouts = waits that ran out in this
+ * call; returns NWQ_ETIMEOUT when there were any (the expected outcome).
+ * Synchronises the state's stream. */
+int nwq_tc_wait_test(nwq_state* st, const nwq_plan* plan, int* timeouts);
+
 /* Test hook: generate and compile (host only; nothing is loaded on a device)
  * the run-time specialised kernel of every eligible sweep of a plan.  Sweeps
  * over at least NWQ_JIT_MIN_BITS index bits (default 18: state vectors of
@@ -349,11 +358,13 @@ int nwq_plan_last_run_dw(const nwq_plan* plan, int* dw);
 /* Arithmetic of the plan's run-time specialised sweep kernels, for roofline
  * accounting (host only): per state element, summed over the sweeps that
  * have such a kernel (*sweeps of them, may be NULL), the multiply-adds and
- * multiplies of the kernels' value type as generated.  dw = 0: the kernels of
- * the plan's own precision (one FP64 / FP32 instruction each); dw = 1: the
- * double-word kernels of an FP64 plan (a multiply-add is 15 FP32
- * instructions, a multiply 7). */
-int nwq_plan_kernel_arith(const nwq_plan* plan, int dw, double* fma_per_elem, double* mul_per_elem, int* sweeps);
+ * multiplies of the kernels' value type as generated, and *instr_per_elem the
+ * arithmetic-pipe instructions they make.  dw = 0: the kernels of the plan's
+ * own precision (one FP64 / FP32 instruction each); dw = 1: the double-word
+ * kernels of an FP64 plan (a multiply-add is 12 FP32 instructions, a
+ * multiply 4). */
+int nwq_plan_kernel_arith(const nwq_plan* plan, int dw, double* fma_per_elem, double* mul_per_elem,
+                          double* instr_per_elem, int* sweeps);
 
 /* Queue background compilation of the plan's specialised sweep kernels that
  * are not compiled yet (one compiler thread per process) and return at once;

@@ -110,8 +110,9 @@ def lib():
                                   P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint64), P(i32), P(i32),
                                   P(i32), P(i32)]),
         "nwq_tc_timeouts": (i32, [P(i32)]),
+        "nwq_tc_wait_test": (i32, [vp, vp, P(i32)]),
         "nwq_plan_jit_prefetch": (i32, [vp, P(i32)]),
-        "nwq_plan_kernel_arith": (i32, [vp, i32, P(dbl), P(dbl), P(i32)]),
+        "nwq_plan_kernel_arith": (i32, [vp, i32, P(dbl), P(dbl), P(dbl), P(i32)]),
         "nwq_plan_last_run_dw": (i32, [vp, P(i32)]),
         "nwq_jit_shutdown": (i32, []),
         "nwq_expect_pauli_sum": (i32, [vp, P(PauliTerm), sz, P(dbl), u32]),

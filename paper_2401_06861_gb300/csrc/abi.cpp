@@ -429,6 +429,11 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
     return !e ? -1 : (e[0] == '1' ? 1 : 0);
   }();
   pl->p.dw = dtype == NWQ_F64 && (env_dw == 1 || (env_dw == -1 && !(flags & NWQ_PLAN_FP64)));
+  // double-word complex128 sweeps are FP32-issue bound: tiles of 2^11 give
+  // every thread of a 256-thread CTA a register group of 8 amplitudes in each
+  // phase (2^10 tiles, sized for the FP64 pipe, leave half of them idle)
+  if (pl->p.dw && kind == NWQ_SV && !(tuning && tuning->tile_bits) && !std::getenv("NWQ_TILE_BITS"))
+    o.tile_bits = 11;
   build_plan(ops, o, pl->p);
   pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
   static const bool checks = [] {
@@ -610,6 +615,24 @@ extern "C" int nwq_expect_plan(int n, const nwq_pauli_term* terms, size_t nt, in
   return NWQ_OK;
 }
 
+extern "C" int nwq_tc_wait_test(nwq_state* st, const nwq_plan* plan, int* timeouts) {
+  if (!st || !plan || !timeouts) return fail(NWQ_EINVAL, "NULL argument");
+  Plan& p = const_cast<Plan&>(plan->p);
+  if (!p.tc || p.tcg.empty()) return fail(NWQ_EINVAL, "not a tensor-core plan");
+  if (p.kind != st->kind || p.n != st->n || p.dtype != st->dtype) return fail(NWQ_EINVAL, "plan does not match state");
+  int rc = plan_upload(p, st->stream);
+  if (rc) return rc;
+  int before = 0, after = 0;
+  CK(cudaStreamSynchronize(st->stream), "wait test");
+  CK(tc_timeouts(&before), "tensor-core status read");
+  const float* tab = (const float*)((const char*)p.dev + p.tc_off);
+  CK(launch_tc_block(st->buf, p.tcg[0], tab, st->sm_count, st->stream, true), "tensor-core wait test launch");
+  CK(cudaStreamSynchronize(st->stream), "wait test");
+  CK(tc_timeouts(&after), "tensor-core status read");
+  *timeouts = after - before;
+  return *timeouts > 0 ? fail(NWQ_ETIMEOUT, "tensor-core MMA-completion waits ran out (MMAs withheld)") : NWQ_OK;
+}
+
 extern "C" int nwq_tc_timeouts(int* count) {
   if (!count) return fail(NWQ_EINVAL, "count is NULL");
   CK(cudaDeviceSynchronize(), "device synchronize");
@@ -638,9 +661,9 @@ extern "C" int nwq_plan_last_run_dw(const nwq_plan* plan, int* dw) {
 }
 
 extern "C" int nwq_plan_kernel_arith(const nwq_plan* plan, int dw, double* fma_per_elem, double* mul_per_elem,
-                                     int* sweeps) {
-  if (!plan || !fma_per_elem || !mul_per_elem) return fail(NWQ_EINVAL, "NULL argument");
-  const int e = jit_plan_arith(plan->p, dw != 0, fma_per_elem, mul_per_elem);
+                                     double* instr_per_elem, int* sweeps) {
+  if (!plan || !fma_per_elem || !mul_per_elem || !instr_per_elem) return fail(NWQ_EINVAL, "NULL argument");
+  const int e = jit_plan_arith(plan->p, dw != 0, fma_per_elem, mul_per_elem, instr_per_elem);
   if (sweeps) *sweeps = e;
   return NWQ_OK;
 }

@@ -183,6 +183,14 @@ __device__ __forceinline__ Dw dw_fma(Dw a, Dw b, Dw c) {  // a b + c
   const float h = __fadd_rn(s, e);
   return Dw{h, __fsub_rn(e, __fsub_rn(h, s))};
 }
+__device__ __forceinline__ Dw dw_add(Dw a, Dw b) {  // a + b (TwoSum of the high parts, then Fast2Sum)
+  const float s = __fadd_rn(a.h, b.h);
+  const float v = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, e);
+  return Dw{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
 // (s, c) += v, sign flipped when sg = 0x80000000
 __device__ __forceinline__ void dw_acc(float& s, float& c, Dw v, uint32_t sg) {
   const float vh = __int_as_float(__float_as_int(v.h) ^ (int)sg), vl = __int_as_float(__float_as_int(v.l) ^ (int)sg);
@@ -206,6 +214,7 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
   uint64_t* hoff = reinterpret_cast<uint64_t*>(smem_raw + sizeof(double2) * (size_t)nel);
   ExpTerm* st = reinterpret_cast<ExpTerm*>(hoff + (1u << P.h));
   double* red = reinterpret_cast<double*>(st + P.nk);  // [warp][term] FP64 sums
+  float2* wht = reinterpret_cast<float2*>(red + kWarps * P.nk);  // [k][thread] transforms (8-byte aligned)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   for (int i = tid; i < P.nk; i += kExpThreads) st[i] = terms[P.k0 + i];
@@ -233,35 +242,51 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
       tw[l] = make_float4(x.h, x.l, y.h, y.l);
       p[j] = dw_fma(y, y, dw_mul(x, x));
     }
+    // Z-type strings: element l = tid + 128 j has sign (-1)^{|tid & zl| + |j & (zl >> 7)|}, so a
+    // thread's signed sum over its 32 probabilities is +- entry (zl >> 7) of their Walsh-Hadamard
+    // transform W[k] = sum_j (-1)^{|j & k|} p_j: one transform serves every Z-type string
+#pragma unroll
+    for (int b = 1; b < E; b <<= 1) {
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        if (j & b) continue;
+        const Dw a0 = p[j], a1 = p[j | b];
+        p[j] = dw_add(a0, a1);
+        p[j | b] = dw_add(a0, Dw{-a1.h, -a1.l});
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < E; j++) wht[j * kExpThreads + tid] = make_float2(p[j].h, p[j].l);
     __syncthreads();
 
     for (int k = 0; k < P.nk; k++) {
       const ExpTerm tm = st[k];
-      const uint32_t hi = (uint32_t)__popc((uint32_t)lane & (tm.zl >> 7)) & 1u;
-      uint32_t W = __ballot_sync(0xffffffffu, hi);
-      const uint32_t flip = ((uint32_t)__popc((uint32_t)tid & tm.zl & 127u) + (uint32_t)__popcll(base & tm.zh) +
-                             (uint32_t)(tm.y == 1 || tm.y == 2)) & 1u;
-      W ^= 0u - flip;
+      const uint32_t flip = ((uint32_t)__popcll(base & tm.zh) + (uint32_t)(tm.y == 1 || tm.y == 2)) & 1u;
       float as = 0.f, ac = 0.f;
       if (tm.xl == 0) {
+        const float2 w = wht[((tm.zl >> 7) & 31u) * kExpThreads + tid];
+        const uint32_t sg = ((((uint32_t)__popc((uint32_t)tid & tm.zl & 127u)) ^ flip) & 1u) << 31;
+        as = __int_as_float(__float_as_int(w.x) ^ (int)sg);
+        ac = __int_as_float(__float_as_int(w.y) ^ (int)sg);
+      } else {
+        // each pair (l, l ^ xl) once, l with the lowest bit of xl clear: the partner's
+        // product is the same value (Re part for even y, Im part for odd y), so the pair
+        // contributes twice the value of its first member
+        const int pb = __ffs(tm.xl) - 1;
+        const uint32_t lo = (1u << pb) - 1u;
+        const bool im = (tm.y & 1) != 0;
 #pragma unroll
-        for (int j = 0; j < E; j++) dw_acc(as, ac, p[j], (W << (31 - j)) & 0x80000000u);
-      } else if ((tm.y & 1) == 0) {  // Re(conj(q) s) = q.x s.x + q.y s.y
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-          const uint32_t l = tid + kExpThreads * j;
+        for (int m = 0; m < E / 2; m++) {
+          const uint32_t kk = tid + kExpThreads * m;
+          const uint32_t l = ((kk & ~lo) << 1) | (kk & lo);
           const float4 sv = tw[l], qv = tw[l ^ tm.xl];
-          const Dw w = dw_fma(Dw{qv.x, qv.y}, Dw{sv.x, sv.y}, dw_mul(Dw{qv.z, qv.w}, Dw{sv.z, sv.w}));
-          dw_acc(as, ac, w, (W << (31 - j)) & 0x80000000u);
+          const Dw w = im ? dw_fma(Dw{qv.x, qv.y}, Dw{sv.z, sv.w}, dw_mul(Dw{-qv.z, -qv.w}, Dw{sv.x, sv.y}))
+                          : dw_fma(Dw{qv.x, qv.y}, Dw{sv.x, sv.y}, dw_mul(Dw{qv.z, qv.w}, Dw{sv.z, sv.w}));
+          const uint32_t sg = ((((uint32_t)__popc(l & tm.zl)) ^ flip) & 1u) << 31;
+          dw_acc(as, ac, w, sg);
         }
-      } else {  // Im(conj(q) s) = q.x s.y - q.y s.x
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-          const uint32_t l = tid + kExpThreads * j;
-          const float4 sv = tw[l], qv = tw[l ^ tm.xl];
-          const Dw w = dw_fma(Dw{qv.x, qv.y}, Dw{sv.z, sv.w}, dw_mul(Dw{-qv.z, -qv.w}, Dw{sv.x, sv.y}));
-          dw_acc(as, ac, w, (W << (31 - j)) & 0x80000000u);
-        }
+        as = __fmul_rn(as, 2.f);  // exact
+        ac = __fmul_rn(ac, 2.f);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
@@ -363,8 +388,11 @@ bool expect_fp64_only() {
   return on;
 }
 
+constexpr size_t kDwWhtBytes = 32 * kExpThreads * sizeof(float2);  // per-thread transforms of sv_expect_tiled_dw
+
 cudaError_t launch_tiled_dw(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
                             int ncols, int grid, size_t smem, cudaStream_t s) {
+  smem += kDwWhtBytes;
   static std::atomic<int> attr_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);

@@ -325,9 +325,13 @@ void append_coefs(std::vector<unsigned char>& out, const unsigned char* src, siz
 // product takes the exact error of the high parts' product from an FMA and
 // adds the cross terms (Dekker's product with an FMA); the sum of the product
 // and c adds the high parts with Knuth's TwoSum (exact) and the low parts in
-// float, then renormalises with Fast2Sum (Joldes, Muller, Popescu 2017,
-// double-word building blocks).  Error: a few 2^-48 of |a b| + |c|.  The _rn
-// intrinsics keep the compiler from contracting or reordering these steps.
+// float (Joldes, Muller, Popescu 2017, double-word building blocks).  Results
+// are not renormalised (no final Fast2Sum): the pair (rounded sum, collected
+// error) already represents the value to a few 2^-48 of |a b| + |c|, the next
+// operation treats it the same way, and the conversion back to FP64 adds the
+// two parts exactly.  The _rn intrinsics keep the compiler from contracting or
+// reordering these steps.
+constexpr double kDwFmaInstr = 12, kDwMulInstr = 4;  // FP32 instructions of fma() and operator* below
 const char* kDwPrelude = R"DW(struct __align__(8) dw {
   float h, l;
   dw() = default;
@@ -344,8 +348,7 @@ __device__ __forceinline__ dw operator*(dw a, dw b) {
   float pl = __fmaf_rn(a.h, b.h, -ph);
   pl = __fmaf_rn(a.h, b.l, pl);
   pl = __fmaf_rn(a.l, b.h, pl);
-  const float h = __fadd_rn(ph, pl);
-  return dw(h, __fsub_rn(pl, __fsub_rn(h, ph)));
+  return dw(ph, pl);
 }
 __device__ __forceinline__ dw fma(dw a, dw b, dw c) {
   const float ph = __fmul_rn(a.h, b.h);
@@ -354,10 +357,8 @@ __device__ __forceinline__ dw fma(dw a, dw b, dw c) {
   pl = __fmaf_rn(a.l, b.h, pl);
   const float s = __fadd_rn(ph, c.h);
   const float v = __fsub_rn(s, ph);
-  float e = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, v)), __fsub_rn(c.h, v));
-  e = __fadd_rn(e, __fadd_rn(pl, c.l));
-  const float h = __fadd_rn(s, e);
-  return dw(h, __fsub_rn(e, __fsub_rn(h, s)));
+  const float e = __fadd_rn(__fsub_rn(ph, __fsub_rn(s, v)), __fsub_rn(c.h, v));
+  return dw(s, __fadd_rn(e, __fadd_rn(pl, c.l)));
 }
 )DW";
 
@@ -666,7 +667,23 @@ struct Gen {
         for (int b = 0; b < RB; b++)
           if ((i >> b) & 1) l |= 1u << P.u[b];
         roff[i] = swz(es, l);
-        o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
+      }
+      // Registers on the tile's lowest bits are consecutive elements: VW of
+      // them (16 bytes at most) move as one vector access, 16-byte aligned
+      // (gb and the offsets have those bits clear; the row padding keeps
+      // runs of VW inside one 128-byte row).
+      const int VW = (16 / es >= 4 && RB >= 2 && P.u[0] == 0 && P.u[1] == 1) ? 4
+                     : (16 / es >= 2 && RB >= 1 && P.u[0] == 0) ? 2 : 1;
+      for (int i = 0; i < NR; i += VW) {
+        if (VW == 1) {
+          o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
+          continue;
+        }
+        o << "    C";
+        for (int k = 0; k < VW; k++) o << (k ? ", " : " ") << r(i + k);
+        o << "; { const Vec" << VW << " v = *reinterpret_cast<const Vec" << VW << "*>(gt + " << roff[i] << ");";
+        for (int k = 0; k < VW; k++) o << " " << r(i + k) << " = v.e[" << k << "];";
+        o << " }\n";
       }
       const std::string before = o.str();
       if (real) {
@@ -682,7 +699,15 @@ struct Gen {
         fma_per_elem += (double)nf / NR;
         mul_per_elem += (double)nm / NR;
       }
-      for (int i = 0; i < NR; i++) o << "    gt[" << roff[i] << "] = " << r(i) << ";\n";
+      for (int i = 0; i < NR; i += VW) {
+        if (VW == 1) {
+          o << "    gt[" << roff[i] << "] = " << r(i) << ";\n";
+          continue;
+        }
+        o << "    { Vec" << VW << " v;";
+        for (int k = 0; k < VW; k++) o << " v.e[" << k << "] = " << r(i + k) << ";";
+        o << " *reinterpret_cast<Vec" << VW << "*>(gt + " << roff[i] << ") = v; }\n";
+      }
       o << "    }\n    __syncthreads();\n";
     }
     if (!ok) return false;
@@ -709,6 +734,8 @@ struct Gen {
         << "__device__ __forceinline__ C from_table(CT v) { return v; }\n";
     }
     o << "struct Coef { C c[" << npk << "]; };\n"
+      << "struct __align__(2 * sizeof(C)) Vec2 { C e[2]; };\n"
+      << "struct __align__(4 * sizeof(C) <= 16 ? 4 * sizeof(C) : 16) Vec4 { C e[4]; };\n"
       << "__device__ __forceinline__ unsigned long long dep(unsigned long long v, unsigned long long mask) {\n"
       << "  unsigned long long out = 0;\n"
       << "  while (v && mask) { unsigned long long lb = mask & (~mask + 1ull); if (v & 1ull) out |= lb; v >>= 1; mask ^= lb; }\n"
@@ -797,7 +824,7 @@ struct Gen {
   size_t smem = 0;
   // arithmetic per state element of this sweep, counted on the emitted source:
   // multiply-adds and multiplies of R values (one FP64 instruction each; a
-  // double-word multiply-add is 15 FP32 instructions, a multiply 7)
+  // double-word multiply-add is 12 FP32 instructions, a multiply 4)
   double fma_per_elem = 0.0, mul_per_elem = 0.0;
 };
 
@@ -932,7 +959,7 @@ int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log) 
   return 0;
 }
 
-int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem) {
+int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem, double* instr_per_elem) {
   *fma_per_elem = *mul_per_elem = 0.0;
   int eligible = 0;
   for (size_t i = 0; i < p.sweeps.size(); i++) {
@@ -945,6 +972,10 @@ int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per
     *mul_per_elem += g.mul_per_elem;
     eligible++;
   }
+  // instructions of the arithmetic pipe: one each (FP64 or FP32 kernels), or
+  // the FP32 instructions of the double-word operations of kDwPrelude
+  *instr_per_elem = dw && p.dtype == NWQ_F64 ? kDwFmaInstr * *fma_per_elem + kDwMulInstr * *mul_per_elem
+                                             : *fma_per_elem + *mul_per_elem;
   return eligible;
 }
 

@@ -40,8 +40,8 @@ int jit_prefetch(const Plan& p);
 // Arithmetic of the plan's specialised kernels per state element, summed over
 // the eligible sweeps (their count is returned): multiply-adds and multiplies
 // of the kernels' value type, counted on the generated source (dw: the
-// double-word kernels).
-int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem);
+// double-word kernels), and the arithmetic-pipe instructions they make.
+int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem, double* instr_per_elem);
 
 // Stop the background compiler (queued kernels stay uncompiled; the one in
 // progress finishes) and join its thread.  Idempotent.

@@ -674,15 +674,32 @@ cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, c
 
 // ------------------------------------------------------------------ double words
 // In place, pairs of doubles: to_dw turns each double v into the float pair
-// (h, l), h = v rounded to float and l = v - h rounded to float, in the same
-// 8 bytes; back, each pair becomes the double h + l.
+// (h, l) in the same 8 bytes by integer operations (GB300 runs FP64 <-> FP32
+// conversions on its FP64 pipe): h keeps the top 24 significant bits of v,
+// l the next 23, rounded, so |v - h - l| <= 2^-47 |v|; magnitudes below
+// 2^-103 become 0.  Back, each pair becomes the double h + l.
+__device__ __forceinline__ float2 dw_split_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+  const unsigned e = (hi32 >> 20) & 0x7ffu;  // biased exponent
+  // h: exponent rebiased 1023 -> 127, the top 23 fraction bits
+  const unsigned hb = (hi32 & 0x80000000u) | (__funnelshift_l(lo32, hi32 - (896u << 20), 3) & 0x7fffffffu);
+  // l: the other 29 fraction bits r (value r 2^(E-52)) as (2^(E-23) + q 2^(E-46)) - 2^(E-23),
+  // q = r / 64 rounded (at most 2^23), exact by Sterbenz's lemma
+  const unsigned mb = (hb & 0xff800000u) - (23u << 23);
+  const unsigned q = ((lo32 & 0x1fffffffu) + 32u) >> 6;
+  const float l = __fsub_rn(__int_as_float((int)(mb + q)), __int_as_float((int)mb));
+  if (e < 920u) return make_float2(0.f, 0.f);  // |x| < 2^-103
+  if (e > 1150u) return make_float2(__int_as_float((int)((hi32 & 0x80000000u) | 0x7f800000u)), 0.f);
+  return make_float2(__int_as_float((int)hb), l);
+}
+
 __global__ void dw_convert_kernel(void* __restrict__ data, uint64_t npairs, int to_dw) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < npairs; i += (uint64_t)gridDim.x * blockDim.x) {
     if (to_dw) {
       const double2 d = reinterpret_cast<const double2*>(data)[i];
-      const float h0 = __double2float_rn(d.x), h1 = __double2float_rn(d.y);
-      const float l0 = __double2float_rn(d.x - (double)h0), l1 = __double2float_rn(d.y - (double)h1);
-      reinterpret_cast<float4*>(data)[i] = make_float4(h0, l0, h1, l1);
+      const float2 a = dw_split_bits(d.x), c = dw_split_bits(d.y);
+      reinterpret_cast<float4*>(data)[i] = make_float4(a.x, a.y, c.x, c.y);
     } else {
       const float4 f = reinterpret_cast<const float4*>(data)[i];
       reinterpret_cast<double2*>(data)[i] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);

@@ -44,7 +44,10 @@ void tc_geometry(const int* q, int n, TcGeom& g);
 // hi / lo TF32 parts of the real 64 x 64 form of U (out: kTcMatFloats floats).
 void tc_matrix_tables(const TcBlock& b, float* out);
 // One pass of one block over the state (psi: 2^n complex64, in place).
-cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, int sm_count, cudaStream_t s);
+// wait_test: withhold the MMAs so every MMA-completion wait runs out (test of
+// the bounded waits; the tiles are left unwritten).
+cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, int sm_count, cudaStream_t s,
+                            bool wait_test = false);
 // Number of bounded waits that ran out in the tensor-core kernel since the
 // library was loaded on the current device (0 in a healthy run; synchronises).
 cudaError_t tc_timeouts(int* count);

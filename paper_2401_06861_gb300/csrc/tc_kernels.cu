@@ -90,8 +90,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitPolls; i++)
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t polls) {
+  for (uint32_t i = 0; i < polls; i++)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -151,7 +151,8 @@ __device__ __forceinline__ void store_pair(float2* psi, uint64_t amp, uint64_t g
 // other tile qubits (a warp covers >= 256 contiguous bytes), lane bits 0..2
 // chosen so that each quarter-warp writes 8 distinct 16-byte bank groups.
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
-    tc_block_kernel(float2* __restrict__ psi, const float4* __restrict__ mats, const __grid_constant__ TcGeom g) {
+    tc_block_kernel(float2* __restrict__ psi, const float4* __restrict__ mats, const __grid_constant__ TcGeom g,
+                    uint32_t wait_polls, int issue_mma) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sb = (raw + 1023u) & ~1023u;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
   auto mma_group = [&](bool lo_pass) {
     fence_async_smem();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && issue_mma) {  // issue_mma = 0 only in the wait test: nothing arrives on the barrier
       tc_fence_after();
 #pragma unroll
       for (int p = 0; p < 2; p++) {
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     }
   };
   auto mma_wait = [&]() -> bool {
-    const bool ok = mbar_wait_bounded(bar, phase);
+    const bool ok = mbar_wait_bounded(bar, phase, wait_polls);
     if (__syncthreads_or(!ok)) return false;
     phase ^= 1u;
     tc_fence_after();
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 #undef TC_SI
   if (timed_out) {
     if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
-    mbar_wait_bounded(bar, phase);  // one more bounded wait for the MMAs in flight
+    mbar_wait_bounded(bar, phase, wait_polls);  // one more bounded wait for the MMAs in flight
   }
   tc_fence_before();
   __syncthreads();
@@ -310,7 +311,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 
 }  // namespace
 
-cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, int sm_count, cudaStream_t s) {
+cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, int sm_count, cudaStream_t s,
+                            bool wait_test) {
   static std::atomic<int> attr_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -327,7 +329,9 @@ cudaError_t launch_tc_block(void* psi, const TcGeom& g, const float* mats_dev, i
   // taken from the occupancy query, which under-reports this kernel.
   uint64_t grid = (uint64_t)sm_count * kTcCtasPerSm;
   if (grid > g.ntiles) grid = g.ntiles;
-  tc_block_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>((float2*)psi, (const float4*)mats_dev, g);
+  // the wait test withholds the MMAs and bounds each wait at 4096 polls
+  tc_block_kernel<<<(unsigned)grid, kTcThreads, kTcSmem, s>>>((float2*)psi, (const float4*)mats_dev, g,
+                                                                wait_test ? 4096u : kWaitPolls, wait_test ? 0 : 1);
   g_launches += 1;
   return cudaGetLastError();
 }

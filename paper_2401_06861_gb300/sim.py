@@ -321,12 +321,13 @@ class Plan:
 
     def kernel_arith(self, dw=False):
         """Per state element, summed over the sweeps with specialised kernels:
-        (multiply-adds, multiplies, sweeps) as generated (dw: the double-word
-        kernels of an FP64 plan)."""
-        f, m, sw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        (multiply-adds, multiplies, arithmetic-pipe instructions, sweeps) as
+        generated (dw: the double-word kernels of an FP64 plan, whose
+        instructions are FP32 ones)."""
+        f, m, i, sw = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         check(L.lib().nwq_plan_kernel_arith(self.h, 1 if dw else 0, ctypes.byref(f), ctypes.byref(m),
-                                            ctypes.byref(sw)))
-        return f.value, m.value, sw.value
+                                            ctypes.byref(i), ctypes.byref(sw)))
+        return f.value, m.value, i.value, sw.value
 
     def last_run_dw(self):
         """True when the latest run took the double-word path."""

@@ -24,8 +24,9 @@ def gpu():
     from paper_2401_06861_gb300 import build
     build.build()
     torch.cuda.init()
+    before = sim.tc_timeouts()
     yield
-    assert sim.tc_timeouts() == 0
+    assert sim.tc_timeouts() == before  # no bounded wait ran out in this module
 
 
 def maxerr(a, b):
