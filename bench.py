@@ -632,7 +632,8 @@ def run_sv_cases(args):
                  "fused64": (args.sv_n - 1, L.F64, 0, max(1, args.steps // 3)),
                  "plain32": (args.sv_n, L.F32, L.PLAN_PLAIN, 1),
                  "tc32": (args.sv_n, L.F32, L.PLAN_TC, max(1, args.steps // 3)),
-                 "commute32": (args.sv_n, L.F32, L.PLAN_COMMUTE, args.steps)}
+                 "commute32": (args.sv_n, L.F32, L.PLAN_COMMUTE, args.steps),
+                 "nocommute32": (args.sv_n, L.F32, L.PLAN_NO_COMMUTE, args.steps)}
     cases = [all_cases[c] for c in args.sv_cases.split(",")]
     for n, dtype, flags, steps in cases:
         if args.sv_circuit == "tfim":
@@ -674,7 +675,8 @@ def run_sv_cases(args):
             fpk = 152 * 2 * 2.07e9
             roof = {"bound": "alu", "achieved": fp64, "peak": fpk, "unit": "FP64 instructions/s", "frac": fp64 / fpk,
                     "fp_ops_per_amp": info["fma_per_elem"], "hbm_gbs": gb, "hbm_frac": gb / peak}
-        pname = ("tc" if flags & L.PLAN_TC else "fused_commute" if flags & L.PLAN_COMMUTE
+        pname = ("tc" if flags & L.PLAN_TC else "fused_no_commute" if flags & L.PLAN_NO_COMMUTE
+                 else "fused_commute" if flags & L.PLAN_COMMUTE
                  else "plain" if flags else "fused")
         line = {"workload": wname, "plan": pname,
                 "dtype": "c64" if dtype == L.F32 else "c128", "metric": "gate-updates/s",
@@ -1082,7 +1084,7 @@ def main():
                     help="large-SV circuit: TFIM Trotter chain, or random dense one/two-qubit gates")
     ap.add_argument("--sv-cases", default="fused32,fused64,plain32,tc32",
                     help="comma list of fused32, fused64, plain32, tc32 (tensor-core blocks), "
-                         "commute32 (fused, diagonal operators commuting)")
+                         "commute32 (fused, diagonal operators commuting: the default), nocommute32")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serial-seconds", type=float, default=5.0)
     ap.add_argument("--serve-slots", type=int, default=8)

@@ -109,9 +109,10 @@ enum nwq_plan_flags {
   NWQ_PLAN_TC = 16u,         /* dense five-qubit blocks on the tensor cores (see below) */
   NWQ_PLAN_COMMUTE = 32u,    /* state vectors: when grouping sweeps, a diagonal operator may move ahead of
                                 skipped diagonal operators (they commute): fewer passes for circuits
-                                of diagonal gates (opt-in) */
+                                of diagonal gates (the default; kept for callers that name it) */
   NWQ_PLAN_DW = 64u,         /* FP64 plans: double-word sweeps (the default; see below) */
-  NWQ_PLAN_FP64 = 128u       /* FP64 plans: FP64-pipe sweeps only, never double words */
+  NWQ_PLAN_FP64 = 128u,      /* FP64 plans: FP64-pipe sweeps only, never double words */
+  NWQ_PLAN_NO_COMMUTE = 256u /* state vectors: group sweeps in operator order only */
 };
 
 /* Double-word sweeps (the default for FP64 plans; NWQ_PLAN_FP64 or NWQ_DW=0 in

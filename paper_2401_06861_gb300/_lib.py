@@ -20,7 +20,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBUDGET, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, 
 F32, F64 = 1, 2
 SV, DM = 1, 2
 PLAN_FUSED, PLAN_PLAIN, PLAN_NO_MERGE, PLAN_NO_RESCALE, PLAN_INTERPRETED, PLAN_TC, PLAN_COMMUTE = 0, 1, 2, 4, 8, 16, 32
-PLAN_DW, PLAN_FP64 = 64, 128
+PLAN_DW, PLAN_FP64, PLAN_NO_COMMUTE = 64, 128, 256
 PROBE_FP64_FMA, PROBE_FP32_FMA = 0, 1
 EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2

@@ -68,7 +68,9 @@ static void plan_options(int kind, int dtype, uint32_t flags, PlanOptions& o) {
     if (v >= 4 && v <= kMaxTileBits && (2 * esz << v) <= (size_t)kMaxDynSmem) o.tile_bits = v;
   }
   o.plain = (flags & NWQ_PLAN_PLAIN) != 0;
-  o.commute = kind == NWQ_SV && (flags & NWQ_PLAN_COMMUTE) != 0 && !o.plain;
+  // state vectors: diagonal operators may pass skipped diagonal operators
+  // when grouping sweeps, unless NWQ_PLAN_NO_COMMUTE
+  o.commute = kind == NWQ_SV && !(flags & NWQ_PLAN_NO_COMMUTE) && !o.plain;
   o.merge = !(flags & (NWQ_PLAN_PLAIN | NWQ_PLAN_NO_MERGE));
 }
 
@@ -363,20 +365,24 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
   if (kind == NWQ_SV && nm) return fail(NWQ_EINVAL, "noise model needs a density matrix");
   for (size_t i = 0; i < ng; i++)
     if (gates[i].reserved || gates[i].reserved2) return fail(NWQ_EINVAL, "reserved gate field not 0");
-  // NWQ_PLAN=plain|fused|tc|commute picks the plan form when the call names
-  // none (no PLAIN / TC / COMMUTE flag, no tuning); tc applies where it is
-  // supported, commute to state vectors.
+  // NWQ_PLAN=plain|fused|tc|commute|nocommute picks the plan form when the
+  // call names none (no PLAIN / TC / COMMUTE / NO_COMMUTE flag, no tuning);
+  // tc applies where it is supported; commute (the default) and nocommute to
+  // state vectors.
   static const int env_plan = [] {
     const char* e = std::getenv("NWQ_PLAN");
     if (!e) return 0;
     if (!std::strcmp(e, "plain")) return 1;
     if (!std::strcmp(e, "tc")) return 2;
     if (!std::strcmp(e, "commute")) return 3;
+    if (!std::strcmp(e, "nocommute")) return 4;
     return 0;
   }();
-  if (env_plan && !tuning && !(flags & (NWQ_PLAN_PLAIN | NWQ_PLAN_TC | NWQ_PLAN_COMMUTE))) {
+  if (env_plan && !tuning &&
+      !(flags & (NWQ_PLAN_PLAIN | NWQ_PLAN_TC | NWQ_PLAN_COMMUTE | NWQ_PLAN_NO_COMMUTE))) {
     if (env_plan == 1) flags |= NWQ_PLAN_PLAIN;
     else if (env_plan == 3) flags |= NWQ_PLAN_COMMUTE;
+    else if (env_plan == 4) flags |= NWQ_PLAN_NO_COMMUTE;
     else if (kind == NWQ_SV && dtype == NWQ_F32 && n >= kTcMinQubits) flags |= NWQ_PLAN_TC;
   }
   auto pl = std::make_unique<nwq_plan>();

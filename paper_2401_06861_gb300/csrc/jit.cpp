@@ -85,13 +85,16 @@ bool jit_sync_all() {  // compile one-shot plans' kernels before running them to
   }();
   return on;
 }
-int jit_min_blocks() {  // __launch_bounds__ minimum resident blocks per SM
-  static const int b = [] {
+// __launch_bounds__ minimum resident blocks per SM: NWQ_JIT_MINB, else 3 for
+// double-word complex kernels (measured: n = 33 complex128 plan run 4.16 ->
+// 3.99 s) and 2 for the others (double-word DM 28.1 ms per step at 2, 30.2 at 3)
+int jit_min_blocks(bool dw_complex) {
+  static const int env = [] {
     const char* e = std::getenv("NWQ_JIT_MINB");
-    const int v = e ? std::atoi(e) : 2;
-    return v < 1 ? 1 : (v > 4 ? 4 : v);
+    const int v = e ? std::atoi(e) : 0;
+    return v < 0 ? 0 : (v > 4 ? 4 : v);
   }();
-  return b;
+  return env ? env : (dw_complex ? 3 : 2);
 }
 int jit_min_bits() {
   static const int b = [] {
@@ -743,7 +746,7 @@ struct Gen {
       << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
       << "  unsigned a = (unsigned)__cvta_generic_to_shared(s);\n"
       << "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(a), \"l\"(g) : \"memory\");\n}\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << jit_min_blocks()
+      << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << jit_min_blocks(dw && !real)
       << ") nwq_jit_sweep(C* __restrict__ state, "
       << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const CT* __restrict__ pcs, "
       << "const Coef K) {\n"
@@ -836,7 +839,8 @@ struct Gen {
 std::string struct_key(const Plan& p, const SweepDesc& sd, bool dw) {
   std::string key;
   auto put = [&](const void* d, size_t n) { key.append(reinterpret_cast<const char*>(d), n); };
-  const int32_t hdr[9] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h, sd.prb, jit_min_blocks(),
+  const int32_t hdr[9] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h, sd.prb,
+                          jit_min_blocks(dw && p.is_complex && p.dtype == NWQ_F64),
                           dw ? 1 : 0};
   put(hdr, sizeof(hdr));
   if (p.is_complex) {

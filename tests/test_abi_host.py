@@ -134,7 +134,8 @@ def test_specialised_sweep_kernels_compile(dtype):
     plans = [(20, inputs.large_sv_tfim(20, 3)[0], 0), (19, inputs.random_circuit(19, 400, 23), 0),
              (18, inputs.hea_ansatz(18, 3, inputs.hea_params(18, 3, 1)[0])[0], 0),
              (20, inputs.random_circuit(20, 60, 29), L.PLAN_NO_MERGE),
-             (20, inputs.large_sv_tfim(20, 4)[0], L.PLAN_COMMUTE)]
+             (20, inputs.large_sv_tfim(20, 4)[0], L.PLAN_COMMUTE),
+             (20, inputs.large_sv_tfim(20, 4)[0], L.PLAN_NO_COMMUTE)]
     total = 0
     for n, gates, flags in plans:
         p = sim.Plan(L.SV, n, gates, dtype, flags=flags)

@@ -59,8 +59,10 @@ def test_nwq_plan_environment_override():
     assert tc["c64"]["tc"] and not tc["c128"]["tc"] and tc["c128"]["sweeps"] == base["c128"]["sweeps"]
     assert tc["c64_plain_flag"]["sweeps"] == ng and not tc["c64_plain_flag"]["tc"]  # an explicit flag wins
     assert probe("fused") == base
-    commute = probe("commute")  # the random circuit has diagonal gates to commute
-    assert commute["c64"]["sweeps"] <= base["c64"]["sweeps"] and not commute["c64"]["tc"]
+    commute = probe("commute")  # the default for state vectors
+    assert commute["c64"]["sweeps"] == base["c64"]["sweeps"] and not commute["c64"]["tc"]
+    nocommute = probe("nocommute")  # the random circuit has diagonal gates to commute
+    assert nocommute["c64"]["sweeps"] >= base["c64"]["sweeps"] and not nocommute["c64"]["tc"]
 
 
 class _StubLib:

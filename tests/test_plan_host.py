@@ -93,7 +93,9 @@ def test_commuting_plans_need_fewer_sweeps_for_diagonal_bonds():
     # the depth-10 chain at n = 34: CX RZ CX bonds merge into diagonal
     # operators, which now share sweeps across Trotter steps
     gates, _ = inputs.large_sv_tfim(34, 10)
-    with sim.Plan(L.SV, 34, gates, L.F32) as a, sim.Plan(L.SV, 34, gates, L.F32, flags=L.PLAN_COMMUTE) as b:
+    with sim.Plan(L.SV, 34, gates, L.F32, flags=L.PLAN_NO_COMMUTE) as a, \
+            sim.Plan(L.SV, 34, gates, L.F32, flags=L.PLAN_COMMUTE) as b, sim.Plan(L.SV, 34, gates, L.F32) as c:
+        assert c.info()["sweeps"] == b.info()["sweeps"]  # commuting is the default
         ia, ib = a.info(), b.info()
     assert ib["ops"] == ia["ops"] and ib["fma_per_elem"] == ia["fma_per_elem"]
     assert ib["sweeps"] <= 0.6 * ia["sweeps"]
