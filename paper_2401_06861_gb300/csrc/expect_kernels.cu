@@ -217,10 +217,15 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
   float2* wht = reinterpret_cast<float2*>(red + kWarps * P.nk);  // [k][thread] transforms (8-byte aligned)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int i = tid; i < P.nk; i += kExpThreads) st[i] = terms[P.k0 + i];
+  bool zterm = false;  // does this pass have a Z-type string (diagonal: needs the probabilities)?
+  for (int i = tid; i < P.nk; i += kExpThreads) {
+    st[i] = terms[P.k0 + i];
+    zterm |= st[i].xl == 0;
+  }
   for (uint32_t j = tid; j < (1u << P.h); j += kExpThreads) hoff[j] = deposit(j, P.hmask);
   for (int i = tid; i < kWarps * P.nk; i += kExpThreads) red[i] = 0.0;
   const uint32_t lowmask = (1u << P.m) - 1u;
+  zterm = __syncthreads_or(zterm);
 
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = deposit(t, P.fmask);
@@ -233,30 +238,40 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
     }
     cp_async_commit();
     cp_async_wait<0>();
-    Dw p[E];
-#pragma unroll
-    for (int j = 0; j < E; j++) {
-      const uint32_t l = tid + kExpThreads * j;
-      const double2 a = tile[l];
-      const Dw x = dw_split(a.x), y = dw_split(a.y);
-      tw[l] = make_float4(x.h, x.l, y.h, y.l);
-      p[j] = dw_fma(y, y, dw_mul(x, x));
-    }
-    // Z-type strings: element l = tid + 128 j has sign (-1)^{|tid & zl| + |j & (zl >> 7)|}, so a
-    // thread's signed sum over its 32 probabilities is +- entry (zl >> 7) of their Walsh-Hadamard
-    // transform W[k] = sum_j (-1)^{|j & k|} p_j: one transform serves every Z-type string
-#pragma unroll
-    for (int b = 1; b < E; b <<= 1) {
+    if (zterm) {
+      Dw p[E];
 #pragma unroll
       for (int j = 0; j < E; j++) {
-        if (j & b) continue;
-        const Dw a0 = p[j], a1 = p[j | b];
-        p[j] = dw_add(a0, a1);
-        p[j | b] = dw_add(a0, Dw{-a1.h, -a1.l});
+        const uint32_t l = tid + kExpThreads * j;
+        const double2 a = tile[l];
+        const Dw x = dw_split(a.x), y = dw_split(a.y);
+        tw[l] = make_float4(x.h, x.l, y.h, y.l);
+        p[j] = dw_fma(y, y, dw_mul(x, x));
+      }
+      // Z-type strings: element l = tid + 128 j has sign (-1)^{|tid & zl| + |j & (zl >> 7)|}, so a
+      // thread's signed sum over its 32 probabilities is +- entry (zl >> 7) of their Walsh-Hadamard
+      // transform W[k] = sum_j (-1)^{|j & k|} p_j: one transform serves every Z-type string
+#pragma unroll
+      for (int b = 1; b < E; b <<= 1) {
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+          if (j & b) continue;
+          const Dw a0 = p[j], a1 = p[j | b];
+          p[j] = dw_add(a0, a1);
+          p[j | b] = dw_add(a0, Dw{-a1.h, -a1.l});
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < E; j++) wht[j * kExpThreads + tid] = make_float2(p[j].h, p[j].l);
+    } else {  // only X-type strings in this pass: the split amplitudes alone
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        const uint32_t l = tid + kExpThreads * j;
+        const double2 a = tile[l];
+        const Dw x = dw_split(a.x), y = dw_split(a.y);
+        tw[l] = make_float4(x.h, x.l, y.h, y.l);
       }
     }
-#pragma unroll
-    for (int j = 0; j < E; j++) wht[j * kExpThreads + tid] = make_float2(p[j].h, p[j].l);
     __syncthreads();
 
     for (int k = 0; k < P.nk; k++) {
