@@ -104,6 +104,23 @@ int jit_min_bits() {
   return b;
 }
 
+// Register bits of real (density-matrix) phases, 4..6 (NWQ_JIT_REAL_RB for
+// FP32 plans, NWQ_JIT_REAL_RB_DW for double-word ones).  FP32 plans take 6:
+// two noisy two-qubit operators sharing a qubit fit one phase, which halves
+// the shared-memory passes of these shared-memory-bound kernels (n = 13 noisy
+// TFIM: 9.18 -> 7.06 ms per step); their kernels run 128 threads per CTA (one
+// register group of 64 coefficients per thread).  Double-word plans, bound by
+// their arithmetic, keep 4.
+int real_register_bits(bool fp32) {
+  auto env = [](const char* name, int dflt) {
+    const char* e = std::getenv(name);
+    const int v = e ? std::atoi(e) : dflt;
+    return v < 4 ? 4 : (v > 6 ? 6 : v);
+  };
+  static const int f32 = env("NWQ_JIT_REAL_RB", 6), f64 = env("NWQ_JIT_REAL_RB_DW", 4);
+  return fp32 ? f32 : f64;
+}
+
 // ------------------------------------------------------------------ compiled kernels
 // One packed parameter range: cnt > 0: coefficients [pc0 + rel, + cnt) of the
 // complex table; cnt == 0: the coefficient of entry ent0 + rel of a real plan.
@@ -124,6 +141,7 @@ struct JitKernel {
   std::string src;
   std::vector<RecipeItem> recipe;
   size_t smem = 0;
+  int threads = kJitThreads;
   bool usable = false;  // the generator accepted the structure
 };
 
@@ -393,6 +411,8 @@ struct Gen {
         dw(dw_ && p_.dtype == NWQ_F64) {}
   int es;   // bytes per state element (= per coefficient)
   bool dw;  // FP64 values as double words (two floats), FP32-pipe arithmetic
+  int rrb = 4;          // register bits of real phases
+  int th = kJitThreads;  // threads per CTA
 
   uint32_t pack_real(size_t entry, double v) {  // one real coefficient (entry index of the plan)
     uint32_t at = (uint32_t)(param.size() / cs);
@@ -415,16 +435,17 @@ struct Gen {
   // remaining entry, in the row kernel's order; identity rows cost nothing.
   void op_real(const DevOp& d, const uint8_t* u) {
     auto regbit = [&](int pos) {
-      for (int q = 0; q < 4; q++)
+      for (int q = 0; q < rrb; q++)
         if (u[q] == pos) return q;
       return -1;
     };
     auto reg = [&](uint32_t off) {  // register index of a tile-local offset over the operator bits
       uint32_t x = 0;
-      for (int q = 0; q < 4; q++)
+      for (int q = 0; q < rrb; q++)
         if ((off >> u[q]) & 1u) x |= 1u << q;
       return x;
     };
+    const int NRR = 1 << rrb;
     if (d.k < 1 || d.k > 4) {
       ok = false;
       return;
@@ -440,10 +461,10 @@ struct Gen {
     }
     const int D = 1 << d.k;
     const size_t esz = p.ent_bytes;
-    for (int ob = 0; ob < 16; ob++) {
+    for (int ob = 0; ob < NRR; ob++) {
       if (ob & rmask) continue;
       o << "    {";
-      for (int s = 0; s < 16; s++)
+      for (int s = 0; s < NRR; s++)
         if ((s & ~(int)rmask) == 0) o << " const R t" << (ob | s) << " = " << r(ob | s) << ";";
       o << "\n";
       for (int i = 0; i < D; i++) {
@@ -479,14 +500,14 @@ struct Gen {
   }
 
   // Register phases of a real sweep: consecutive operators while their bits
-  // fit 4 register bits (padded with the lowest unused tile bits).
-  bool real_phases(std::vector<std::pair<std::array<uint8_t, 4>, std::vector<int>>>& out) {
+  // fit rrb register bits (padded with the lowest unused tile bits).
+  bool real_phases(std::vector<std::pair<std::array<uint8_t, 6>, std::vector<int>>>& out) {
     uint32_t U = 0;
     std::vector<int> cur;
     auto flush = [&]() {
       if (cur.empty()) return;
-      for (int b = 0; b < sd.T && __builtin_popcount(U) < 4; b++) U |= 1u << b;
-      std::array<uint8_t, 4> u{};
+      for (int b = 0; b < sd.T && __builtin_popcount(U) < rrb; b++) U |= 1u << b;
+      std::array<uint8_t, 6> u{};
       int q = 0;
       for (int b = 0; b < sd.T; b++)
         if ((U >> b) & 1u) u[q++] = (uint8_t)b;
@@ -499,7 +520,7 @@ struct Gen {
       if (d.k < 1 || d.k > 4) return false;
       uint32_t bits = 0;
       for (int t = 0; t < d.k; t++) bits |= 1u << d.lb[t];
-      if (__builtin_popcount(U | bits) > 4) flush();
+      if (__builtin_popcount(U | bits) > rrb) flush();
       U |= bits;
       cur.push_back(o2);
     }
@@ -638,45 +659,50 @@ struct Gen {
   }
 
   bool run(std::string& src) {
-    const int T = sd.T, m = sd.m, h = sd.h, RB = real ? 4 : sd.prb, NR = 1 << RB;
+    rrb = real ? real_register_bits(es == 4) : 4;
+    const int T = sd.T, m = sd.m, h = sd.h, RB = real ? rrb : sd.prb, NR = 1 << RB;
     const int lvpe = es == 16 ? 0 : (es == 8 ? 1 : 2);
-    if (RB < 1 || RB > 4 || T < RB || T > 13 || m < lvpe || m + h != T || p.B - T > 24) return false;
+    if (RB < 1 || RB > (real ? 6 : 4) || T < RB || T > 13 || m < lvpe || m + h != T || p.B - T > 24) return false;
     if (real && p.ent_bytes != (p.dtype == NWQ_F64 ? 16u : 8u)) return false;
     const size_t PE = padded_elems(T);
     const uint32_t NG = 1u << (T - RB);
-    std::vector<std::pair<std::array<uint8_t, 4>, std::vector<int>>> rph;
+    // wider real phases: one register group per thread in CTAs of 128
+    th = (real && rrb > 4 && NG < (uint32_t)kJitThreads) ? 128 : kJitThreads;
+    std::vector<std::pair<std::array<uint8_t, 6>, std::vector<int>>> rph;
     if (real && !real_phases(rph)) return false;
     const uint32_t nphase = real ? (uint32_t)rph.size() : sd.nph;
     std::ostringstream body;
     o.swap(body);
     for (uint32_t ph = 0; ph < nphase && ok; ph++) {
       PhaseDesc P{};
+      uint8_t ub[6] = {0, 0, 0, 0, 0, 0};  // tile bit of register bit b
       if (real) {
-        for (int q = 0; q < 4; q++) P.u[q] = rph[ph].first[q];
+        for (int q = 0; q < RB; q++) ub[q] = rph[ph].first[q];
       } else {
         P = p.phases[sd.ph0 + ph];
+        for (int q = 0; q < 4; q++) ub[q] = P.u[q];
       }
       o << "    // phase " << ph << "\n";
-      o << "    for (unsigned g = threadIdx.x; g < " << NG << "u; g += " << kJitThreads << "u) {\n";
+      o << "    for (unsigned g = threadIdx.x; g < " << NG << "u; g += " << th << "u) {\n";
       o << "    unsigned gb = g;\n";
       for (int t = 0; t < RB; t++) {
-        const uint32_t lowm = (1u << P.u[t]) - 1u;
+        const uint32_t lowm = (1u << ub[t]) - 1u;
         o << "    gb = ((gb & " << (~lowm) << "u) << 1) | (gb & " << lowm << "u);\n";
       }
       o << "    C* gt = tile + " << swz_expr(es, "gb") << ";\n";
-      uint32_t roff[16];
+      uint32_t roff[64];
       for (int i = 0; i < NR; i++) {
         uint32_t l = 0;
         for (int b = 0; b < RB; b++)
-          if ((i >> b) & 1) l |= 1u << P.u[b];
+          if ((i >> b) & 1) l |= 1u << ub[b];
         roff[i] = swz(es, l);
       }
       // Registers on the tile's lowest bits are consecutive elements: VW of
       // them (16 bytes at most) move as one vector access, 16-byte aligned
       // (gb and the offsets have those bits clear; the row padding keeps
       // runs of VW inside one 128-byte row).
-      const int VW = (16 / es >= 4 && RB >= 2 && P.u[0] == 0 && P.u[1] == 1) ? 4
-                     : (16 / es >= 2 && RB >= 1 && P.u[0] == 0) ? 2 : 1;
+      const int VW = (16 / es >= 4 && RB >= 2 && ub[0] == 0 && ub[1] == 1) ? 4
+                     : (16 / es >= 2 && RB >= 1 && ub[0] == 0) ? 2 : 1;
       for (int i = 0; i < NR; i += VW) {
         if (VW == 1) {
           o << "    C " << r(i) << " = gt[" << roff[i] << "];\n";
@@ -690,7 +716,7 @@ struct Gen {
       }
       const std::string before = o.str();
       if (real) {
-        for (int oi : rph[ph].second) op_real(p.ops[sd.op0 + oi], P.u);
+        for (int oi : rph[ph].second) op_real(p.ops[sd.op0 + oi], ub);
       } else {
         for (uint32_t q = 0; q < P.nops && ok; q++) op(NR, p.pops[P.op0 + q]);
       }
@@ -746,7 +772,7 @@ struct Gen {
       << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
       << "  unsigned a = (unsigned)__cvta_generic_to_shared(s);\n"
       << "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(a), \"l\"(g) : \"memory\");\n}\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << kJitThreads << ", " << jit_min_blocks(dw && !real)
+      << "extern \"C\" __global__ void __launch_bounds__(" << th << ", " << jit_min_blocks(dw && !real)
       << ") nwq_jit_sweep(C* __restrict__ state, "
       << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const CT* __restrict__ pcs, "
       << "const Coef K) {\n"
@@ -754,18 +780,18 @@ struct Gen {
       << "  C* tile = (C*)sm;\n  C* ntile = tile + " << PE << ";\n  C* dtab = tile + " << 2 * PE << ";\n"
       << "  unsigned long long* hoff = (unsigned long long*)(sm + " << hoff_byte << ");\n"
       << "  unsigned long long* btab = (unsigned long long*)(sm + " << btab_byte << ");\n"
-      << "  for (unsigned j = threadIdx.x; j < " << (1u << h) << "u; j += " << kJitThreads << "u) hoff[j] = dep(j, hmask);\n"
+      << "  for (unsigned j = threadIdx.x; j < " << (1u << h) << "u; j += " << th << "u) hoff[j] = dep(j, hmask);\n"
       << "  // tile base = OR of 4 pieces, each depositing " << pb << " bits of the tile index on fmask\n"
-      << "  for (unsigned j = threadIdx.x; j < " << 4 * nb << "u; j += " << kJitThreads
+      << "  for (unsigned j = threadIdx.x; j < " << 4 * nb << "u; j += " << th
       << "u) btab[j] = dep((unsigned long long)(j & " << nb - 1 << "u) << (" << pb << "u * (j >> " << pb
       << ")), fmask);\n";
     for (const Tab& t : tabs)
-      o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << kJitThreads << "u) dtab[" << t.dst
+      o << "  for (unsigned j = threadIdx.x; j < " << t.cnt << "u; j += " << th << "u) dtab[" << t.dst
         << " + j] = from_table(pcs[" << t.src << " + j]);\n";
     const int VPE = 16 / es, lvpc = m - lvpe;
     const uint32_t nvec = (1u << T) / VPE;
-    const uint32_t NVT = (nvec + kJitThreads - 1) / kJitThreads;  // vectors per thread
-    const bool ragged = nvec % kJitThreads != 0;
+    const uint32_t NVT = (nvec + th - 1) / th;  // vectors per thread
+    const bool ragged = nvec % th != 0;
     // per-thread vector offsets inside a tile (global) and shared-memory slots
     // (swz is additive over the disjoint bits of threadIdx.x * VPE and 256 * i * VPE).
     // The global offsets are read from the shared table where used, once per
@@ -774,13 +800,13 @@ struct Gen {
     o << "  __syncthreads();\n"
       << "  const unsigned s0 = " << swz_expr(es, "(threadIdx.x * " + std::to_string(VPE) + "u)") << ";\n";
     for (uint32_t i = 0; i < NVT; i++) {
-      const std::string v = "(threadIdx.x + " + std::to_string(i * kJitThreads) + "u)";
+      const std::string v = "(threadIdx.x + " + std::to_string(i * th) + "u)";
       o << "#define o" << i << " (hoff[" << v << " >> " << lvpc << "] + (unsigned long long)(" << v << " & "
         << ((1u << lvpc) - 1u) << "u) * " << VPE << ")\n";
     }
-    auto sidx = [&](uint32_t i) { return std::to_string(swz(es, i * kJitThreads * VPE)); };
+    auto sidx = [&](uint32_t i) { return std::to_string(swz(es, i * th * VPE)); };
     auto guard = [&](uint32_t i) -> std::string {
-      return (ragged && i == NVT - 1) ? "if (threadIdx.x + " + std::to_string(i * kJitThreads) + "u < " +
+      return (ragged && i == NVT - 1) ? "if (threadIdx.x + " + std::to_string(i * th) + "u < " +
                                             std::to_string(nvec) + "u) "
                                       : "";
     };
@@ -839,7 +865,8 @@ struct Gen {
 std::string struct_key(const Plan& p, const SweepDesc& sd, bool dw) {
   std::string key;
   auto put = [&](const void* d, size_t n) { key.append(reinterpret_cast<const char*>(d), n); };
-  const int32_t hdr[9] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h, sd.prb,
+  const int32_t hdr[9] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h,
+                          p.is_complex ? sd.prb : real_register_bits(p.dtype == NWQ_F32 && !dw),
                           jit_min_blocks(dw && p.is_complex && p.dtype == NWQ_F64),
                           dw ? 1 : 0};
   put(hdr, sizeof(hdr));
@@ -889,6 +916,7 @@ bool describe(JitKernel& jk, const Plan& p, const SweepDesc& sd, bool dw) {
       jk.src = std::move(src);
       jk.recipe = std::move(g.recipe);
       jk.smem = g.smem;
+      jk.threads = g.th;
     }
     jk.described = true;
   }
@@ -1071,7 +1099,7 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
   }
   if (js.per_sm == 0) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kJitThreads, js.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, js.k->threads, js.smem);
     if (e != cudaSuccess) {
       *err = e;
       return true;
@@ -1092,7 +1120,7 @@ bool jit_launch_sweep(Plan& p, size_t sweep, const PhaseTables& pt, void* state,
   const void* pcs = p.is_complex && pt.pc ? (const char*)pt.pc + (size_t)sd.pc0 * (p.dtype == NWQ_F64 ? 16 : 8)
                                           : nullptr;
   void* args[] = {&state, &ntiles, &hmask, &fmask, (void*)&pcs, js.param.data()};
-  e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kJitThreads), args, js.smem, s);
+  e = cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(js.k->threads), args, js.smem, s);
   g_launches += 1;
   *err = e;
   return true;
