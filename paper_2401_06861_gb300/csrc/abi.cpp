@@ -63,6 +63,7 @@ static void plan_options(int kind, int dtype, uint32_t flags, PlanOptions& o) {
   // run faster with 4 resident CTAs per SM than with 2), >= 128 contiguous bytes
   o.tile_bits = esz == 16 ? 10 : esz == 8 ? 12 : 13;
   o.min_low = esz == 16 ? 3 : esz == 8 ? 4 : 5;
+  if (const char* mo = std::getenv("NWQ_SWEEP_MAX_OPS")) o.max_sweep_ops = std::atoi(mo) > 0 ? std::atoi(mo) : 0;
   if (const char* tb = std::getenv("NWQ_TILE_BITS")) {
     int v = std::atoi(tb);
     if (v >= 4 && v <= kMaxTileBits && (2 * esz << v) <= (size_t)kMaxDynSmem) o.tile_bits = v;

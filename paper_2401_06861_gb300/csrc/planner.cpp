@@ -948,6 +948,7 @@ void build_plan(std::vector<BitOp>& ops, const PlanOptions& opt, Plan& plan) {
         done[i] = 1;
         order.push_back((int)i);
         if (opt.plain) break;
+        if (opt.max_sweep_ops && (int)order.size() - first >= opt.max_sweep_ops) break;
       } else {
         (diag[i] ? blocked_nd : blocked) |= m;
       }

@@ -35,6 +35,7 @@ struct PlanOptions {
   int lookahead = 4096;   // operators scanned when filling a sweep
   int rescale_qubits = 0; // DM: deferred per-qubit scaling over this many qubits (0 = off)
   int register_bits = 0;  // complex sweeps: register-group bits per thread (0: 3 for FP64, 4 for FP32)
+  int max_sweep_ops = 0;  // operators per sweep at most (0: no limit)
 };
 
 struct Plan {
