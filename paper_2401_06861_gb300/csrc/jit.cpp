@@ -87,14 +87,15 @@ bool jit_sync_all() {  // compile one-shot plans' kernels before running them to
 }
 // __launch_bounds__ minimum resident blocks per SM: NWQ_JIT_MINB, else 3 for
 // double-word complex kernels (measured: n = 33 complex128 plan run 4.16 ->
-// 3.99 s) and 2 for the others (double-word DM 28.1 ms per step at 2, 30.2 at 3)
-int jit_min_blocks(bool dw_complex) {
+// 3.99 s) and FP32 density-matrix kernels (n = 13: 7.05 -> 6.92 ms per step),
+// 2 for the others (double-word DM 28.1 ms per step at 2, 30.2 at 3)
+int jit_min_blocks(bool dw_complex, bool fp32_real) {
   static const int env = [] {
     const char* e = std::getenv("NWQ_JIT_MINB");
     const int v = e ? std::atoi(e) : 0;
     return v < 0 ? 0 : (v > 4 ? 4 : v);
   }();
-  return env ? env : (dw_complex ? 3 : 2);
+  return env ? env : ((dw_complex || fp32_real) ? 3 : 2);
 }
 int jit_min_bits() {
   static const int b = [] {
@@ -772,7 +773,7 @@ struct Gen {
       << "__device__ __forceinline__ void cpa16(void* s, const void* g) {\n"
       << "  unsigned a = (unsigned)__cvta_generic_to_shared(s);\n"
       << "  asm volatile(\"cp.async.cg.shared.global [%0], [%1], 16;\\n\" :: \"r\"(a), \"l\"(g) : \"memory\");\n}\n"
-      << "extern \"C\" __global__ void __launch_bounds__(" << th << ", " << jit_min_blocks(dw && !real)
+      << "extern \"C\" __global__ void __launch_bounds__(" << th << ", " << jit_min_blocks(dw && !real, real && es == 4)
       << ") nwq_jit_sweep(C* __restrict__ state, "
       << "unsigned long long ntiles, unsigned long long hmask, unsigned long long fmask, const CT* __restrict__ pcs, "
       << "const Coef K) {\n"
@@ -867,7 +868,8 @@ std::string struct_key(const Plan& p, const SweepDesc& sd, bool dw) {
   auto put = [&](const void* d, size_t n) { key.append(reinterpret_cast<const char*>(d), n); };
   const int32_t hdr[9] = {p.is_complex ? 1 : 0, p.dtype, p.B - sd.T, sd.T, sd.m, sd.h,
                           p.is_complex ? sd.prb : real_register_bits(p.dtype == NWQ_F32 && !dw),
-                          jit_min_blocks(dw && p.is_complex && p.dtype == NWQ_F64),
+                          jit_min_blocks(dw && p.is_complex && p.dtype == NWQ_F64,
+                                         !p.is_complex && p.dtype == NWQ_F32),
                           dw ? 1 : 0};
   put(hdr, sizeof(hdr));
   if (p.is_complex) {
