@@ -438,13 +438,13 @@ extern "C" int nwq_plan_create_tuned(int kind, int n, int dtype, const nwq_gate*
   // double-word complex128 sweeps are FP32-issue bound: tiles of 2^11 give
   // every thread of a 256-thread CTA a register group of 8 amplitudes in each
   // phase (2^10 tiles, sized for the FP64 pipe, leave half of them idle)
-  if (pl->p.dw && kind == NWQ_SV && !(tuning && tuning->tile_bits) && !std::getenv("NWQ_TILE_BITS"))
-    o.tile_bits = 11;
+  const bool dw_sv = pl->p.dw && kind == NWQ_SV && n >= jit_min_state_bits();  // run by specialised kernels
+  if (dw_sv && !(tuning && tuning->tile_bits) && !std::getenv("NWQ_TILE_BITS")) o.tile_bits = 11;
   // and at most 16 operators per sweep: their generated code then stays in the
   // instruction cache (n = 33 depth-10 chain: 30 sweeps instead of 27, plan run
   // 3.68 -> 3.59 s); NWQ_SWEEP_MAX_OPS sets the cap of every plan (0: none)
   if (const char* mo = std::getenv("NWQ_SWEEP_MAX_OPS")) o.max_sweep_ops = std::max(0, std::atoi(mo));
-  else if (pl->p.dw && kind == NWQ_SV) o.max_sweep_ops = 16;
+  else if (dw_sv) o.max_sweep_ops = 16;
   build_plan(ops, o, pl->p);
   pl->p.interpreted = (flags & NWQ_PLAN_INTERPRETED) != 0;
   static const bool checks = [] {

@@ -993,6 +993,8 @@ int jit_build_check(const Plan& p, int* eligible, int* built, std::string* log) 
   return 0;
 }
 
+int jit_min_state_bits() { return jit_enabled() ? jit_min_bits() : 64; }
+
 int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem, double* instr_per_elem) {
   *fma_per_elem = *mul_per_elem = 0.0;
   int eligible = 0;

@@ -43,6 +43,9 @@ int jit_prefetch(const Plan& p);
 // double-word kernels), and the arithmetic-pipe instructions they make.
 int jit_plan_arith(const Plan& p, bool dw, double* fma_per_elem, double* mul_per_elem, double* instr_per_elem);
 
+// States of at least this many index bits run specialised kernels (64: never).
+int jit_min_state_bits();
+
 // Stop the background compiler (queued kernels stay uncompiled; the one in
 // progress finishes) and join its thread.  Idempotent.
 void jit_shutdown();
