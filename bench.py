@@ -659,7 +659,6 @@ def run_sv_cases(args):
         e = st.expect(inputs.tfim_terms(n, 1.0, h), sum=True, normalize=True)
         nrm = st.norm()
         st.close()
-        plan.close()
         gb = info["bytes"] / sec / 1e9
         if flags & L.PLAN_TC:  # dense blocks on the tensor cores: HBM bound, TF32 pipe reported beside it
             tf = 2.0 * info["fma_per_elem"] * 2.0 ** n / sec / 1e12
@@ -669,11 +668,15 @@ def run_sv_cases(args):
         elif dtype == L.F32:  # complex64: HBM bound
             roof = {"bound": "hbm", "achieved": gb, "peak": peak, "unit": "GB/s", "frac": gb / peak,
                     "fp_ops_per_amp": info["fma_per_elem"]}
-        else:  # complex128: FP64 pipe bound (2 FP64 instructions / clock / SM); the plan counts them per amplitude
-            fp64 = info["fma_per_elem"] * 2.0 ** n / sec
-            fpk = 152 * 2 * 2.07e9
-            roof = {"bound": "alu", "achieved": fp64, "peak": fpk, "unit": "FP64 instructions/s", "frac": fp64 / fpk,
-                    "fp_ops_per_amp": info["fma_per_elem"], "hbm_gbs": gb, "hbm_frac": gb / peak}
+        else:  # complex128: arithmetic-pipe bound (double words: FP32 pipe; else FP64), instructions as generated
+            dw_ran = plan.last_run_dw()
+            _, _, instr, _ = plan.kernel_arith(dw=dw_ran)
+            pipe = "FP32" if dw_ran else "FP64"
+            rate = probe_rate(L.PROBE_FP32_FMA if dw_ran else L.PROBE_FP64_FMA)
+            ach = instr * 2.0 ** n / sec
+            roof = {"bound": "alu", "achieved": ach, "peak": rate, "unit": f"{pipe} instructions/s",
+                    "frac": ach / rate, "instr_per_amp": instr, "hbm_gbs": gb, "hbm_frac": gb / peak}
+        plan.close()
         pname = ("tc" if flags & L.PLAN_TC else "fused_no_commute" if flags & L.PLAN_NO_COMMUTE
                  else "fused_commute" if flags & L.PLAN_COMMUTE
                  else "plain" if flags else "fused")
