@@ -1,39 +1,65 @@
-"""One state vector sharded over G = 2^g GPUs by its top qubits.
+"""One state sharded over several GPUs by its top qubits.
 
-The paper runs SV-Sim on multi-node, multi-GPU systems for states that do not
-fit one device (Sec. II; Sec. V).  Here the 2^n amplitudes are split by the
-top g bits of the *physical* index: slice r (rank r) holds the 2^L amplitudes
-(L = n - g) whose top g physical bits equal r.  A qubit map assigns each
-logical qubit a physical bit; qubits on bits below L are local, the g
-others are global (they select the slice).
+The paper runs SV-Sim and DM-Sim on multi-node, multi-GPU systems for states
+that do not fit one device (Sec. II; Sec. V).  Here g qubits are *global*:
+they select the slice (the rank) and the other L = n - g are *local*.  A qubit
+map assigns each logical qubit a physical position; positions below L are
+local, position L + j is global qubit j.
+
+A state's flat index is made of one or two *planes* of n bits, each holding
+one bit per qubit at the qubit's physical position:
+
+* state vector (one plane): amplitude index b.  Slice r holds the 2^L
+  amplitudes whose top g physical bits equal r (world 2^g).
+* density matrix (two planes): the library's Pauli-basis coefficients
+  r[x + 2^n z] = Tr(rho P(x, z)) (x plane low, z plane high), or a row-major
+  rho[r, c] (flat c + 2^n r: column plane low, row plane high).  Slice
+  s = x_glob + 2^g z_glob (resp. c_glob + 2^g r_glob) holds the 4^L entries
+  with those global bits, itself laid out as an L-qubit state of the same
+  basis (world 4^g).
 
 * A gate whose qubits are all local runs on every slice as a gate of an
-  L-qubit state vector (the library's sweep kernels, unchanged).
-* A gate on a global qubit first swaps that qubit with a local one: with
-  global bit L + j and local bit l, rank r keeps the half of its slice whose
-  bit l equals bit j of r and exchanges the other half with rank r ^ 2^j
-  (one send and one receive of 2^(L-1) amplitudes; with l = L - 1 the half
-  is contiguous).  The received half is staged in local memory and copied
-  into place; the two qubits' physical bits trade places in the map.
-* <P> of a Pauli string whose X support is local is a sum over the slices of
-  local sums, the global Z bits contributing the sign (-1)^{|r & z_glob|};
-  strings with global X support first swap those qubits in (X support on at
-  most L qubits; wider strings are refused).  One all-reduce of the per-term
-  sums ends the evaluation.
+  L-qubit state (the library's sweep kernels, unchanged).  For a density
+  matrix this holds on every slice, not only on the Hermitian diagonal ones:
+  a channel on local qubits acts on the flat state as (its local action) x I,
+  one linear map per slice.
+* A gate on a global qubit first swaps that qubit with a local one, one plane
+  at a time: with global bit L + j and local bit l of a plane, rank r keeps
+  the half of its slice whose local bit equals its rank bit and exchanges the
+  other half with the rank that differs in that rank bit (one send and one
+  receive of half a slice; contiguous when l is the plane's top local bit).
+  The received half is staged in local memory and copied into place; the two
+  qubits' physical positions trade places in the map.
+* <P> of a Pauli string:
+  - state vector: a sum over the slices of local sums, the global Z bits
+    giving the sign (-1)^{|r & z_glob|}; strings with global X support first
+    swap those qubits in (X support on at most L qubits; wider strings are
+    refused).
+  - density matrix, Pauli basis: the coefficient of P itself, held by the one
+    slice whose global bits are P's (no exchange at all).
+  - density matrix, row-major rho: Tr(rho P) = sum_r rho[r, r ^ x] phase(r);
+    slice (c_glob, r_glob) contributes iff c_glob = r_glob ^ x_glob, its
+    local trace times i^{|x_glob & z_glob|} (-1)^{|r_glob & z_glob|}.
+  One all-reduce of the per-term sums ends the evaluation.
 
-Slice storage and local arithmetic come from a backend (``GpuSlices``: the
-library on the rank's GPU; the tests use the CPU oracle on each slice), and
-the exchange from a transport: ``DistTransport`` (torch.distributed point to
-point, NCCL between GPUs or gloo on CPU, one slice per process) or
-``LocalTransport`` (all slices in one process, halves swapped by copies).
+Slice storage and local arithmetic come from a backend (``GpuSlices`` /
+``GpuDMSlices``: the library on the rank's GPU; the tests use the CPU oracle
+on each slice), and the exchange from a transport: ``DistTransport``
+(torch.distributed point to point, NCCL between GPUs or gloo on CPU, one
+slice per process) or ``LocalTransport`` (all slices in one process, halves
+swapped by copies).
 """
 from __future__ import annotations
 
 import numpy as np
 
 
+def _popcount(v):
+    return bin(v).count("1")
+
+
 class QubitMap:
-    """Logical qubit -> physical bit (a permutation of 0..n-1)."""
+    """Logical qubit -> physical position (a permutation of 0..n-1)."""
 
     def __init__(self, n):
         self.n = n
@@ -55,22 +81,22 @@ class QubitMap:
         return out
 
 
-def half_view(t, L, l, c):
-    """The 2^(L-1) elements of a 2^L slice whose bit l is c, as a view."""
-    return t.view(1 << (L - 1 - l), 2, 1 << l)[:, c, :]
+def half_view(t, bits, l, c):
+    """The 2^(bits-1) elements of a 2^bits slice whose bit l is c, as a view."""
+    return t.view(1 << (bits - 1 - l), 2, 1 << l)[:, c, :]
 
 
 class LocalTransport:
     """All slices in this process: a pairwise exchange swaps two halves."""
 
     def exchange(self, sv, j, l):
-        L = sv.L
+        """Swap rank bit j with local bit l of every slice."""
         for r in sv.ranks:
             p = r ^ (1 << j)
             if p < r:
                 continue
-            a = half_view(sv.tensor(r), L, l, 1 - ((r >> j) & 1))
-            b = half_view(sv.tensor(p), L, l, 1 - ((p >> j) & 1))
+            a = half_view(sv.tensor(r), sv.local_bits, l, 1 - ((r >> j) & 1))
+            b = half_view(sv.tensor(p), sv.local_bits, l, 1 - ((p >> j) & 1))
             stage = a.clone()  # staged, then both halves written
             a.copy_(b)
             b.copy_(stage)
@@ -89,13 +115,14 @@ class DistTransport:
     def __init__(self, chunk=1 << 26):
         import torch.distributed as dist
         self.dist = dist
-        self.chunk = chunk  # amplitudes per message (bounds the staging buffer)
+        self.chunk = chunk  # elements per message (bounds the staging buffer)
 
     def exchange(self, sv, j, l):
+        """Swap rank bit j with local bit l of this rank's slice."""
         (r,) = sv.ranks
         p = r ^ (1 << j)
-        mine = half_view(sv.tensor(r), sv.L, l, 1 - ((r >> j) & 1))
-        if mine.is_contiguous():  # l = L - 1: one contiguous half, in chunks
+        mine = half_view(sv.tensor(r), sv.local_bits, l, 1 - ((r >> j) & 1))
+        if mine.is_contiguous():  # l is the top local bit: one contiguous half, in chunks
             flat = mine.reshape(-1)
             for a in range(0, flat.numel(), self.chunk):
                 b = min(flat.numel(), a + self.chunk)
@@ -127,32 +154,32 @@ class DistTransport:
         return out
 
 
-class ShardedSV:
-    """An n-qubit state vector over 2^g slices (see the module notes).
+class _Sharded:
+    """Qubit map, slices and the swap of a global qubit with a local one,
+    common to state vectors (one plane) and density matrices (two planes)."""
 
-    ranks: the slice indices this process holds (all of them with
-    LocalTransport, its own rank with DistTransport).  backend: slice storage
-    and local arithmetic (zeros / unit / tensor / apply / expect / numpy)."""
+    planes = 1
 
-    def __init__(self, n, g, backend, transport, ranks, comm_device="cpu"):
+    def __init__(self, n, g, backend, transport, ranks, comm_device):
         if not 0 <= g < n:
             raise ValueError("need 0 <= g < n")
         self.n, self.g, self.L = n, g, n - g
-        self.world = 1 << g
+        self.local_bits = self.planes * self.L
+        self.world = 1 << (self.planes * g)
         self.backend, self.transport = backend, transport
         self.ranks = sorted(ranks)
+        if not all(0 <= r < self.world for r in self.ranks):
+            raise ValueError("rank outside the world")
         self.comm_device = comm_device
         self.map = QubitMap(n)
-        self.slices = {r: (backend.unit(self.L) if r == 0 else backend.zeros(self.L)) for r in self.ranks}
         self.exchanges = 0
 
     def tensor(self, r):
         return self.backend.tensor(self.slices[r])
 
-    # ------------------------------------------------------------ layout
     def _make_local(self, qubits, keep=()):
         """Swap every global qubit of ``qubits`` with a local one (the highest
-        local bit whose qubit is not in ``keep``)."""
+        local position whose qubit is not in ``keep``)."""
         keep = set(keep) | set(qubits)
         for q in qubits:
             bit = self.map.phys[q]
@@ -162,29 +189,59 @@ class ShardedSV:
             if not victims:
                 raise ValueError("not enough local qubits for this gate or term")
             l = victims[0]
-            self.transport.exchange(self, bit - self.L, l)
+            for h in range(self.planes):  # one pairwise exchange per plane
+                self.transport.exchange(self, (bit - self.L) + h * self.g, l + h * self.L)
             self.map.swap_bits(bit, l)
             self.exchanges += 1
 
-    # ------------------------------------------------------------ circuits
-    def apply(self, gates):
-        """Apply gates (name, logical qubits, params), grouping runs of gates
-        whose qubits are local into one call per slice."""
+    def _runs(self, gates):
+        """Yield runs of gates (physical local qubits) between the swaps
+        that make a gate's global qubits local."""
         run = []
         for name, qs, prm in gates:
             if any(self.map.phys[q] >= self.L for q in qs):
-                self._flush(run)
+                if run:
+                    yield run
                 run = []
                 self._make_local(qs)
             run.append((name, tuple(self.map.phys[q] for q in qs), prm))
-        self._flush(run)
-
-    def _flush(self, run):
         if run:
+            yield run
+
+    def _unpermute(self, phys):
+        """A flat physical-order array of planes x n bits -> logical order."""
+        idx = np.arange(phys.size, dtype=np.int64)
+        logical = np.zeros_like(idx)
+        for h in range(self.planes):
+            for q in range(self.n):
+                logical |= ((idx >> (self.map.phys[q] + h * self.n)) & 1) << (q + h * self.n)
+        out = np.zeros_like(phys)
+        out[logical] = phys
+        return out
+
+    def _gathered(self):
+        parts = self.transport.gather(self, [(r, self.backend.numpy(self.slices[r])) for r in self.ranks])
+        return [p for part in parts for p in (part if isinstance(part, list) else [part])]
+
+
+class ShardedSV(_Sharded):
+    """An n-qubit state vector over 2^g slices (see the module notes).
+
+    ranks: the slice indices this process holds (all of them with
+    LocalTransport, its own rank with DistTransport).  backend: slice storage
+    and local arithmetic (zeros / unit / tensor / apply / expect / numpy)."""
+
+    def __init__(self, n, g, backend, transport, ranks, comm_device="cpu"):
+        super().__init__(n, g, backend, transport, ranks, comm_device)
+        self.slices = {r: (backend.unit(self.L) if r == 0 else backend.zeros(self.L)) for r in self.ranks}
+
+    def apply(self, gates):
+        """Apply gates (name, logical qubits, params), grouping runs of gates
+        whose qubits are local into one call per slice."""
+        for run in self._runs(gates):
             for r in self.ranks:
                 self.backend.apply(self.slices[r], run)
 
-    # ------------------------------------------------------------ measurement
     def expect(self, terms):
         """Per-term <P> (coefficients not applied), summed over all slices.
         Terms are evaluated in order, in batches under one qubit map; a term
@@ -201,14 +258,14 @@ class ShardedSV:
             for r in self.ranks:
                 v = self.backend.expect(self.slices[r], loc)
                 for (k, _, _, gz), vk in zip(batch, v):
-                    vals[k] += -vk if bin(r & gz).count("1") & 1 else vk
+                    vals[k] += -vk if _popcount(r & gz) & 1 else vk
             batch.clear()
 
         for k, (x, z, _) in enumerate(terms):
             x, z = x & full, z & full
             xs = [q for q in range(self.n) if (x >> q) & 1 and self.map.phys[q] >= self.L]
             if xs:
-                if bin(x).count("1") > self.L:
+                if _popcount(x) > self.L:
                     raise ValueError("a Pauli string with X support on more than n - g qubits needs more local "
                                      "qubits than a slice has")
                 flush()
@@ -223,24 +280,101 @@ class ShardedSV:
 
     def state(self):
         """The full state in logical qubit order (for tests; every rank gets it)."""
-        parts = self.transport.gather(self, [(r, self.backend.numpy(self.slices[r])) for r in self.ranks])
-        flat = [p for part in parts for p in (part if isinstance(part, list) else [part])]
         phys = np.zeros(1 << self.n, np.complex128)
-        for r, a in flat:
+        for r, a in self._gathered():
             phys[r << self.L:(r + 1) << self.L] = a
-        # physical index -> logical index
-        idx = np.arange(1 << self.n, dtype=np.int64)
-        logical = np.zeros_like(idx)
-        for q in range(self.n):
-            logical |= ((idx >> self.map.phys[q]) & 1) << q
-        out = np.zeros_like(phys)
-        out[logical] = phys
+        return self._unpermute(phys)
+
+
+class ShardedDM(_Sharded):
+    """An n-qubit density matrix over 4^g slices (see the module notes).
+
+    backend.basis is "pauli" (slices of the library's Pauli-basis
+    coefficients) or "matrix" (slices of a row-major rho).  backend: zeros /
+    unit / tensor / apply(slice, gates, noise) / expect(slice, terms) ->
+    complex local traces Tr(P_loc X) / numpy.  ``noise`` (as the library's
+    noise model, T1 / T2 per logical qubit) applies after every gate."""
+
+    planes = 2
+
+    def __init__(self, n, g, backend, transport, ranks, comm_device="cpu"):
+        super().__init__(n, g, backend, transport, ranks, comm_device)
+        if backend.basis not in ("pauli", "matrix"):
+            raise ValueError("unknown slice basis")
+        self.basis = backend.basis
+        gm = (1 << g) - 1
+        # |0..0><0..0|: Pauli basis r[x, z] = [x = 0] (every z); rho: one entry.
+        unit = (lambda r: (r & gm) == 0) if self.basis == "pauli" else (lambda r: r == 0)
+        self.slices = {r: (backend.unit(self.L) if unit(r) else backend.zeros(self.L)) for r in self.ranks}
+
+    def _local_noise(self, noise):
+        """The noise model with T1 / T2 at the local physical positions."""
+        if noise is None:
+            return None
+        out = dict(noise)
+        lq = [self.map.logical_at(b) for b in range(self.L)]
+        out["T1_us"] = np.asarray(noise["T1_us"], np.float64)[lq]
+        out["T2_us"] = np.asarray(noise["T2_us"], np.float64)[lq]
         return out
+
+    def apply(self, gates, noise=None):
+        """Apply gates (name, logical qubits, params), each followed by its
+        noise, grouping runs of gates whose qubits are local into one call
+        per slice."""
+        for run in self._runs(gates):
+            nl = self._local_noise(noise)
+            for r in self.ranks:
+                self.backend.apply(self.slices[r], run, nl)
+
+    def _factor(self, r, xg, zg):
+        """Weight of slice r's local trace in Tr(rho P) (module notes)."""
+        lo, hi = r & ((1 << self.g) - 1), r >> self.g
+        if self.basis == "pauli":
+            return 1.0 if (lo, hi) == (xg, zg) else 0.0
+        if lo != hi ^ xg:  # column bits = row bits ^ x on the global qubits
+            return 0.0
+        return (1j ** (_popcount(xg & zg) & 3)) * (-1.0 if _popcount(hi & zg) & 1 else 1.0)
+
+    def expect(self, terms):
+        """Per-term Tr(rho P) (coefficients not applied); no exchange."""
+        vals = np.zeros(len(terms))
+        full = (1 << self.n) - 1
+        lowm = (1 << self.L) - 1
+        mapped = [(self.map.mask(x & full), self.map.mask(z & full)) for x, z, _ in terms]
+        for r in self.ranks:
+            mine = []
+            for k, (px, pz) in enumerate(mapped):
+                f = self._factor(r, px >> self.L, pz >> self.L)
+                if f != 0:
+                    mine.append((k, px & lowm, pz & lowm, f))
+            if not mine:
+                continue
+            v = self.backend.expect(self.slices[r], [(lx, lz, 1.0) for _, lx, lz, _ in mine])
+            for (k, _, _, f), vk in zip(mine, v):
+                vals[k] += (f * vk).real
+        return self.transport.allreduce(self, vals)
+
+    def energy(self, terms):
+        return float(np.dot(self.expect(terms), [t[2] for t in terms]))
+
+    def state(self):
+        """The full flat state (4^n entries, the backend's basis) in logical
+        qubit order (for tests; every rank gets it)."""
+        n, L, g = self.n, self.L, self.g
+        parts = self._gathered()
+        phys = np.zeros(1 << (2 * n), np.result_type(*[a.dtype for _, a in parts]))
+        s = np.arange(1 << (2 * L), dtype=np.int64)
+        base = (s & ((1 << L) - 1)) | ((s >> L) << n)  # slice bits of both planes
+        for r, a in parts:
+            lo, hi = r & ((1 << g) - 1), r >> g
+            phys[base | (lo << L) | (hi << (n + L))] = a
+        return self._unpermute(phys)
 
 
 class GpuSlices:
-    """Slices on this process's GPU: a torch complex tensor per slice, run by
-    the library as an L-qubit state vector over the caller's buffer."""
+    """State-vector slices on this process's GPU: a torch complex tensor per
+    slice, run by the library as an L-qubit state vector over the caller's
+    buffer."""
 
     def __init__(self, dtype=None, stream=None):
         import torch
@@ -251,10 +385,11 @@ class GpuSlices:
         self.stream = stream
 
     def _new(self, L_, unit):
+        from . import _lib as L
         from .sim import State
-        t = self.torch.zeros(1 << L_, dtype=self.torch.complex128 if self.dtype == 2 else self.torch.complex64,
+        t = self.torch.zeros(1 << L_, dtype=self.torch.complex128 if self.dtype == L.F64 else self.torch.complex64,
                              device="cuda")
-        st = State(1, L_, self.dtype, buf=t.data_ptr(), buf_bytes=t.numel() * t.element_size(),
+        st = State(L.SV, L_, self.dtype, buf=t.data_ptr(), buf_bytes=t.numel() * t.element_size(),
                    stream=self.stream)  # initialised to |0..0>
         if not unit:
             st.sync()
@@ -282,3 +417,53 @@ class GpuSlices:
     def numpy(self, h):
         h[1].sync()
         return h[0].cpu().numpy().astype(np.complex128)
+
+
+class GpuDMSlices:
+    """Density-matrix slices on this process's GPU: a torch real tensor of
+    4^L Pauli-basis coefficients per slice, run by the library as an L-qubit
+    density matrix over the caller's buffer."""
+
+    basis = "pauli"
+
+    def __init__(self, dtype=None, stream=None):
+        import torch
+
+        from . import _lib as L
+        self.torch = torch
+        self.dtype = L.F64 if dtype is None else dtype
+        self.stream = stream
+
+    def _new(self, L_, unit):
+        from . import _lib as L
+        from .sim import State
+        t = self.torch.zeros(1 << (2 * L_), dtype=self.torch.float64 if self.dtype == L.F64 else self.torch.float32,
+                             device="cuda")
+        st = State(L.DM, L_, self.dtype, buf=t.data_ptr(), buf_bytes=t.numel() * t.element_size(),
+                   stream=self.stream)  # initialised to |0..0><0..0|
+        if not unit:
+            st.sync()
+            t.zero_()
+        return (t, st)
+
+    def zeros(self, L_):
+        return self._new(L_, False)
+
+    def unit(self, L_):
+        return self._new(L_, True)
+
+    def tensor(self, h):
+        h[1].sync()
+        return h[0]
+
+    def apply(self, h, gates, noise):
+        self.torch.cuda.synchronize()
+        h[1].apply(gates, noise)
+
+    def expect(self, h, terms):
+        self.torch.cuda.synchronize()
+        return h[1].expect(terms).astype(np.complex128)
+
+    def numpy(self, h):
+        h[1].sync()
+        return h[0].cpu().numpy().astype(np.float64)
