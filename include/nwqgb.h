@@ -446,7 +446,14 @@ int nwq_expect_launch_shape(const nwq_state* st, size_t nt, int noalloc, int* gr
  * (the division removes the norm drift of FP32 storage; <psi|psi> is
  * written to norms[job] when norms is not NULL).  One CTA evaluates one job
  * with the whole 2^n state in shared memory; jobs of different templates
- * (different qubit counts) share one launch.  Limits: n <= 13 (F64) or
+ * (different qubit counts) share one launch.  F64 batches compute in
+ * double words by default: the state in shared memory as float pairs
+ * (h + l, |x - h - l| <= 2^-47 |x| when split from FP64), gates, norms and
+ * term products in double-word arithmetic on the FP32 pipe (Joldes, Muller,
+ * Popescu 2017: exact FMA-based products, TwoSum), per-thread sums as
+ * compensated float pairs added across the CTA in FP64; gate matrices and
+ * energies in FP64.  NWQ_BATCH_FP64_PIPE selects FP64 arithmetic throughout.
+ * Limits: n <= 13 (F64) or
  * 14 (F32); gate kinds CX, CZ, SWAP, RZZ and every one-qubit kind (angles
  * from parameters on RX, RY, RZ, P, U3 and RZZ); MAT2 is not supported. */
 typedef struct {
@@ -462,8 +469,10 @@ typedef struct {
 typedef struct nwq_batch nwq_batch;
 
 enum nwq_batch_flags {
-  NWQ_BATCH_GRAPH = 1u  /* launch through a captured CUDA graph, captured on first use and
-                           recaptured when pointers or the job count change */
+  NWQ_BATCH_GRAPH = 1u,     /* launch through a captured CUDA graph, captured on first use and
+                               recaptured when pointers or the job count change */
+  NWQ_BATCH_FP64_PIPE = 2u  /* F64 batches: arithmetic on the FP64 pipe instead of the default
+                               double words (below) */
 };
 
 /* Validate and upload templates.  The device tables are allocated and

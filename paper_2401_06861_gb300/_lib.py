@@ -26,6 +26,7 @@ EXPECT_TERMS, EXPECT_SUM, EXPECT_NORMALIZE = 0, 1, 2
 NOISE_RZ_VIRTUAL, NOISE_DEPOL_PAULI_FORM = 1, 2
 NOALLOC_MAX_TERMS = 256
 BATCH_GRAPH = 1
+BATCH_FP64_PIPE = 2
 
 GATE_KIND = {"ID": 1, "X": 2, "Y": 3, "Z": 4, "H": 5, "S": 6, "SDG": 7, "T": 8, "TDG": 9, "SX": 10,
              "RX": 11, "RY": 12, "RZ": 13, "P": 14, "U3": 15, "MAT1": 16,

@@ -46,6 +46,7 @@ struct BatchArgs {
   int njobs, nparams, out_stride, ntemplates;
   int max_n, max_gates, max_terms;
   int threads;  // threads per CTA: 128, 256 or 512
+  int dw;       // FP64 batches: 1 = double-word arithmetic on the FP32 pipe, 0 = the FP64 pipe
 };
 constexpr int kBatchThreadChoices[3] = {128, 256, 512};
 

@@ -266,6 +266,7 @@ extern "C" int nwq_batch_run(nwq_batch* b, const double* params, const int32_t* 
   a.max_terms = b->max_terms;
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = b->dtype == NWQ_F64;
+  a.dw = f64 && !(flags & NWQ_BATCH_FP64_PIPE);
   if (!(flags & NWQ_BATCH_GRAPH)) {
     cudaError_t e = launch_batch(f64, a, b->sm_count, s);
     return e == cudaSuccess ? NWQ_OK : set_error(NWQ_ECUDA, cudaGetErrorString(e));

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "batch.hpp"
+#include "dw.cuh"
 #include "kernels.hpp"
 
 namespace nwq {
@@ -275,6 +276,167 @@ __global__ void __launch_bounds__(TH) batch_kernel(BatchArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ double words
+// FP64 batches in double-word arithmetic (the default for FP64 batches; the
+// FP64-pipe kernel above runs with NWQ_BATCH_FP64_PIPE): the state in shared
+// memory as float pairs (re.h, re.l, im.h, im.l: 16 bytes per amplitude, as
+// complex128), gate matrices built in FP64 as above and split into float
+// pairs, every gate, norm and term product in double words on the FP32 pipe
+// (dw.cuh), each thread's sums kept as compensated float pairs and added
+// across the block in FP64.
+struct GateMatDw {
+  float4 m[4];  // (re.h, re.l, im.h, im.l) per entry
+  int cls;
+};
+static_assert(sizeof(GateMatDw) <= sizeof(GateMat<double>), "the FP64 kernel's shared-memory layout");
+
+__device__ __forceinline__ float4 pack_dw(Dw re, Dw im) { return make_float4(re.h, re.l, im.h, im.l); }
+
+// a b (complex)
+__device__ __forceinline__ float4 cmul_dw(float4 a, float4 b) {
+  const Dw ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+  return pack_dw(dw_fma(ar, br, dw_mul(dw_neg(ai), bi)), dw_fma(ar, bi, dw_mul(ai, br)));
+}
+
+// a x + b y (complex)
+__device__ __forceinline__ float4 cmul2_dw(float4 a, float4 x, float4 b, float4 y) {
+  const Dw ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+  const Dw xr{x.x, x.y}, xi{x.z, x.w}, yr{y.x, y.y}, yi{y.z, y.w};
+  return pack_dw(dw_fma(ar, xr, dw_fma(dw_neg(ai), xi, dw_fma(br, yr, dw_mul(dw_neg(bi), yi)))),
+                 dw_fma(ar, xi, dw_fma(ai, xr, dw_fma(br, yi, dw_mul(bi, yr)))));
+}
+
+__device__ void apply_gate_dw(float4* __restrict__ psi, int n, const BGate& g, const GateMatDw& G) {
+  const uint32_t half = 1u << (n - 1);
+  const uint32_t q0 = g.q0, q1 = g.q1;
+  const uint32_t m0 = 1u << q0, m1 = 1u << q1;
+  switch (G.cls) {
+    case BG_CX:
+    case BG_CZ:
+    case BG_SWAP: {
+      const uint32_t lo = q0 < q1 ? q0 : q1, hi = q0 < q1 ? q1 : q0;
+      for (uint32_t t = threadIdx.x; t < (half >> 1); t += blockDim.x) {
+        uint32_t b = t;
+        b = ((b >> lo) << (lo + 1)) | (b & ((1u << lo) - 1));
+        b = ((b >> hi) << (hi + 1)) | (b & ((1u << hi) - 1));
+        if (G.cls == BG_CX) {
+          const float4 a = psi[b | m0], d = psi[b | m0 | m1];
+          psi[b | m0] = d;
+          psi[b | m0 | m1] = a;
+        } else if (G.cls == BG_CZ) {
+          const float4 a = psi[b | m0 | m1];
+          psi[b | m0 | m1] = make_float4(-a.x, -a.y, -a.z, -a.w);
+        } else {
+          const float4 a = psi[b | m0], d = psi[b | m1];
+          psi[b | m0] = d;
+          psi[b | m1] = a;
+        }
+      }
+      return;
+    }
+    case BG_DIAG2:
+      for (uint32_t b = threadIdx.x; b < 2 * half; b += blockDim.x) {
+        const uint32_t par = ((b >> q0) ^ (b >> q1)) & 1u;
+        psi[b] = cmul_dw(G.m[par], psi[b]);
+      }
+      return;
+    case BG_DIAG:
+      for (uint32_t b = threadIdx.x; b < 2 * half; b += blockDim.x) psi[b] = cmul_dw(G.m[(b >> q0) & 1u ? 3 : 0], psi[b]);
+      return;
+    default:
+      break;
+  }
+  for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+    const uint32_t i0 = ((t >> q0) << (q0 + 1)) | (t & (m0 - 1)), i1 = i0 | m0;
+    const float4 a = psi[i0], d = psi[i1];
+    float4 o0, o1;
+    if (G.cls == BG_REAL) {
+      const Dw r0{G.m[0].x, G.m[0].y}, r1{G.m[1].x, G.m[1].y}, r2{G.m[2].x, G.m[2].y}, r3{G.m[3].x, G.m[3].y};
+      const Dw ar{a.x, a.y}, ai{a.z, a.w}, dr{d.x, d.y}, di{d.z, d.w};
+      o0 = pack_dw(dw_fma(r0, ar, dw_mul(r1, dr)), dw_fma(r0, ai, dw_mul(r1, di)));
+      o1 = pack_dw(dw_fma(r2, ar, dw_mul(r3, dr)), dw_fma(r2, ai, dw_mul(r3, di)));
+    } else {
+      o0 = cmul2_dw(G.m[0], a, G.m[1], d);
+      o1 = cmul2_dw(G.m[2], a, G.m[3], d);
+    }
+    psi[i0] = o0;
+    psi[i1] = o1;
+  }
+}
+
+template <int TH>
+__global__ void __launch_bounds__(TH) batch_kernel_dw(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* psi = reinterpret_cast<float4*>(smem);
+  // the FP64 kernel's layout: state, gate matrices (FP64 size), reductions
+  GateMatDw* mats = reinterpret_cast<GateMatDw*>(smem + ((size_t)sizeof(double2) << a.max_n));
+  double* red = reinterpret_cast<double*>(reinterpret_cast<GateMat<double>*>(mats) + a.max_gates);  // 32 doubles
+  double* vals = red + 32;                                                                          // max_terms + 1
+  __shared__ int s_job;
+  for (int iter = 0; iter < a.njobs; iter++) {  // bounded: at most njobs jobs per CTA
+    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int job = s_job;
+    __syncthreads();
+    if (job >= a.njobs) break;
+    const int tid = a.job_template ? a.job_template[job] : 0;
+    if (tid < 0 || tid >= a.ntemplates) {  // invalid template index: NaN energies
+      for (int e = threadIdx.x; e < a.out_stride; e += blockDim.x) a.out[(size_t)job * a.out_stride + e] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
+    const BTemplate T = a.templates[tid];
+    const double* p = a.params + (size_t)job * a.nparams;
+    const int n = T.n;
+    const uint32_t N = 1u << n;
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = make_float4(b == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) {
+      GateMat<double> m;
+      make_gate<double>(a.gates[T.g0 + k], a.gates, p, m);
+      GateMatDw d;
+      for (int e = 0; e < 4; e++) d.m[e] = pack_dw(dw_split(m.m[e].x), dw_split(m.m[e].y));
+      d.cls = m.cls;
+      mats[k] = d;
+    }
+    __syncthreads();
+    for (int k = 0; k < T.ng; k++) {
+      apply_gate_dw(psi, n, a.gates[T.g0 + k], mats[k]);
+      __syncthreads();
+    }
+    float s = 0.f, c = 0.f;
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+      const float4 v = psi[b];
+      const Dw re{v.x, v.y}, im{v.z, v.w};
+      dw_acc(s, c, dw_fma(re, re, dw_mul(im, im)), 0u);
+    }
+    const double nrm = block_sum((double)s + (double)c, red);
+    for (int t = 0; t < T.nt; t++) {
+      const BTerm tm = a.terms[T.t0 + t];
+      const bool imag = tm.y & 1;
+      const uint32_t neg0 = (tm.y == 1 || tm.y == 2) ? 0x80000000u : 0u;
+      s = 0.f;
+      c = 0.f;
+      for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+        const float4 pv = psi[b];
+        const float4 qv = tm.x ? psi[b ^ tm.x] : pv;
+        const Dw pr{pv.x, pv.y}, pi{pv.z, pv.w}, qr{qv.x, qv.y}, qi{qv.z, qv.w};
+        // Re or Im of conj(q) p
+        const Dw v = imag ? dw_fma(qr, pi, dw_mul(dw_neg(qi), pr)) : dw_fma(qr, pr, dw_mul(qi, pi));
+        dw_acc(s, c, v, neg0 ^ ((__popc(b & tm.z) & 1u) << 31));
+      }
+      const double acc = block_sum((double)s + (double)c, red);
+      if (threadIdx.x == 0) vals[t] = acc / nrm;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < T.ne; e += blockDim.x) {
+      double sum = 0;
+      for (int t = 0; t < T.nt; t++) sum = fma(a.coeffs[T.c0 + e * T.nt + t], vals[t], sum);
+      a.out[(size_t)job * a.out_stride + e] = sum;
+    }
+    if (a.norms && threadIdx.x == 0) a.norms[job] = nrm;
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ quantum trajectories
 // Noisy state vectors by Monte-Carlo unravelling of the device noise model
 // (the stochastic alternative to the density matrix of paper Sec. II/III):
@@ -465,8 +627,18 @@ size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
   return (c << max_n) + gm * (size_t)max_gates + 8 * (32 + (size_t)max_terms + 1);
 }
 
-template <class R, int TH>
+// Batched kernel of a precision mode: 0 FP32, 1 FP64 on the FP64 pipe, 2 FP64
+// in double words.
+template <int MODE, int TH>
+static void (*batch_fn())(BatchArgs) {
+  if constexpr (MODE == 0) return batch_kernel<float, TH>;
+  else if constexpr (MODE == 1) return batch_kernel<double, TH>;
+  else return batch_kernel_dw<TH>;
+}
+
+template <int MODE, int TH>
 static cudaError_t launch_batch_t(const BatchArgs& a, size_t smem, int sm_count, cudaStream_t s) {
+  void (*fn)(BatchArgs) = batch_fn<MODE, TH>();
   // The attribute is a per-function maximum shared by every caller (several
   // host threads may launch concurrently): set it once to the largest size any
   // batch may use, never per call.
@@ -478,33 +650,39 @@ static cudaError_t launch_batch_t(const BatchArgs& a, size_t smem, int sm_count,
   {
     std::lock_guard<std::mutex> lk(attr_mu);
     if (attr_dev != dev) {
-      e = cudaFuncSetAttribute(batch_kernel<R, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
       if (e == cudaSuccess) attr_dev = dev;
     }
   }
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<R, TH>, TH, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TH, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = sm_count * per_sm;
   if (grid > a.njobs) grid = a.njobs;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  batch_kernel<R, TH><<<grid, TH, smem, s>>>(a);
+  fn<<<grid, TH, smem, s>>>(a);
   g_launches += 1;
   return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_batch_m(const BatchArgs& a, size_t smem, int sm_count, cudaStream_t s) {
+  switch (a.threads) {
+    case 128: return launch_batch_t<MODE, 128>(a, smem, sm_count, s);
+    case 256: return launch_batch_t<MODE, 256>(a, smem, sm_count, s);
+    case 512: return launch_batch_t<MODE, 512>(a, smem, sm_count, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_batch(bool f64, const BatchArgs& a, int sm_count, cudaStream_t s) {
   const size_t smem = batch_smem_bytes(f64, a.max_n, a.max_gates, a.max_terms);
   if (smem > (size_t)kBatchMaxSmem) return cudaErrorInvalidValue;
-  switch (a.threads) {
-    case 128: return f64 ? launch_batch_t<double, 128>(a, smem, sm_count, s) : launch_batch_t<float, 128>(a, smem, sm_count, s);
-    case 256: return f64 ? launch_batch_t<double, 256>(a, smem, sm_count, s) : launch_batch_t<float, 256>(a, smem, sm_count, s);
-    case 512: return f64 ? launch_batch_t<double, 512>(a, smem, sm_count, s) : launch_batch_t<float, 512>(a, smem, sm_count, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (!f64) return launch_batch_m<0>(a, smem, sm_count, s);
+  return a.dw ? launch_batch_m<2>(a, smem, sm_count, s) : launch_batch_m<1>(a, smem, sm_count, s);
 }
 
 }  // namespace nwq

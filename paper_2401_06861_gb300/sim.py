@@ -395,11 +395,13 @@ class Batch:
         self.keep = None
 
     def run(self, params_ptr, njobs, out_ptr, out_stride=None, job_template_ptr=None, norms_ptr=None,
-            stream=None, graph=False):
+            stream=None, graph=False, fp64_pipe=False):
+        """fp64_pipe: FP64 batches on the FP64 pipe instead of double words."""
+        flags = (L.BATCH_GRAPH if graph else 0) | (L.BATCH_FP64_PIPE if fp64_pipe else 0)
         check(L.lib().nwq_batch_run(self.h, ctypes.c_void_p(params_ptr), ctypes.c_void_p(job_template_ptr)
                                     if job_template_ptr else None, njobs, ctypes.c_void_p(out_ptr),
                                     out_stride or self.max_ne, ctypes.c_void_p(norms_ptr) if norms_ptr else None,
-                                    ctypes.c_void_p(stream) if stream else None, L.BATCH_GRAPH if graph else 0))
+                                    ctypes.c_void_p(stream) if stream else None, flags))
 
     def set_shape(self, threads=256, fusion=0):
         """Threads per CTA (128 / 256 / 512) and gate-fusion width (0 / 1)."""

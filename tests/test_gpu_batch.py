@@ -241,3 +241,37 @@ def test_batch_full_size_bench_configuration():
         assert rel(got[sample], ref, n, np.array(H_LIST)[None, :]).max() <= tol
         assert np.all(got >= e0[None, :] - 1e-6)
         b.close()
+
+
+@pytest.mark.parametrize("fp64_pipe", [False, True])
+def test_batch_fp64_double_words_and_fp64_pipe_match_the_oracle(fp64_pipe):
+    # FP64 batches run in double words by default and on the FP64 pipe with
+    # NWQ_BATCH_FP64_PIPE: every gate class (mixed templates), every kernel
+    # shape, norms written, against the oracle at 1e-12
+    import torch
+    tmpl, nps = [], []
+    for i, n in enumerate((2, 6, 9, 12)):
+        g, pidx, k = _mixed_template(n, 70 + i)
+        tmpl.append((n, g, pidx))
+        nps.append(k)
+    nparams, njobs = max(nps), 48
+    params = np.random.default_rng(71).uniform(-np.pi, np.pi, (njobs, nparams))
+    jt = np.arange(njobs, dtype=np.int32) % len(tmpl)
+    b = Batch([tfim_energy_template(n, g, pidx) for n, g, pidx in tmpl], nparams, L.F64)
+    s = torch.cuda.current_stream().cuda_stream
+    p = torch.from_numpy(params).cuda()
+    j = torch.from_numpy(jt).cuda()
+    ref = np.array([oracle_energies(tmpl[t][0], tmpl[t][1], tmpl[t][2], params[i]) for i, t in enumerate(jt)])
+    nref = np.array([tmpl[t][0] for t in jt])[:, None]
+    for fusion in (0, 1):
+        for threads in (128, 256, 512):
+            b.set_shape(threads, fusion)
+            out = torch.zeros(njobs, 3, dtype=torch.float64, device="cuda")
+            norms = torch.zeros(njobs, dtype=torch.float64, device="cuda")
+            b.run(p.data_ptr(), njobs, out.data_ptr(), job_template_ptr=j.data_ptr(), norms_ptr=norms.data_ptr(),
+                  stream=s, fp64_pipe=fp64_pipe)
+            torch.cuda.synchronize()
+            err = rel(out.cpu().numpy(), ref, nref, np.array(H_LIST)[None, :]).max()
+            assert err <= 1e-12, (threads, fusion, err)
+            assert np.max(np.abs(norms.cpu().numpy() - 1.0)) <= 1e-12
+    b.close()
