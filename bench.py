@@ -989,7 +989,12 @@ def run_traj(args):
         st.run(plan)
         e_dm = st.expect(terms, sum=True)
         dm_s = time.perf_counter() - t0
-    for dtype, name in ((L.F64, "f64"), (L.F32, "f32")):
+    # F64 trajectories run in double words by default; NWQ_DW=0 gives the FP64-pipe kernel
+    for dtype, name, env_dw in ((L.F64, "f64", None), (L.F64, "f64_fp64_pipe", "0"), (L.F32, "f32", None)):
+        if env_dw is None:
+            os.environ.pop("NWQ_DW", None)
+        else:
+            os.environ["NWQ_DW"] = env_dw
         sim.trajectories(n, gates, noise, terms, coeffs, 64, dtype, seed=1)  # warm-up
         d = sim.trajectory_draws(n, gates, noise)
         u = np.random.default_rng(2).random((ntraj, d))
@@ -1001,9 +1006,12 @@ def run_traj(args):
                 "draws_per_trajectory": d, "wall_s": sec, "energy_mean": float(e.mean()),
                 "energy_stderr": float(e.std() / np.sqrt(ntraj)), "energy_density_matrix": e_dm,
                 "density_matrix_s": dm_s,
+                "arithmetic": {"f64": "FP64 in double words (FP32 pipe)", "f64_fp64_pipe": "FP64 pipe",
+                               "f32": "FP32"}[name],
                 "note": "host wall clock incl. the host->device copy of the draws; the density matrix value is one "
                         "FP64 run of the same circuit"}
         print(json.dumps(line), flush=True)
+    os.environ.pop("NWQ_DW", None)
 
 
 def serve_oracle_check(reqs, res, budget_s=20.0, every=100):

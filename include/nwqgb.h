@@ -529,7 +529,11 @@ int nwq_batch_destroy(nwq_batch* b);
  * nwq_traj_draws(...) values in [0, 1), consumed in the order above.
  * out (device) [t * ne + e] = sum_k coeffs[e * nt + k] <P_k> / <psi|psi> of
  * trajectory t.  Gates: the kinds of the batched kernel with fixed angles
- * (param_idx = -1), no MAT2; n <= 13 (F64) / 14 (F32).  Synchronises the stream. */
+ * (param_idx = -1), no MAT2; n <= 13 (F64) / 14 (F32).  Arithmetic as the
+ * batched kernel: F64 in double words (NWQ_DW=0 in the environment, read on
+ * every call, selects the FP64 pipe), F32 with FP64-accurate reductions
+ * (exact products, compensated float-pair sums); the P1 sums and the
+ * renormalisation factors are FP64.  Synchronises the stream. */
 int nwq_traj_draws(const nwq_gate* gates, size_t ng, int n, const nwq_noise_model* noise, size_t* draws);
 int nwq_traj_run(int n, int dtype, const nwq_gate* gates, size_t ng, const nwq_noise_model* noise,
                  const nwq_pauli_term* terms, size_t nt, const double* coeffs, int ne, const double* uniforms,

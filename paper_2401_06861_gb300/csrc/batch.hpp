@@ -68,6 +68,7 @@ struct TrajArgs {
   double* out;      // ntraj x ne energies
   int* counter;
   int n, ng, nt, ne, draws, ntraj, threads;
+  int dw;  // FP64: 1 = double-word arithmetic on the FP32 pipe, 0 = the FP64 pipe
 };
 
 size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms);

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -470,6 +471,9 @@ extern "C" int nwq_traj_run(int n, int dtype, const nwq_gate* gates, size_t ng, 
     a.draws = draws;
     a.ntraj = ntraj;
     a.threads = 256;
+    // FP64 trajectories in double words unless NWQ_DW=0 (read on every call)
+    const char* env_dw = std::getenv("NWQ_DW");
+    a.dw = f64 && !(env_dw && env_dw[0] == '0');
     e = launch_traj(f64, a, sms, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables go out of scope

@@ -1,7 +1,9 @@
 // Batched evaluation of parametrised circuits (the VQE inner loop of paper
 // Sec. III): one CTA per job (one parameter set of one circuit template),
 // the whole 2^n state resident in shared memory, gates applied in place,
-// Pauli-term expectations reduced in FP64, energies written per job.
+// Pauli-term expectations reduced with FP64 accuracy (FP64 arithmetic, or
+// exact products and compensated float-pair sums, added across the CTA in
+// FP64), energies written per job.
 // Jobs are taken from an atomic work queue (a persistent grid), so templates
 // of different qubit counts and depths balance across SMs in one launch.
 #include <cuda_runtime.h>
@@ -207,83 +209,13 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-template <class R, int TH>
-__global__ void __launch_bounds__(TH) batch_kernel(BatchArgs a) {
-  using C = typename C2<R>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  C* psi = reinterpret_cast<C*>(smem);
-  GateMat<R>* mats = reinterpret_cast<GateMat<R>*>(smem + ((size_t)sizeof(C) << a.max_n));
-  double* red = reinterpret_cast<double*>(mats + a.max_gates);  // 32 doubles
-  double* vals = red + 32;                                       // max_terms + 1 doubles
-  __shared__ int s_job;
-  for (int iter = 0; iter < a.njobs; iter++) {  // bounded: at most njobs jobs per CTA
-    if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
-    __syncthreads();
-    const int job = s_job;
-    __syncthreads();
-    if (job >= a.njobs) break;
-    const int tid = a.job_template ? a.job_template[job] : 0;
-    if (tid < 0 || tid >= a.ntemplates) {  // invalid template index: NaN energies
-      for (int e = threadIdx.x; e < a.out_stride; e += blockDim.x) a.out[(size_t)job * a.out_stride + e] = __longlong_as_double(0x7ff8000000000000ll);
-      continue;
-    }
-    const BTemplate T = a.templates[tid];
-    const double* p = a.params + (size_t)job * a.nparams;
-    const int n = T.n;
-    const uint32_t N = 1u << n;
-    // |0..0>
-    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = C{b == 0 ? (R)1 : (R)0, 0};
-    // per-job gate matrices (each thread builds different gates)
-    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) make_gate<R>(a.gates[T.g0 + k], a.gates, p, mats[k]);
-    __syncthreads();
-    for (int k = 0; k < T.ng; k++) {
-      apply_gate<R>(psi, n, a.gates[T.g0 + k], mats[k]);
-      __syncthreads();
-    }
-    // norm and per-term expectations in FP64
-    double nrm = 0;
-    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
-      double re = psi[b].x, im = psi[b].y;
-      nrm = fma(re, re, fma(im, im, nrm));
-    }
-    nrm = block_sum(nrm, red);
-    for (int t = 0; t < T.nt; t++) {
-      const BTerm tm = a.terms[T.t0 + t];
-      double acc = 0;
-      for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
-        double pr = psi[b].x, pi = psi[b].y;
-        double qr = pr, qi = pi;
-        if (tm.x) {
-          qr = psi[b ^ tm.x].x;
-          qi = psi[b ^ tm.x].y;
-        }
-        double wr = fma(qr, pr, qi * pi), wi = fma(qr, pi, -qi * pr);
-        double v = (tm.y & 1) ? wi : wr;
-        int neg = ((tm.y == 1) || (tm.y == 2)) ^ (__popc(b & tm.z) & 1);
-        acc += neg ? -v : v;
-      }
-      acc = block_sum(acc, red);
-      if (threadIdx.x == 0) vals[t] = acc / nrm;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < T.ne; e += blockDim.x) {
-      double s = 0;
-      for (int t = 0; t < T.nt; t++) s = fma(a.coeffs[T.c0 + e * T.nt + t], vals[t], s);
-      a.out[(size_t)job * a.out_stride + e] = s;
-    }
-    if (a.norms && threadIdx.x == 0) a.norms[job] = nrm;
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------------ double words
-// FP64 batches in double-word arithmetic (the default for FP64 batches; the
-// FP64-pipe kernel above runs with NWQ_BATCH_FP64_PIPE): the state in shared
-// memory as float pairs (re.h, re.l, im.h, im.l: 16 bytes per amplitude, as
-// complex128), gate matrices built in FP64 as above and split into float
-// pairs, every gate, norm and term product in double words on the FP32 pipe
-// (dw.cuh), each thread's sums kept as compensated float pairs and added
-// across the block in FP64.
+// FP64 batches and trajectories in double-word arithmetic (the default; the
+// FP64-pipe kernels run on request): the state in shared memory as float
+// pairs (re.h, re.l, im.h, im.l: 16 bytes per amplitude, as complex128),
+// gate matrices built in FP64 and split into float pairs, every gate, norm
+// and term product in double words on the FP32 pipe (dw.cuh), each thread's
+// sums kept as compensated float pairs and added across the block in FP64.
 struct GateMatDw {
   float4 m[4];  // (re.h, re.l, im.h, im.l) per entry
   int cls;
@@ -364,14 +296,153 @@ __device__ void apply_gate_dw(float4* __restrict__ psi, int n, const BGate& g, c
   }
 }
 
-template <int TH>
-__global__ void __launch_bounds__(TH) batch_kernel_dw(BatchArgs a) {
+// ------------------------------------------------------------------ precision modes
+// The batched and trajectory kernels run in one of three modes: 0 FP32
+// (float2 amplitudes), 1 FP64 on the FP64 pipe (double2), 2 FP64 in double
+// words (float4: re.h, re.l, im.h, im.l).  The helpers below are overloaded
+// on the amplitude type.
+template <int M>
+struct Mode;
+
+__device__ __forceinline__ void put_real(float2& v, float x) { v = make_float2(x, 0.f); }
+__device__ __forceinline__ void put_real(double2& v, float x) { v = make_double2(x, 0.0); }
+__device__ __forceinline__ void put_real(float4& v, float x) { v = make_float4(x, 0.f, 0.f, 0.f); }
+
+__device__ __forceinline__ void build_mat(const BGate& g, const BGate* all, const double* p, GateMat<float>& out) {
+  make_gate<float>(g, all, p, out);
+}
+__device__ __forceinline__ void build_mat(const BGate& g, const BGate* all, const double* p, GateMat<double>& out) {
+  make_gate<double>(g, all, p, out);
+}
+__device__ __forceinline__ void build_mat(const BGate& g, const BGate* all, const double* p, GateMatDw& out) {
+  GateMat<double> m;
+  make_gate<double>(g, all, p, m);
+  for (int e = 0; e < 4; e++) out.m[e] = pack_dw(dw_split(m.m[e].x), dw_split(m.m[e].y));
+  out.cls = m.cls;
+}
+
+__device__ __forceinline__ void apply_m(float2* psi, int n, const BGate& g, const GateMat<float>& G) {
+  apply_gate<float>(psi, n, g, G);
+}
+__device__ __forceinline__ void apply_m(double2* psi, int n, const BGate& g, const GateMat<double>& G) {
+  apply_gate<double>(psi, n, g, G);
+}
+__device__ __forceinline__ void apply_m(float4* psi, int n, const BGate& g, const GateMatDw& G) {
+  apply_gate_dw(psi, n, g, G);
+}
+
+// -i v and -v
+__device__ __forceinline__ float2 mul_mi(float2 v) { return make_float2(v.y, -v.x); }
+__device__ __forceinline__ double2 mul_mi(double2 v) { return make_double2(v.y, -v.x); }
+__device__ __forceinline__ float4 mul_mi(float4 v) { return make_float4(v.z, v.w, -v.x, -v.y); }
+__device__ __forceinline__ float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ double2 neg(double2 v) { return make_double2(-v.x, -v.y); }
+__device__ __forceinline__ float4 neg(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+
+// v f for an FP64 factor f: FP64 product (double2); float pair f = fh + fl with
+// one FMA, x fl + x fh (float2); double-word product (float4)
+struct Factor {
+  double d;
+  float h, l;
+  Dw w;
+  __device__ explicit Factor(double f) : d(f), h((float)f), l((float)(f - (double)(float)f)), w(dw_split(f)) {}
+};
+__device__ __forceinline__ float2 scale(float2 v, const Factor& f) {
+  return make_float2(__fmaf_rn(v.x, f.l, __fmul_rn(v.x, f.h)), __fmaf_rn(v.y, f.l, __fmul_rn(v.y, f.h)));
+}
+__device__ __forceinline__ double2 scale(double2 v, const Factor& f) { return make_double2(v.x * f.d, v.y * f.d); }
+__device__ __forceinline__ float4 scale(float4 v, const Factor& f) {
+  return pack_dw(dw_mul(Dw{v.x, v.y}, f.w), dw_mul(Dw{v.z, v.w}, f.w));
+}
+
+// Per-thread sums of |v|^2 and of the term values Re / Im conj(q) p with a
+// sign: FP64 arithmetic (FP64 mode); compensated float pairs with exact
+// products (FP32: TwoProduct) or double-word products (double words).
+struct AccF64 {
+  double s = 0.0;
+  __device__ void abs2(double2 v) { s = fma(v.x, v.x, fma(v.y, v.y, s)); }
+  __device__ void term(double2 q, double2 p, bool imag, bool neg) {
+    const double v = imag ? fma(q.x, p.y, -q.y * p.x) : fma(q.x, p.x, q.y * p.y);
+    s += neg ? -v : v;
+  }
+  __device__ double value() const { return s; }
+};
+struct AccPair {
+  float s = 0.f, c = 0.f;
+  __device__ void abs2(float2 v) {
+    dw_acc(s, c, two_prod(v.x, v.x), 0u);
+    dw_acc(s, c, two_prod(v.y, v.y), 0u);
+  }
+  __device__ void abs2(float4 v) {
+    const Dw re{v.x, v.y}, im{v.z, v.w};
+    dw_acc(s, c, dw_fma(re, re, dw_mul(im, im)), 0u);
+  }
+  __device__ void term(float2 q, float2 p, bool imag, bool neg) {  // qr pr + qi pi, or qr pi - qi pr
+    const uint32_t sg = neg ? 0x80000000u : 0u;
+    dw_acc(s, c, two_prod(q.x, imag ? p.y : p.x), sg);
+    dw_acc(s, c, two_prod(q.y, imag ? p.x : p.y), imag ? sg ^ 0x80000000u : sg);
+  }
+  __device__ void term(float4 q, float4 p, bool imag, bool neg) {
+    const Dw pr{p.x, p.y}, pi{p.z, p.w}, qr{q.x, q.y}, qi{q.z, q.w};
+    const Dw v = imag ? dw_fma(qr, pi, dw_mul(dw_neg(qi), pr)) : dw_fma(qr, pr, dw_mul(qi, pi));
+    dw_acc(s, c, v, neg ? 0x80000000u : 0u);
+  }
+  __device__ double value() const { return (double)s + (double)c; }
+};
+
+template <>
+struct Mode<0> {
+  using E = float2;
+  using Mat = GateMat<float>;
+  using Acc = AccPair;
+};
+template <>
+struct Mode<1> {
+  using E = double2;
+  using Mat = GateMat<double>;
+  using Acc = AccF64;
+};
+template <>
+struct Mode<2> {
+  using E = float4;
+  using Mat = GateMatDw;
+  using Acc = AccPair;
+};
+static_assert(sizeof(GateMatDw) == sizeof(GateMat<double>), "FP64 modes share one shared-memory layout");
+
+// Norm and per-term values <P_t> / norm of the state in shared memory (vals[t],
+// written by thread 0; the caller synchronises before reading them).
+template <int M>
+__device__ double norm_and_terms(const typename Mode<M>::E* __restrict__ psi, uint32_t N,
+                                 const BTerm* __restrict__ terms, int nt, double* red, double* vals) {
+  using Acc = typename Mode<M>::Acc;
+  Acc an;
+  for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) an.abs2(psi[b]);
+  const double nrm = block_sum(an.value(), red);
+  for (int t = 0; t < nt; t++) {
+    const BTerm tm = terms[t];
+    const bool imag = tm.y & 1, neg0 = tm.y == 1 || tm.y == 2;
+    Acc at;
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
+      const auto pv = psi[b];
+      const auto qv = tm.x ? psi[b ^ tm.x] : pv;
+      at.term(qv, pv, imag, neg0 ^ (bool)(__popc(b & tm.z) & 1));
+    }
+    const double acc = block_sum(at.value(), red);
+    if (threadIdx.x == 0) vals[t] = acc / nrm;
+  }
+  return nrm;
+}
+
+template <int M, int TH>
+__global__ void __launch_bounds__(TH) batch_kernel(BatchArgs a) {
+  using E = typename Mode<M>::E;
+  using Mat = typename Mode<M>::Mat;
   extern __shared__ __align__(16) unsigned char smem[];
-  float4* psi = reinterpret_cast<float4*>(smem);
-  // the FP64 kernel's layout: state, gate matrices (FP64 size), reductions
-  GateMatDw* mats = reinterpret_cast<GateMatDw*>(smem + ((size_t)sizeof(double2) << a.max_n));
-  double* red = reinterpret_cast<double*>(reinterpret_cast<GateMat<double>*>(mats) + a.max_gates);  // 32 doubles
-  double* vals = red + 32;                                                                          // max_terms + 1
+  E* psi = reinterpret_cast<E*>(smem);
+  Mat* mats = reinterpret_cast<Mat*>(smem + (sizeof(E) << a.max_n));
+  double* red = reinterpret_cast<double*>(mats + a.max_gates);  // 32 doubles
+  double* vals = red + 32;                                       // max_terms + 1 doubles
   __shared__ int s_job;
   for (int iter = 0; iter < a.njobs; iter++) {  // bounded: at most njobs jobs per CTA
     if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
@@ -388,49 +459,21 @@ __global__ void __launch_bounds__(TH) batch_kernel_dw(BatchArgs a) {
     const double* p = a.params + (size_t)job * a.nparams;
     const int n = T.n;
     const uint32_t N = 1u << n;
-    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = make_float4(b == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
-    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) {
-      GateMat<double> m;
-      make_gate<double>(a.gates[T.g0 + k], a.gates, p, m);
-      GateMatDw d;
-      for (int e = 0; e < 4; e++) d.m[e] = pack_dw(dw_split(m.m[e].x), dw_split(m.m[e].y));
-      d.cls = m.cls;
-      mats[k] = d;
-    }
+    // |0..0>
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) put_real(psi[b], b == 0 ? 1.f : 0.f);
+    // per-job gate matrices (each thread builds different gates)
+    for (int k = threadIdx.x; k < T.ng; k += blockDim.x) build_mat(a.gates[T.g0 + k], a.gates, p, mats[k]);
     __syncthreads();
     for (int k = 0; k < T.ng; k++) {
-      apply_gate_dw(psi, n, a.gates[T.g0 + k], mats[k]);
+      apply_m(psi, n, a.gates[T.g0 + k], mats[k]);
       __syncthreads();
     }
-    float s = 0.f, c = 0.f;
-    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
-      const float4 v = psi[b];
-      const Dw re{v.x, v.y}, im{v.z, v.w};
-      dw_acc(s, c, dw_fma(re, re, dw_mul(im, im)), 0u);
-    }
-    const double nrm = block_sum((double)s + (double)c, red);
-    for (int t = 0; t < T.nt; t++) {
-      const BTerm tm = a.terms[T.t0 + t];
-      const bool imag = tm.y & 1;
-      const uint32_t neg0 = (tm.y == 1 || tm.y == 2) ? 0x80000000u : 0u;
-      s = 0.f;
-      c = 0.f;
-      for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
-        const float4 pv = psi[b];
-        const float4 qv = tm.x ? psi[b ^ tm.x] : pv;
-        const Dw pr{pv.x, pv.y}, pi{pv.z, pv.w}, qr{qv.x, qv.y}, qi{qv.z, qv.w};
-        // Re or Im of conj(q) p
-        const Dw v = imag ? dw_fma(qr, pi, dw_mul(dw_neg(qi), pr)) : dw_fma(qr, pr, dw_mul(qi, pi));
-        dw_acc(s, c, v, neg0 ^ ((__popc(b & tm.z) & 1u) << 31));
-      }
-      const double acc = block_sum((double)s + (double)c, red);
-      if (threadIdx.x == 0) vals[t] = acc / nrm;
-    }
+    const double nrm = norm_and_terms<M>(psi, N, a.terms + T.t0, T.nt, red, vals);
     __syncthreads();
     for (int e = threadIdx.x; e < T.ne; e += blockDim.x) {
-      double sum = 0;
-      for (int t = 0; t < T.nt; t++) sum = fma(a.coeffs[T.c0 + e * T.nt + t], vals[t], sum);
-      a.out[(size_t)job * a.out_stride + e] = sum;
+      double s = 0;
+      for (int t = 0; t < T.nt; t++) s = fma(a.coeffs[T.c0 + e * T.nt + t], vals[t], s);
+      a.out[(size_t)job * a.out_stride + e] = s;
     }
     if (a.norms && threadIdx.x == 0) a.norms[job] = nrm;
     __syncthreads();
@@ -446,41 +489,43 @@ __global__ void __launch_bounds__(TH) batch_kernel_dw(BatchArgs a) {
 //     Pauli string s = 1 + floor(x 4^k / p) (<= 4^k - 1) is applied,
 //     s & 3 on q0 and s >> 2 on q1 (0 I, 1 X, 2 Y, 3 Z);
 //   relaxation on each gate qubit: amplitude damping (gamma) then phase
-//     damping (lambda), one draw x each: with P1 = prob(q = 1) (FP64 block
-//     sum), the jump |0><1| (resp. |1><1|) when x < rate P1, else
-//     diag(1, sqrt(1 - rate)); the state is renormalised in FP64.
+//     damping (lambda), one draw x each: with P1 = prob(q = 1) (a block sum
+//     with FP64 accuracy), the jump |0><1| (resp. |1><1|) when x < rate P1,
+//     else diag(1, sqrt(1 - rate)); the state is renormalised by FP64 factors.
 // Every thread reads the same draw and the same P1, so branches are uniform.
-template <class C>
-__device__ void apply_pauli(C* __restrict__ psi, int n, int q, int a) {
+template <class E>
+__device__ void apply_pauli(E* __restrict__ psi, int n, int q, int a) {
   const uint32_t half = 1u << (n - 1), m = 1u << q;
   for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
     const uint32_t b0 = ((t >> q) << (q + 1)) | (t & (m - 1)), b1 = b0 | m;
-    const C x0 = psi[b0], x1 = psi[b1];
+    const E x0 = psi[b0], x1 = psi[b1];
     if (a == 1) {  // X
       psi[b0] = x1;
       psi[b1] = x0;
     } else if (a == 2) {  // Y: (x0, x1) -> (-i x1, i x0)
-      psi[b0] = C{x1.y, -x1.x};
-      psi[b1] = C{-x0.y, x0.x};
+      psi[b0] = mul_mi(x1);
+      psi[b1] = neg(mul_mi(x0));
     } else {  // Z
-      psi[b1] = C{-x1.x, -x1.y};
+      psi[b1] = neg(x1);
     }
   }
 }
 
-template <class R, int TH>
-__global__ void __launch_bounds__(TH) traj_kernel(TrajArgs a) {
-  using C = typename C2<R>::T;
+template <int M>
+__global__ void __launch_bounds__(256) traj_kernel(TrajArgs a) {
+  using E = typename Mode<M>::E;
+  using Mat = typename Mode<M>::Mat;
+  using Acc = typename Mode<M>::Acc;
   extern __shared__ __align__(16) unsigned char smem[];
-  C* psi = reinterpret_cast<C*>(smem);
-  GateMat<R>* mats = reinterpret_cast<GateMat<R>*>(smem + ((size_t)sizeof(C) << a.n));
+  E* psi = reinterpret_cast<E*>(smem);
+  Mat* mats = reinterpret_cast<Mat*>(smem + (sizeof(E) << a.n));
   double* red = reinterpret_cast<double*>(mats + a.ng);  // 32 doubles
   double* vals = red + 32;                                // nt doubles
   __shared__ int s_job;
   const int n = a.n;
   const uint32_t N = 1u << n, half = N >> 1;
   // fixed circuit: gate matrices once per CTA
-  for (int k = threadIdx.x; k < a.ng; k += blockDim.x) make_gate<R>(a.gates[k], a.gates, nullptr, mats[k]);
+  for (int k = threadIdx.x; k < a.ng; k += blockDim.x) build_mat(a.gates[k], a.gates, nullptr, mats[k]);
   __syncthreads();
   for (int iter = 0; iter < a.ntraj; iter++) {  // bounded: at most ntraj trajectories per CTA
     if (threadIdx.x == 0) s_job = atomicAdd(a.counter, 1);
@@ -490,11 +535,11 @@ __global__ void __launch_bounds__(TH) traj_kernel(TrajArgs a) {
     if (job >= a.ntraj) break;
     const double* u = a.u + (size_t)job * a.draws;
     int used = 0;
-    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) psi[b] = C{b == 0 ? (R)1 : (R)0, 0};
+    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) put_real(psi[b], b == 0 ? 1.f : 0.f);
     __syncthreads();
     for (int g = 0; g < a.ng; g++) {
       const BGate& G = a.gates[g];
-      apply_gate<R>(psi, n, G, mats[g]);
+      apply_m(psi, n, G, mats[g]);
       __syncthreads();
       const TNoise& T = a.noise[g];
       if (T.pdep > 0) {
@@ -506,7 +551,7 @@ __global__ void __launch_bounds__(TH) traj_kernel(TrajArgs a) {
           for (int w = 0; w < T.k; w++) {
             const int pa = (s >> (2 * w)) & 3;
             if (pa) {
-              apply_pauli<C>(psi, n, w == 0 ? G.q0 : G.q1, pa);
+              apply_pauli(psi, n, w == 0 ? G.q0 : G.q1, pa);
               __syncthreads();
             }
           }
@@ -519,58 +564,32 @@ __global__ void __launch_bounds__(TH) traj_kernel(TrajArgs a) {
         for (int step = 0; step < 2; step++) {
           const double rate = step == 0 ? T.gamma[w] : T.lambda[w];
           const double x = u[used++];
-          double p1 = 0.0;
-          for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
-            const C v = psi[((t >> q) << (q + 1)) | (t & (m - 1)) | m];
-            p1 = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, p1));
-          }
-          p1 = block_sum(p1, red);
+          Acc ap;
+          for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) ap.abs2(psi[((t >> q) << (q + 1)) | (t & (m - 1)) | m]);
+          const double p1 = block_sum(ap.value(), red);
           const bool jump = x < rate * p1;
           const double f0 = jump ? 0.0 : 1.0 / sqrt(1.0 - rate * p1);  // |0> part
-          const double f1 = jump ? 1.0 / sqrt(p1) : sqrt(1.0 - rate) * f0;
+          const Factor F0(f0), F1(jump ? 1.0 / sqrt(p1) : sqrt(1.0 - rate) * f0);
           for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
             const uint32_t b0 = ((t >> q) << (q + 1)) | (t & (m - 1)), b1 = b0 | m;
-            const C x0 = psi[b0], x1 = psi[b1];
+            const E x0 = psi[b0], x1 = psi[b1];
             if (jump && step == 0) {  // |0><1|: the |1> part moves down
-              psi[b0] = C{(R)(x1.x * f1), (R)(x1.y * f1)};
-              psi[b1] = C{0, 0};
+              psi[b0] = scale(x1, F1);
+              put_real(psi[b1], 0.f);
             } else if (jump) {  // |1><1|: the |0> part vanishes
-              psi[b0] = C{0, 0};
-              psi[b1] = C{(R)(x1.x * f1), (R)(x1.y * f1)};
+              put_real(psi[b0], 0.f);
+              psi[b1] = scale(x1, F1);
             } else {
-              psi[b0] = C{(R)(x0.x * f0), (R)(x0.y * f0)};
-              psi[b1] = C{(R)(x1.x * f1), (R)(x1.y * f1)};
+              psi[b0] = scale(x0, F0);
+              psi[b1] = scale(x1, F1);
             }
           }
           __syncthreads();
         }
       }
     }
-    // energies of the (normalised) final state, FP64 accumulation
-    double nrm = 0;
-    for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
-      double re = psi[b].x, im = psi[b].y;
-      nrm = fma(re, re, fma(im, im, nrm));
-    }
-    nrm = block_sum(nrm, red);
-    for (int t = 0; t < a.nt; t++) {
-      const BTerm tm = a.terms[t];
-      double acc = 0;
-      for (uint32_t b = threadIdx.x; b < N; b += blockDim.x) {
-        double pr = psi[b].x, pi = psi[b].y;
-        double qr = pr, qi = pi;
-        if (tm.x) {
-          qr = psi[b ^ tm.x].x;
-          qi = psi[b ^ tm.x].y;
-        }
-        double wr = fma(qr, pr, qi * pi), wi = fma(qr, pi, -qi * pr);
-        double v = (tm.y & 1) ? wi : wr;
-        int neg = ((tm.y == 1) || (tm.y == 2)) ^ (__popc(b & tm.z) & 1);
-        acc += neg ? -v : v;
-      }
-      acc = block_sum(acc, red);
-      if (threadIdx.x == 0) vals[t] = acc / nrm;
-    }
+    // energies of the (normalised) final state
+    norm_and_terms<M>(psi, N, a.terms, a.nt, red, vals);
     __syncthreads();
     for (int e = threadIdx.x; e < a.ne; e += blockDim.x) {
       double s = 0;
@@ -587,7 +606,7 @@ size_t traj_smem_bytes(bool f64, int n, int ng, int nt) {
   return (c << n) + gm * (size_t)(ng > 0 ? ng : 1) + 8 * (32 + (size_t)nt + 1);
 }
 
-template <class R>
+template <int M>
 static cudaError_t launch_traj_t(const TrajArgs& a, size_t smem, int sm_count, cudaStream_t s) {
   static int attr_dev = -1;
   static std::mutex attr_mu;
@@ -597,20 +616,20 @@ static cudaError_t launch_traj_t(const TrajArgs& a, size_t smem, int sm_count, c
   {
     std::lock_guard<std::mutex> lk(attr_mu);
     if (attr_dev != dev) {
-      e = cudaFuncSetAttribute(traj_kernel<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
+      e = cudaFuncSetAttribute(traj_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchMaxSmem);
       if (e == cudaSuccess) attr_dev = dev;
     }
   }
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_kernel<R, 256>, 256, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, traj_kernel<M>, 256, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = sm_count * per_sm;
   if (grid > a.ntraj) grid = a.ntraj;
   e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  traj_kernel<R, 256><<<grid, 256, smem, s>>>(a);
+  traj_kernel<M><<<grid, 256, smem, s>>>(a);
   g_launches += 1;
   return cudaGetLastError();
 }
@@ -618,7 +637,8 @@ static cudaError_t launch_traj_t(const TrajArgs& a, size_t smem, int sm_count, c
 cudaError_t launch_traj(bool f64, const TrajArgs& a, int sm_count, cudaStream_t s) {
   const size_t smem = traj_smem_bytes(f64, a.n, a.ng, a.nt);
   if (smem > (size_t)kBatchMaxSmem || a.ntraj < 1) return cudaErrorInvalidValue;
-  return f64 ? launch_traj_t<double>(a, smem, sm_count, s) : launch_traj_t<float>(a, smem, sm_count, s);
+  if (!f64) return launch_traj_t<0>(a, smem, sm_count, s);
+  return a.dw ? launch_traj_t<2>(a, smem, sm_count, s) : launch_traj_t<1>(a, smem, sm_count, s);
 }
 
 size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
@@ -631,9 +651,7 @@ size_t batch_smem_bytes(bool f64, int max_n, int max_gates, int max_terms) {
 // in double words.
 template <int MODE, int TH>
 static void (*batch_fn())(BatchArgs) {
-  if constexpr (MODE == 0) return batch_kernel<float, TH>;
-  else if constexpr (MODE == 1) return batch_kernel<double, TH>;
-  else return batch_kernel_dw<TH>;
+  return batch_kernel<MODE, TH>;
 }
 
 template <int MODE, int TH>

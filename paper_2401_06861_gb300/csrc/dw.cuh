@@ -42,6 +42,12 @@ __device__ __forceinline__ Dw dw_split(double x) {
 
 __device__ __forceinline__ double dw_to_double(Dw a) { return (double)a.h + (double)a.l; }
 
+// The exact product of two floats as a float pair (TwoProduct with an FMA).
+__device__ __forceinline__ Dw two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return Dw{p, __fmaf_rn(a, b, -p)};
+}
+
 __device__ __forceinline__ Dw dw_neg(Dw a) { return Dw{-a.h, -a.l}; }
 
 __device__ __forceinline__ Dw dw_mul(Dw a, Dw b) {

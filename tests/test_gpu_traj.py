@@ -30,9 +30,13 @@ def circuit(n, seed):
     return inputs.random_circuit(n, 60, seed, names=names)
 
 
-@pytest.mark.parametrize("dtype", [L.F64, L.F32])
+@pytest.mark.parametrize("dtype", [L.F64, "f64_pipe", L.F32])
 @pytest.mark.parametrize("n", [1, 3, 6, 9])
-def test_each_trajectory_matches_the_oracle(n, dtype):
+def test_each_trajectory_matches_the_oracle(n, dtype, monkeypatch):
+    # F64 trajectories run in double words by default; NWQ_DW=0 selects the FP64 pipe
+    if dtype == "f64_pipe":
+        monkeypatch.setenv("NWQ_DW", "0")
+        dtype = L.F64
     g, noise = circuit(n, 60 + n), strong_noise(n, 61 + n)
     terms = inputs.tfim_terms(n) + inputs.z_terms(n) + [(1, 3, 1.0)] if n > 1 else inputs.z_terms(n)
     coeffs = np.eye(len(terms))  # one row per term: every <P_k>
