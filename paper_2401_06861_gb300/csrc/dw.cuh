@@ -93,4 +93,25 @@ __device__ __forceinline__ void dw_acc(float& s, float& c, Dw v, uint32_t sg) {
   s = t;
 }
 
+// (s, c) += a1 b1 + a2 b2 without renormalising the products: the exact high
+// products (one FMA each for their rounding errors), the cross terms and the
+// errors collected in float, TwoSum of the two high products, then TwoSum of
+// that into the running sum s; every low-order part goes to c.
+__device__ __forceinline__ void dw_acc_prod2(float& s, float& c, Dw a1, Dw b1, Dw a2, Dw b2) {
+  const float p1 = __fmul_rn(a1.h, b1.h), p2 = __fmul_rn(a2.h, b2.h);
+  float lo = __fadd_rn(__fmaf_rn(a1.h, b1.h, -p1), __fmaf_rn(a2.h, b2.h, -p2));
+  lo = __fmaf_rn(a1.h, b1.l, lo);
+  lo = __fmaf_rn(a1.l, b1.h, lo);
+  lo = __fmaf_rn(a2.h, b2.l, lo);
+  lo = __fmaf_rn(a2.l, b2.h, lo);
+  const float h = __fadd_rn(p1, p2);
+  const float v = __fsub_rn(h, p1);
+  const float eh = __fadd_rn(__fsub_rn(p1, __fsub_rn(h, v)), __fsub_rn(p2, v));
+  const float t = __fadd_rn(s, h);
+  const float z = __fsub_rn(t, s);
+  const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(h, z));
+  c = __fadd_rn(c, __fadd_rn(e, __fadd_rn(eh, lo)));
+  s = t;
+}
+
 }  // namespace nwq

@@ -58,6 +58,7 @@ void plan_sv_expect(int n, const nwq_pauli_term* terms, size_t nt, bool norm, Sv
         et.zh = z & ~S;
         et.y = __builtin_popcountll(x & z) & 3;
         et.out = t < 0 ? (int)nt : t;
+        if (et.xl == 0) P.zt = 1;
       }
       h.passes[c.npass++] = P;
     }
@@ -123,7 +124,9 @@ void sv_expect_shape(const nwq_state* st, size_t nt, size_t scratch_limit, int* 
   uint64_t fb = (N + 255) / 256;
   if (fb > (uint64_t)st->sm_count * 4) fb = (uint64_t)st->sm_count * 4;
   uint64_t g = 1ull << (st->n - (st->n < kExpTileBits ? st->n : kExpTileBits));
-  if (g > (uint64_t)st->sm_count * (f64 ? 2 : 4)) g = (uint64_t)st->sm_count * (f64 ? 2 : 4);
+  // at most 3 (FP64) / 4 (FP32) CTAs per SM; each pass's launch takes at most
+  // as many CTAs as fit on the device at once (launch_sv_expect_tiled)
+  if (g > (uint64_t)st->sm_count * (f64 ? 3 : 4)) g = (uint64_t)st->sm_count * (f64 ? 3 : 4);
   if (scratch_limit) {
     if (fb > (uint64_t)kNoallocMaxGeneralBlocks) fb = kNoallocMaxGeneralBlocks;
     while (g > 1 && sv_expect_scratch_bytes(nt, (int)g, (int)fb) > scratch_limit) g--;

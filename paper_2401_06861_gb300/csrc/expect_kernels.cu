@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
                                                                   ExpPass P, const ExpTerm* __restrict__ terms,
                                                                   double* __restrict__ part, int ncols) {
   constexpr int kWarps = kExpThreads / 32;
+  constexpr int kGrp = 8;  // terms per warp reduce-scatter
   static_assert(E == 32, "full 2^12 tiles");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t nel = 1u << P.T;
@@ -161,15 +163,14 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
   float2* wht = reinterpret_cast<float2*>(red + kWarps * P.nk);  // [k][thread] transforms (8-byte aligned)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  bool zterm = false;  // does this pass have a Z-type string (diagonal: needs the probabilities)?
-  for (int i = tid; i < P.nk; i += kExpThreads) {
-    st[i] = terms[P.k0 + i];
-    zterm |= st[i].xl == 0;
-  }
+  // a pass with a Z-type string (diagonal: read from the probabilities) has the transform
+  // buffer; the host sets P.zt exactly when a term of the pass has xl = 0
+  const bool zterm = P.zt != 0;
+  for (int i = tid; i < P.nk; i += kExpThreads) st[i] = terms[P.k0 + i];
   for (uint32_t j = tid; j < (1u << P.h); j += kExpThreads) hoff[j] = deposit(j, P.hmask);
   for (int i = tid; i < kWarps * P.nk; i += kExpThreads) red[i] = 0.0;
   const uint32_t lowmask = (1u << P.m) - 1u;
-  zterm = __syncthreads_or(zterm);
+  __syncthreads();
 
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint64_t base = deposit(t, P.fmask);
@@ -218,41 +219,88 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
     }
     __syncthreads();
 
-    for (int k = 0; k < P.nk; k++) {
-      const ExpTerm tm = st[k];
-      const uint32_t flip = ((uint32_t)__popcll(base & tm.zh) + (uint32_t)(tm.y == 1 || tm.y == 2)) & 1u;
-      float as = 0.f, ac = 0.f;
-      if (tm.xl == 0) {
-        const float2 w = wht[((tm.zl >> 7) & 31u) * kExpThreads + tid];
-        const uint32_t sg = ((((uint32_t)__popc((uint32_t)tid & tm.zl & 127u)) ^ flip) & 1u) << 31;
-        as = __int_as_float(__float_as_int(w.x) ^ (int)sg);
-        ac = __int_as_float(__float_as_int(w.y) ^ (int)sg);
-      } else {
-        // each pair (l, l ^ xl) once, l with the lowest bit of xl clear: the partner's
-        // product is the same value (Re part for even y, Im part for odd y), so the pair
-        // contributes twice the value of its first member
-        const int pb = __ffs(tm.xl) - 1;
-        const uint32_t lo = (1u << pb) - 1u;
-        const bool im = (tm.y & 1) != 0;
+    // Terms in groups of kGrp: each thread forms its compensated pair (s, c) for every term of
+    // the group, then one reduce-scatter across the warp (halving the values held per lane at
+    // lane offsets 16, 8, 4, then two butterfly levels) leaves the warp's sum of term
+    // g = (lane >> 2) in lanes 4g .. 4g + 3.
+    for (int k0 = 0; k0 < P.nk; k0 += kGrp) {
+      float gs[kGrp], gc[kGrp];
 #pragma unroll
-        for (int m = 0; m < E / 2; m++) {
-          const uint32_t kk = tid + kExpThreads * m;
-          const uint32_t l = ((kk & ~lo) << 1) | (kk & lo);
-          const float4 sv = tw[l], qv = tw[l ^ tm.xl];
-          const Dw w = im ? dw_fma(Dw{qv.x, qv.y}, Dw{sv.z, sv.w}, dw_mul(Dw{-qv.z, -qv.w}, Dw{sv.x, sv.y}))
-                          : dw_fma(Dw{qv.x, qv.y}, Dw{sv.x, sv.y}, dw_mul(Dw{qv.z, qv.w}, Dw{sv.z, sv.w}));
-          const uint32_t sg = ((((uint32_t)__popc(l & tm.zl)) ^ flip) & 1u) << 31;
-          dw_acc(as, ac, w, sg);
+      for (int g = 0; g < kGrp; g++) {
+        float as = 0.f, ac = 0.f;
+        if (k0 + g < P.nk) {
+          const ExpTerm tm = st[k0 + g];
+          const uint32_t flip = ((uint32_t)__popcll(base & tm.zh) + (uint32_t)(tm.y == 1 || tm.y == 2)) & 1u;
+          if (tm.xl == 0) {
+            if (zterm) {  // always: P.zt covers every Z-type string of the pass
+              const float2 w = wht[((tm.zl >> 7) & 31u) * kExpThreads + tid];
+              const uint32_t sg = ((((uint32_t)__popc((uint32_t)tid & tm.zl & 127u)) ^ flip) & 1u) << 31;
+              as = __int_as_float(__float_as_int(w.x) ^ (int)sg);
+              ac = __int_as_float(__float_as_int(w.y) ^ (int)sg);
+            }
+          } else if (tm.zl == 0 && (tm.xl & (tm.xl - 1)) == 0) {
+            // one X qubit in the tile and no Z bit there (so y = 0): every pair (l, l + xl), l
+            // with bit xl clear, carries the term's sign, applied once; l = kk with a zero
+            // inserted at bit xl, i.e. kk + (kk & ~(xl - 1))
+            const uint32_t nlo = ~(tm.xl - 1u);
+#pragma unroll 4
+            for (int m = 0; m < E / 2; m++) {
+              const uint32_t kk = tid + kExpThreads * m;
+              const uint32_t l = kk + (kk & nlo);
+              const float4 sv = tw[l], qv = tw[l + tm.xl];
+              dw_acc_prod2(as, ac, Dw{qv.x, qv.y}, Dw{sv.x, sv.y}, Dw{qv.z, qv.w}, Dw{sv.z, sv.w});
+            }
+            const int sg = (int)(flip << 31);
+            as = __int_as_float(__float_as_int(__fmul_rn(as, 2.f)) ^ sg);  // twice each pair, exact
+            ac = __int_as_float(__float_as_int(__fmul_rn(ac, 2.f)) ^ sg);
+          } else {
+            // each pair (l, l ^ xl) once, l with the lowest bit of xl clear: the partner's
+            // product is the same value (Re part for even y, Im part for odd y), so the pair
+            // contributes twice the value of its first member
+            const int pb = __ffs(tm.xl) - 1;
+            const uint32_t lo = (1u << pb) - 1u;
+            const bool im = (tm.y & 1) != 0;
+#pragma unroll 4
+            for (int m = 0; m < E / 2; m++) {
+              const uint32_t kk = tid + kExpThreads * m;
+              const uint32_t l = ((kk & ~lo) << 1) | (kk & lo);
+              const float4 sv = tw[l], qv = tw[l ^ tm.xl];
+              // w = a1 b1 + a2 b2: Re (qr sr + qi si) or Im (qr si - qi sr) of conj(q) s, the
+              // sign of the term folded into a1 and a2 (exact)
+              const uint32_t sg = ((((uint32_t)__popc(l & tm.zl)) ^ flip) & 1u) << 31;
+              const uint32_t sg2 = im ? sg ^ 0x80000000u : sg;
+              const Dw a1{__int_as_float(__float_as_int(qv.x) ^ (int)sg), __int_as_float(__float_as_int(qv.y) ^ (int)sg)};
+              const Dw a2{__int_as_float(__float_as_int(qv.z) ^ (int)sg2), __int_as_float(__float_as_int(qv.w) ^ (int)sg2)};
+              const Dw b1 = im ? Dw{sv.z, sv.w} : Dw{sv.x, sv.y}, b2 = im ? Dw{sv.x, sv.y} : Dw{sv.z, sv.w};
+              dw_acc_prod2(as, ac, a1, b1, a2, b2);
+            }
+            as = __fmul_rn(as, 2.f);  // exact
+            ac = __fmul_rn(ac, 2.f);
+          }
         }
-        as = __fmul_rn(as, 2.f);  // exact
-        ac = __fmul_rn(ac, 2.f);
+        gs[g] = as;
+        gc[g] = ac;
       }
 #pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const float os = __shfl_xor_sync(0xffffffffu, as, o), oc = __shfl_xor_sync(0xffffffffu, ac, o);
-        dw_acc(as, ac, Dw{os, oc}, 0u);
+      for (int half = kGrp / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;  // keep the upper half of the values
+#pragma unroll
+        for (int j = 0; j < half; j++) {
+          const float ks = up ? gs[j + half] : gs[j], kc = up ? gc[j + half] : gc[j];
+          const float ss = up ? gs[j] : gs[j + half], sc = up ? gc[j] : gc[j + half];
+          const float rs = __shfl_xor_sync(0xffffffffu, ss, o), rc = __shfl_xor_sync(0xffffffffu, sc, o);
+          gs[j] = ks;
+          gc[j] = kc;
+          dw_acc(gs[j], gc[j], Dw{rs, rc}, 0u);
+        }
       }
-      if (lane == 0) red[warp * P.nk + k] += (double)as + (double)ac;
+#pragma unroll
+      for (int o = 2; o; o >>= 1) {
+        const float rs = __shfl_xor_sync(0xffffffffu, gs[0], o), rc = __shfl_xor_sync(0xffffffffu, gc[0], o);
+        dw_acc(gs[0], gc[0], Dw{rs, rc}, 0u);
+      }
+      const int k = k0 + (lane >> 2);
+      if ((lane & 3) == 0 && k < P.nk) red[warp * P.nk + k] += (double)gs[0] + (double)gc[0];
     }
   }
   __syncthreads();
@@ -321,6 +369,17 @@ __global__ void reduce_partials(const double* __restrict__ part, int nblocks, in
   out[idx ? idx[t] : t] = v;
 }
 
+// A pass launches at most the CTAs that fit on the device at once (its tiles
+// are taken by a grid-stride loop), so a pass whose shared memory allows
+// fewer CTAs per SM than the call's grid assumes runs no second wave.
+int fit_grid(const void* fn, int grid, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kExpThreads, smem) != cudaSuccess || per_sm < 1)
+    return grid;
+  return std::min(grid, per_sm * sms);
+}
+
 template <class R, int E>
 cudaError_t launch_tiled_e(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
                            int ncols, int grid, size_t smem, cudaStream_t s) {
@@ -334,6 +393,7 @@ cudaError_t launch_tiled_e(const void* psi, uint64_t ntiles, const ExpPass& P, c
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
+  grid = fit_grid((const void*)sv_expect_tiled<R, E>, grid, smem);
   sv_expect_tiled<R, E><<<grid, kExpThreads, smem, s>>>((const C*)psi, ntiles, P, terms, part, ncols);
   return cudaGetLastError();
 }
@@ -351,7 +411,7 @@ constexpr size_t kDwWhtBytes = 32 * kExpThreads * sizeof(float2);  // per-thread
 
 cudaError_t launch_tiled_dw(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
                             int ncols, int grid, size_t smem, cudaStream_t s) {
-  smem += kDwWhtBytes;
+  if (P.zt) smem += kDwWhtBytes;  // passes of X-type strings only take no transform buffer (3 CTAs per SM)
   static std::atomic<int> attr_dev{-1};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -361,6 +421,7 @@ cudaError_t launch_tiled_dw(const void* psi, uint64_t ntiles, const ExpPass& P, 
     if (e != cudaSuccess) return e;
     attr_dev = dev;
   }
+  grid = fit_grid((const void*)sv_expect_tiled_dw<32>, grid, smem);
   sv_expect_tiled_dw<32><<<grid, kExpThreads, smem, s>>>((const double2*)psi, ntiles, P, terms, part, ncols);
   return cudaGetLastError();
 }

@@ -31,7 +31,8 @@ struct ExpTerm {
 };
 struct ExpPass {
   uint64_t hmask, fmask;
-  int32_t T, m, h, k0, nk, pad;
+  int32_t T, m, h, k0, nk;
+  int32_t zt;  // 1 when a term of the pass has no X support (Z-type: read from the probabilities)
 };
 static_assert(sizeof(ExpTerm) == 24, "ExpTerm layout");
 
