@@ -275,3 +275,29 @@ def test_batch_fp64_double_words_and_fp64_pipe_match_the_oracle(fp64_pipe):
             assert err <= 1e-12, (threads, fusion, err)
             assert np.max(np.abs(norms.cpu().numpy() - 1.0)) <= 1e-12
     b.close()
+
+
+@pytest.mark.parametrize("dtype,n", [(L.F64, 13), ("f64_pipe", 13), (L.F32, 14)])
+def test_batch_at_the_largest_qubit_counts(dtype, n):
+    # the largest states the batched kernel takes (shared memory: 2^13 x 16 bytes
+    # FP64 or double words, 2^14 x 8 bytes FP32), every kernel shape, against the oracle
+    import torch
+    pipe = dtype == "f64_pipe"
+    dtype = L.F64 if pipe else dtype
+    layers, nsets = 2, 6
+    gates, pidx = inputs.hea_ansatz(n, layers)
+    params = inputs.hea_params(n, layers, nsets, seed=4100 + n)
+    b = Batch([tfim_energy_template(n, gates, pidx)], layers * 2 * n, dtype)
+    p = torch.from_numpy(params).cuda()
+    ref = np.array([oracle_energies(n, gates, pidx, params[s]) for s in range(nsets)])
+    for fusion in (0, 1):
+        for threads in (128, 256, 512):
+            b.set_shape(threads, fusion)
+            out = torch.zeros(nsets, 3, dtype=torch.float64, device="cuda")
+            b.run(p.data_ptr(), nsets, out.data_ptr(), fp64_pipe=pipe)
+            torch.cuda.synchronize()
+            err = rel(out.cpu().numpy(), ref, n, np.array(H_LIST)[None, :]).max()
+            assert err <= (1e-12 if dtype == L.F64 else 1e-6), (threads, fusion, err)
+    b.close()
+    with pytest.raises(L.NwqError):  # one qubit more does not fit
+        Batch([tfim_energy_template(n + 1, *inputs.hea_ansatz(n + 1, 1))], 2 * (n + 1), dtype)
