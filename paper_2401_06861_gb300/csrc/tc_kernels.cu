@@ -136,6 +136,12 @@ __device__ __forceinline__ float4 load_pair(const float2* psi, uint64_t amp, uin
   const float2 a = __ldcs(psi + amp), b = __ldcs(psi + amp + gp);
   return make_float4(a.x, a.y, b.x, b.y);
 }
+// Bring the lines of a pair into L2 (no register, no wait: the loads of that
+// tile one iteration later then hit L2 instead of HBM).
+__device__ __forceinline__ void prefetch_pair(const float2* psi, uint64_t amp, uint64_t gp, bool q0) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + amp));
+  if (!q0) asm volatile("prefetch.global.L2 [%0];" ::"l"(psi + amp + gp));
+}
 __device__ __forceinline__ void store_pair(float2* psi, uint64_t amp, uint64_t gp, bool q0, float4 v) {
   if (q0) {
     __stcs((float4*)(psi + amp), v);
@@ -272,6 +278,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
       const uint64_t a = tile_base(next) + goff;
 #pragma unroll
       for (int i = 0; i < 16; i++) r[i] = load_pair(psi, a + TC_GI(i), gp, q0);
+      const uint32_t after = next + gridDim.x;  // the tile after that: into L2 now
+      if (after < g.ntiles) {
+        const uint64_t b = tile_base(after) + goff;
+#pragma unroll
+        for (int i = 0; i < 16; i++) prefetch_pair(psi, b + TC_GI(i), gp, q0);
+      }
     }
     if (!mma_wait()) {
       timed_out = true;
