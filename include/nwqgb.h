@@ -124,9 +124,16 @@ enum nwq_plan_flags {
  * multiply-add on the FP32 pipe (error-free product and sum transformations,
  * relative error a few 2^-48 of the operands; Dekker, and Joldes, Muller and
  * Popescu, "Tight and rigorous error bounds for basic building blocks of
- * double-word arithmetic", 2017).  The state stays complex128 / FP64 between
- * calls: a plan run converts it to the double-word layout (same bytes) before
- * its first sweep and back after its last.  It applies when every sweep of
+ * double-word arithmetic", 2017).  A plan run converts the state to the
+ * double-word layout (same bytes) before its first sweep.  A caller-owned
+ * buffer (dev_buf) is converted back after the last sweep, so it holds
+ * complex128 / FP64 values whenever a call returns.  A library-owned state
+ * keeps the double-word layout until a call needs FP64 values: a reset of a
+ * state vector writes |0..0> in that layout, complex128 expectation passes over
+ * full tiles read it as it is, and every other call (copies, probabilities,
+ * density-matrix expectations, strings wider than a tile, FP64-pipe, FP32 and
+ * interpreted plans) converts it back first; loads replace it.  Results are the
+ * same either way up to the double words' rounding.  It applies when every sweep of
  * the plan runs a specialised kernel (states of >= NWQ_JIT_MIN_BITS index
  * bits, the kernels compiled); otherwise the plan runs its FP64 kernels.
  * Such plans keep deferred scale factors within the float exponent range. */
@@ -194,8 +201,11 @@ int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst_on_device)
 /* DM only: load raw Pauli-basis coefficients (4^n reals in the state's
  * precision, as nwq_dm_copy_pauli writes them): with nwq_dm_copy_pauli /
  * nwq_state_copy and nwq_state_load for state vectors, a bit-exact checkpoint
- * of a run between two circuits (a long run resumes from host memory).
- * Synchronises the stream. */
+ * of a run between two circuits (a long run resumes from host memory): the
+ * resumed run ends bit-identical to the checkpointed state going on.  (A copy
+ * of a state in the double-word layout first rounds it to its FP64 values in
+ * place, see the double-word notes; a run that takes no copy keeps the double
+ * words and agrees to the FP64 tolerance.)  Synchronises the stream. */
 int nwq_dm_load_pauli(nwq_state* st, const void* src, size_t bytes, int src_on_device);
 
 /* Free the handle.  Library-owned device memory is released stream-ordered

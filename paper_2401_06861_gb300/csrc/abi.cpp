@@ -128,10 +128,18 @@ static int plan_upload(Plan& p, cudaStream_t s) {
   return NWQ_OK;
 }
 
-static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
+// st: the state whose buffer data is (NULL for scratch buffers).  A
+// double-word run leaves a library-owned state in the double-word layout
+// (dw_resident) and starts from it; every other plan needs the FP64 layout.
+static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count, nwq_state* st = nullptr) {
   NvtxRange range("nwq plan run");
   int rc = plan_upload(p, s);
   if (rc) return rc;
+  const bool dw = !p.tc && p.dw && jit_dw_ready(p);
+  if (st && !dw) {
+    cudaError_t e = state_to_f64(st);
+    if (e != cudaSuccess) return cuda_fail(e, "double-word conversion");
+  }
   if (p.tc) {  // dense five-qubit blocks on the tensor cores, one pass each
     const float* tab = (const float*)((const char*)p.dev + p.tc_off);
     for (size_t i = 0; i < p.tcg.size(); i++) {
@@ -146,11 +154,11 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
   PhaseTables pt{(const PhaseDesc*)((const char*)p.dev + p.pt_off[0]), (const PhaseOp*)((const char*)p.dev + p.pt_off[1]),
                  (const char*)p.dev + p.pt_off[2]};
   // double-word plans: the state goes to the double-word layout for the
-  // sweeps when every sweep has its double-word kernel, and back after them
-  const bool dw = p.dw && jit_dw_ready(p);
+  // sweeps when every sweep has its double-word kernel (unless it is there
+  // already), and back after them unless the library owns it
   p.last_run_dw = dw;
   const uint64_t ndouble = (p.is_complex ? 2ull : 1ull) << p.B;
-  if (dw) {
+  if (dw && !(st && st->dw_resident)) {
     cudaError_t e = launch_dw_convert(data, ndouble, true, sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "double-word conversion");
   }
@@ -167,7 +175,10 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count) {
     }
     if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
   }
-  if (dw) {
+  if (dw && st && st->owned) {
+    st->dw_resident = true;
+  } else if (dw) {
+    if (st) st->dw_resident = false;
     cudaError_t e = launch_dw_convert(data, ndouble, false, sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "double-word conversion");
   }
@@ -222,8 +233,18 @@ extern "C" int nwq_dm_create(int n, int dtype, void* dev_buf, size_t buf_bytes, 
 
 extern "C" int nwq_state_reset(nwq_state* st) {
   if (!st) return fail(NWQ_EINVAL, "state is NULL");
-  cudaError_t e = launch_init(st->kind == NWQ_SV, f64_of(st->dtype), st->buf, st->n, st->sm_count, st->stream);
+  // a state vector left in the double-word layout is reset in that layout (its next
+  // double-word run then needs no conversion); anything else in FP64 / FP32
+  const bool dw = st->dw_resident && st->kind == NWQ_SV;
+  cudaError_t e = launch_init(st->kind == NWQ_SV, f64_of(st->dtype), st->buf, st->n, st->sm_count, st->stream, dw);
+  st->dw_resident = dw && e == cudaSuccess;
   return e == cudaSuccess ? NWQ_OK : cuda_fail(e, "state reset");
+}
+
+// The FP64 layout before a reader or writer of the buffer (see dw_resident).
+static int state_f64(nwq_state* st) {
+  cudaError_t e = state_to_f64(st);
+  return e == cudaSuccess ? NWQ_OK : cuda_fail(e, "double-word conversion");
 }
 
 extern "C" int nwq_destroy(nwq_state* st) {
@@ -275,6 +296,7 @@ static int dm_to_rho(nwq_state* st, void* dst_dev) {
 
 extern "C" int nwq_state_copy(nwq_state* st, void* dst, size_t bytes, int dst_on_device) {
   if (!st || !dst) return fail(NWQ_EINVAL, "NULL argument");
+  if (int rc = state_f64(st)) return rc;
   if (st->kind == NWQ_SV) {
     if (bytes < st->bytes) return fail(NWQ_EINVAL, "destination too small");
     CK(cudaMemcpyAsync(dst, st->buf, st->bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -302,6 +324,7 @@ extern "C" int nwq_dm_copy_pauli(nwq_state* st, void* dst, size_t bytes, int dst
   if (!st || !dst) return fail(NWQ_EINVAL, "NULL argument");
   if (st->kind != NWQ_DM) return fail(NWQ_EINVAL, "not a density matrix");
   if (bytes < st->bytes) return fail(NWQ_EINVAL, "destination too small");
+  if (int rc = state_f64(st)) return rc;
   CK(cudaMemcpyAsync(dst, st->buf, st->bytes, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      st->stream),
      "copy");
@@ -313,6 +336,7 @@ extern "C" int nwq_dm_load_pauli(nwq_state* st, const void* src, size_t bytes, i
   if (!st || !src) return fail(NWQ_EINVAL, "NULL argument");
   if (st->kind != NWQ_DM) return fail(NWQ_EINVAL, "not a density matrix");
   if (bytes != st->bytes) return fail(NWQ_EINVAL, "size mismatch");
+  st->dw_resident = false;  // overwritten in the FP64 layout
   CK(cudaMemcpyAsync(st->buf, src, bytes, src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      st->stream),
      "state load");
@@ -325,12 +349,14 @@ extern "C" int nwq_state_load(nwq_state* st, const void* src, size_t bytes, int 
   cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (st->kind == NWQ_SV) {
     if (bytes != st->bytes) return fail(NWQ_EINVAL, "size mismatch");
+    st->dw_resident = false;  // overwritten in the FP64 layout
     CK(cudaMemcpyAsync(st->buf, src, bytes, kind, st->stream), "state load");
     CK(cudaStreamSynchronize(st->stream), "state load");
     return NWQ_OK;
   }
   size_t need = 2 * st->bytes;
   if (bytes != need) return fail(NWQ_EINVAL, "size mismatch");
+  st->dw_resident = false;  // overwritten in the FP64 layout
   void* tmp = nullptr;
   CK(cudaMallocAsync(&tmp, need, st->stream), "scratch allocation");
   int rc = NWQ_OK;
@@ -463,7 +489,7 @@ extern "C" int nwq_plan_run(nwq_state* st, const nwq_plan* plan) {
   if (!st || !plan) return fail(NWQ_EINVAL, "NULL argument");
   const Plan& p = plan->p;
   if (p.kind != st->kind || p.n != st->n || p.dtype != st->dtype) return fail(NWQ_EINVAL, "plan does not match state");
-  return plan_launch(const_cast<Plan&>(p), st->buf, st->stream, st->sm_count);
+  return plan_launch(const_cast<Plan&>(p), st->buf, st->stream, st->sm_count, st);
 }
 
 extern "C" int nwq_plan_autotune(nwq_state* st, const nwq_gate* gates, size_t ng, const nwq_noise_model* nm,
@@ -740,6 +766,7 @@ extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, 
   cudaStream_t s = st->stream;
 
   if (st->kind == NWQ_DM) {
+    if (int rc = state_f64(st)) return rc;
     std::vector<uint64_t> h(3 * nt);
     for (size_t t = 0; t < nt; t++) {
       h[t] = terms[t].x_mask;
@@ -816,6 +843,7 @@ extern "C" int nwq_probs(nwq_state* st, double readout_e, double* out_host) {
   if (!st || !out_host) return fail(NWQ_EINVAL, "NULL argument");
   if (st->n > 30) return fail(NWQ_EUNSUPPORTED, "probabilities limited to n <= 30");
   if (!(readout_e >= 0.0 && readout_e <= 0.5)) return fail(NWQ_EINVAL, "readout error outside [0, 0.5]");
+  if (int rc = state_f64(st)) return rc;
   cudaStream_t s = st->stream;
   uint64_t N = 1ull << st->n;
   double* p = nullptr;

@@ -135,7 +135,15 @@ void sv_expect_shape(const nwq_state* st, size_t nt, size_t scratch_limit, int* 
   *fblocks = (int)fb;
 }
 
-cudaError_t sv_expect_enqueue(const nwq_state* st, const nwq_pauli_term* terms, size_t nt, uint32_t flags,
+cudaError_t state_to_f64(nwq_state* st) {
+  if (!st->dw_resident) return cudaSuccess;
+  const uint64_t ndouble = (st->kind == NWQ_SV ? 2ull : 1ull) << st->B;
+  const cudaError_t e = launch_dw_convert(st->buf, ndouble, false, st->sm_count, st->stream);
+  if (e == cudaSuccess) st->dw_resident = false;
+  return e;
+}
+
+cudaError_t sv_expect_enqueue(nwq_state* st, const nwq_pauli_term* terms, size_t nt, uint32_t flags,
                               double* out_host, const SvExpectHost& h, const SvExpectCounts& c, int grid,
                               int fblocks, unsigned char* stage, unsigned char* dev) {
   const bool sum = (flags & NWQ_EXPECT_SUM) != 0;
@@ -163,12 +171,19 @@ cudaError_t sv_expect_enqueue(const nwq_state* st, const nwq_pauli_term* terms, 
   for (size_t t = 0; t < nt; t++) std::memcpy(stage + o_coef + t * 8, &terms[t].coeff, 8);
   double* dv = (double*)(dev + o_vals);
   double* dpart = (double*)(dev + o_part);
-  cudaError_t e = cudaMemcpyAsync(dev, stage, o_vals, cudaMemcpyHostToDevice, s);
+  // a state in the double-word layout: read as it is by full complex128 tile passes only
+  bool dwin = st->dw_resident && c.nchunk == 0 && !expect_fp64_only();
+  for (int i = 0; i < c.npass && dwin; i++) dwin = h.passes[i].T == kExpTileBits;
+  cudaError_t e = dwin ? cudaSuccess : state_to_f64(st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev, stage, o_vals, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && c.npass) {
     // columns of general terms (and the norm column when unused) stay zero
     e = cudaMemsetAsync(dpart, 0, (size_t)grid * ncols * 8, s);
-    for (int i = 0; i < c.npass && e == cudaSuccess; i++)
-      e = launch_sv_expect_tiled(f64, st->buf, st->n, h.passes[i], (const ExpTerm*)dev, dpart, ncols, grid, s);
+    for (int i = 0; i < c.npass && e == cudaSuccess; i++) {
+      ExpPass P = h.passes[i];
+      P.dwin = dwin ? 1 : 0;
+      e = launch_sv_expect_tiled(f64, st->buf, st->n, P, (const ExpTerm*)dev, dpart, ncols, grid, s);
+    }
     if (e == cudaSuccess) e = launch_reduce_partials(dpart, grid, ncols, nullptr, dv, s);
   }
   for (int k = 0; k < c.nchunk && e == cudaSuccess; k++) {

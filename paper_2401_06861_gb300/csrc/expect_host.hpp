@@ -51,11 +51,17 @@ constexpr size_t sv_expect_scratch_bytes(size_t nt, int grid, int fblocks) {
 constexpr int kNoallocMaxGeneralBlocks = 256;
 void sv_expect_shape(const nwq_state* st, size_t nt, size_t scratch_limit, int* grid, int* fblocks);
 
+// A state left in the double-word layout by a plan run back to its FP64
+// layout (stream-ordered, allocates nothing); no-op otherwise.
+cudaError_t state_to_f64(nwq_state* st);
+
 // Stage the tables (stage: sv_expect_stage_bytes(nt) host bytes), copy them
 // to dev (sv_expect_scratch_bytes(nt, grid, fblocks) device bytes) and enqueue
 // every launch on st's stream, ending with the copy of the result to out_host.
+// A state in the double-word layout is read as it is when every pass is a
+// full complex128 tile pass, and converted back to FP64 first otherwise.
 // The caller synchronises the stream before reading out_host.
-cudaError_t sv_expect_enqueue(const nwq_state* st, const nwq_pauli_term* terms, size_t nt, uint32_t flags,
+cudaError_t sv_expect_enqueue(nwq_state* st, const nwq_pauli_term* terms, size_t nt, uint32_t flags,
                               double* out_host, const SvExpectHost& h, const SvExpectCounts& c, int grid,
                               int fblocks, unsigned char* stage, unsigned char* dev);
 

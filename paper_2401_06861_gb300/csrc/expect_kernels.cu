@@ -188,9 +188,17 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
 #pragma unroll
       for (int j = 0; j < E; j++) {
         const uint32_t l = tid + kExpThreads * j;
-        const double2 a = tile[l];
-        const Dw x = dw_split(a.x), y = dw_split(a.y);
-        tw[l] = make_float4(x.h, x.l, y.h, y.l);
+        Dw x, y;
+        if (P.dwin) {  // the state already holds float pairs
+          const float4 v = tw[l];
+          x = Dw{v.x, v.y};
+          y = Dw{v.z, v.w};
+        } else {
+          const double2 a = tile[l];
+          x = dw_split(a.x);
+          y = dw_split(a.y);
+          tw[l] = make_float4(x.h, x.l, y.h, y.l);
+        }
         p[j] = dw_fma(y, y, dw_mul(x, x));
       }
       // Z-type strings: element l = tid + 128 j has sign (-1)^{|tid & zl| + |j & (zl >> 7)|}, so a
@@ -208,7 +216,7 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
       }
 #pragma unroll
       for (int j = 0; j < E; j++) wht[j * kExpThreads + tid] = make_float2(p[j].h, p[j].l);
-    } else {  // only X-type strings in this pass: the split amplitudes alone
+    } else if (!P.dwin) {  // only X-type strings in this pass: the split amplitudes alone
 #pragma unroll
       for (int j = 0; j < E; j++) {
         const uint32_t l = tid + kExpThreads * j;
@@ -398,14 +406,6 @@ cudaError_t launch_tiled_e(const void* psi, uint64_t ntiles, const ExpPass& P, c
   return cudaGetLastError();
 }
 
-// NWQ_EXPECT_FP64=1: complex128 passes on the FP64 pipe only (no double words)
-bool expect_fp64_only() {
-  static const bool on = [] {
-    const char* e = std::getenv("NWQ_EXPECT_FP64");
-    return e && e[0] == '1';
-  }();
-  return on;
-}
 
 constexpr size_t kDwWhtBytes = 32 * kExpThreads * sizeof(float2);  // per-thread transforms of sv_expect_tiled_dw
 
@@ -429,7 +429,7 @@ cudaError_t launch_tiled_dw(const void* psi, uint64_t ntiles, const ExpPass& P, 
 template <class R>
 cudaError_t launch_tiled_r(const void* psi, uint64_t ntiles, const ExpPass& P, const ExpTerm* terms, double* part,
                            int ncols, int grid, size_t smem, cudaStream_t s) {
-  if (sizeof(R) == 8 && P.T == 12 && !expect_fp64_only())
+  if (sizeof(R) == 8 && P.T == 12 && (P.dwin || !expect_fp64_only()))
     return launch_tiled_dw(psi, ntiles, P, terms, part, ncols, grid, smem, s);
   switch (P.T <= 7 ? 0 : P.T - 7) {
     case 0: return launch_tiled_e<R, 1>(psi, ntiles, P, terms, part, ncols, grid, smem, s);
@@ -443,6 +443,15 @@ cudaError_t launch_tiled_r(const void* psi, uint64_t ntiles, const ExpPass& P, c
 }
 
 }  // namespace
+
+// NWQ_EXPECT_FP64=1: complex128 passes on the FP64 pipe only (no double words)
+bool expect_fp64_only() {
+  static const bool on = [] {
+    const char* e = std::getenv("NWQ_EXPECT_FP64");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
 
 size_t sv_expect_tiled_smem(bool f64, const ExpPass& P) {
   return ((size_t)(f64 ? 16 : 8) << P.T) + ((size_t)8 << P.h) + (size_t)P.nk * sizeof(ExpTerm) +

@@ -32,7 +32,8 @@ struct ExpTerm {
 struct ExpPass {
   uint64_t hmask, fmask;
   int32_t T, m, h, k0, nk;
-  int32_t zt;  // 1 when a term of the pass has no X support (Z-type: read from the probabilities)
+  int32_t zt;    // 1 when a term of the pass has no X support (Z-type: read from the probabilities)
+  int32_t dwin;  // 1: the state holds the double-word layout (complex128, full tiles only)
 };
 static_assert(sizeof(ExpTerm) == 24, "ExpTerm layout");
 
@@ -47,7 +48,9 @@ struct PhaseTables {
 // kernel; everything else (real DM sweeps, tiny tiles) the row kernel.
 cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDesc& sd, const DevOp* ops,
                          const void* ents, const PhaseTables* pt, int sm_count, cudaStream_t s);
-cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s);
+cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s, bool dw = false);
+// NWQ_EXPECT_FP64=1 in the environment: complex128 expectation passes on the FP64 pipe
+bool expect_fp64_only();
 // FP64 array of ndouble values (even) to the double-word layout (to_dw) or back, in place.
 cudaError_t launch_dw_convert(void* data, uint64_t ndouble, bool to_dw, int sm_count, cudaStream_t s);
 cudaError_t launch_real_to_cplx(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);

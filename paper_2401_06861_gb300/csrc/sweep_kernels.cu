@@ -11,6 +11,7 @@
 // density matrix is held as its 4^n real Pauli coefficients and every gate
 // plus its noise is one real Pauli-transfer matrix on bits (q, q+n), so the
 // same engine serves both (complex elements for SV, real for DM).
+#include <cstring>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -649,11 +650,11 @@ cudaError_t launch_sweep(bool cplx, bool f64, void* state, int B, const SweepDes
 // ------------------------------------------------------------------ init
 // SV: psi = |0..0>.  DM (Pauli basis): r[x + 2^n z] = Tr(|0><0| P(x,z)) = [x == 0].
 template <class R>
-__global__ void init_kernel(R* __restrict__ s, uint64_t count, uint64_t xmask, int cplx) {
+__global__ void init_kernel(R* __restrict__ s, uint64_t count, uint64_t xmask, int cplx, R one) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
     R v = 0;
     if (cplx) {
-      v = (i == 0) ? R(1) : R(0);
+      v = (i == 0) ? one : R(0);
     } else {
       v = ((i & xmask) == 0) ? R(1) : R(0);
     }
@@ -661,13 +662,18 @@ __global__ void init_kernel(R* __restrict__ s, uint64_t count, uint64_t xmask, i
   }
 }
 
-cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s) {
-  // SV: 2^n complex = 2^(n+1) reals, only real[0] = 1.  DM: 4^n reals.
+cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s, bool dw) {
+  // SV: 2^n complex = 2^(n+1) reals, only real[0] = 1.  DM: 4^n reals.  dw (FP64 SV):
+  // the double-word layout, real[0] = the float pair (1, 0) in its 8 bytes.
   uint64_t count = cplx ? (2ull << n) : (1ull << (2 * n));
   uint64_t xmask = (1ull << n) - 1;
   unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
-  if (f64) init_kernel<double><<<grid, 256, 0, s>>>((double*)state, count, xmask, cplx);
-  else init_kernel<float><<<grid, 256, 0, s>>>((float*)state, count, xmask, cplx);
+  uint64_t one_bits = 0x3ff0000000000000ull;  // 1.0
+  if (dw && cplx) one_bits = 0x3f800000ull;  // h = 1.0f (IEEE bits), l = 0
+  double one;
+  std::memcpy(&one, &one_bits, 8);
+  if (f64) init_kernel<double><<<grid, 256, 0, s>>>((double*)state, count, xmask, cplx, one);
+  else init_kernel<float><<<grid, 256, 0, s>>>((float*)state, count, xmask, cplx, 1.0f);
   g_launches += 1;
   return cudaGetLastError();
 }

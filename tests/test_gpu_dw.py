@@ -120,3 +120,81 @@ def test_dw_tfim_chain_matches_free_fermions():
     print(f"dw tfim n={n}: max term error {err:.3e}, norm-1 {nrm - 1:.2e}")
     assert err <= 1e-12
     assert abs(nrm - 1) <= 1e-12
+
+
+# ---------------------------------------------------------------- double-word residency
+# A library-owned FP64 state keeps the double-word layout a double-word plan run
+# leaves (no conversion back); reset keeps it, full-tile expectation passes read it
+# as it is, and every other reader or plan converts it back first.
+
+def test_resident_layout_through_reset_runs_expectations_and_copies():
+    n = 18  # the double-word kernels take states of >= 18 index bits
+    gates = inputs.large_sv_tfim(n, 3)[0]
+    terms = inputs.tfim_terms(n) + inputs.z_terms(n) + inputs.random_pauli_terms(n, 20, 61)
+    wide = [((1 << n) - 1, 0, 1.0), ((1 << n) - 1 ^ 0x3, (1 << n) - 1, -0.5)]  # X wider than a tile
+    ref = oracle.sv_run(n, gates)
+    eref = oracle.sv_expect(ref, n, terms)
+    with State(L.SV, n, L.F64) as st, Plan(L.SV, n, gates, L.F64, flags=L.PLAN_DW) as p, \
+            Plan(L.SV, n, gates, L.F64, flags=L.PLAN_FP64) as q:
+        for rep in range(3):  # the second and third runs start from a reset in the double-word layout
+            st.reset()
+            st.run(p)
+            assert p.last_run_dw()
+            assert maxerr(st.expect(terms), eref) <= 1e-12, rep              # read in the double-word layout
+            assert abs(st.expect(terms, sum=True, normalize=True) - oracle.energy(eref, terms)) <= 1e-11
+        assert maxerr(st.copy(), ref) <= 1e-12                               # converted back for the copy
+        st.run(p)                                                            # twice the circuit, from FP64
+        ref2 = oracle.sv_run(n, gates, ref)
+        assert maxerr(st.expect(wide), oracle.sv_expect(ref2, n, wide)) <= 1e-12  # general kernel: back to FP64
+        st.reset()
+        st.run(p)
+        st.run(q)                                                            # FP64-pipe plan after a resident run
+        assert maxerr(st.copy(), ref2) <= 1e-12
+        st.reset()
+        st.run(p)
+        probs = st.probs(0.0)
+        assert maxerr(probs, np.abs(ref) ** 2) <= 1e-12
+        st.reset()
+        st.run(p)
+        out = np.zeros(len(terms))
+        arr = L.encode_terms(terms)
+        import ctypes
+        L.check(L.lib().nwq_expect_pauli_sum_noalloc(st.h, arr, len(terms),
+                                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                     L.EXPECT_TERMS))
+        assert maxerr(out, eref) <= 1e-12
+        st.load(ref2)                                                        # a load replaces the layout
+        assert maxerr(st.copy(), ref2) <= 1e-15
+
+
+def test_caller_owned_buffers_hold_fp64_after_double_word_runs():
+    import torch
+    n = 18
+    gates = inputs.large_sv_tfim(n, 2)[0]
+    t = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
+    with State(L.SV, n, L.F64, buf=t.data_ptr(), buf_bytes=t.numel() * 16) as st, \
+            Plan(L.SV, n, gates, L.F64, flags=L.PLAN_DW) as p:
+        st.run(p)
+        st.sync()
+        assert p.last_run_dw()
+        assert maxerr(t.cpu().numpy(), oracle.sv_run(n, gates)) <= 1e-12    # the caller's bytes are FP64
+
+
+def test_resident_density_matrix_readers():
+    n = 9  # 18 index bits
+    gates, noise = inputs.dm_noisy_tfim(n, 3)
+    terms = inputs.tfim_terms(n) + inputs.z_terms(n)
+    rho = oracle.dm_run(n, gates, noise)
+    with State(L.DM, n, L.F64) as st, Plan(L.DM, n, gates, L.F64, noise, flags=L.PLAN_DW) as p:
+        for _ in range(2):
+            st.reset()
+            st.run(p)
+            assert p.last_run_dw()
+            assert maxerr(st.expect(terms), oracle.dm_expect(rho, n, terms)) <= 1e-12
+            st.run(p)
+            rho2 = oracle.dm_run(n, gates, noise, rho0=rho)
+            assert maxerr(st.probs(0.02), oracle.dm_probs(rho2, n, 0.02)) <= 1e-12
+            st.run(p)
+            pa = st.pauli()
+            st.load_pauli(pa)
+            assert maxerr(st.pauli(), pa) == 0.0
