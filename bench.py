@@ -1016,6 +1016,36 @@ def run_traj(args):
     os.environ.pop("NWQ_DW", None)
 
 
+def run_peaks(args):
+    """The arithmetic roofline denominators: nwq_peak_probe (independent FMA
+    chains on every SM, about 60 ms per call after a warm-up launch) for the
+    FP64 and FP32 pipes, five calls each with nvidia-smi clocks sampled
+    around them; one JSON line per pipe."""
+    import statistics
+
+    import torch
+
+    from paper_2401_06861_gb300 import _lib as L
+    from paper_2401_06861_gb300 import build
+    build.build()
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    for what, pipe in ((L.PROBE_FP64_FMA, "FP64"), (L.PROBE_FP32_FMA, "FP32")):
+        probe_rate(what)  # warm-up
+        clocks = Clocks(dev)
+        vals = [probe_rate(what) for _ in range(5)]
+        ck = clocks.stop()
+        med = statistics.median(vals)
+        mhz = (ck or {}).get("sm_mhz") or 0.0
+        print(json.dumps({"workload": "peak_probe", "pipe": pipe, "metric": "FMA instructions/s", "value": med,
+                          "unit": "FMA/s", "flops": 2 * med, "calls": vals, "sms": sms,
+                          "fma_per_sm_per_clock": med / (sms * mhz * 1e6) if mhz else None, "clocks": ck,
+                          "kernel": "fma_chains (csrc/probe.cu): " + ("8 FP64 chains, 4096 iterations per thread"
+                                                                      if what == L.PROBE_FP64_FMA else
+                                                                      "16 FP32 chains, 2^17 iterations per thread")}),
+              flush=True)
+
+
 def serve_oracle_check(reqs, res, budget_s=20.0, every=100):
     """cpu_baseline leg of the serving line: the CPU oracle on a sample of the
     served requests (every 100th completed request with SV n <= 16 or DM n <= 9,
@@ -1106,7 +1136,8 @@ def main():
     ap.add_argument("--no-fp64-side", action="store_true",
                     help="skip the one FP64-pipe run beside a double-word headline")
     ap.add_argument("--workload", default="sv",
-                    choices=["sv", "dm", "dm32", "sv-cases", "sv-errors", "vqe", "vqe-cobyla", "serve", "traj"],
+                    choices=["sv", "dm", "dm32", "sv-cases", "sv-errors", "vqe", "vqe-cobyla", "serve", "traj",
+                             "peaks"],
                     help="sv: the default line (n=33 complex128 TFIM, depth 10); dm: noisy DM TFIM n=13; "
                          "the others print design-note lines")
     ap.add_argument("--vqe-maxiter", type=int, default=2000)
@@ -1139,6 +1170,8 @@ def main():
         return run_vqe_cobyla(args)
     if args.workload == "traj":
         return run_traj(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     if args.workload == "dm32":
         return run_dm32(args)
     if args.workload == "vqe":

@@ -425,8 +425,11 @@ int nwq_probs(nwq_state* st, double readout_e, double* out_host);
  *   - the first call on a device looks up the scratch array's device address
  *     on that device, making that device current for the lookup and then
  *     restoring the caller's device (host threads that change the current
- *     device at the same moment race with it); make that first call before
- *     any stream capture;
+ *     device at the same moment race with it);
+ *   - the call cannot be captured in a CUDA graph: it synchronises the
+ *     state's stream and copies the results into pageable host memory;
+ *   - a state left in the double-word layout by a plan run is read as it is
+ *     or converted back in place (no allocation either way);
  *   - all calls share the scratch array (it keeps the last call's contents),
  *     so calls that overlap on the GPU race: serialise them;
  *   - state vectors: at most 256 blocks for strings whose X support fits no

@@ -161,6 +161,9 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count, nwq_st
   if (dw && !(st && st->dw_resident)) {
     cudaError_t e = launch_dw_convert(data, ndouble, true, sm_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "double-word conversion");
+  } else if (dw && !st->dw_exact) {  // left by an earlier run: low parts renormalised first
+    cudaError_t e = launch_dw_renormalize(data, ndouble, sm_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "double-word renormalisation");
   }
   for (size_t i = 0; i < p.sweeps.size(); i++) {
     const SweepDesc& sd = p.sweeps[i];
@@ -177,6 +180,7 @@ static int plan_launch(Plan& p, void* data, cudaStream_t s, int sm_count, nwq_st
   }
   if (dw && st && st->owned) {
     st->dw_resident = true;
+    st->dw_exact = false;
   } else if (dw) {
     if (st) st->dw_resident = false;
     cudaError_t e = launch_dw_convert(data, ndouble, false, sm_count, s);
@@ -238,6 +242,7 @@ extern "C" int nwq_state_reset(nwq_state* st) {
   const bool dw = st->dw_resident && st->kind == NWQ_SV;
   cudaError_t e = launch_init(st->kind == NWQ_SV, f64_of(st->dtype), st->buf, st->n, st->sm_count, st->stream, dw);
   st->dw_resident = dw && e == cudaSuccess;
+  st->dw_exact = st->dw_resident;  // |0..0> is exact in either layout
   return e == cudaSuccess ? NWQ_OK : cuda_fail(e, "state reset");
 }
 

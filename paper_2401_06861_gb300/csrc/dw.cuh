@@ -50,6 +50,14 @@ __device__ __forceinline__ Dw two_prod(float a, float b) {
 
 __device__ __forceinline__ Dw dw_neg(Dw a) { return Dw{-a.h, -a.l}; }
 
+// The same value h + l with |l| <= ulp(h) / 2 (TwoSum, exact): the pairs a
+// sweep writes leave their low parts unnormalised.
+__device__ __forceinline__ Dw dw_norm(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  const float v = __fsub_rn(s, h);
+  return Dw{s, __fadd_rn(__fsub_rn(h, __fsub_rn(s, v)), __fsub_rn(l, v))};
+}
+
 __device__ __forceinline__ Dw dw_mul(Dw a, Dw b) {
   const float ph = __fmul_rn(a.h, b.h);
   float pl = __fmaf_rn(a.h, b.h, -ph);

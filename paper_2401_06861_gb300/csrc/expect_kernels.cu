@@ -189,10 +189,11 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
       for (int j = 0; j < E; j++) {
         const uint32_t l = tid + kExpThreads * j;
         Dw x, y;
-        if (P.dwin) {  // the state already holds float pairs
+        if (P.dwin) {  // the state already holds float pairs: renormalised (exactly) in place
           const float4 v = tw[l];
-          x = Dw{v.x, v.y};
-          y = Dw{v.z, v.w};
+          x = dw_norm(v.x, v.y);
+          y = dw_norm(v.z, v.w);
+          tw[l] = make_float4(x.h, x.l, y.h, y.l);
         } else {
           const double2 a = tile[l];
           x = dw_split(a.x);
@@ -216,7 +217,15 @@ __global__ void __launch_bounds__(kExpThreads) sv_expect_tiled_dw(const double2*
       }
 #pragma unroll
       for (int j = 0; j < E; j++) wht[j * kExpThreads + tid] = make_float2(p[j].h, p[j].l);
-    } else if (!P.dwin) {  // only X-type strings in this pass: the split amplitudes alone
+    } else if (P.dwin) {  // only X-type strings: the resident pairs renormalised in place
+#pragma unroll
+      for (int j = 0; j < E; j++) {
+        const uint32_t l = tid + kExpThreads * j;
+        const float4 v = tw[l];
+        const Dw x = dw_norm(v.x, v.y), y = dw_norm(v.z, v.w);
+        tw[l] = make_float4(x.h, x.l, y.h, y.l);
+      }
+    } else {  // only X-type strings in this pass: the split amplitudes alone
 #pragma unroll
       for (int j = 0; j < E; j++) {
         const uint32_t l = tid + kExpThreads * j;

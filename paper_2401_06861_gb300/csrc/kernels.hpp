@@ -53,6 +53,7 @@ cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, c
 bool expect_fp64_only();
 // FP64 array of ndouble values (even) to the double-word layout (to_dw) or back, in place.
 cudaError_t launch_dw_convert(void* data, uint64_t ndouble, bool to_dw, int sm_count, cudaStream_t s);
+cudaError_t launch_dw_renormalize(void* data, uint64_t ndouble, int sm_count, cudaStream_t s);
 cudaError_t launch_real_to_cplx(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_cplx_to_real(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_sv_abs2(bool f64, const void* psi, double* p, uint64_t count, int sm_count, cudaStream_t s);

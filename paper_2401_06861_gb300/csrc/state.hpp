@@ -19,6 +19,7 @@ struct nwq_state {
   // The buffer holds the double-word layout a double-word plan run left there
   // (library-owned FP64 states only; every FP64 reader converts it back first).
   bool dw_resident = false;
+  bool dw_exact = false;  // resident pairs normalised (a reset or a renormalisation wrote them)
   cudaStream_t stream = nullptr;
   int device = 0, sm_count = 1;
   std::unique_ptr<nwq_plan> p2r, r2p;                // DM conversions

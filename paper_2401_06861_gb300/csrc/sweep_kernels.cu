@@ -700,9 +700,23 @@ __device__ __forceinline__ float2 dw_split_bits(double x) {
   return make_float2(__int_as_float((int)hb), l);
 }
 
+// mode 1: FP64 -> double words; 0: back; 2: double words renormalised in place
+// (TwoSum of each pair, exact: the sweeps' multiply-adds leave the low parts
+// unnormalised, and a state kept in the double-word layout over several runs
+// is renormalised before the next one).
+__device__ __forceinline__ float2 dw_renorm_pair(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  const float v = __fsub_rn(s, h);
+  return make_float2(s, __fadd_rn(__fsub_rn(h, __fsub_rn(s, v)), __fsub_rn(l, v)));
+}
+
 __global__ void dw_convert_kernel(void* __restrict__ data, uint64_t npairs, int to_dw) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < npairs; i += (uint64_t)gridDim.x * blockDim.x) {
-    if (to_dw) {
+    if (to_dw == 2) {
+      const float4 f = reinterpret_cast<const float4*>(data)[i];
+      const float2 a = dw_renorm_pair(f.x, f.y), c = dw_renorm_pair(f.z, f.w);
+      reinterpret_cast<float4*>(data)[i] = make_float4(a.x, a.y, c.x, c.y);
+    } else if (to_dw) {
       const double2 d = reinterpret_cast<const double2*>(data)[i];
       const float2 a = dw_split_bits(d.x), c = dw_split_bits(d.y);
       reinterpret_cast<float4*>(data)[i] = make_float4(a.x, a.y, c.x, c.y);
@@ -711,6 +725,15 @@ __global__ void dw_convert_kernel(void* __restrict__ data, uint64_t npairs, int 
       reinterpret_cast<double2*>(data)[i] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
     }
   }
+}
+
+cudaError_t launch_dw_renormalize(void* data, uint64_t ndouble, int sm_count, cudaStream_t s) {
+  const uint64_t npairs = ndouble / 2;
+  unsigned grid = (unsigned)std::min<uint64_t>((npairs + 255) / 256, (uint64_t)sm_count * 8);
+  if (grid == 0) return cudaSuccess;
+  dw_convert_kernel<<<grid, 256, 0, s>>>(data, npairs, 2);
+  g_launches += 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dw_convert(void* data, uint64_t ndouble, bool to_dw, int sm_count, cudaStream_t s) {
