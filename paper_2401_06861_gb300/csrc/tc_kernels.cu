@@ -289,6 +289,22 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
       timed_out = true;
       break;
     }
+    if (g.direct) {
+      // 4'. this thread's accumulator lane is its own column (row tid of A) and columns 4i..4i+3
+      // are its pair i: stored straight back, 32 columns at a time; no shared-memory pass, and
+      // A is not read here, so the next tile's split needs no extra barrier (the one before
+      // its MMAs also orders these accumulator reads before them)
+#pragma unroll
+      for (int hh = 0; hh < 2; hh++) {
+        float d[32];
+        tmem_ld32(tmem_row + 32u * (uint32_t)hh, d);
+#pragma unroll
+        for (int c = 0; c < 8; c++)
+          store_pair(psi, cur + TC_GI(8 * hh + c), gp, q0, make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]));
+      }
+      tc_fence_before();
+      continue;
+    }
     // 4. accumulator lane tid (one state column) -> shared memory (the A layout), 32 columns at a time
 #pragma unroll
     for (int hh = 0; hh < 2; hh++) {

@@ -261,9 +261,11 @@ void tc_geometry(const int* q, int n, TcGeom& g) {
     role_q[p] = other[order[p - 1]].qubit;
     role_w[p] = other[order[p - 1]].w;
   }
+  g.direct = 1;
   for (int p = 0; p < kTcTileBits; p++) {
     g.gw[p] = 1ull << role_q[p];
     g.sw[p] = role_w[p];
+    if (p >= 1 && role_w[p] != (p <= kTcRowBits ? mw[p - 1] : jw[p - kTcRowBits])) g.direct = 0;
   }
   uint64_t tmask = smask;
   for (int r = 0; r < kTcRowBits; r++) tmask |= 1ull << rows[r];
