@@ -73,8 +73,9 @@ bool verify_tc(const Plan& p, std::string& err) {
     // Emulate the kernel's addressing of one tile (thread tid, step i, pair
     // element e): each amplitude must land in the operand slot of its column
     // m (the 7 lowest qubits outside the block) and block index j, a pair in
-    // one 16-byte chunk, each slot once; each warp's accesses must stay within
-    // 512 contiguous amplitudes apart from the pair partner (coalescing).
+    // one 16-byte chunk, each slot once; each warp's accesses must be coalesced
+    // (lane bits below qubit 6, or runs of 16 amplitudes); with the direct
+    // write-back, thread tid must own column tid and step i chunk i.
     int rows[kTcRowBits], nr = 0;
     uint64_t bmask = 0;
     for (int i = 0; i < kTcBits; i++) bmask |= 1ull << blk.q[i];
@@ -105,7 +106,13 @@ bool verify_tc(const Plan& p, std::string& err) {
           const uint32_t want_s = (j >> 4) * 16384u + m * 128u + ((((j >> 1) & 7u) ^ (m & 7u)) << 4) + (j & 1u) * 8u;
           if (s != want_s || s >= 32768u || (s & 7u) || slot[s >> 3]++)
             return fail_at(err, "tensor-core operand addressing", b, tid);
-          if (e == 0 && ((g.gw[1] | g.gw[2] | g.gw[3] | g.gw[4] | g.gw[5]) >> 6) != 0)
+          if (g.direct && (m != (uint32_t)tid || (j >> 1) != (uint32_t)i))
+            return fail_at(err, "tensor-core direct write-back mapping", b, tid);
+          // coalescing: the lane bits are qubits below 6, or (direct write-back geometry) lane
+          // bits 0..3 are qubits 0..3, so each warp access covers runs of 16 amplitudes
+          const bool lanes_low = ((g.gw[1] | g.gw[2] | g.gw[3] | g.gw[4] | g.gw[5]) >> 6) == 0;
+          const bool lanes_runs = g.direct && (g.gw[1] | g.gw[2] | g.gw[3] | g.gw[4]) == 15;
+          if (e == 0 && !lanes_low && !lanes_runs)
             return fail_at(err, "tensor-core lane bits above qubit 5", b, tid);
         }
       }

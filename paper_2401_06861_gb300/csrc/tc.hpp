@@ -31,8 +31,8 @@ struct TcGeom {
   uint32_t sw[kTcTileBits];  // shared-memory byte offset of tile bit p in the operand layout (XOR-combined)
   uint32_t ntiles;           // 2^(n - 12)
   // 1 when thread t's lane and warp bits are the row bits m0..m6 in order and its loop
-  // steps the K chunks j1..j4 (blocks on qubits >= 7): its accumulator lane t then holds
-  // exactly the amplitudes it loaded, which it stores back without a shared-memory pass
+  // steps the K chunks j1..j4 (blocks with no qubit below 4): its accumulator lane t then
+  // holds exactly the amplitudes it loaded, which it stores back without a shared-memory pass
   uint32_t direct;
 };
 

@@ -246,20 +246,37 @@ void tc_geometry(const int* q, int n, TcGeom& g) {
   uint32_t role_w[kTcTileBits];
   role_q[0] = q[0];
   role_w[0] = jw[0];
-  std::vector<int> order;  // indices into other, in role order 1..11
-  std::vector<char> used(other.size(), 0);
-  for (int k = 0; k < 3; k++)
-    for (int c = 0; c < 5; c++)
-      if (!used[c] && other[c].bank == (1u << k)) {
-        used[c] = 1;
-        order.push_back(c);
-        break;
-      }
-  for (int c = 0; c < (int)other.size(); c++)
-    if (!used[c]) order.push_back(c);
-  for (int p = 1; p < kTcTileBits; p++) {
-    role_q[p] = other[order[p - 1]].qubit;
-    role_w[p] = other[order[p - 1]].w;
+  bool low = false;  // a block qubit among 0..3
+  for (int i = 0; i < kTcBits; i++) low |= q[i] < 4;
+  if (!low) {
+    // rows m0..m6 on the lane and warp bits in order, K chunks j1..j4 on the loop steps:
+    // each thread's accumulator lane is the column it loaded (direct write-back), the lane
+    // bits 0..2 (m0..m2) cover bank bits 1, 2, 4, and with qubits 0..3 rows a warp access
+    // still covers runs of 16 consecutive amplitudes (128 bytes)
+    for (int r = 0; r < kTcRowBits; r++) {
+      role_q[1 + r] = rows[r];
+      role_w[1 + r] = mw[r];
+    }
+    for (int i = 1; i < kTcBits; i++) {
+      role_q[kTcRowBits + i] = q[i];
+      role_w[kTcRowBits + i] = jw[i];
+    }
+  } else {
+    std::vector<int> order;  // indices into other, in role order 1..11
+    std::vector<char> used(other.size(), 0);
+    for (int k = 0; k < 3; k++)
+      for (int c = 0; c < 5; c++)
+        if (!used[c] && other[c].bank == (1u << k)) {
+          used[c] = 1;
+          order.push_back(c);
+          break;
+        }
+    for (int c = 0; c < (int)other.size(); c++)
+      if (!used[c]) order.push_back(c);
+    for (int p = 1; p < kTcTileBits; p++) {
+      role_q[p] = other[order[p - 1]].qubit;
+      role_w[p] = other[order[p - 1]].w;
+    }
   }
   g.direct = 1;
   for (int p = 0; p < kTcTileBits; p++) {

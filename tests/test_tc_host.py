@@ -193,3 +193,14 @@ def test_fusion_with_many_diagonal_gates_reproduces_oracle(seed):
         _, _, on = pl.layout()
     assert sum(on) == len(gates) and len(blocks) > 3
     assert np.max(np.abs(run_blocks(n, blocks, psi0) - oracle.sv_run(n, gates, psi0))) <= 1e-12
+
+
+def test_tfim_n34_plan_geometry_verifies():
+    # the benchmark's n = 34 chain: every block's tile geometry checked on the host (operand
+    # slots, coalescing, and for blocks without qubits 0..3 the direct write-back mapping:
+    # thread t owns column t, loop step i chunk i)
+    n = 34
+    gates, _ = inputs.large_sv_tfim(n, 10)
+    with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+        pl.verify()
+        assert len(pl.tc_blocks()) == pl.info()["sweeps"]
