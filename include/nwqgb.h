@@ -128,11 +128,12 @@ enum nwq_plan_flags {
  * double-word layout (same bytes) before its first sweep.  A caller-owned
  * buffer (dev_buf) is converted back after the last sweep, so it holds
  * complex128 / FP64 values whenever a call returns.  A library-owned state
- * keeps the double-word layout until a call needs FP64 values: a reset of a
- * state vector writes |0..0> in that layout, complex128 expectation passes over
- * full tiles read it as it is, and every other call (copies, probabilities,
- * density-matrix expectations, strings wider than a tile, FP64-pipe, FP32 and
- * interpreted plans) converts it back first; loads replace it.  Results are the
+ * keeps the double-word layout until a call needs FP64 values: a reset writes
+ * |0..0> (|0..0><0..0|) in that layout, complex128 expectation passes over
+ * full tiles and density-matrix expectations and probabilities read it as it
+ * is, and every other call (copies, state-vector probabilities, strings wider
+ * than a tile, FP64-pipe, FP32 and interpreted plans) converts it back first;
+ * loads replace it.  Results are the
  * same either way up to the double words' rounding.  It applies when every sweep of
  * the plan runs a specialised kernel (states of >= NWQ_JIT_MIN_BITS index
  * bits, the kernels compiled); otherwise the plan runs its FP64 kernels.

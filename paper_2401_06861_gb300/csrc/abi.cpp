@@ -237,9 +237,9 @@ extern "C" int nwq_dm_create(int n, int dtype, void* dev_buf, size_t buf_bytes, 
 
 extern "C" int nwq_state_reset(nwq_state* st) {
   if (!st) return fail(NWQ_EINVAL, "state is NULL");
-  // a state vector left in the double-word layout is reset in that layout (its next
+  // a state left in the double-word layout is reset in that layout (its next
   // double-word run then needs no conversion); anything else in FP64 / FP32
-  const bool dw = st->dw_resident && st->kind == NWQ_SV;
+  const bool dw = st->dw_resident;
   cudaError_t e = launch_init(st->kind == NWQ_SV, f64_of(st->dtype), st->buf, st->n, st->sm_count, st->stream, dw);
   st->dw_resident = dw && e == cudaSuccess;
   st->dw_exact = st->dw_resident;  // |0..0> is exact in either layout
@@ -770,8 +770,7 @@ extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, 
   const bool f64 = f64_of(st->dtype);
   cudaStream_t s = st->stream;
 
-  if (st->kind == NWQ_DM) {
-    if (int rc = state_f64(st)) return rc;
+  if (st->kind == NWQ_DM) {  // coefficients read as they are, FP64 or double words
     std::vector<uint64_t> h(3 * nt);
     for (size_t t = 0; t < nt; t++) {
       h[t] = terms[t].x_mask;
@@ -786,7 +785,8 @@ extern "C" int nwq_expect_pauli_sum(nwq_state* st, const nwq_pauli_term* terms, 
     int rc = NWQ_OK;
     cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-      e = launch_dm_expect(f64, st->buf, st->n, dx, dx + nt, (const double*)(dx + 2 * nt), (int)nt, dout, sum, norm, s);
+      e = launch_dm_expect(f64, st->buf, st->n, dx, dx + nt, (const double*)(dx + 2 * nt), (int)nt, dout, sum, norm, s,
+                           st->dw_resident);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dout, outn * 8, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) rc = cuda_fail(e, "expectation");
     cudaFreeAsync(d, s);
@@ -848,7 +848,8 @@ extern "C" int nwq_probs(nwq_state* st, double readout_e, double* out_host) {
   if (!st || !out_host) return fail(NWQ_EINVAL, "NULL argument");
   if (st->n > 30) return fail(NWQ_EUNSUPPORTED, "probabilities limited to n <= 30");
   if (!(readout_e >= 0.0 && readout_e <= 0.5)) return fail(NWQ_EINVAL, "readout error outside [0, 0.5]");
-  if (int rc = state_f64(st)) return rc;
+  if (st->kind == NWQ_SV)  // density matrices read their diagonal coefficients in either layout
+    if (int rc = state_f64(st)) return rc;
   cudaStream_t s = st->stream;
   uint64_t N = 1ull << st->n;
   double* p = nullptr;
@@ -860,7 +861,7 @@ extern "C" int nwq_probs(nwq_state* st, double readout_e, double* out_host) {
     if (e != cudaSuccess) rc = cuda_fail(e, "probabilities");
     if (!rc && readout_e > 0) rc = plan_launch(probs_plan(st, readout_e, false)->p, p, s, st->sm_count);
   } else {
-    e = launch_dm_diag(f64_of(st->dtype), st->buf, p, st->n, readout_e, st->sm_count, s);
+    e = launch_dm_diag(f64_of(st->dtype), st->buf, p, st->n, readout_e, st->sm_count, s, st->dw_resident);
     if (e != cudaSuccess) rc = cuda_fail(e, "probabilities");
     if (!rc) rc = plan_launch(probs_plan(st, 0.0, true)->p, p, s, st->sm_count);
   }

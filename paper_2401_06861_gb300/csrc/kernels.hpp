@@ -57,7 +57,8 @@ cudaError_t launch_dw_renormalize(void* data, uint64_t ndouble, int sm_count, cu
 cudaError_t launch_real_to_cplx(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_cplx_to_real(bool f64, const void* in, void* out, uint64_t count, int sm_count, cudaStream_t s);
 cudaError_t launch_sv_abs2(bool f64, const void* psi, double* p, uint64_t count, int sm_count, cudaStream_t s);
-cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, int sm_count, cudaStream_t s);
+cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, int sm_count, cudaStream_t s,
+                           bool dw = false);
 cudaError_t launch_sv_expect_group(bool f64, const void* psi, int n, uint64_t x, const uint64_t* zm, const int* ym,
                                    int nt, double* part, int nblocks, const int* idx, double* out, cudaStream_t s);
 size_t sv_expect_tiled_smem(bool f64, const ExpPass& P);
@@ -66,7 +67,8 @@ cudaError_t launch_sv_expect_tiled(bool f64, const void* psi, int n, const ExpPa
 cudaError_t launch_reduce_partials(const double* part, int nblocks, int nt, const int* idx, double* out,
                                    cudaStream_t s);
 cudaError_t launch_dm_expect(bool f64, const void* r, int n, const uint64_t* xm, const uint64_t* zm,
-                             const double* coef, int nt, double* out, int sum, int normalize, cudaStream_t s);
+                             const double* coef, int nt, double* out, int sum, int normalize, cudaStream_t s,
+                             bool dw = false);
 cudaError_t launch_weighted_sum(const double* v, const double* coef, int nt, double* out, cudaStream_t s);
 cudaError_t launch_scale(double* v, int nt, const double* denom, cudaStream_t s);
 

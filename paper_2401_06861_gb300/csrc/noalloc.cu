@@ -101,10 +101,10 @@ extern "C" int nwq_expect_pauli_sum_noalloc(nwq_state* st, const nwq_pauli_term*
       double c = terms[t].coeff;
       __builtin_memcpy(&h[2 * nt + t], &c, sizeof(double));
     }
-    e = state_to_f64(st);  // a double-word layout left by a plan run goes back in place
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dz, h, 3 * nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = launch_dm_expect(f64, st->buf, st->n, dz, dz + nt, (const double*)(dz + 2 * nt), (int)nt, dv, sum, norm, s);
+    e = cudaMemcpyAsync(dz, h, 3 * nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)  // coefficients read as they are, FP64 or double words
+      e = launch_dm_expect(f64, st->buf, st->n, dz, dz + nt, (const double*)(dz + 2 * nt), (int)nt, dv, sum, norm, s,
+                           st->dw_resident);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, dv, (sum ? 1 : nt) * sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = e2;

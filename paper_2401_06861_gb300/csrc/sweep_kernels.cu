@@ -656,20 +656,20 @@ __global__ void init_kernel(R* __restrict__ s, uint64_t count, uint64_t xmask, i
     if (cplx) {
       v = (i == 0) ? one : R(0);
     } else {
-      v = ((i & xmask) == 0) ? R(1) : R(0);
+      v = ((i & xmask) == 0) ? one : R(0);
     }
     s[i] = v;
   }
 }
 
 cudaError_t launch_init(bool cplx, bool f64, void* state, int n, int sm_count, cudaStream_t s, bool dw) {
-  // SV: 2^n complex = 2^(n+1) reals, only real[0] = 1.  DM: 4^n reals.  dw (FP64 SV):
-  // the double-word layout, real[0] = the float pair (1, 0) in its 8 bytes.
+  // SV: 2^n complex = 2^(n+1) reals, only real[0] = 1.  DM: 4^n reals, 1 where x = 0.  dw
+  // (FP64): the double-word layout, each 1 as the float pair (1, 0) in its 8 bytes.
   uint64_t count = cplx ? (2ull << n) : (1ull << (2 * n));
   uint64_t xmask = (1ull << n) - 1;
   unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
   uint64_t one_bits = 0x3ff0000000000000ull;  // 1.0
-  if (dw && cplx) one_bits = 0x3f800000ull;  // h = 1.0f (IEEE bits), l = 0
+  if (dw) one_bits = 0x3f800000ull;  // h = 1.0f (IEEE bits), l = 0
   double one;
   std::memcpy(&one, &one_bits, 8);
   if (f64) init_kernel<double><<<grid, 256, 0, s>>>((double*)state, count, xmask, cplx, one);
@@ -782,9 +782,21 @@ __global__ void sv_abs2(const typename Cplx<R>::T* __restrict__ psi, double* __r
     p[i] = fma(re, re, im * im);
   }
 }
+// Pauli coefficient i as FP64: from FP64 / FP32 storage, or (DW) from the float
+// pair h + l of a density matrix left in the double-word layout.
+template <class R, bool DW>
+__device__ __forceinline__ double coef_at(const R* __restrict__ r, uint64_t i) {
+  if constexpr (DW) {
+    const float2 v = reinterpret_cast<const float2*>(r)[i];
+    return (double)v.x + (double)v.y;
+  } else {
+    return (double)r[i];
+  }
+}
+
 // DM: g[z] = r[z << n] (1 - 2e)^{|z|} / 2^n ; a Walsh-Hadamard transform of g
 // over n bits then gives the outcome distribution with readout error e.
-template <class R>
+template <class R, bool DW>
 __global__ void dm_diag_gather(const R* __restrict__ r, double* __restrict__ g, int n, double one_m_2e) {
   uint64_t N = 1ull << n;
   double scale = ldexp(1.0, -n);
@@ -798,7 +810,7 @@ __global__ void dm_diag_gather(const R* __restrict__ r, double* __restrict__ g, 
       b *= b;
       w >>= 1;
     }
-    g[z] = (double)r[z << n] * f;
+    g[z] = coef_at<R, DW>(r, z << n) * f;
   }
 }
 
@@ -809,31 +821,32 @@ cudaError_t launch_sv_abs2(bool f64, const void* psi, double* p, uint64_t count,
   g_launches += 1;
   return cudaGetLastError();
 }
-cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, int sm_count, cudaStream_t s) {
+cudaError_t launch_dm_diag(bool f64, const void* r, double* g, int n, double e, int sm_count, cudaStream_t s, bool dw) {
   uint64_t count = 1ull << n;
   unsigned grid = (unsigned)std::min<uint64_t>((count + 255) / 256, (uint64_t)sm_count * 8);
-  if (f64) dm_diag_gather<double><<<grid, 256, 0, s>>>((const double*)r, g, n, 1.0 - 2.0 * e);
-  else dm_diag_gather<float><<<grid, 256, 0, s>>>((const float*)r, g, n, 1.0 - 2.0 * e);
+  if (f64 && dw) dm_diag_gather<double, true><<<grid, 256, 0, s>>>((const double*)r, g, n, 1.0 - 2.0 * e);
+  else if (f64) dm_diag_gather<double, false><<<grid, 256, 0, s>>>((const double*)r, g, n, 1.0 - 2.0 * e);
+  else dm_diag_gather<float, false><<<grid, 256, 0, s>>>((const float*)r, g, n, 1.0 - 2.0 * e);
   g_launches += 1;
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ DM expectations
-template <class R>
+template <class R, bool DW>
 __global__ void dm_expect_gather(const R* __restrict__ r, int n, const uint64_t* __restrict__ xm,
                                  const uint64_t* __restrict__ zm, const double* __restrict__ coef, int nt,
                                  double* __restrict__ out, int sum, int normalize) {
-  const double tr = normalize ? (double)r[0] : 1.0;  // Tr(rho) = coefficient of the identity string
+  const double tr = normalize ? coef_at<R, DW>(r, 0) : 1.0;  // Tr(rho) = coefficient of the identity string
   if (sum) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       double acc = 0;
-      for (int t = 0; t < nt; t++) acc = fma(coef[t], (double)r[xm[t] | (zm[t] << n)], acc);
+      for (int t = 0; t < nt; t++) acc = fma(coef[t], coef_at<R, DW>(r, xm[t] | (zm[t] << n)), acc);
       out[0] = acc / tr;
     }
     return;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x)
-    out[t] = (double)r[xm[t] | (zm[t] << n)] / tr;
+    out[t] = coef_at<R, DW>(r, xm[t] | (zm[t] << n)) / tr;
 }
 
 __global__ void weighted_sum(const double* __restrict__ v, const double* __restrict__ coef, int nt,
@@ -846,10 +859,14 @@ __global__ void weighted_sum(const double* __restrict__ v, const double* __restr
 }
 
 cudaError_t launch_dm_expect(bool f64, const void* r, int n, const uint64_t* xm, const uint64_t* zm,
-                             const double* coef, int nt, double* out, int sum, int normalize, cudaStream_t s) {
+                             const double* coef, int nt, double* out, int sum, int normalize, cudaStream_t s, bool dw) {
   int grid = sum ? 1 : (nt + 255) / 256;
-  if (f64) dm_expect_gather<double><<<grid, 256, 0, s>>>((const double*)r, n, xm, zm, coef, nt, out, sum, normalize);
-  else dm_expect_gather<float><<<grid, 256, 0, s>>>((const float*)r, n, xm, zm, coef, nt, out, sum, normalize);
+  if (f64 && dw)
+    dm_expect_gather<double, true><<<grid, 256, 0, s>>>((const double*)r, n, xm, zm, coef, nt, out, sum, normalize);
+  else if (f64)
+    dm_expect_gather<double, false><<<grid, 256, 0, s>>>((const double*)r, n, xm, zm, coef, nt, out, sum, normalize);
+  else
+    dm_expect_gather<float, false><<<grid, 256, 0, s>>>((const float*)r, n, xm, zm, coef, nt, out, sum, normalize);
   g_launches += 1;
   return cudaGetLastError();
 }
