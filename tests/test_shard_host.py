@@ -265,14 +265,15 @@ def test_sharded_pauli_coefficients_match_the_oracle(n, g):
     assert np.max(np.abs(dm.expect(terms) - oracle.dm_expect(ref, n, terms))) <= 1e-12
 
 
-def _dm_rank(rank, ws, port, n, q):
+def _dm_rank(rank, ws, port, n, q, basis="matrix"):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     g = (ws.bit_length() - 1) // 2
     gates, noise, terms = dm_workload(n, 800 + n)
-    dm = ShardedDM(n, g, OracleDMSlices(), DistTransport(chunk=1 << (2 * (n - g) - 3)), ranks=[rank])
+    backend = OracleDMSlices() if basis == "matrix" else OraclePauliSlices()
+    dm = ShardedDM(n, g, backend, DistTransport(chunk=1 << (2 * (n - g) - 3)), ranks=[rank])
     dm.apply(gates, noise)
     vals = dm.expect(terms)
     state = dm.state()
@@ -281,13 +282,14 @@ def _dm_rank(rank, ws, port, n, q):
     q.put((rank, dm.exchanges, vals, state))
 
 
-def test_gloo_ranks_each_holding_one_density_matrix_slice():
+@pytest.mark.parametrize("basis", ["matrix", "pauli"])
+def test_gloo_ranks_each_holding_one_density_matrix_slice(basis):
     import torch.multiprocessing as mp
     ws, n = 4, 5
     ctx = mp.get_context("spawn")
     qu = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_dm_rank, args=(r, ws, port, n, qu)) for r in range(ws)]
+    procs = [ctx.Process(target=_dm_rank, args=(r, ws, port, n, qu, basis)) for r in range(ws)]
     for p in procs:
         p.start()
     out = sorted((qu.get(timeout=180) for _ in procs), key=lambda t: t[0])
@@ -297,7 +299,8 @@ def test_gloo_ranks_each_holding_one_density_matrix_slice():
     gates, noise, terms = dm_workload(n, 800 + n)
     ref = oracle.dm_run(n, gates, noise)
     eref = oracle.dm_expect(ref, n, terms)
+    sref = ref.reshape(-1) if basis == "matrix" else oracle.dm_expect(ref, n, all_strings(n))
     for rank, exchanges, vals, state in out:
         assert exchanges == out[0][1] > 0
         assert np.max(np.abs(vals - eref)) <= 1e-12
-        assert np.max(np.abs(state - ref.reshape(-1))) <= 1e-12
+        assert np.max(np.abs(state - sref)) <= 1e-12
