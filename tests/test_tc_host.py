@@ -204,3 +204,18 @@ def test_tfim_n34_plan_geometry_verifies():
     with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
         pl.verify()
         assert len(pl.tc_blocks()) == pl.info()["sweeps"]
+
+
+@pytest.mark.parametrize("n", [12, 17, 26, 34])
+def test_random_block_positions_verify(n):
+    # one fused block per circuit, on five random qubits (blocks with and without qubits 0..3,
+    # so both thread-role layouts): the host check of operand slots, coalescing and, for the
+    # direct write-back layout, the thread-to-column mapping
+    rng = np.random.default_rng(900 + n)
+    for _ in range(12):
+        qs = sorted(int(q) for q in rng.choice(n, size=5, replace=False))
+        gates = [inputs.gate("CX", (qs[i], qs[i + 1])) for i in range(4)]
+        gates += [inputs.gate("RY", (q,), (float(rng.uniform(-3, 3)),)) for q in qs]
+        with sim.Plan(L.SV, n, gates, dtype=L.F32, flags=L.PLAN_TC) as pl:
+            pl.verify()
+            assert [sorted(b[0]) for b in pl.tc_blocks()] == [qs]
